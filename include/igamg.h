@@ -1,0 +1,174 @@
+/*
+ * igamg.h -- C ABI of the GB300 (sm_103a) extrapolated geometric-multigrid
+ * solver for isogeometric (tensor-product B-spline) Poisson problems.
+ *
+ * Method: Mouhssine, Ratnani, Sadok, "Vector extrapolation methods applied to
+ * geometric multigrid solvers for isogeometric analysis" (2024).
+ *   - model problem and discrete system A^h u^h = b^h ............ Sec. 2, Eq. (1)-(3)
+ *   - open knot vectors, Cox-de Boor B-splines ...................... Sec. 2.3, Eq. (moneq)
+ *   - coarse grid 2h, prolongation P, restriction R = P^T ........... Sec. 2, Eq. (4)
+ *   - mu-cycle (V-cycle for mu = 1) ................................. Sec. 2.1, Algorithm 2
+ *   - multigrid as the fixed-point map s_{k+1} = G(s_k) ............. Sec. 2.5, Eq. (fixedpoint)
+ *   - RRE / MPE extrapolation ........................................ Sec. 3, Algorithms 3-4
+ *   - restarted extrapolation ........................................ Sec. 3.2, Algorithm 5
+ *
+ * Conventions for every entry point
+ *   - Every call returns an igamg_status; nothing throws or aborts.  After a
+ *     failure igamg_last_error() gives a one-line message (per thread).
+ *   - "d_" pointers are CUDA device pointers on the current device; "h_"
+ *     pointers are host pointers.  The caller owns every pointer it passes; the
+ *     library never frees them and keeps none of them after the call returns.
+ *   - Grid vectors hold the interior unknowns only (homogeneous Dirichlet data
+ *     removes the first and last B-spline per direction): m_d = n_d + p - 2
+ *     per direction, C order with x fastest, index = i + m_x (j + m_y k).
+ *   - "stream" is a cudaStream_t (NULL = legacy default stream).  Calls only
+ *     enqueue work on it unless stated otherwise; igamg_solve synchronises it.
+ *   - Scratch memory: calls that need it take (d_ws, ws_bytes); query the size
+ *     with igamg_workspace_bytes().  The hot path allocates no device memory.
+ *   - The context owns the device copies of its 1D factors, transfer
+ *     operators and coarse-solve data (allocated by igamg_assemble, freed by
+ *     igamg_destroy).  One context must not be used by two threads at once.
+ */
+#ifndef IGAMG_H
+#define IGAMG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    IGAMG_OK = 0,
+    IGAMG_EINVAL = 1,      /* bad argument (size, degree, dimension, pointer, alignment) */
+    IGAMG_ENOMEM = 2,      /* host or device allocation failed, or workspace too small */
+    IGAMG_ECUDA = 3,       /* a CUDA runtime call failed */
+    IGAMG_ENOTCONV = 4,    /* max_cycles reached; d_x still holds the last iterate */
+    IGAMG_EBREAKDOWN = 5,  /* non-finite residual (NaN/Inf in the data or the iteration) */
+    IGAMG_ETIMEOUT = 6     /* a bounded device-side wait gave up */
+} igamg_status;
+
+typedef enum { IGAMG_EXTRAP_NONE = 0, IGAMG_RRE = 1, IGAMG_MPE = 2 } igamg_extrap;
+
+/* Arithmetic of the multigrid cycle.  IGAMG_FP64: everything in FP64.
+ * IGAMG_FP32_IR: V-cycles in FP32 inside FP64 iterative refinement; residuals,
+ * the extrapolation Gram/least-squares solve and iterate updates in FP64. */
+typedef enum { IGAMG_FP64 = 0, IGAMG_FP32_IR = 1 } igamg_prec;
+
+/* igamg_solve flags */
+#define IGAMG_FLAG_X0_GIVEN 1u   /* start from d_x instead of s_0 = 0 */
+#define IGAMG_FLAG_ABS_TOL  2u   /* test ||b - A t|| <= tol instead of ||b - A t|| / ||b|| <= tol */
+#define IGAMG_FLAG_NO_GRAPH 4u   /* enqueue kernels directly instead of replaying a CUDA graph */
+
+typedef struct igamg_ctx igamg_ctx;
+
+/* ---------------------------------------------------------------- set-up */
+
+/* Create a problem context: dimension dim in {2, 3}, spline degree p in
+ * [1, 7], n_elems[d] >= 2 elements in direction d (x first) on a uniform open
+ * knot vector of [0, 1] (Sec. 2.3), and n_levels grids (0 = coarsen until every
+ * direction has <= 8 elements).  Coarse grids keep every other breakpoint
+ * (mesh 2h, Sec. 2), plus the last one when the count is odd.
+ * Errors: EINVAL for dim/p/n out of range or too many levels; ENOMEM. */
+igamg_status igamg_setup(int dim, int p, const int* n_elems, int n_levels, igamg_ctx** out);
+
+/* Host assembly + one upload: per level and direction the banded 1D Galerkin
+ * mass M_d and stiffness K_d ((p+1)-point Gauss quadrature per element), the
+ * 1D prolongation P_d by knot insertion, the inverse diagonal of A on every
+ * level, and the generalised eigenpairs K V = M V Lambda used for the exact
+ * coarsest-grid solve.  Errors: ECUDA, ENOMEM. */
+igamg_status igamg_assemble(igamg_ctx* ctx);
+
+/* Sizes: number of levels, and per level (0 = coarsest) the interior unknowns
+ * per direction.  h_m must hold 3*n_levels ints (unused directions get 1). */
+igamg_status igamg_info(const igamg_ctx* ctx, int* n_levels, int* h_m);
+
+/* Copy a 1D factor of `level` and direction d to the host, in banded form:
+ * which = 0 mass M, 1 stiffness K (rows x (2p+1), entry [i][k] = F[i][i+k-p]),
+ * 2 prolongation P from level-1 (dense rows_fine x cols_coarse).
+ * h_out must hold rows*cols doubles; rows/cols are returned. */
+igamg_status igamg_get_factor(const igamg_ctx* ctx, int level, int d, int which,
+                              double* h_out, int* rows, int* cols);
+
+/* Scratch bytes needed by igamg_solve for restart number k and precision. */
+size_t igamg_workspace_bytes(const igamg_ctx* ctx, int k, int prec);
+
+/* Load vector b_I = int f phi_I on the finest grid with (p+1)^dim Gauss points
+ * per element (Sec. 2, Eq. (2)) for the sine series
+ *   f = sum_k c[k_{dim-1}..k_0] prod_d sin((k_d+1) pi x_d),
+ * h_coeffs holding modes^dim doubles (x mode fastest).  Writes d_b (finest N). */
+igamg_status igamg_rhs_sine(igamg_ctx* ctx, int modes, const double* h_coeffs, double* d_b,
+                            void* stream);
+
+/* ---------------------------------------------------------------- solve */
+
+/* Restarted extrapolation (Algorithm 5) around the V-cycle (Algorithm 2, mu=1,
+ * one multicolour Gauss-Seidel sweep before and after the coarse correction,
+ * (p+1)^dim colours, ascending before and descending after).
+ * Each restart cycle runs k+1 V-cycles from s_0, extrapolates t by RRE
+ * (Algorithm 3) or MPE (Algorithm 4) through the Gram matrix of the
+ * differences, and stops when ||b - A t|| / ||b|| <= tol (or the absolute test
+ * with IGAMG_FLAG_ABS_TOL); else s_0 := t.  With IGAMG_EXTRAP_NONE each cycle
+ * is a single V-cycle and k is ignored.  k in [1, 16].
+ * d_b: finest right-hand side (read only).  d_x: solution (written; read as
+ * s_0 with IGAMG_FLAG_X0_GIVEN).  h_hist (may be NULL) receives max_cycles+1
+ * relative residuals: entry 0 for s_0, entry c after cycle c.  h_cycles and
+ * h_vcycles receive the restart cycles and V-cycles run.
+ * Returns OK on convergence, ENOTCONV after max_cycles (d_x = last iterate),
+ * EBREAKDOWN on a non-finite residual.  Synchronises `stream`. */
+igamg_status igamg_solve(igamg_ctx* ctx, const double* d_b, double* d_x, double tol,
+                         int extrap, int k, int max_cycles, int prec, unsigned flags,
+                         void* d_ws, size_t ws_bytes, void* stream,
+                         double* h_hist, int* h_cycles, int* h_vcycles);
+
+/* --------------------------------------------- components (FP64, for checks) */
+
+/* y = A_level x, A = sum_d K_d (x) prod_{e!=d} M_e (matrix free, sum-factorised). */
+igamg_status igamg_apply(igamg_ctx* ctx, int level, const double* d_x, double* d_y,
+                         void* d_ws, size_t ws_bytes, void* stream);
+
+/* One multicolour Gauss-Seidel sweep on `level`, in place on d_x
+ * (descending = 0: colours ascending; 1: descending). */
+igamg_status igamg_smooth(igamg_ctx* ctx, int level, double* d_x, const double* d_b,
+                          int descending, void* d_ws, size_t ws_bytes, void* stream);
+
+/* d_coarse = P_level^T d_fine (restriction from `level` to level-1). */
+igamg_status igamg_restrict(igamg_ctx* ctx, int level, const double* d_fine, double* d_coarse,
+                            void* d_ws, size_t ws_bytes, void* stream);
+
+/* d_fine += P_level d_coarse (prolongation from level-1 to `level`). */
+igamg_status igamg_prolong(igamg_ctx* ctx, int level, const double* d_coarse, double* d_fine,
+                           void* d_ws, size_t ws_bytes, void* stream);
+
+/* d_e = A_0^{-1} d_r on the coarsest level (fast diagonalisation). */
+igamg_status igamg_coarse_solve(igamg_ctx* ctx, const double* d_r, double* d_e, void* stream);
+
+/* One V-cycle (Algorithm 2, mu = 1) in place on the finest d_x with right side
+ * d_b, in the given precision (FP32_IR: one refinement step
+ * x += sigma V32(0; (b - A x) / sigma)). */
+igamg_status igamg_vcycle(igamg_ctx* ctx, double* d_x, const double* d_b, int prec,
+                          void* d_ws, size_t ws_bytes, void* stream);
+
+/* One RRE / MPE extrapolation (Algorithms 3-4, via the Gram matrix of the
+ * differences) on q+2 iterates of length n stored at d_S + j*ld (j = 0..q+1):
+ * writes t to d_t, the q+2 combination weights to h_gamma (gamma_{q+1} is
+ * non-zero only on the breakdown fallback) and the q actually used to h_qused
+ * (-1 = fallback t = s_{q+1}).  Needs igamg_extrap_workspace_bytes(n, q). */
+size_t igamg_extrap_workspace_bytes(long n, int q);
+igamg_status igamg_extrapolate(long n, int q, int method, const double* d_S, long ld,
+                               double* d_t, double* h_gamma, int* h_qused,
+                               void* d_ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------- misc */
+
+void igamg_destroy(igamg_ctx* ctx);
+const char* igamg_status_str(int status);
+const char* igamg_last_error(void);
+/* Number of kernel launches this thread has enqueued (including graph nodes
+ * replayed), for launch accounting in benchmarks. */
+long long igamg_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IGAMG_H */

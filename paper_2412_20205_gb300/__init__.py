@@ -1,0 +1,249 @@
+"""GB300-native extrapolated geometric multigrid for isogeometric Poisson problems.
+
+Thin Python binding of the C-ABI library ``libigamg.so`` (declared in
+``include/igamg.h``).  The functions below carry the C names and only marshal
+arguments; every step of the solve runs in the library's CUDA kernels.
+PyTorch is used for device memory and streams only.  If the library has not
+been built, or no CUDA device is present for a GPU call, the calls raise --
+there is no CPU fallback.
+"""
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libigamg.so")
+
+IGAMG_OK, IGAMG_EINVAL, IGAMG_ENOMEM, IGAMG_ECUDA, IGAMG_ENOTCONV, IGAMG_EBREAKDOWN, IGAMG_ETIMEOUT = range(7)
+IGAMG_EXTRAP_NONE, IGAMG_RRE, IGAMG_MPE = 0, 1, 2
+IGAMG_FP64, IGAMG_FP32_IR = 0, 1
+IGAMG_FLAG_X0_GIVEN, IGAMG_FLAG_ABS_TOL, IGAMG_FLAG_NO_GRAPH = 1, 2, 4
+
+EXTRAP = {"none": IGAMG_EXTRAP_NONE, "rre": IGAMG_RRE, "mpe": IGAMG_MPE}
+PREC = {"fp64": IGAMG_FP64, "fp32_ir": IGAMG_FP32_IR}
+
+_lib = None
+
+
+class IgamgError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        lib = _load()
+        super().__init__(f"{where}: {lib.igamg_status_str(status).decode()} "
+                         f"({lib.igamg_last_error().decode()})")
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(LIB_PATH)
+    c_int, c_double, c_long, c_size = ctypes.c_int, ctypes.c_double, ctypes.c_long, ctypes.c_size_t
+    vp, ip, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
+    sigs = {
+        "igamg_setup": (c_int, [c_int, c_int, ip, c_int, ctypes.POINTER(vp)]),
+        "igamg_assemble": (c_int, [vp]),
+        "igamg_info": (c_int, [vp, ip, ip]),
+        "igamg_get_factor": (c_int, [vp, c_int, c_int, c_int, dp, ip, ip]),
+        "igamg_workspace_bytes": (c_size, [vp, c_int, c_int]),
+        "igamg_rhs_sine": (c_int, [vp, c_int, dp, vp, vp]),
+        "igamg_solve": (c_int, [vp, vp, vp, c_double, c_int, c_int, c_int, c_int, ctypes.c_uint,
+                                vp, c_size, vp, dp, ip, ip]),
+        "igamg_apply": (c_int, [vp, c_int, vp, vp, vp, c_size, vp]),
+        "igamg_smooth": (c_int, [vp, c_int, vp, vp, c_int, vp, c_size, vp]),
+        "igamg_restrict": (c_int, [vp, c_int, vp, vp, vp, c_size, vp]),
+        "igamg_prolong": (c_int, [vp, c_int, vp, vp, vp, c_size, vp]),
+        "igamg_coarse_solve": (c_int, [vp, vp, vp, vp]),
+        "igamg_vcycle": (c_int, [vp, vp, vp, c_int, vp, c_size, vp]),
+        "igamg_extrap_workspace_bytes": (c_size, [c_long, c_int]),
+        "igamg_extrapolate": (c_int, [c_long, c_int, c_int, vp, c_long, vp, dp, ip, vp, c_size, vp]),
+        "igamg_destroy": (None, [vp]),
+        "igamg_status_str": (ctypes.c_char_p, [c_int]),
+        "igamg_last_error": (ctypes.c_char_p, []),
+        "igamg_launch_count": (ctypes.c_longlong, []),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def lib():
+    """The loaded ctypes library (raises if it has not been built)."""
+    return _load()
+
+
+def _check(status, where):
+    if status != IGAMG_OK:
+        raise IgamgError(status, where)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dbl(arr):
+    return arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+# ------------------------------------------------------------------ C names
+def igamg_setup(dim, p, n_elems, n_levels=0):
+    n = list(n_elems) if hasattr(n_elems, "__len__") else [int(n_elems)] * dim
+    arr = (ctypes.c_int * 3)(*(n + [1] * (3 - len(n))))
+    ctx = ctypes.c_void_p()
+    _check(_load().igamg_setup(dim, p, arr, n_levels, ctypes.byref(ctx)), "igamg_setup")
+    return ctx
+
+
+def igamg_assemble(ctx):
+    _check(_load().igamg_assemble(ctx), "igamg_assemble")
+
+
+def igamg_info(ctx):
+    nl = ctypes.c_int()
+    _check(_load().igamg_info(ctx, ctypes.byref(nl), None), "igamg_info")
+    m = (ctypes.c_int * (3 * nl.value))()
+    _check(_load().igamg_info(ctx, ctypes.byref(nl), m), "igamg_info")
+    return [tuple(m[3 * l:3 * l + 3]) for l in range(nl.value)]
+
+
+def igamg_get_factor(ctx, level, d, which):
+    import numpy as np
+    rows, cols = ctypes.c_int(), ctypes.c_int()
+    _check(_load().igamg_get_factor(ctx, level, d, which, None, ctypes.byref(rows), ctypes.byref(cols)),
+           "igamg_get_factor")
+    out = np.zeros((rows.value, cols.value))
+    _check(_load().igamg_get_factor(ctx, level, d, which, _dbl(out), ctypes.byref(rows), ctypes.byref(cols)),
+           "igamg_get_factor")
+    return out
+
+
+def igamg_workspace_bytes(ctx, k, prec):
+    return int(_load().igamg_workspace_bytes(ctx, k, prec))
+
+
+def igamg_rhs_sine(ctx, coeffs, b, stream=None):
+    import numpy as np
+    c = np.ascontiguousarray(coeffs, dtype=np.float64)
+    _check(_load().igamg_rhs_sine(ctx, c.shape[0], _dbl(c), _ptr(b), _stream(stream)), "igamg_rhs_sine")
+
+
+def igamg_solve(ctx, b, x, tol, extrap, k, max_cycles, prec, flags, ws, stream=None):
+    """Returns (status, history[0..cycles], cycles, vcycles); ENOTCONV is not raised."""
+    import numpy as np
+    hist = np.zeros(max_cycles + 1)
+    cyc, vc = ctypes.c_int(), ctypes.c_int()
+    st = _load().igamg_solve(ctx, _ptr(b), _ptr(x), tol, extrap, k, max_cycles, prec, flags,
+                             _ptr(ws), ws.numel() * ws.element_size(), _stream(stream), _dbl(hist),
+                             ctypes.byref(cyc), ctypes.byref(vc))
+    if st not in (IGAMG_OK, IGAMG_ENOTCONV):
+        _check(st, "igamg_solve")
+    return st, hist[: cyc.value + 1], cyc.value, vc.value
+
+
+def igamg_apply(ctx, level, x, y, ws, stream=None):
+    _check(_load().igamg_apply(ctx, level, _ptr(x), _ptr(y), _ptr(ws), ws.numel(), _stream(stream)),
+           "igamg_apply")
+
+
+def igamg_smooth(ctx, level, x, b, descending, ws, stream=None):
+    _check(_load().igamg_smooth(ctx, level, _ptr(x), _ptr(b), int(descending), _ptr(ws), ws.numel(),
+                                _stream(stream)), "igamg_smooth")
+
+
+def igamg_restrict(ctx, level, fine, coarse, ws, stream=None):
+    _check(_load().igamg_restrict(ctx, level, _ptr(fine), _ptr(coarse), _ptr(ws), ws.numel(),
+                                  _stream(stream)), "igamg_restrict")
+
+
+def igamg_prolong(ctx, level, coarse, fine, ws, stream=None):
+    _check(_load().igamg_prolong(ctx, level, _ptr(coarse), _ptr(fine), _ptr(ws), ws.numel(),
+                                 _stream(stream)), "igamg_prolong")
+
+
+def igamg_coarse_solve(ctx, r, e, stream=None):
+    _check(_load().igamg_coarse_solve(ctx, _ptr(r), _ptr(e), _stream(stream)), "igamg_coarse_solve")
+
+
+def igamg_vcycle(ctx, x, b, prec, ws, stream=None):
+    _check(_load().igamg_vcycle(ctx, _ptr(x), _ptr(b), prec, _ptr(ws), ws.numel(), _stream(stream)),
+           "igamg_vcycle")
+
+
+def igamg_extrap_workspace_bytes(n, q):
+    return int(_load().igamg_extrap_workspace_bytes(n, q))
+
+
+def igamg_extrapolate(n, q, method, S, ld, t, ws, stream=None):
+    import numpy as np
+    gamma = np.zeros(q + 2)
+    qused = ctypes.c_int()
+    _check(_load().igamg_extrapolate(n, q, method, _ptr(S), ld, _ptr(t), _dbl(gamma), ctypes.byref(qused),
+                                     _ptr(ws), ws.numel(), _stream(stream)), "igamg_extrapolate")
+    return gamma, qused.value
+
+
+def igamg_destroy(ctx):
+    _load().igamg_destroy(ctx)
+
+
+def igamg_launch_count():
+    return int(_load().igamg_launch_count())
+
+
+# ------------------------------------------------------------------ convenience
+class Solver:
+    """One problem: context + device workspace (a torch uint8 tensor)."""
+
+    def __init__(self, dim, p, n, n_levels=0, k=10, prec="fp32_ir", device="cuda"):
+        import torch
+        self.dim, self.p = dim, p
+        self.ctx = igamg_setup(dim, p, n, n_levels)
+        igamg_assemble(self.ctx)
+        self.levels = igamg_info(self.ctx)
+        m = self.levels[-1]
+        self.N = m[0] * m[1] * m[2]
+        nbytes = max(igamg_workspace_bytes(self.ctx, k, PREC["fp32_ir"]),
+                     igamg_workspace_bytes(self.ctx, k, PREC["fp64"]))
+        self.ws = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.k_max = k
+
+    def rhs_sine(self, coeffs, b=None):
+        import torch
+        if b is None:
+            b = torch.empty(self.N, dtype=torch.float64, device=self.ws.device)
+        igamg_rhs_sine(self.ctx, coeffs, b)
+        return b
+
+    def solve(self, b, x=None, tol=1e-10, method="rre", k=5, max_cycles=200, prec="fp64",
+              x0_given=False, absolute=False, graph=True):
+        import torch
+        if x is None:
+            x = torch.zeros(self.N, dtype=torch.float64, device=self.ws.device)
+        flags = (IGAMG_FLAG_X0_GIVEN if x0_given else 0) | (IGAMG_FLAG_ABS_TOL if absolute else 0) | \
+                (0 if graph else IGAMG_FLAG_NO_GRAPH)
+        st, hist, cyc, vc = igamg_solve(self.ctx, b, x, tol, EXTRAP[method], k, max_cycles, PREC[prec],
+                                        flags, self.ws)
+        return dict(x=x, status=st, history=hist, cycles=cyc, vcycles=vc, converged=st == IGAMG_OK)
+
+    def close(self):
+        if self.ctx:
+            igamg_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,853 @@
+// C ABI of the solver: context, set-up/upload, workspace layout, the V-cycle
+// sequencer (Algorithm 2, mu = 1) and the restarted extrapolation loop
+// (Algorithm 5 with Algorithms 3-4), replayed as a CUDA graph per restart.
+#include "../../include/igamg.h"
+#include "device.hpp"
+#include "host_setup.hpp"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace igamg;
+
+namespace {
+
+thread_local std::string g_err;
+
+igamg_status fail(igamg_status st, const std::string& msg) {
+    g_err = msg;
+    return st;
+}
+
+#define CUDA_TRY(call)                                                                   \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(IGAMG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+struct HostLevel {
+    int m[3] = {1, 1, 1};
+    std::vector<double> breaks[3];
+    Factor1D f[3];
+    // prolongation from the next coarser level (empty on level 0)
+    std::vector<double> P[3];
+    int pmf[3] = {0, 0, 0}, pmc[3] = {0, 0, 0};
+    std::vector<int> plo[3], rlo[3];
+    std::vector<double> pv[3], rv[3];
+    int pw[3] = {0, 0, 0}, rw[3] = {0, 0, 0};
+    size_t N() const { return (size_t)m[0] * m[1] * m[2]; }
+};
+
+// Bump allocator over a device buffer (base == nullptr: size query only).
+struct Carver {
+    char* base;
+    size_t off = 0;
+    explicit Carver(void* b) : base((char*)b) {}
+    template <typename T>
+    T* take(size_t count) {
+        off = (off + 255) & ~(size_t)255;
+        T* p = base ? (T*)(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+template <typename T>
+struct LevelBuf {
+    T* x = nullptr;   // x, TM, TK contiguous (zeroed together)
+    T* TM = nullptr;
+    T* TK = nullptr;
+    T* b = nullptr;
+    T* r = nullptr;
+    T* tmp1 = nullptr;
+    T* tmp2 = nullptr;
+};
+
+struct Workspace {
+    std::vector<LevelBuf<double>> d;
+    std::vector<LevelBuf<float>> f;
+    double* S = nullptr;      // k+2 iterates, stride ld
+    size_t ld = 0;
+    double* partial = nullptr;
+    size_t npartial = 0;
+    double* gamma = nullptr;
+    int* qused = nullptr;
+    ExtrapInfo* info = nullptr;
+    double* scal = nullptr;   // [0] ||b||, [1] last residual norm, [2..] spare
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct igamg_ctx {
+    int dim = 2, p = 1, L = 1;
+    std::vector<HostLevel> hl;
+    std::vector<double> cV[3], claminv;     // coarsest fast diagonalisation (host)
+    bool assembled = false;
+    void* dmem = nullptr;
+    std::vector<LevelView<double>> lv64;
+    std::vector<LevelView<float>> lv32;
+    std::vector<TransferView<double>> tv64;
+    std::vector<TransferView<float>> tv32;
+    CoarseView<double> cv64{};
+    CoarseView<float> cv32{};
+    // sine-moment tables for the load vector (finest level)
+    cudaStream_t cap = nullptr;             // capture stream
+    double* h_pin = nullptr;                // pinned host scalars
+    cudaGraphExec_t exec = nullptr;
+    long long exec_launches = 0;
+    struct Key {
+        const void* b = nullptr;
+        const void* ws = nullptr;
+        int k = -1, extrap = -1, prec = -1, abs_tol = -1;
+        bool operator==(const Key& o) const {
+            return b == o.b && ws == o.ws && k == o.k && extrap == o.extrap && prec == o.prec &&
+                   abs_tol == o.abs_tol;
+        }
+    } key;
+};
+
+namespace {
+
+size_t finestN(const igamg_ctx* c) { return c->hl.back().N(); }
+
+Workspace carve(const igamg_ctx* c, void* base, int k, int prec) {
+    Workspace w;
+    Carver cv(base);
+    const int L = c->L;
+    w.d.resize(L);
+    for (int l = 0; l < L; ++l) {
+        const size_t N = c->hl[l].N();
+        LevelBuf<double>& B = w.d[l];
+        B.x = cv.take<double>(3 * N);
+        if (B.x) { B.TM = B.x + N; B.TK = B.x + 2 * N; }
+        B.b = cv.take<double>(N);
+        B.r = cv.take<double>(N);
+        B.tmp1 = cv.take<double>(N);
+        B.tmp2 = cv.take<double>(N);
+    }
+    if (prec == IGAMG_FP32_IR) {
+        w.f.resize(L);
+        for (int l = 0; l < L; ++l) {
+            const size_t N = c->hl[l].N();
+            LevelBuf<float>& B = w.f[l];
+            B.x = cv.take<float>(3 * N);
+            if (B.x) { B.TM = B.x + N; B.TK = B.x + 2 * N; }
+            B.b = cv.take<float>(N);
+            B.r = cv.take<float>(N);
+            B.tmp1 = cv.take<float>(N);
+            B.tmp2 = cv.take<float>(N);
+        }
+    }
+    const size_t N = finestN(c);
+    w.ld = (N + 31) & ~(size_t)31;
+    w.S = cv.take<double>(w.ld * (size_t)(k + 2));
+    const size_t rows = (size_t)c->hl.back().m[1] * c->hl.back().m[2];
+    const size_t np = (size_t)(kMaxQ + 1) * (kMaxQ + 2) / 2;
+    w.npartial = std::max(rows, (size_t)dev::gram_blocks(N) * np);
+    w.npartial = std::max(w.npartial, (size_t)1024);
+    w.partial = cv.take<double>(w.npartial);
+    w.gamma = cv.take<double>(kMaxQ + 2);
+    w.qused = cv.take<int>(4);
+    w.info = cv.take<ExtrapInfo>(1);
+    w.scal = cv.take<double>(8);
+    w.bytes = cv.off + 256;
+    return w;
+}
+
+void compact_transfer(HostLevel& H, int d) {
+    const int mf = H.pmf[d], mc = H.pmc[d];
+    const std::vector<double>& P = H.P[d];
+    H.plo[d].assign(mf, 0);
+    H.rlo[d].assign(mc, 0);
+    int pw = 1, rw = 1;
+    std::vector<int> phi(mf, 0), rhi(mc, 0);
+    for (int i = 0; i < mf; ++i) {
+        int lo = -1, hi = -1;
+        for (int J = 0; J < mc; ++J)
+            if (P[(size_t)i * mc + J] != 0.0) { if (lo < 0) lo = J; hi = J; }
+        if (lo < 0) { lo = 0; hi = 0; }
+        H.plo[d][i] = lo;
+        phi[i] = hi;
+        pw = std::max(pw, hi - lo + 1);
+    }
+    for (int J = 0; J < mc; ++J) {
+        int lo = -1, hi = -1;
+        for (int i = 0; i < mf; ++i)
+            if (P[(size_t)i * mc + J] != 0.0) { if (lo < 0) lo = i; hi = i; }
+        if (lo < 0) { lo = 0; hi = 0; }
+        H.rlo[d][J] = lo;
+        rhi[J] = hi;
+        rw = std::max(rw, hi - lo + 1);
+    }
+    H.pw[d] = pw;
+    H.rw[d] = rw;
+    H.pv[d].assign((size_t)mf * pw, 0.0);
+    H.rv[d].assign((size_t)mc * rw, 0.0);
+    for (int i = 0; i < mf; ++i)
+        for (int s = 0; s < pw; ++s) {
+            const int J = H.plo[d][i] + s;
+            if (J < mc) H.pv[d][(size_t)i * pw + s] = P[(size_t)i * mc + J];
+        }
+    for (int J = 0; J < mc; ++J)
+        for (int s = 0; s < rw; ++s) {
+            const int i = H.rlo[d][J] + s;
+            if (i < mf) H.rv[d][(size_t)J * rw + s] = P[(size_t)i * mc + J];
+        }
+}
+
+template <typename T>
+std::vector<T> band_major(const Factor1D& f, bool stiff) {
+    const int m = f.m, bw = 2 * f.p + 1;
+    std::vector<T> out((size_t)bw * m);
+    const std::vector<double>& src = stiff ? f.K : f.M;
+    for (int i = 0; i < m; ++i)
+        for (int b = 0; b < bw; ++b) out[(size_t)b * m + i] = (T)src[(size_t)i * bw + b];
+    return out;
+}
+
+// ------------------------------------------------------------ V-cycle sequencer
+template <typename T>
+struct Views;
+template <>
+struct Views<double> {
+    static const std::vector<LevelView<double>>& lv(const igamg_ctx* c) { return c->lv64; }
+    static const std::vector<TransferView<double>>& tv(const igamg_ctx* c) { return c->tv64; }
+    static const CoarseView<double>& cv(const igamg_ctx* c) { return c->cv64; }
+    static std::vector<LevelBuf<double>>& buf(Workspace& w) { return w.d; }
+};
+template <>
+struct Views<float> {
+    static const std::vector<LevelView<float>>& lv(const igamg_ctx* c) { return c->lv32; }
+    static const std::vector<TransferView<float>>& tv(const igamg_ctx* c) { return c->tv32; }
+    static const CoarseView<float>& cv(const igamg_ctx* c) { return c->cv32; }
+    static std::vector<LevelBuf<float>>& buf(Workspace& w) { return w.f; }
+};
+
+// Algorithm 2 (mu = 1, nu1 = nu2 = 1) from level `top` down to the coarsest
+// and back.  x_top / b_top are the top level's iterate and right side; the
+// top level's TM/TK must match x_top unless top_zero (then x_top = 0 is set).
+template <typename T>
+void vcycle(const igamg_ctx* c, cudaStream_t s, Workspace& w, int top, T* x_top, const T* b_top,
+            bool top_zero) {
+    const auto& lv = Views<T>::lv(c);
+    const auto& tv = Views<T>::tv(c);
+    auto& B = Views<T>::buf(w);
+    const int dim = c->dim;
+    for (int l = top; l >= 1; --l) {
+        T* x = (l == top) ? x_top : B[l].x;
+        const T* b = (l == top) ? b_top : B[l].b;
+        const size_t N = lv[l].n();
+        if (l != top || top_zero) {
+            if (x == B[l].x) dev::fill_zero<T>(s, B[l].x, 3 * N);
+            else {
+                dev::fill_zero<T>(s, x, N);
+                dev::fill_zero<T>(s, B[l].TM, 2 * N);
+            }
+        }
+        dev::gs_sweep<T>(s, dim, lv[l], false, x, b, B[l].TM, B[l].TK);               // pre-smooth
+        dev::residual<T, T>(s, dim, lv[l], b, B[l].TM, B[l].TK, B[l].r, nullptr);      // r = b - A u
+        dev::restrict_<T>(s, dim, tv[l], B[l].r, B[l - 1].b, B[l].tmp1, B[l].tmp2);   // R = P^T
+    }
+    {
+        T* x0 = (top == 0) ? x_top : B[0].x;
+        const T* b0 = (top == 0) ? b_top : B[0].b;
+        dev::coarse_solve<T>(s, dim, Views<T>::cv(c), b0, x0);                          // direct
+    }
+    for (int l = 1; l <= top; ++l) {
+        T* x = (l == top) ? x_top : B[l].x;
+        const T* b = (l == top) ? b_top : B[l].b;
+        T* e = (l - 1 == top) ? x_top : B[l - 1].x;
+        dev::prolong_add<T>(s, dim, tv[l], lv[l], e, x, B[l].TM, B[l].TK, B[l].tmp1, B[l].tmp2);
+        dev::gs_sweep<T>(s, dim, lv[l], true, x, b, B[l].TM, B[l].TK);                // post-smooth
+    }
+}
+
+// One V-cycle (fixed-point step s_{i+1} = G(s_i), Eq. fixedpoint) from S_in to
+// S_out on the finest level; the finest FP64 TM/TK match S_in on entry and
+// S_out on exit.
+void fixed_point_step(const igamg_ctx* c, cudaStream_t s, Workspace& w, int prec, const double* d_b,
+                      double* S_in, double* S_out) {
+    const int top = c->L - 1;
+    const size_t N = finestN(c);
+    LevelBuf<double>& F = w.d[top];
+    if (prec == IGAMG_FP64) {
+        if (S_out != S_in) cudaMemcpyAsync(S_out, S_in, N * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        vcycle<double>(c, s, w, top, S_out, d_b, false);
+        if (top == 0)   // single grid: the direct solve changed x without refreshing its row sums
+            dev::xpass<double, double>(s, c->lv64[0], S_out, nullptr, nullptr, 0, nullptr, nullptr, 0, F.TM, F.TK);
+    } else {
+        LevelBuf<float>& G = w.f[top];
+        // r = b - A s in FP64, rounded to FP32; e = V32(0; r); s_out = s_in + e (FP64)
+        dev::residual<double, float>(s, c->dim, c->lv64[top], d_b, F.TM, F.TK, G.b, nullptr);
+        vcycle<float>(c, s, w, top, G.x, G.b, true);
+        dev::xpass<double, float>(s, c->lv64[top], S_in, S_out, G.x, 0, nullptr, nullptr, 0, F.TM, F.TK);
+    }
+}
+
+// ||b - A x|| / denom into scal[1] using the finest TM/TK (which match x).
+void residual_norm(const igamg_ctx* c, cudaStream_t s, Workspace& w, const double* d_b,
+                   const double* denom) {
+    const int top = c->L - 1;
+    LevelBuf<double>& F = w.d[top];
+    dev::residual<double, double>(s, c->dim, c->lv64[top], d_b, F.TM, F.TK, F.r, w.partial);
+    dev::norm_final(s, w.partial, c->lv64[top].rows(), denom, w.scal, 1);
+}
+
+// One restart cycle of Algorithm 5 (or one plain V-cycle for extrap = NONE).
+void restart_body(const igamg_ctx* c, cudaStream_t s, Workspace& w, int extrap, int k, int prec,
+                  const double* d_b, const double* denom) {
+    const size_t N = finestN(c);
+    const int top = c->L - 1;
+    if (extrap == IGAMG_EXTRAP_NONE) {
+        fixed_point_step(c, s, w, prec, d_b, w.S, w.S);
+    } else {
+        for (int i = 0; i <= k; ++i)
+            fixed_point_step(c, s, w, prec, d_b, w.S + (size_t)i * w.ld, w.S + (size_t)(i + 1) * w.ld);
+        const int nb = dev::gram_blocks(N);
+        dev::extrap_gammas(s, k, extrap, w.S, w.ld, N, w.partial, nb, w.info, w.gamma, w.qused);
+        // t = sum_j gamma_j s_j -> S_0, with fresh FP64 row sums for the residual
+        dev::xpass<double, double>(s, c->lv64[top], nullptr, w.S, nullptr, k + 2, w.gamma, w.S, w.ld,
+                                   w.d[top].TM, w.d[top].TK);
+    }
+    residual_norm(c, s, w, d_b, denom);
+}
+
+igamg_status check_ctx(const igamg_ctx* c, bool need_assembled = true) {
+    if (!c) return fail(IGAMG_EINVAL, "null context");
+    if (need_assembled && !c->assembled) return fail(IGAMG_EINVAL, "context not assembled");
+    return IGAMG_OK;
+}
+
+igamg_status check_ws(const igamg_ctx* c, void* ws, size_t bytes, int k, int prec) {
+    const size_t need = carve(c, nullptr, k, prec).bytes;
+    if (!ws) return fail(IGAMG_EINVAL, "null workspace");
+    if (((uintptr_t)ws & 255) != 0) return fail(IGAMG_EINVAL, "workspace must be 256-byte aligned");
+    if (bytes < need) return fail(IGAMG_ENOMEM, "workspace too small: need " + std::to_string(need));
+    return IGAMG_OK;
+}
+
+}  // namespace
+
+// ======================================================================= C ABI
+extern "C" {
+
+const char* igamg_status_str(int st) {
+    switch (st) {
+        case IGAMG_OK: return "ok";
+        case IGAMG_EINVAL: return "invalid argument";
+        case IGAMG_ENOMEM: return "out of memory";
+        case IGAMG_ECUDA: return "CUDA error";
+        case IGAMG_ENOTCONV: return "not converged";
+        case IGAMG_EBREAKDOWN: return "breakdown (non-finite residual)";
+        case IGAMG_ETIMEOUT: return "device wait timed out";
+        default: return "unknown status";
+    }
+}
+
+const char* igamg_last_error(void) { return g_err.c_str(); }
+
+long long igamg_launch_count(void) { return launch_count(); }
+
+igamg_status igamg_setup(int dim, int p, const int* n_elems, int n_levels, igamg_ctx** out) {
+    if (!out || !n_elems) return fail(IGAMG_EINVAL, "null pointer");
+    *out = nullptr;
+    if (dim != 2 && dim != 3) return fail(IGAMG_EINVAL, "dim must be 2 or 3");
+    if (p < 1 || p > kMaxP) return fail(IGAMG_EINVAL, "p must be in [1, 7]");
+    for (int d = 0; d < dim; ++d)
+        if (n_elems[d] < 2 || n_elems[d] > 4096) return fail(IGAMG_EINVAL, "n_elems must be in [2, 4096]");
+    if (n_levels < 0 || n_levels > 16) return fail(IGAMG_EINVAL, "n_levels must be in [0, 16]");
+    igamg_ctx* c = new (std::nothrow) igamg_ctx();
+    if (!c) return fail(IGAMG_ENOMEM, "host allocation");
+    c->dim = dim;
+    c->p = p;
+    try {
+        std::vector<std::vector<std::vector<double>>> chain;
+        std::vector<std::vector<double>> br(3);
+        for (int d = 0; d < dim; ++d) br[d] = uniform_breaks(n_elems[d]);
+        chain.push_back(br);
+        auto nel = [&](const std::vector<std::vector<double>>& b) {
+            int mx = 0;
+            for (int d = 0; d < dim; ++d) mx = std::max(mx, (int)b[d].size() - 1);
+            return mx;
+        };
+        if (n_levels == 0) {
+            while (nel(chain.back()) > 8) {
+                std::vector<std::vector<double>> nb(3);
+                for (int d = 0; d < dim; ++d) nb[d] = coarsen_breaks(chain.back()[d]);
+                chain.push_back(nb);
+            }
+        } else {
+            for (int l = 1; l < n_levels; ++l) {
+                std::vector<std::vector<double>> nb(3);
+                for (int d = 0; d < dim; ++d) {
+                    if ((int)chain.back()[d].size() - 1 < 2) { delete c; return fail(IGAMG_EINVAL, "too many levels"); }
+                    nb[d] = coarsen_breaks(chain.back()[d]);
+                }
+                chain.push_back(nb);
+            }
+        }
+        std::reverse(chain.begin(), chain.end());       // level 0 = coarsest
+        c->L = (int)chain.size();
+        c->hl.resize(c->L);
+        for (int l = 0; l < c->L; ++l) {
+            HostLevel& H = c->hl[l];
+            for (int d = 0; d < dim; ++d) {
+                H.breaks[d] = chain[l][d];
+                H.f[d] = assemble_1d(H.breaks[d], p);
+                H.m[d] = H.f[d].m;
+                if (H.m[d] < 1) { delete c; return fail(IGAMG_EINVAL, "a level has no interior unknowns"); }
+                if (l > 0) {
+                    H.P[d] = prolongation_1d(H.breaks[d], chain[l - 1][d], p, &H.pmf[d], &H.pmc[d]);
+                    compact_transfer(H, d);
+                }
+            }
+        }
+        if (c->hl.back().m[0] > 5000) { delete c; return fail(IGAMG_EINVAL, "row length above 5000"); }
+        const HostLevel& H0 = c->hl[0];
+        const size_t N0 = H0.N();
+        if (N0 > 12000) { delete c; return fail(IGAMG_EINVAL, "coarsest grid too large for the direct solve"); }
+        std::vector<double> lam[3];
+        for (int d = 0; d < dim; ++d) generalized_eigen(H0.f[d], c->cV[d], lam[d]);
+        c->claminv.resize(N0);
+        for (int k = 0; k < H0.m[2]; ++k)
+            for (int j = 0; j < H0.m[1]; ++j)
+                for (int i = 0; i < H0.m[0]; ++i) {
+                    double s = lam[0][i] + lam[1][j] + (dim == 3 ? lam[2][k] : 0.0);
+                    c->claminv[((size_t)k * H0.m[1] + j) * H0.m[0] + i] = 1.0 / s;
+                }
+    } catch (const std::exception& e) {
+        delete c;
+        return fail(IGAMG_EINVAL, std::string("setup: ") + e.what());
+    }
+    *out = c;
+    return IGAMG_OK;
+}
+
+igamg_status igamg_info(const igamg_ctx* c, int* n_levels, int* h_m) {
+    if (igamg_status st = check_ctx(c, false)) return st;
+    if (n_levels) *n_levels = c->L;
+    if (h_m)
+        for (int l = 0; l < c->L; ++l)
+            for (int d = 0; d < 3; ++d) h_m[3 * l + d] = c->hl[l].m[d];
+    return IGAMG_OK;
+}
+
+igamg_status igamg_get_factor(const igamg_ctx* c, int level, int d, int which, double* h_out, int* rows,
+                              int* cols) {
+    if (igamg_status st = check_ctx(c, false)) return st;
+    if (level < 0 || level >= c->L || d < 0 || d >= c->dim || which < 0 || which > 2)
+        return fail(IGAMG_EINVAL, "bad level/direction/which");
+    const HostLevel& H = c->hl[level];
+    if (which < 2) {
+        const std::vector<double>& F = which == 0 ? H.f[d].M : H.f[d].K;
+        if (rows) *rows = H.f[d].m;
+        if (cols) *cols = 2 * c->p + 1;
+        if (h_out) std::memcpy(h_out, F.data(), F.size() * sizeof(double));
+    } else {
+        if (level == 0) return fail(IGAMG_EINVAL, "level 0 has no prolongation");
+        if (rows) *rows = H.pmf[d];
+        if (cols) *cols = H.pmc[d];
+        if (h_out) std::memcpy(h_out, H.P[d].data(), H.P[d].size() * sizeof(double));
+    }
+    return IGAMG_OK;
+}
+
+igamg_status igamg_assemble(igamg_ctx* c) {
+    if (igamg_status st = check_ctx(c, false)) return st;
+    if (c->assembled) return IGAMG_OK;
+    const int dim = c->dim, p = c->p, L = c->L;
+    // host staging of every device array, then one allocation and copies
+    struct Blob {
+        std::vector<char> bytes;
+        size_t off = 0;
+    };
+    std::vector<std::pair<size_t, std::vector<char>>> pieces;
+    size_t total = 0;
+    auto add = [&](const void* src, size_t bytes) -> size_t {
+        total = (total + 255) & ~(size_t)255;
+        const size_t off = total;
+        std::vector<char> v((const char*)src, (const char*)src + bytes);
+        pieces.emplace_back(off, std::move(v));
+        total += bytes;
+        return off;
+    };
+    struct LevelOff {
+        size_t Mb[3][2], Kb[3][2], inv[2];
+        size_t plo[3], rlo[3], pv[3][2], rv[3][2];
+    };
+    std::vector<LevelOff> lo(L);
+    for (int l = 0; l < L; ++l) {
+        const HostLevel& H = c->hl[l];
+        for (int d = 0; d < dim; ++d) {
+            auto m64 = band_major<double>(H.f[d], false), k64 = band_major<double>(H.f[d], true);
+            auto m32 = band_major<float>(H.f[d], false), k32 = band_major<float>(H.f[d], true);
+            lo[l].Mb[d][0] = add(m64.data(), m64.size() * 8);
+            lo[l].Kb[d][0] = add(k64.data(), k64.size() * 8);
+            lo[l].Mb[d][1] = add(m32.data(), m32.size() * 4);
+            lo[l].Kb[d][1] = add(k32.data(), k32.size() * 4);
+            if (l > 0) {
+                lo[l].plo[d] = add(H.plo[d].data(), H.plo[d].size() * 4);
+                lo[l].rlo[d] = add(H.rlo[d].data(), H.rlo[d].size() * 4);
+                std::vector<float> pf(H.pv[d].begin(), H.pv[d].end()), rf(H.rv[d].begin(), H.rv[d].end());
+                lo[l].pv[d][0] = add(H.pv[d].data(), H.pv[d].size() * 8);
+                lo[l].rv[d][0] = add(H.rv[d].data(), H.rv[d].size() * 8);
+                lo[l].pv[d][1] = add(pf.data(), pf.size() * 4);
+                lo[l].rv[d][1] = add(rf.data(), rf.size() * 4);
+            }
+        }
+        // inverse diagonal of A: 1 / sum_d K_d(i_d,i_d) prod_{e!=d} M_e(i_e,i_e)
+        const size_t N = H.N();
+        std::vector<double> inv(N);
+        std::vector<float> inv32(N);
+        const int bw = 2 * p + 1;
+        for (int k = 0; k < H.m[2]; ++k)
+            for (int j = 0; j < H.m[1]; ++j)
+                for (int i = 0; i < H.m[0]; ++i) {
+                    const int idx[3] = {i, j, k};
+                    double s = 0.0;
+                    for (int d = 0; d < dim; ++d) {
+                        double t = H.f[d].K[(size_t)idx[d] * bw + p];
+                        for (int e = 0; e < dim; ++e)
+                            if (e != d) t *= H.f[e].M[(size_t)idx[e] * bw + p];
+                        s += t;
+                    }
+                    const size_t o = ((size_t)k * H.m[1] + j) * H.m[0] + i;
+                    inv[o] = 1.0 / s;
+                    inv32[o] = (float)(1.0 / s);
+                }
+        lo[l].inv[0] = add(inv.data(), N * 8);
+        lo[l].inv[1] = add(inv32.data(), N * 4);
+    }
+    size_t cVo[3][2], cLo[2];
+    for (int d = 0; d < dim; ++d) {
+        std::vector<float> f(c->cV[d].begin(), c->cV[d].end());
+        cVo[d][0] = add(c->cV[d].data(), c->cV[d].size() * 8);
+        cVo[d][1] = add(f.data(), f.size() * 4);
+    }
+    {
+        std::vector<float> f(c->claminv.begin(), c->claminv.end());
+        cLo[0] = add(c->claminv.data(), c->claminv.size() * 8);
+        cLo[1] = add(f.data(), f.size() * 4);
+    }
+    void* dm = nullptr;
+    if (cudaMalloc(&dm, total) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(IGAMG_ENOMEM, "device allocation of the operator data");
+    }
+    for (auto& pc : pieces) {
+        cudaError_t e = cudaMemcpy((char*)dm + pc.first, pc.second.data(), pc.second.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(dm);
+            return fail(IGAMG_ECUDA, std::string("upload: ") + cudaGetErrorString(e));
+        }
+    }
+    c->dmem = dm;
+    char* base = (char*)dm;
+    c->lv64.resize(L);
+    c->lv32.resize(L);
+    c->tv64.resize(L);
+    c->tv32.resize(L);
+    for (int l = 0; l < L; ++l) {
+        const HostLevel& H = c->hl[l];
+        LevelView<double>& a = c->lv64[l];
+        LevelView<float>& f = c->lv32[l];
+        for (int d = 0; d < 3; ++d) {
+            a.m[d] = f.m[d] = H.m[d];
+            a.Mb[d] = a.Kb[d] = nullptr;
+            f.Mb[d] = f.Kb[d] = nullptr;
+        }
+        a.p = f.p = p;
+        for (int d = 0; d < dim; ++d) {
+            a.Mb[d] = (const double*)(base + lo[l].Mb[d][0]);
+            a.Kb[d] = (const double*)(base + lo[l].Kb[d][0]);
+            f.Mb[d] = (const float*)(base + lo[l].Mb[d][1]);
+            f.Kb[d] = (const float*)(base + lo[l].Kb[d][1]);
+        }
+        a.invdiag = (const double*)(base + lo[l].inv[0]);
+        f.invdiag = (const float*)(base + lo[l].inv[1]);
+        TransferView<double>& t = c->tv64[l];
+        TransferView<float>& tf = c->tv32[l];
+        std::memset(&t, 0, sizeof(t));
+        std::memset(&tf, 0, sizeof(tf));
+        if (l > 0)
+            for (int d = 0; d < 3; ++d) {
+                const int mf = (d < dim) ? H.m[d] : 1, mc = (d < dim) ? c->hl[l - 1].m[d] : 1;
+                t.mf[d] = tf.mf[d] = mf;
+                t.mc[d] = tf.mc[d] = mc;
+                if (d >= dim) continue;
+                t.pw[d] = tf.pw[d] = H.pw[d];
+                t.rw[d] = tf.rw[d] = H.rw[d];
+                t.plo[d] = tf.plo[d] = (const int*)(base + lo[l].plo[d]);
+                t.rlo[d] = tf.rlo[d] = (const int*)(base + lo[l].rlo[d]);
+                t.pv[d] = (const double*)(base + lo[l].pv[d][0]);
+                t.rv[d] = (const double*)(base + lo[l].rv[d][0]);
+                tf.pv[d] = (const float*)(base + lo[l].pv[d][1]);
+                tf.rv[d] = (const float*)(base + lo[l].rv[d][1]);
+            }
+    }
+    for (int d = 0; d < 3; ++d) {
+        c->cv64.m[d] = c->cv32.m[d] = c->hl[0].m[d];
+        c->cv64.V[d] = (d < dim) ? (const double*)(base + cVo[d][0]) : nullptr;
+        c->cv32.V[d] = (d < dim) ? (const float*)(base + cVo[d][1]) : nullptr;
+    }
+    c->cv64.laminv = (const double*)(base + cLo[0]);
+    c->cv32.laminv = (const float*)(base + cLo[1]);
+    CUDA_TRY(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+    CUDA_TRY(cudaMallocHost(&c->h_pin, 64));
+    c->assembled = true;
+    return IGAMG_OK;
+}
+
+size_t igamg_workspace_bytes(const igamg_ctx* c, int k, int prec) {
+    if (!c || k < 0 || k > kMaxQ) return 0;
+    return carve(c, nullptr, std::max(k, 1), prec).bytes;
+}
+
+igamg_status igamg_rhs_sine(igamg_ctx* c, int modes, const double* h_coeffs, double* d_b, void* stream) {
+    if (igamg_status st = check_ctx(c)) return st;
+    if (modes < 1 || modes > 64 || !h_coeffs || !d_b) return fail(IGAMG_EINVAL, "bad rhs arguments");
+    const HostLevel& H = c->hl.back();
+    const int dim = c->dim;
+    std::vector<double> g[3];
+    for (int d = 0; d < dim; ++d) g[d] = sine_moments(H.breaks[d], c->p, modes);
+    // H[(kz*modes + ky) * m_x + i] = sum_kx c[kz][ky][kx] gx[kx][i]
+    const int mx = H.m[0];
+    const int outer = (dim == 3) ? modes * modes : modes;
+    std::vector<double> Hx((size_t)outer * mx, 0.0);
+    for (int o = 0; o < outer; ++o)
+        for (int kx = 0; kx < modes; ++kx) {
+            const double cc = h_coeffs[(size_t)o * modes + kx];
+            if (cc == 0.0) continue;
+            for (int i = 0; i < mx; ++i) Hx[(size_t)o * mx + i] += cc * g[0][(size_t)kx * mx + i];
+        }
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t nH = Hx.size(), nY = g[1].size(), nZ = (dim == 3) ? g[2].size() : 0;
+    double* tmp = nullptr;
+    CUDA_TRY(cudaMallocAsync((void**)&tmp, (nH + nY + nZ + 1) * sizeof(double), s));
+    CUDA_TRY(cudaMemcpyAsync(tmp, Hx.data(), nH * 8, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(tmp + nH, g[1].data(), nY * 8, cudaMemcpyHostToDevice, s));
+    if (nZ) CUDA_TRY(cudaMemcpyAsync(tmp + nH + nY, g[2].data(), nZ * 8, cudaMemcpyHostToDevice, s));
+    dev::rhs_sine(s, dim, H.m, modes, tmp, tmp + nH, nZ ? tmp + nH + nY : nullptr, d_b);
+    CUDA_TRY(cudaFreeAsync(tmp, s));
+    CUDA_TRY(cudaStreamSynchronize(s));       // host staging vectors go out of scope
+    CUDA_TRY(cudaGetLastError());
+    return IGAMG_OK;
+}
+
+igamg_status igamg_solve(igamg_ctx* c, const double* d_b, double* d_x, double tol, int extrap, int k,
+                         int max_cycles, int prec, unsigned flags, void* d_ws, size_t ws_bytes,
+                         void* stream, double* h_hist, int* h_cycles, int* h_vcycles) {
+    if (igamg_status st = check_ctx(c)) return st;
+    if (!d_b || !d_x) return fail(IGAMG_EINVAL, "null vector");
+    if (extrap < 0 || extrap > 2 || prec < 0 || prec > 1) return fail(IGAMG_EINVAL, "bad extrap/prec");
+    if (extrap != IGAMG_EXTRAP_NONE && (k < 1 || k > kMaxQ)) return fail(IGAMG_EINVAL, "k must be in [1, 12]");
+    if (max_cycles < 0 || !(tol >= 0.0)) return fail(IGAMG_EINVAL, "bad max_cycles/tol");
+    const int kk = (extrap == IGAMG_EXTRAP_NONE) ? 1 : k;
+    if (igamg_status st = check_ws(c, d_ws, ws_bytes, kk, prec)) return st;
+    Workspace w = carve(c, d_ws, kk, prec);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t N = finestN(c);
+    const int top = c->L - 1;
+    if (h_cycles) *h_cycles = 0;
+    if (h_vcycles) *h_vcycles = 0;
+    // ||b|| (denominator of the relative test)
+    dev::sumsq_partial(s, d_b, N, w.partial, 256);
+    dev::norm_final(s, w.partial, 256, nullptr, w.scal, 0);
+    if (flags & IGAMG_FLAG_X0_GIVEN)
+        CUDA_TRY(cudaMemcpyAsync(w.S, d_x, N * 8, cudaMemcpyDeviceToDevice, s));
+    else
+        dev::fill_zero<double>(s, w.S, N);
+    dev::xpass<double, double>(s, c->lv64[top], w.S, w.S, nullptr, 0, nullptr, nullptr, 0,
+                               w.d[top].TM, w.d[top].TK);
+    const double* denom = (flags & IGAMG_FLAG_ABS_TOL) ? nullptr : w.scal;
+    CUDA_TRY(cudaMemcpyAsync(c->h_pin, w.scal, 8, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    const double bnorm = c->h_pin[0];
+    if (!std::isfinite(bnorm)) return fail(IGAMG_EBREAKDOWN, "non-finite right-hand side");
+    if (bnorm == 0.0 && !(flags & IGAMG_FLAG_ABS_TOL)) {           // b = 0: x = 0 is exact
+        CUDA_TRY(cudaMemsetAsync(d_x, 0, N * 8, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        if (h_hist) h_hist[0] = 0.0;
+        return IGAMG_OK;
+    }
+    residual_norm(c, s, w, d_b, denom);
+    CUDA_TRY(cudaMemcpyAsync(c->h_pin, w.scal + 1, 8, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    CUDA_TRY(cudaGetLastError());
+    double res = c->h_pin[0];
+    if (h_hist) h_hist[0] = res;
+    igamg_status result = IGAMG_ENOTCONV;
+    if (res <= tol) result = IGAMG_OK;
+    const bool use_graph = !(flags & IGAMG_FLAG_NO_GRAPH);
+    if (use_graph && result != IGAMG_OK && max_cycles > 0) {
+        igamg_ctx::Key key;
+        key.b = d_b; key.ws = d_ws; key.k = kk; key.extrap = extrap; key.prec = prec;
+        key.abs_tol = denom == nullptr;
+        if (!(c->exec && c->key == key)) {
+            if (c->exec) { cudaGraphExecDestroy(c->exec); c->exec = nullptr; }
+            cudaGraph_t g = nullptr;
+            const long long before = launch_count();
+            CUDA_TRY(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+            restart_body(c, c->cap, w, extrap, kk, prec, d_b, denom);
+            cudaError_t ce = cudaStreamEndCapture(c->cap, &g);
+            if (ce != cudaSuccess) return fail(IGAMG_ECUDA, std::string("capture: ") + cudaGetErrorString(ce));
+            c->exec_launches = launch_count() - before;
+            count_launch(-c->exec_launches);
+            ce = cudaGraphInstantiate(&c->exec, g, 0);
+            cudaGraphDestroy(g);
+            if (ce != cudaSuccess) { c->exec = nullptr; return fail(IGAMG_ECUDA, std::string("instantiate: ") + cudaGetErrorString(ce)); }
+            c->key = key;
+        }
+    }
+    int cyc = 0;
+    for (cyc = 1; cyc <= max_cycles && result != IGAMG_OK; ++cyc) {
+        if (use_graph) {
+            CUDA_TRY(cudaGraphLaunch(c->exec, s));
+            count_launch(c->exec_launches);
+        } else {
+            restart_body(c, s, w, extrap, kk, prec, d_b, denom);
+        }
+        CUDA_TRY(cudaMemcpyAsync(c->h_pin, w.scal + 1, 8, cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        res = c->h_pin[0];
+        if (h_hist) h_hist[cyc] = res;
+        if (h_cycles) *h_cycles = cyc;
+        if (h_vcycles) *h_vcycles = cyc * (extrap == IGAMG_EXTRAP_NONE ? 1 : kk + 1);
+        if (!std::isfinite(res)) { result = IGAMG_EBREAKDOWN; fail(result, "non-finite residual"); break; }
+        if (res <= tol) result = IGAMG_OK;
+    }
+    CUDA_TRY(cudaMemcpyAsync(d_x, w.S, N * 8, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    CUDA_TRY(cudaGetLastError());
+    if (result == IGAMG_ENOTCONV) fail(result, "max_cycles reached");
+    return result;
+}
+
+igamg_status igamg_apply(igamg_ctx* c, int level, const double* d_x, double* d_y, void* d_ws,
+                         size_t ws_bytes, void* stream) {
+    if (igamg_status st = check_ctx(c)) return st;
+    if (level < 0 || level >= c->L || !d_x || !d_y) return fail(IGAMG_EINVAL, "bad apply arguments");
+    if (igamg_status st = check_ws(c, d_ws, ws_bytes, 1, IGAMG_FP64)) return st;
+    Workspace w = carve(c, d_ws, 1, IGAMG_FP64);
+    cudaStream_t s = (cudaStream_t)stream;
+    LevelBuf<double>& B = w.d[level];
+    dev::xpass<double, double>(s, c->lv64[level], d_x, nullptr, nullptr, 0, nullptr, nullptr, 0, B.TM, B.TK);
+    dev::residual<double, double>(s, c->dim, c->lv64[level], nullptr, B.TM, B.TK, d_y, nullptr);
+    CUDA_TRY(cudaGetLastError());
+    return IGAMG_OK;
+}
+
+igamg_status igamg_smooth(igamg_ctx* c, int level, double* d_x, const double* d_b, int descending,
+                          void* d_ws, size_t ws_bytes, void* stream) {
+    if (igamg_status st = check_ctx(c)) return st;
+    if (level < 0 || level >= c->L || !d_x || !d_b) return fail(IGAMG_EINVAL, "bad smooth arguments");
+    if (igamg_status st = check_ws(c, d_ws, ws_bytes, 1, IGAMG_FP64)) return st;
+    Workspace w = carve(c, d_ws, 1, IGAMG_FP64);
+    cudaStream_t s = (cudaStream_t)stream;
+    LevelBuf<double>& B = w.d[level];
+    dev::xpass<double, double>(s, c->lv64[level], d_x, nullptr, nullptr, 0, nullptr, nullptr, 0, B.TM, B.TK);
+    dev::gs_sweep<double>(s, c->dim, c->lv64[level], descending != 0, d_x, d_b, B.TM, B.TK);
+    CUDA_TRY(cudaGetLastError());
+    return IGAMG_OK;
+}
+
+igamg_status igamg_restrict(igamg_ctx* c, int level, const double* d_fine, double* d_coarse, void* d_ws,
+                            size_t ws_bytes, void* stream) {
+    if (igamg_status st = check_ctx(c)) return st;
+    if (level < 1 || level >= c->L || !d_fine || !d_coarse) return fail(IGAMG_EINVAL, "bad restrict arguments");
+    if (igamg_status st = check_ws(c, d_ws, ws_bytes, 1, IGAMG_FP64)) return st;
+    Workspace w = carve(c, d_ws, 1, IGAMG_FP64);
+    dev::restrict_<double>((cudaStream_t)stream, c->dim, c->tv64[level], d_fine, d_coarse, w.d[level].tmp1,
+                           w.d[level].tmp2);
+    CUDA_TRY(cudaGetLastError());
+    return IGAMG_OK;
+}
+
+igamg_status igamg_prolong(igamg_ctx* c, int level, const double* d_coarse, double* d_fine, void* d_ws,
+                           size_t ws_bytes, void* stream) {
+    if (igamg_status st = check_ctx(c)) return st;
+    if (level < 1 || level >= c->L || !d_fine || !d_coarse) return fail(IGAMG_EINVAL, "bad prolong arguments");
+    if (igamg_status st = check_ws(c, d_ws, ws_bytes, 1, IGAMG_FP64)) return st;
+    Workspace w = carve(c, d_ws, 1, IGAMG_FP64);
+    LevelBuf<double>& B = w.d[level];
+    dev::prolong_add<double>((cudaStream_t)stream, c->dim, c->tv64[level], c->lv64[level], d_coarse, d_fine,
+                             B.TM, B.TK, B.tmp1, B.tmp2);
+    CUDA_TRY(cudaGetLastError());
+    return IGAMG_OK;
+}
+
+igamg_status igamg_coarse_solve(igamg_ctx* c, const double* d_r, double* d_e, void* stream) {
+    if (igamg_status st = check_ctx(c)) return st;
+    if (!d_r || !d_e) return fail(IGAMG_EINVAL, "null vector");
+    dev::coarse_solve<double>((cudaStream_t)stream, c->dim, c->cv64, d_r, d_e);
+    CUDA_TRY(cudaGetLastError());
+    return IGAMG_OK;
+}
+
+igamg_status igamg_vcycle(igamg_ctx* c, double* d_x, const double* d_b, int prec, void* d_ws, size_t ws_bytes,
+                          void* stream) {
+    if (igamg_status st = check_ctx(c)) return st;
+    if (!d_x || !d_b || prec < 0 || prec > 1) return fail(IGAMG_EINVAL, "bad vcycle arguments");
+    if (igamg_status st = check_ws(c, d_ws, ws_bytes, 1, prec)) return st;
+    Workspace w = carve(c, d_ws, 1, prec);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int top = c->L - 1;
+    dev::xpass<double, double>(s, c->lv64[top], d_x, nullptr, nullptr, 0, nullptr, nullptr, 0, w.d[top].TM,
+                               w.d[top].TK);
+    fixed_point_step(c, s, w, prec, d_b, d_x, d_x);
+    CUDA_TRY(cudaGetLastError());
+    return IGAMG_OK;
+}
+
+size_t igamg_extrap_workspace_bytes(long n, int q) {
+    if (n <= 0 || q < 1 || q > kMaxQ) return 0;
+    const size_t np = (size_t)(q + 1) * (q + 2) / 2;
+    return ((size_t)dev::gram_blocks((size_t)n) * np * 8 + 255) / 256 * 256 + 512 +
+           (sizeof(ExtrapInfo) + 255) / 256 * 256;
+}
+
+igamg_status igamg_extrapolate(long n, int q, int method, const double* d_S, long ld, double* d_t,
+                               double* h_gamma, int* h_qused, void* d_ws, size_t ws_bytes, void* stream) {
+    if (n <= 0 || q < 1 || q > kMaxQ || (method != IGAMG_RRE && method != IGAMG_MPE) || !d_S || !d_t || ld < n)
+        return fail(IGAMG_EINVAL, "bad extrapolation arguments");
+    if (!d_ws || ws_bytes < igamg_extrap_workspace_bytes(n, q) || ((uintptr_t)d_ws & 255))
+        return fail(IGAMG_EINVAL, "workspace missing, unaligned or too small");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nb = dev::gram_blocks((size_t)n);
+    const size_t np = (size_t)(q + 1) * (q + 2) / 2;
+    double* partial = (double*)d_ws;
+    char* tail = (char*)d_ws + ((size_t)nb * np * 8 + 255) / 256 * 256;
+    double* gamma = (double*)tail;
+    int* qused = (int*)(tail + 256);
+    ExtrapInfo* info = (ExtrapInfo*)(tail + 512);
+    dev::extrap_gammas(s, q, method, d_S, (size_t)ld, (size_t)n, partial, nb, info, gamma, qused);
+    dev::combine(s, q, gamma, d_S, (size_t)ld, (size_t)n, d_t);
+    double hg[kMaxQ + 2];
+    int hq = 0;
+    CUDA_TRY(cudaMemcpyAsync(hg, gamma, (q + 2) * 8, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(&hq, qused, 4, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    CUDA_TRY(cudaGetLastError());
+    if (h_gamma) std::memcpy(h_gamma, hg, (q + 2) * 8);
+    if (h_qused) *h_qused = hq;
+    return IGAMG_OK;
+}
+
+void igamg_destroy(igamg_ctx* c) {
+    if (!c) return;
+    if (c->exec) cudaGraphExecDestroy(c->exec);
+    if (c->cap) cudaStreamDestroy(c->cap);
+    if (c->h_pin) cudaFreeHost(c->h_pin);
+    if (c->dmem) cudaFree(c->dmem);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,118 @@
+// Device-side views and kernel launch wrappers (internal; not part of the C ABI).
+#pragma once
+#include <cstddef>
+#include <cuda_runtime.h>
+
+namespace igamg {
+
+constexpr int kMaxP = 7;
+constexpr int kMaxQ = 12;                 // largest restart number k
+
+// One grid level as the kernels see it.  Grid vectors are rows of length m[0]
+// (x fastest); rows are indexed j + m[1] k.  Bands are stored band-major:
+// Mb[d][b * m[d] + i] = M_d(i, i + b - p), zero outside the matrix.
+template <typename T>
+struct LevelView {
+    int m[3];
+    int p;
+    const T* Mb[3];
+    const T* Kb[3];
+    const T* invdiag;                     // 1 / A_ii
+    size_t n() const { return (size_t)m[0] * m[1] * m[2]; }
+    int rows() const { return m[1] * m[2]; }
+};
+
+// 1D transfer between a fine level and the next coarser one, direction d.
+// Row form of P (prolongation): fine i -> coarse [plo[i], plo[i] + pw).
+// Column form (restriction R = P^T): coarse I -> fine [rlo[I], rlo[I] + rw).
+template <typename T>
+struct TransferView {
+    int mf[3], mc[3];
+    int pw[3], rw[3];
+    const int* plo[3];
+    const T* pv[3];
+    const int* rlo[3];
+    const T* rv[3];
+};
+
+// Coarsest-grid fast diagonalisation: A_0^{-1} = V diag(laminv) V^T with
+// V = V_z (x) V_y (x) V_x; V[d] is m x m row-major (column I = eigenvector I).
+template <typename T>
+struct CoarseView {
+    int m[3];
+    const T* V[3];
+    const T* laminv;                      // 1 / (lam_x + lam_y (+ lam_z)), x fastest
+};
+
+// Device-side state of one extrapolation (CholeskyQR2 pass-1 results).
+struct ExtrapInfo {
+    int done, a, dep, pad;
+    double D[kMaxQ + 1];
+    double R1h[(kMaxQ + 1) * (kMaxQ + 1)];
+    double R1p[(kMaxQ + 1) * (kMaxQ + 1)];
+    double R1pinv[kMaxQ + 1];
+};
+
+// Launch accounting (kernels enqueued by this thread).
+void count_launch(long long n = 1);
+long long launch_count();
+
+namespace dev {
+
+// T_M = (I (x) M_x) x, T_K = (I (x) K_x) x row by row.  With add != nullptr the
+// row is first replaced by x + add (written to x_out), with nS > 0 by
+// sum_j gamma[j] S_j (written to x_out).
+template <typename T, typename A>
+void xpass(cudaStream_t s, const LevelView<T>& L, const T* x, T* x_out, const A* add,
+           int nS, const double* gamma, const T* S, size_t ldS, T* TM, T* TK);
+
+// One multicolour Gauss-Seidel sweep (all (p+1)^dim colours) in row phases.
+template <typename T>
+void gs_sweep(cudaStream_t s, int dim, const LevelView<T>& L, bool descending, T* x,
+              const T* b, T* TM, T* TK);
+
+// r = b - A x from the row partial sums; optional per-row partial ||r||^2.
+template <typename T, typename R>
+void residual(cudaStream_t s, int dim, const LevelView<T>& L, const T* b, const T* TM,
+              const T* TK, R* r, double* partial);
+
+// coarse = P^T fine (tmp holds the intermediate axis passes).
+template <typename T>
+void restrict_(cudaStream_t s, int dim, const TransferView<T>& P, const T* fine, T* coarse,
+               T* tmp1, T* tmp2);
+
+// x += P e, then refresh the row partial sums of x.
+template <typename T>
+void prolong_add(cudaStream_t s, int dim, const TransferView<T>& P, const LevelView<T>& Lf,
+                 const T* e, T* x, T* TM, T* TK, T* tmp1, T* tmp2);
+
+// e = A_0^{-1} r on the coarsest grid.
+template <typename T>
+void coarse_solve(cudaStream_t s, int dim, const CoarseView<T>& C, const T* r, T* e);
+
+// Partial sums of squares of v (deterministic): nblocks partials.
+void sumsq_partial(cudaStream_t s, const double* v, size_t n, double* partial, int nblocks);
+// out[slot] = sqrt(sum partial) / (*denom), and non-finite flag.
+void norm_final(cudaStream_t s, const double* partial, int nparts, const double* denom,
+                double* out, int slot);
+
+// RRE / MPE on S_0..S_{q+1} (stride ld): the gammas (q+2 entries) and
+// q_used on the device, via two Gram passes (CholeskyQR2).
+int gram_blocks(size_t n);
+void gram_partial(cudaStream_t s, int q, const double* S, size_t ld, size_t n, double* partial,
+                  int nblocks);
+void extrap_gammas(cudaStream_t s, int q, int method, const double* S, size_t ld, size_t n,
+                   double* partial, int nblocks, ExtrapInfo* info, double* gamma, int* qused);
+// t = sum_{j=0}^{q+1} gamma_j S_j (elementwise).
+void combine(cudaStream_t s, int q, const double* gamma, const double* S, size_t ld, size_t n,
+             double* t);
+
+// b = sum_k H[k](outer directions) ... : load vector from separable sine moments.
+void rhs_sine(cudaStream_t s, int dim, const int* m, int modes, const double* gx_H,
+              const double* gy, const double* gz, double* b);
+
+template <typename T>
+void fill_zero(cudaStream_t s, T* p, size_t n);
+
+}  // namespace dev
+}  // namespace igamg

@@ -1,0 +1,893 @@
+// CUDA kernels of the extrapolated multigrid solver (sm_103a).
+//
+// Precision: every kernel is templated on the working type T (double for the
+// FP64 path, float inside the FP32 V-cycles of iterative refinement).  On
+// GB300 the FP64 pipe delivers about 1/58 of the FP32 rate, so the FP64
+// kernels are bound by FP64 instruction count: the layouts below are chosen to
+// minimise FP64 arithmetic (row partial sums are kept, not recomputed).
+//
+// Operator (Sec. 2, Eq. (2)): A = sum_d K_d (x) prod_{e!=d} M_e on interior
+// unknowns, x fastest.  Writing T_M = (I (x) M_x) x and T_K = (I (x) K_x) x
+// ("row partial sums", one x-direction contraction per row), the product
+// splits into row couplings:
+//   2D: (A x)_row = sum_{dj} Ky(j, j+dj) T_M(row+dj) + My(j, j+dj) T_K(row+dj)
+//   3D: coefficients Kz My + Mz Ky on T_M and Mz My on T_K, over (dj, dk).
+#include "device.hpp"
+
+#include <cstdio>
+
+namespace igamg {
+
+namespace {
+thread_local long long g_launches = 0;
+}
+void count_launch(long long n) { g_launches += n; }
+long long launch_count() { return g_launches; }
+
+namespace dev {
+
+constexpr int kThreads = 256;
+constexpr int kMaxNb = (2 * kMaxP + 1) * (2 * kMaxP + 1);
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum (deterministic order); result valid in thread 0.
+template <typename T>
+__device__ T block_sum(T v, T* red) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    T s = 0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x + 31) / 32; ++i) s += red[i];
+    __syncthreads();
+    return s;
+}
+
+// Row-coupling coefficients of row (j, k): for neighbour q = (dj, dk) the
+// weights on T_M and T_K, and the neighbour's row index (-1 outside).
+template <typename T, int DIM>
+__device__ void row_couplings(const LevelView<T>& L, int j, int k, T* cM, T* cK, int* nrow) {
+    const int p = L.p, w = 2 * p + 1, my = L.m[1], mz = L.m[2];
+    const int nnb = (DIM == 3) ? w * w : w;
+    for (int q = threadIdx.x; q < nnb; q += blockDim.x) {
+        const int dj = (q % w) - p, dk = (DIM == 3) ? (q / w) - p : 0;
+        const int jj = j + dj, kk = k + dk;
+        const bool ok = jj >= 0 && jj < my && kk >= 0 && kk < mz;
+        T a = 0, c = 0;
+        if (ok) {
+            const T myv = L.Mb[1][(dj + p) * my + j], kyv = L.Kb[1][(dj + p) * my + j];
+            if (DIM == 2) {
+                a = kyv;
+                c = myv;
+            } else {
+                const T mzv = L.Mb[2][(dk + p) * mz + k], kzv = L.Kb[2][(dk + p) * mz + k];
+                a = kzv * myv + mzv * kyv;
+                c = mzv * myv;
+            }
+        }
+        cM[q] = a;
+        cK[q] = c;
+        nrow[q] = ok ? (kk * my + jj) : -1;
+    }
+}
+
+// ---------------------------------------------------------------- x-pass
+// One CTA per row.  Source row: x, or x + add (iterative-refinement update),
+// or sum_j gamma_j S_j (extrapolated combination); written to x_out when it
+// differs from x.  Then T_M, T_K of the row.
+template <typename T, typename A>
+__global__ void __launch_bounds__(kThreads) k_xpass(LevelView<T> L, const T* __restrict__ x,
+                                                     T* __restrict__ x_out, const A* __restrict__ add,
+                                                     int nS, const double* __restrict__ gamma,
+                                                     const T* __restrict__ S, size_t ldS,
+                                                     T* __restrict__ TM, T* __restrict__ TK) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* xs = reinterpret_cast<T*>(smem_raw);
+    const int mx = L.m[0], p = L.p;
+    const size_t base = (size_t)blockIdx.x * mx;
+    __shared__ double g[kMaxQ + 2];
+    if (nS > 0) {
+        for (int j = threadIdx.x; j < nS; j += blockDim.x) g[j] = gamma[j];
+        __syncthreads();
+    }
+    for (int ii = threadIdx.x; ii < mx + 2 * p; ii += blockDim.x) {
+        const int i = ii - p;
+        T v = 0;
+        if (i >= 0 && i < mx) {
+            if (nS > 0) {
+                double s = 0.0;
+                for (int j = 0; j < nS; ++j)
+                    if (g[j] != 0.0) s += g[j] * (double)S[(size_t)j * ldS + base + i];
+                v = (T)s;
+                x_out[base + i] = v;
+            } else if (add != nullptr) {
+                v = x[base + i] + (T)add[base + i];
+                x_out[base + i] = v;
+            } else {
+                v = x[base + i];
+            }
+        }
+        xs[ii] = v;
+    }
+    __syncthreads();
+    const T* Mx = L.Mb[0];
+    const T* Kx = L.Kb[0];
+    for (int i = threadIdx.x; i < mx; i += blockDim.x) {
+        T am = 0, ak = 0;
+        for (int b = 0; b <= 2 * p; ++b) {
+            const T xv = xs[i + b];
+            am += Mx[b * mx + i] * xv;
+            ak += Kx[b * mx + i] * xv;
+        }
+        TM[base + i] = am;
+        TK[base + i] = ak;
+    }
+}
+
+// ---------------------------------------------------------------- GS phase
+// Multicolour Gauss-Seidel, colour c = cx + (p+1) cy (+ (p+1)^2 cz).  For a
+// fixed (cy, cz) the rows j = cy mod (p+1) (k = cz mod (p+1)) are updated; no
+// two of them couple, and within a row the colours cx = 0..p form a 1D
+// multicolour sweep with the frozen off-row part F = sum_{row' != row}
+// (cM T_M + cK T_K).  The row's own T_M, T_K are updated incrementally from
+// the corrections of each colour, so a full sweep costs about one apply.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads) k_gs_phase(LevelView<T> L, int cy, int cz, int descending,
+                                                        T* __restrict__ x, const T* __restrict__ b,
+                                                        T* __restrict__ TM, T* __restrict__ TK) {
+    const int mx = L.m[0], my = L.m[1], p = L.p, P1 = p + 1;
+    const int nty = (my - cy + p) / P1;
+    const int j = cy + P1 * (blockIdx.x % nty);
+    const int k = (DIM == 3) ? cz + P1 * (blockIdx.x / nty) : 0;
+    const size_t base = ((size_t)k * my + j) * mx;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* rhs = reinterpret_cast<T*>(smem_raw);
+    T* tm = rhs + mx;
+    T* tk = tm + mx;
+    T* dl = tk + mx;
+    T* xs = dl + mx;
+    __shared__ T cM[kMaxNb], cK[kMaxNb];
+    __shared__ int nrow[kMaxNb];
+    row_couplings<T, DIM>(L, j, k, cM, cK, nrow);
+    __syncthreads();
+    const int w = 2 * p + 1, nnb = (DIM == 3) ? w * w : w;
+    const int own = (DIM == 3) ? p * w + p : p;
+    for (int i = threadIdx.x; i < mx; i += blockDim.x) {
+        T acc = b[base + i];
+        for (int q = 0; q < nnb; ++q) {
+            const int r = nrow[q];
+            if (q == own || r < 0) continue;
+            const size_t o = (size_t)r * mx + i;
+            acc -= cM[q] * TM[o] + cK[q] * TK[o];
+        }
+        rhs[i] = acc;
+        tm[i] = TM[base + i];
+        tk[i] = TK[base + i];
+        xs[i] = x[base + i];
+    }
+    __syncthreads();
+    const T am = cM[own], ak = cK[own];
+    const T* Mx = L.Mb[0];
+    const T* Kx = L.Kb[0];
+    const T* dinv = L.invdiag + base;
+    for (int c = 0; c < P1; ++c) {
+        const int cx = descending ? p - c : c;
+        for (int i = cx + P1 * (int)threadIdx.x; i < mx; i += P1 * (int)blockDim.x) {
+            const T d = (rhs[i] - (am * tm[i] + ak * tk[i])) * dinv[i];
+            xs[i] += d;
+            dl[i] = d;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < mx; i += blockDim.x) {
+            int r = (cx - i) % P1;
+            if (r < 0) r += P1;
+            T sm = 0, sk = 0;
+            const int i1 = i + r;                       // same-colour node at offset r
+            if (i1 < mx) {
+                sm += Mx[(r + p) * mx + i] * dl[i1];
+                sk += Kx[(r + p) * mx + i] * dl[i1];
+            }
+            if (r >= 1) {                               // and at offset r - (p+1)
+                const int o = r - P1, i2 = i + o;
+                if (i2 >= 0) {
+                    sm += Mx[(o + p) * mx + i] * dl[i2];
+                    sk += Kx[(o + p) * mx + i] * dl[i2];
+                }
+            }
+            tm[i] += sm;
+            tk[i] += sk;
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < mx; i += blockDim.x) {
+        x[base + i] = xs[i];
+        TM[base + i] = tm[i];
+        TK[base + i] = tk[i];
+    }
+}
+
+// ---------------------------------------------------------------- residual
+// r = b - A x (or -A x without b; negate flips the sign) from T_M, T_K.
+template <typename T, typename R, int DIM>
+__global__ void __launch_bounds__(kThreads) k_residual(LevelView<T> L, const T* __restrict__ b,
+                                                        const T* __restrict__ TM, const T* __restrict__ TK,
+                                                        R* __restrict__ r, int negate,
+                                                        double* __restrict__ partial) {
+    const int mx = L.m[0], my = L.m[1];
+    const int row = blockIdx.x, j = row % my, k = row / my;
+    const size_t base = (size_t)row * mx;
+    __shared__ T cM[kMaxNb], cK[kMaxNb];
+    __shared__ int nrow[kMaxNb];
+    __shared__ double red[kThreads / 32];
+    row_couplings<T, DIM>(L, j, k, cM, cK, nrow);
+    __syncthreads();
+    const int w = 2 * L.p + 1, nnb = (DIM == 3) ? w * w : w;
+    double ss = 0.0;
+    for (int i = threadIdx.x; i < mx; i += blockDim.x) {
+        T acc = b ? b[base + i] : (T)0;
+        for (int q = 0; q < nnb; ++q) {
+            const int rr = nrow[q];
+            if (rr < 0) continue;
+            const size_t o = (size_t)rr * mx + i;
+            acc -= cM[q] * TM[o] + cK[q] * TK[o];
+        }
+        if (negate) acc = -acc;
+        r[base + i] = (R)acc;
+        ss += (double)acc * (double)acc;
+    }
+    if (partial) {
+        const double s = block_sum(ss, red);
+        if (threadIdx.x == 0) partial[row] = s;
+    }
+}
+
+// ---------------------------------------------------------------- transfer
+// out (dims d0 x d1 x d2, x fastest) along `axis`: out[.., I, ..] =
+// sum_s val[I*width + s] in[.., lo[I] + s, ..], in having n_in along axis.
+template <typename T>
+__global__ void k_transfer_axis(const T* __restrict__ in, T* __restrict__ out, int d0, int d1, int d2,
+                                int axis, int n_in, const int* __restrict__ lo,
+                                const T* __restrict__ val, int width) {
+    const size_t total = (size_t)d0 * d1 * d2;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int i0 = (int)(idx % d0);
+        const size_t t = idx / d0;
+        const int i1 = (int)(t % d1), i2 = (int)(t / d1);
+        const int I = axis == 0 ? i0 : (axis == 1 ? i1 : i2);
+        const int l = lo[I];
+        T acc = 0;
+        for (int s = 0; s < width; ++s) {
+            const int f = l + s;
+            if (f < 0 || f >= n_in) continue;
+            size_t src;
+            if (axis == 0) src = ((size_t)i2 * d1 + i1) * n_in + f;
+            else if (axis == 1) src = ((size_t)i2 * n_in + f) * d0 + i0;
+            else src = ((size_t)f * d1 + i1) * d0 + i0;
+            acc += val[(size_t)I * width + s] * in[src];
+        }
+        out[idx] = acc;
+    }
+}
+
+// Last prolongation axis fused with the correction x += P e and the x-pass:
+// one CTA per fine row; tmp holds the correction with the last axis coarse.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads) k_prolong_last(LevelView<T> L, const T* __restrict__ tmp,
+                                                            int n_in, const int* __restrict__ lo,
+                                                            const T* __restrict__ val, int width,
+                                                            T* __restrict__ x, T* __restrict__ TM,
+                                                            T* __restrict__ TK) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* xs = reinterpret_cast<T*>(smem_raw);
+    const int mx = L.m[0], my = L.m[1], p = L.p;
+    const int row = blockIdx.x, j = row % my, k = row / my;
+    const int I = (DIM == 2) ? j : k;
+    const size_t base = (size_t)row * mx;
+    const int l = lo[I];
+    for (int ii = threadIdx.x; ii < mx + 2 * p; ii += blockDim.x) {
+        const int i = ii - p;
+        T v = 0;
+        if (i >= 0 && i < mx) {
+            T cor = 0;
+            for (int s = 0; s < width; ++s) {
+                const int f = l + s;
+                if (f < 0 || f >= n_in) continue;
+                const size_t src = (DIM == 2) ? (size_t)f * mx + i : ((size_t)f * my + j) * mx + i;
+                cor += val[(size_t)I * width + s] * tmp[src];
+            }
+            v = x[base + i] + cor;
+            x[base + i] = v;
+        }
+        xs[ii] = v;
+    }
+    __syncthreads();
+    const T* Mx = L.Mb[0];
+    const T* Kx = L.Kb[0];
+    for (int i = threadIdx.x; i < mx; i += blockDim.x) {
+        T am = 0, ak = 0;
+        for (int b = 0; b <= 2 * p; ++b) {
+            const T xv = xs[i + b];
+            am += Mx[b * mx + i] * xv;
+            ak += Kx[b * mx + i] * xv;
+        }
+        TM[base + i] = am;
+        TK[base + i] = ak;
+    }
+}
+
+// ---------------------------------------------------------------- coarse solve
+// Fast diagonalisation in one CTA: e = V diag(laminv) V^T r, V = (x) V_d.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads) k_coarse_fd(CoarseView<T> C, const T* __restrict__ r,
+                                                         T* __restrict__ e) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int m0 = C.m[0], m1 = C.m[1], m2 = (DIM == 3) ? C.m[2] : 1;
+    const int N = m0 * m1 * m2;
+    T* a = reinterpret_cast<T*>(smem_raw);
+    T* bb = a + N;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) a[i] = r[i];
+    __syncthreads();
+    auto pass = [&](const T* in, T* out, int axis, bool transpose) {
+        const int md = C.m[axis];
+        const T* V = C.V[axis];
+        for (int idx = threadIdx.x; idx < N; idx += blockDim.x) {
+            const int i0 = idx % m0, t = idx / m0, i1 = t % m1, i2 = t / m1;
+            const int I = axis == 0 ? i0 : (axis == 1 ? i1 : i2);
+            const int stride = axis == 0 ? 1 : (axis == 1 ? m0 : m0 * m1);
+            const int base = idx - I * stride;
+            T acc = 0;
+            for (int s = 0; s < md; ++s)
+                acc += (transpose ? V[s * md + I] : V[I * md + s]) * in[base + s * stride];
+            out[idx] = acc;
+        }
+        __syncthreads();
+    };
+    T* cur = a;
+    T* nxt = bb;
+    for (int d = 0; d < DIM; ++d) {                 // V^T r
+        pass(cur, nxt, d, true);
+        T* t = cur; cur = nxt; nxt = t;
+    }
+    for (int i = threadIdx.x; i < N; i += blockDim.x) cur[i] *= C.laminv[i];
+    __syncthreads();
+    for (int d = DIM - 1; d >= 0; --d) {            // V (...)
+        pass(cur, nxt, d, false);
+        T* t = cur; cur = nxt; nxt = t;
+    }
+    for (int i = threadIdx.x; i < N; i += blockDim.x) e[i] = cur[i];
+}
+
+// ---------------------------------------------------------------- norms
+__global__ void __launch_bounds__(kThreads) k_sumsq(const double* __restrict__ v, size_t n,
+                                                     double* __restrict__ partial) {
+    __shared__ double red[kThreads / 32];
+    double s = 0.0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        s += v[i] * v[i];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(1024) k_norm_final(const double* __restrict__ partial, int nparts,
+                                                      const double* __restrict__ denom,
+                                                      double* __restrict__ out, int slot) {
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += partial[i];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) {
+        double v = sqrt(s);
+        if (denom) v = v / *denom;
+        out[slot] = v;
+    }
+}
+
+// ---------------------------------------------------------------- extrapolation
+// Gram partials of Delta s_a = s_{a+1} - s_a (a = 0..Q), upper triangle.
+template <int Q>
+__global__ void __launch_bounds__(kThreads) k_gram_partial(const double* __restrict__ S, size_t ld,
+                                                            size_t n, double* __restrict__ partial) {
+    constexpr int NP = (Q + 1) * (Q + 2) / 2;
+    double acc[NP];
+#pragma unroll
+    for (int c = 0; c < NP; ++c) acc[c] = 0.0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        double s[Q + 2];
+#pragma unroll
+        for (int j = 0; j < Q + 2; ++j) s[j] = S[(size_t)j * ld + i];
+        double d[Q + 1];
+#pragma unroll
+        for (int j = 0; j <= Q; ++j) d[j] = s[j + 1] - s[j];
+        int c = 0;
+#pragma unroll
+        for (int a = 0; a <= Q; ++a)
+#pragma unroll
+            for (int bb = a; bb <= Q; ++bb) acc[c++] += d[a] * d[bb];
+    }
+    __shared__ double red[kThreads / 32][NP];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < NP; ++c) {
+        const double v = warp_sum(acc[c]);
+        if (lane == 0) red[w][c] = v;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < NP; c += blockDim.x) {
+        double s = 0.0;
+        for (int ww = 0; ww < (int)blockDim.x / 32; ++ww) s += red[ww][c];
+        partial[(size_t)blockIdx.x * NP + c] = s;
+    }
+}
+
+// Extrapolation coefficients by CholeskyQR2 (Fukaya et al., 2014) on the
+// difference matrix Delta S = [Delta s_0 .. Delta s_q]: the R of Algorithms 3-4
+// is obtained from two Gram passes instead of a Householder QR.
+//   pass 1: G = Delta S^T Delta S; D = sqrt(diag G); Cholesky of the
+//           equilibrated G^ = D^-1 G D^-1 = R1^T R1, stopping at the first
+//           column whose pivot is below tol^2 (column dependent on the
+//           previous ones: the Krylov space is exhausted, q' = that column).
+//   pass 2: W = Delta S_a (R1 D)^-1 for the a leading independent columns,
+//           plus the raw dependent column if any; G2 = Z^T Z = R2^T R2;
+//           R^ = R2 R1 (the column-normalised R of Delta S), and for the
+//           dependent column r = R2^-T (W^T Delta s_dep) / D_dep.
+// Then RRE: R^T R d = e; MPE or a dependent column: R_q d = -r_q, d_q = 1;
+// gamma = d / sum d (with the lambda guard).
+__device__ void reduce_gram(int nz, const double* __restrict__ partial, int nblocks, int np, double* G) {
+    for (int c = threadIdx.x; c < nz * (nz + 1) / 2; c += blockDim.x) {
+        int a = 0, cc = c;
+        while (cc >= nz - a) { cc -= nz - a; ++a; }
+        const int bcol = a + cc;
+        // the partial layout uses the pass's full triangle of size np (q+1 columns)
+        int idx = 0;
+        for (int r = 0; r < a; ++r) idx += (np - r);
+        idx += bcol - a;
+        double s = 0.0;
+        for (int blk = 0; blk < nblocks; ++blk) s += partial[(size_t)blk * (np * (np + 1) / 2) + idx];
+        G[a * nz + bcol] = s;
+        G[bcol * nz + a] = s;
+    }
+}
+
+__device__ void set_fallback(int q, double* gamma, int* qused) {
+    for (int i = 0; i < q + 2; ++i) gamma[i] = 0.0;
+    gamma[q + 1] = 1.0;                                     // the last iterate
+    *qused = -1;
+}
+
+__global__ void __launch_bounds__(kThreads) k_chol1(int q, const double* __restrict__ partial, int nblocks,
+                                                     ExtrapInfo* __restrict__ info, double* __restrict__ gamma,
+                                                     int* __restrict__ qused) {
+    const int n = q + 1;
+    __shared__ double G[(kMaxQ + 1) * (kMaxQ + 1)];
+    reduce_gram(n, partial, nblocks, n, G);
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const double tol2 = 1e-12;                              // (1e-6)^2 on the normalised diagonal
+    double* D = info->D;
+    double* R = info->R1h;
+    for (int i = 0; i < q + 2; ++i) gamma[i] = 0.0;
+    for (int i = 0; i < n; ++i) D[i] = sqrt(G[i * n + i]);
+    info->done = 1;
+    if (!(D[0] > 0.0)) {                                    // Delta s_0 = 0: s_0 is a fixed point
+        gamma[0] = 1.0;
+        *qused = 0;
+        return;
+    }
+    int dep = n;
+    for (int jc = 0; jc < n && dep == n; ++jc) {
+        for (int i = 0; i < jc; ++i) {
+            double s = (D[jc] > 0.0) ? G[i * n + jc] / (D[i] * D[jc]) : 0.0;
+            for (int kk = 0; kk < i; ++kk) s -= R[kk * n + i] * R[kk * n + jc];
+            R[i * n + jc] = s / R[i * n + i];
+        }
+        double piv = (D[jc] > 0.0) ? 1.0 : 0.0;
+        for (int kk = 0; kk < jc; ++kk) piv -= R[kk * n + jc] * R[kk * n + jc];
+        if (jc >= 1 && (!(D[jc] > 0.0) || piv < tol2)) dep = jc;
+        else R[jc * n + jc] = sqrt(piv);
+    }
+    if (dep < n && !(D[dep] > 0.0)) {                       // zero difference: s_dep is a fixed point
+        gamma[dep] = 1.0;
+        *qused = dep;
+        return;
+    }
+    const int a = dep < n ? dep : n;
+    for (int i = 0; i < a; ++i)
+        for (int j = i; j < a; ++j) info->R1p[i * n + j] = R[i * n + j] * D[j];
+    for (int j = 0; j < a; ++j) info->R1pinv[j] = 1.0 / info->R1p[j * n + j];
+    info->a = a;
+    info->dep = dep;
+    info->done = 0;
+}
+
+// Pass 2: Gram of Z = [Delta S_a (R1 D)^-1, Delta s_dep] formed element by element.
+template <int Q>
+__global__ void __launch_bounds__(kThreads) k_gram2_partial(const double* __restrict__ S, size_t ld, size_t n,
+                                                             const ExtrapInfo* __restrict__ info,
+                                                             double* __restrict__ partial) {
+    constexpr int NC = Q + 1, NP = NC * (NC + 1) / 2;
+    if (info->done) return;
+    __shared__ double Rp[NC * NC], Rinv[NC];
+    const int a = info->a, dep = info->dep;
+    for (int i = threadIdx.x; i < NC * NC; i += blockDim.x) Rp[i] = info->R1p[i];
+    for (int i = threadIdx.x; i < NC; i += blockDim.x) Rinv[i] = info->R1pinv[i];
+    __syncthreads();
+    double acc[NP];
+#pragma unroll
+    for (int c = 0; c < NP; ++c) acc[c] = 0.0;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        double s[Q + 2];
+#pragma unroll
+        for (int j = 0; j < Q + 2; ++j) s[j] = S[(size_t)j * ld + e];
+        double z[NC];
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+            const double dj = s[j + 1] - s[j];
+            double v = dj;
+#pragma unroll
+            for (int i = 0; i < j; ++i) v -= z[i] * Rp[i * NC + j];
+            z[j] = (j < a) ? v * Rinv[j] : (j == dep ? dj : 0.0);
+        }
+        int c = 0;
+#pragma unroll
+        for (int i = 0; i < NC; ++i)
+#pragma unroll
+            for (int j = i; j < NC; ++j) acc[c++] += z[i] * z[j];
+    }
+    __shared__ double red[kThreads / 32][NP];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < NP; ++c) {
+        const double v = warp_sum(acc[c]);
+        if (lane == 0) red[w][c] = v;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < NP; c += blockDim.x) {
+        double t = 0.0;
+        for (int ww = 0; ww < (int)blockDim.x / 32; ++ww) t += red[ww][c];
+        partial[(size_t)blockIdx.x * NP + c] = t;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_gamma2(int q, int method, const double* __restrict__ partial,
+                                                      int nblocks, const ExtrapInfo* __restrict__ info,
+                                                      double* __restrict__ gamma, int* __restrict__ qused) {
+    if (info->done) return;
+    const int n = q + 1;
+    const int a = info->a, dep = info->dep, nz = a + (dep < n ? 1 : 0);
+    __shared__ double G2[(kMaxQ + 1) * (kMaxQ + 1)];
+    reduce_gram(nz, partial, nblocks, n, G2);
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const double* D = info->D;
+    const double* R1 = info->R1h;
+    double R2[(kMaxQ + 1) * (kMaxQ + 1)], Rh[(kMaxQ + 1) * (kMaxQ + 1)], d[kMaxQ + 2], y[kMaxQ + 1];
+    for (int i = 0; i < q + 2; ++i) gamma[i] = 0.0;
+    // R2 = chol(G2[0:a, 0:a]) (upper, R2^T R2 = G2)
+    for (int j = 0; j < a; ++j) {
+        for (int i = 0; i < j; ++i) {
+            double s = G2[i * nz + j];
+            for (int kk = 0; kk < i; ++kk) s -= R2[kk * n + i] * R2[kk * n + j];
+            R2[i * n + j] = s / R2[i * n + i];
+        }
+        double piv = G2[j * nz + j];
+        for (int kk = 0; kk < j; ++kk) piv -= R2[kk * n + j] * R2[kk * n + j];
+        if (!(piv > 0.0)) { set_fallback(q, gamma, qused); return; }
+        R2[j * n + j] = sqrt(piv);
+    }
+    // R^ = R2 R1 (upper triangular product, a x a)
+    for (int i = 0; i < a; ++i)
+        for (int j = i; j < a; ++j) {
+            double s = 0.0;
+            for (int kk = i; kk <= j; ++kk) s += R2[i * n + kk] * R1[kk * n + j];
+            Rh[i * n + j] = s;
+        }
+    int qq;
+    if (dep < n || method == 2) {
+        double r[kMaxQ + 1];
+        int na;
+        if (dep < n) {                                      // r = R2^-T (W^T Delta s_dep) / D_dep
+            qq = dep;
+            na = a;
+            for (int i = 0; i < a; ++i) {
+                double s = G2[i * nz + a];
+                for (int kk = 0; kk < i; ++kk) s -= R2[kk * n + i] * r[kk];
+                r[i] = s / R2[i * n + i];
+            }
+            for (int i = 0; i < a; ++i) r[i] /= D[dep];
+        } else {                                            // MPE: r_q = R^[0:q, q]
+            qq = q;
+            na = q;
+            for (int i = 0; i < q; ++i) r[i] = Rh[i * n + q];
+        }
+        for (int i = na - 1; i >= 0; --i) {                 // R^_qq y = -r
+            double s = -r[i];
+            for (int kk = i + 1; kk < na; ++kk) s -= Rh[i * n + kk] * y[kk];
+            y[i] = s / Rh[i * n + i];
+        }
+        for (int i = 0; i < na; ++i) d[i] = y[i] / D[i];
+        d[qq] = 1.0 / D[qq];
+    } else {                                                // RRE: R^T R^ z = D^-1 e, d = z / D
+        qq = q;
+        double z[kMaxQ + 1];
+        for (int i = 0; i < n; ++i) {
+            double s = 1.0 / D[i];
+            for (int kk = 0; kk < i; ++kk) s -= Rh[kk * n + i] * z[kk];
+            z[i] = s / Rh[i * n + i];
+        }
+        for (int i = n - 1; i >= 0; --i) {
+            double s = z[i];
+            for (int kk = i + 1; kk < n; ++kk) s -= Rh[i * n + kk] * z[kk];
+            z[i] = s / Rh[i * n + i];
+        }
+        for (int i = 0; i < n; ++i) d[i] = z[i] / D[i];
+    }
+    double lam = 0.0, asum = 0.0;
+    for (int i = 0; i <= qq; ++i) { lam += d[i]; asum += fabs(d[i]); }
+    bool ok = isfinite(lam) && fabs(lam) > 1e-12 * asum;
+    for (int i = 0; i <= qq && ok; ++i) {
+        gamma[i] = d[i] / lam;
+        ok = isfinite(gamma[i]);
+    }
+    if (!ok) { set_fallback(q, gamma, qused); return; }
+    *qused = qq;
+}
+
+__global__ void k_combine(int nS, const double* __restrict__ gamma, const double* __restrict__ S,
+                          size_t ld, size_t n, double* __restrict__ t) {
+    __shared__ double g[kMaxQ + 2];
+    for (int j = threadIdx.x; j < nS; j += blockDim.x) g[j] = gamma[j];
+    __syncthreads();
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int j = 0; j < nS; ++j)
+            if (g[j] != 0.0) s += g[j] * S[(size_t)j * ld + i];
+        t[i] = s;
+    }
+}
+
+// ---------------------------------------------------------------- load vector
+// b[k][j][i] = sum_{kz} gz[kz][k] sum_{ky} gy[ky][j] H[kz][ky][i] (2D: no kz),
+// H = sum_kx c gx precomputed on the host (separable per sine mode).
+__global__ void k_rhs_sine(int dim, int mx, int my, int mz, int modes, const double* __restrict__ H,
+                           const double* __restrict__ gy, const double* __restrict__ gz,
+                           double* __restrict__ b) {
+    const size_t total = (size_t)mx * my * mz;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(idx % mx);
+        const size_t t = idx / mx;
+        const int j = (int)(t % my), k = (int)(t / my);
+        double s = 0.0;
+        if (dim == 2) {
+            for (int ky = 0; ky < modes; ++ky) s += gy[(size_t)ky * my + j] * H[(size_t)ky * mx + i];
+        } else {
+            for (int kz = 0; kz < modes; ++kz) {
+                double sy = 0.0;
+                for (int ky = 0; ky < modes; ++ky)
+                    sy += gy[(size_t)ky * my + j] * H[((size_t)kz * modes + ky) * mx + i];
+                s += gz[(size_t)kz * mz + k] * sy;
+            }
+        }
+        b[idx] = s;
+    }
+}
+
+template <typename T>
+__global__ void k_fill_zero(T* p, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        p[i] = (T)0;
+}
+
+// ================================================================ launchers
+static int grid_for(size_t n, int per = kThreads) {
+    size_t g = (n + per - 1) / per;
+    if (g > 152 * 16) g = 152 * 16;
+    return (int)(g < 1 ? 1 : g);
+}
+
+template <typename K>
+static void set_smem(K kernel, size_t bytes) {
+    if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename T, typename A>
+void xpass(cudaStream_t s, const LevelView<T>& L, const T* x, T* x_out, const A* add, int nS,
+           const double* gamma, const T* S, size_t ldS, T* TM, T* TK) {
+    const size_t smem = (size_t)(L.m[0] + 2 * L.p) * sizeof(T);
+    set_smem(k_xpass<T, A>, smem);
+    k_xpass<T, A><<<L.rows(), kThreads, smem, s>>>(L, x, x_out, add, nS, gamma, S, ldS, TM, TK);
+    count_launch();
+}
+
+template <typename T>
+void gs_sweep(cudaStream_t s, int dim, const LevelView<T>& L, bool descending, T* x, const T* b,
+              T* TM, T* TK) {
+    const int p = L.p, P1 = p + 1;
+    const size_t smem = (size_t)5 * L.m[0] * sizeof(T);
+    auto launch = [&](int cy, int cz) {
+        const int nty = (L.m[1] - cy + p) / P1;
+        const int ntz = (dim == 3) ? (L.m[2] - cz + p) / P1 : 1;
+        if (nty <= 0 || ntz <= 0) return;
+        if (dim == 2) {
+            set_smem(k_gs_phase<T, 2>, smem);
+            k_gs_phase<T, 2><<<nty * ntz, kThreads, smem, s>>>(L, cy, cz, descending, x, b, TM, TK);
+        } else {
+            set_smem(k_gs_phase<T, 3>, smem);
+            k_gs_phase<T, 3><<<nty * ntz, kThreads, smem, s>>>(L, cy, cz, descending, x, b, TM, TK);
+        }
+        count_launch();
+    };
+    const int ncz = (dim == 3) ? P1 : 1;
+    for (int c = 0; c < P1 * ncz; ++c) {
+        const int cc = descending ? P1 * ncz - 1 - c : c;
+        launch(cc % P1, cc / P1);
+    }
+}
+
+template <typename T, typename R>
+void residual(cudaStream_t s, int dim, const LevelView<T>& L, const T* b, const T* TM, const T* TK,
+              R* r, double* partial) {
+    if (dim == 2) k_residual<T, R, 2><<<L.rows(), kThreads, 0, s>>>(L, b, TM, TK, r, b ? 0 : 1, partial);
+    else k_residual<T, R, 3><<<L.rows(), kThreads, 0, s>>>(L, b, TM, TK, r, b ? 0 : 1, partial);
+    count_launch();
+}
+
+template <typename T>
+void restrict_(cudaStream_t s, int dim, const TransferView<T>& P, const T* fine, T* coarse, T* tmp1,
+               T* tmp2) {
+    // axis by axis: x, then y (then z); dims shrink one axis at a time
+    int d[3] = {P.mf[0], P.mf[1], dim == 3 ? P.mf[2] : 1};
+    const T* in = fine;
+    for (int a = 0; a < dim; ++a) {
+        const int n_in = d[a];
+        d[a] = P.mc[a];
+        T* out = (a == dim - 1) ? coarse : (a == 0 ? tmp1 : tmp2);
+        const size_t total = (size_t)d[0] * d[1] * d[2];
+        k_transfer_axis<T><<<grid_for(total), kThreads, 0, s>>>(in, out, d[0], d[1], d[2], a, n_in,
+                                                                P.rlo[a], P.rv[a], P.rw[a]);
+        count_launch();
+        in = out;
+    }
+}
+
+template <typename T>
+void prolong_add(cudaStream_t s, int dim, const TransferView<T>& P, const LevelView<T>& Lf, const T* e,
+                 T* x, T* TM, T* TK, T* tmp1, T* tmp2) {
+    int d[3] = {P.mc[0], P.mc[1], dim == 3 ? P.mc[2] : 1};
+    const T* in = e;
+    for (int a = 0; a < dim - 1; ++a) {
+        const int n_in = d[a];
+        d[a] = P.mf[a];
+        T* out = (a == 0) ? tmp1 : tmp2;
+        const size_t total = (size_t)d[0] * d[1] * d[2];
+        k_transfer_axis<T><<<grid_for(total), kThreads, 0, s>>>(in, out, d[0], d[1], d[2], a, n_in,
+                                                                P.plo[a], P.pv[a], P.pw[a]);
+        count_launch();
+        in = out;
+    }
+    const int a = dim - 1;
+    const size_t smem = (size_t)(Lf.m[0] + 2 * Lf.p) * sizeof(T);
+    if (dim == 2) {
+        set_smem(k_prolong_last<T, 2>, smem);
+        k_prolong_last<T, 2><<<Lf.rows(), kThreads, smem, s>>>(Lf, in, P.mc[a], P.plo[a], P.pv[a], P.pw[a], x, TM, TK);
+    } else {
+        set_smem(k_prolong_last<T, 3>, smem);
+        k_prolong_last<T, 3><<<Lf.rows(), kThreads, smem, s>>>(Lf, in, P.mc[a], P.plo[a], P.pv[a], P.pw[a], x, TM, TK);
+    }
+    count_launch();
+}
+
+template <typename T>
+void coarse_solve(cudaStream_t s, int dim, const CoarseView<T>& C, const T* r, T* e) {
+    const int N = C.m[0] * C.m[1] * (dim == 3 ? C.m[2] : 1);
+    const size_t smem = (size_t)2 * N * sizeof(T);
+    if (dim == 2) {
+        set_smem(k_coarse_fd<T, 2>, smem);
+        k_coarse_fd<T, 2><<<1, kThreads, smem, s>>>(C, r, e);
+    } else {
+        set_smem(k_coarse_fd<T, 3>, smem);
+        k_coarse_fd<T, 3><<<1, kThreads, smem, s>>>(C, r, e);
+    }
+    count_launch();
+}
+
+void sumsq_partial(cudaStream_t s, const double* v, size_t n, double* partial, int nblocks) {
+    k_sumsq<<<nblocks, kThreads, 0, s>>>(v, n, partial);
+    count_launch();
+}
+
+void norm_final(cudaStream_t s, const double* partial, int nparts, const double* denom, double* out,
+                int slot) {
+    k_norm_final<<<1, 1024, 0, s>>>(partial, nparts, denom, out, slot);
+    count_launch();
+}
+
+int gram_blocks(size_t n) {
+    size_t g = (n + kThreads - 1) / kThreads;
+    if (g > 2 * 152) g = 2 * 152;
+    return (int)(g < 1 ? 1 : g);
+}
+
+void gram_partial(cudaStream_t s, int q, const double* S, size_t ld, size_t n, double* partial, int nblocks) {
+    switch (q) {
+#define IGAMG_GRAM_CASE(Q) \
+    case Q: k_gram_partial<Q><<<nblocks, kThreads, 0, s>>>(S, ld, n, partial); break;
+        IGAMG_GRAM_CASE(1) IGAMG_GRAM_CASE(2) IGAMG_GRAM_CASE(3) IGAMG_GRAM_CASE(4)
+        IGAMG_GRAM_CASE(5) IGAMG_GRAM_CASE(6) IGAMG_GRAM_CASE(7) IGAMG_GRAM_CASE(8)
+        IGAMG_GRAM_CASE(9) IGAMG_GRAM_CASE(10) IGAMG_GRAM_CASE(11) IGAMG_GRAM_CASE(12)
+#undef IGAMG_GRAM_CASE
+        default: return;
+    }
+    count_launch();
+}
+
+void extrap_gammas(cudaStream_t s, int q, int method, const double* S, size_t ld, size_t n,
+                   double* partial, int nblocks, ExtrapInfo* info, double* gamma, int* qused) {
+    gram_partial(s, q, S, ld, n, partial, nblocks);
+    k_chol1<<<1, kThreads, 0, s>>>(q, partial, nblocks, info, gamma, qused);
+    count_launch();
+    switch (q) {
+#define IGAMG_GRAM2_CASE(Q) \
+    case Q: k_gram2_partial<Q><<<nblocks, kThreads, 0, s>>>(S, ld, n, info, partial); break;
+        IGAMG_GRAM2_CASE(1) IGAMG_GRAM2_CASE(2) IGAMG_GRAM2_CASE(3) IGAMG_GRAM2_CASE(4)
+        IGAMG_GRAM2_CASE(5) IGAMG_GRAM2_CASE(6) IGAMG_GRAM2_CASE(7) IGAMG_GRAM2_CASE(8)
+        IGAMG_GRAM2_CASE(9) IGAMG_GRAM2_CASE(10) IGAMG_GRAM2_CASE(11) IGAMG_GRAM2_CASE(12)
+#undef IGAMG_GRAM2_CASE
+        default: return;
+    }
+    count_launch();
+    k_gamma2<<<1, kThreads, 0, s>>>(q, method, partial, nblocks, info, gamma, qused);
+    count_launch();
+}
+
+void combine(cudaStream_t s, int q, const double* gamma, const double* S, size_t ld, size_t n, double* t) {
+    k_combine<<<grid_for(n), kThreads, 0, s>>>(q + 2, gamma, S, ld, n, t);
+    count_launch();
+}
+
+void rhs_sine(cudaStream_t s, int dim, const int* m, int modes, const double* H, const double* gy,
+              const double* gz, double* b) {
+    const size_t total = (size_t)m[0] * m[1] * (dim == 3 ? m[2] : 1);
+    k_rhs_sine<<<grid_for(total), kThreads, 0, s>>>(dim, m[0], m[1], dim == 3 ? m[2] : 1, modes, H, gy, gz, b);
+    count_launch();
+}
+
+template <typename T>
+void fill_zero(cudaStream_t s, T* p, size_t n) {
+    k_fill_zero<T><<<grid_for(n), kThreads, 0, s>>>(p, n);
+    count_launch();
+}
+
+// explicit instantiations
+#define IGAMG_INST(T)                                                                               \
+    template void xpass<T, T>(cudaStream_t, const LevelView<T>&, const T*, T*, const T*, int,       \
+                              const double*, const T*, size_t, T*, T*);                             \
+    template void gs_sweep<T>(cudaStream_t, int, const LevelView<T>&, bool, T*, const T*, T*, T*);  \
+    template void restrict_<T>(cudaStream_t, int, const TransferView<T>&, const T*, T*, T*, T*);   \
+    template void prolong_add<T>(cudaStream_t, int, const TransferView<T>&, const LevelView<T>&,    \
+                                 const T*, T*, T*, T*, T*, T*);                                     \
+    template void coarse_solve<T>(cudaStream_t, int, const CoarseView<T>&, const T*, T*);          \
+    template void fill_zero<T>(cudaStream_t, T*, size_t);
+IGAMG_INST(double)
+IGAMG_INST(float)
+#undef IGAMG_INST
+template void xpass<double, float>(cudaStream_t, const LevelView<double>&, const double*, double*,
+                                   const float*, int, const double*, const double*, size_t, double*,
+                                   double*);
+template void residual<double, double>(cudaStream_t, int, const LevelView<double>&, const double*,
+                                       const double*, const double*, double*, double*);
+template void residual<double, float>(cudaStream_t, int, const LevelView<double>&, const double*,
+                                      const double*, const double*, float*, double*);
+template void residual<float, float>(cudaStream_t, int, const LevelView<float>&, const float*,
+                                     const float*, const float*, float*, double*);
+
+}  // namespace dev
+}  // namespace igamg

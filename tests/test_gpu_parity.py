@@ -1,0 +1,290 @@
+"""GPU parity: every kernel of the CUDA path against the CPU oracle, through the C ABI.
+
+Tolerances: FP64 components agree to round-off (relative 1e-12 for operator
+applications and sweeps, whose results are sums of O(p^dim) terms of one
+sign pattern); whole solves agree to 1e-9 relative at equal cycle counts with
+the stopping cycle within +-1.  FP32 V-cycles are checked against the FP64
+oracle to FP32 accuracy (relative 2e-5 on one cycle's correction).
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from oracle import extrapolation as oex  # noqa: E402
+from oracle import multigrid as omg  # noqa: E402
+from oracle import solver as osolver  # noqa: E402
+from oracle.galerkin import load_vector  # noqa: E402
+import workloads  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import __graft_entry__ as g
+    g.build_library()
+    import paper_2412_20205_gb300 as p
+    assert torch.cuda.is_available()
+    return p
+
+
+DEV = "cuda"
+
+
+def _t(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
+
+
+def _np(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+class Pair:
+    """GPU context and oracle hierarchy for the same (dim, n, p)."""
+
+    def __init__(self, pkg, dim, n, p, n_levels=0):
+        self.pkg = pkg
+        ns = n if hasattr(n, "__len__") else [n] * dim
+        self.ctx = pkg.igamg_setup(dim, p, ns, n_levels)
+        pkg.igamg_assemble(self.ctx)
+        self.H = omg.Hierarchy(dim, ns, p, n_levels=n_levels or None)
+        nb = max(pkg.igamg_workspace_bytes(self.ctx, 12, pkg.IGAMG_FP32_IR),
+                 pkg.igamg_workspace_bytes(self.ctx, 12, pkg.IGAMG_FP64))
+        self.ws = torch.empty(nb, dtype=torch.uint8, device=DEV)
+        assert [tuple(l.m[::1]) + (1,) * (3 - dim) for l in self.H.levels] == \
+            [tuple(m) for m in pkg.igamg_info(self.ctx)]
+
+    def close(self):
+        self.pkg.igamg_destroy(self.ctx)
+
+
+CASES = [(2, 20, 2), (2, 37, 3), (2, 24, 1), (2, 19, 5), (2, (21, 13), 2), (3, 10, 2), (3, 9, 3),
+         (2, 40, 7)]
+
+
+@pytest.fixture(params=CASES, ids=lambda c: f"d{c[0]}n{c[1]}p{c[2]}")
+def pair(request, pkg):
+    dim, n, p = request.param
+    pr = Pair(pkg, dim, n, p)
+    yield pr
+    pr.close()
+
+
+def test_apply_every_level(pkg, pair):
+    rng = np.random.default_rng(0)
+    for l, lev in enumerate(pair.H.levels):
+        x = rng.standard_normal(lev.N)
+        y = torch.empty(lev.N, dtype=torch.float64, device=DEV)
+        pkg.igamg_apply(pair.ctx, l, _t(x), y, pair.ws)
+        ref = lev.A @ x
+        assert _rel(_np(y), ref) < 1e-13, l
+
+
+def test_gs_sweep_every_level_both_orders(pkg, pair):
+    rng = np.random.default_rng(1)
+    for l, lev in enumerate(pair.H.levels):
+        x0, b = rng.standard_normal(lev.N), rng.standard_normal(lev.N)
+        for desc in (0, 1):
+            x = _t(x0)
+            pkg.igamg_smooth(pair.ctx, l, x, _t(b), desc, pair.ws)
+            ref = omg.gs_sweep(lev, x0, b, descending=bool(desc))
+            assert _rel(_np(x), ref) < 1e-12, (l, desc)
+
+
+def test_restrict_and_prolong_every_level(pkg, pair):
+    rng = np.random.default_rng(2)
+    for l in range(1, len(pair.H.levels)):
+        Nf, Nc = pair.H.levels[l].N, pair.H.levels[l - 1].N
+        r = rng.standard_normal(Nf)
+        rc = torch.empty(Nc, dtype=torch.float64, device=DEV)
+        pkg.igamg_restrict(pair.ctx, l, _t(r), rc, pair.ws)
+        assert _rel(_np(rc), pair.H.P[l].T @ r) < 1e-13
+        e, x0 = rng.standard_normal(Nc), rng.standard_normal(Nf)
+        x = _t(x0)
+        pkg.igamg_prolong(pair.ctx, l, _t(e), x, pair.ws)
+        assert _rel(_np(x), x0 + pair.H.P[l] @ e) < 1e-13
+
+
+def test_coarse_solve(pkg, pair):
+    import scipy.linalg as sla
+    rng = np.random.default_rng(3)
+    r = rng.standard_normal(pair.H.levels[0].N)
+    e = torch.empty_like(_t(r))
+    pkg.igamg_coarse_solve(pair.ctx, _t(r), e)
+    assert _rel(_np(e), sla.cho_solve(pair.H.coarse_chol, r)) < 1e-12
+
+
+def test_vcycle_fp64_and_fp32_refinement_step(pkg, pair):
+    rng = np.random.default_rng(4)
+    lev = pair.H.finest
+    coeffs = rng.standard_normal((3,) * pair.H.dim)
+    b = load_vector(lev.breaks, pair.H.p, coeffs)
+    x0 = rng.standard_normal(lev.N) * 1e-3
+    ref = omg.cycle(pair.H, x0, b)
+    x = _t(x0)
+    pkg.igamg_vcycle(pair.ctx, x, _t(b), pkg.IGAMG_FP64, pair.ws)
+    assert _rel(_np(x), ref) < 1e-12
+    # FP32 refinement step: x + V32(0; b - A x); compare the correction
+    x = _t(x0)
+    pkg.igamg_vcycle(pair.ctx, x, _t(b), pkg.IGAMG_FP32_IR, pair.ws)
+    assert _rel(_np(x) - x0, ref - x0) < 2e-5
+
+
+def test_rhs_matches_oracle_quadrature(pkg, pair):
+    coeffs = np.random.default_rng(5).standard_normal((5,) * pair.H.dim)
+    b = torch.empty(pair.H.finest.N, dtype=torch.float64, device=DEV)
+    pkg.igamg_rhs_sine(pair.ctx, coeffs, b)
+    assert _rel(_np(b), load_vector(pair.H.finest.breaks, pair.H.p, coeffs)) < 1e-13
+
+
+# ------------------------------------------------------------------ extrapolation
+def _iterates(dim, n, p, q, seed):
+    prob = osolver.Problem(dim, n, p, workloads.random_sine_coeffs(dim, seed, modes=4))
+    S = [np.zeros(prob.H.finest.N)]
+    for _ in range(q + 1):
+        S.append(prob.cycle(S[-1]))
+    return S
+
+
+@pytest.mark.parametrize("method", ["rre", "mpe"])
+@pytest.mark.parametrize("q", [1, 3, 5, 10, 12])
+def test_extrapolate_matches_oracle(pkg, method, q):
+    S = _iterates(2, 24, 3, q, seed=q)
+    n = len(S[0])
+    ld = n + 5                                     # ragged leading dimension
+    St = torch.zeros((q + 2) * ld, dtype=torch.float64, device=DEV)
+    for j, s in enumerate(S):
+        St[j * ld:j * ld + n] = _t(s)
+    t = torch.empty(n, dtype=torch.float64, device=DEV)
+    ws = torch.empty(pkg.igamg_extrap_workspace_bytes(n, q), dtype=torch.uint8, device=DEV)
+    gamma, qused = pkg.igamg_extrapolate(n, q, pkg.EXTRAP[method], St, ld, t, ws)
+    tref, gref, qref = oex.extrapolate(S, method)
+    assert qused == qref
+    assert _rel(_np(t), tref) < 1e-9
+    if qref > 0:
+        assert abs(gamma[: qref + 1].sum() - 1) < 1e-12
+
+
+def test_extrapolate_breakdown_paths(pkg):
+    rng = np.random.default_rng(9)
+    n, q = 1000, 3
+    base = [rng.standard_normal(n) for _ in range(2)]
+    d = base[1] - base[0]
+    cases = {
+        "fixed": [base[0]] * (q + 2),
+        "lambda0": [base[0], base[1], base[1] + d, base[1] + 2 * d, base[1] + 3 * d],
+        "half": [base[0], base[1], base[1] + 0.5 * d, base[1] + 0.75 * d, base[1] + 0.875 * d],
+    }
+    ws = torch.empty(pkg.igamg_extrap_workspace_bytes(n, q), dtype=torch.uint8, device=DEV)
+    for name, S in cases.items():
+        St = _t(np.concatenate(S))
+        t = torch.empty(n, dtype=torch.float64, device=DEV)
+        gamma, qused = pkg.igamg_extrapolate(n, q, pkg.IGAMG_RRE, St, n, t, ws)
+        tref, _, qref = oex.extrapolate(S, "rre")
+        assert qused == qref, name
+        assert _rel(_np(t), tref) < 1e-12, name
+
+
+# ------------------------------------------------------------------ whole solves
+SOLVES = [(2, 64, 2, "rre", 5), (2, 64, 2, "mpe", 5), (2, 48, 4, "rre", 10), (2, 37, 3, "mpe", 10),
+          (3, 16, 3, "rre", 10), (3, 12, 2, "mpe", 5), (2, 32, 1, "rre", 3), (2, 40, 7, "rre", 8)]
+
+
+@pytest.mark.parametrize("dim,n,p,method,k", SOLVES)
+def test_solve_fp64_matches_oracle(pkg, dim, n, p, method, k):
+    coeffs = workloads.random_sine_coeffs(dim, seed=11, modes=6) if n != 64 else workloads.manufactured_coeffs(dim)
+    prob = osolver.Problem(dim, n, p, coeffs)
+    ref = osolver.solve(prob, method, k=k, tol=1e-10, max_cycles=60, keep_iterates=True)
+    s = pkg.Solver(dim, p, n, k=k)
+    b = s.rhs_sine(coeffs)
+    out = s.solve(b, tol=1e-10, method=method, k=k, prec="fp64", max_cycles=60)
+    assert out["converged"] and ref["converged"]
+    assert abs(out["cycles"] - ref["cycles"]) <= 1
+    # equal cycle counts: run exactly the oracle's cycles
+    c = min(out["cycles"], ref["cycles"])
+    out_c = s.solve(b, tol=0.0, method=method, k=k, prec="fp64", max_cycles=c)
+    assert out_c["cycles"] == c
+    assert _rel(_np(out_c["x"]), ref["iterates"][c - 1]) < 1e-9
+    assert np.allclose(out["history"][: c + 1], ref["history"][: c + 1], rtol=1e-5, atol=1e-16)
+    s.close()
+
+
+@pytest.mark.parametrize("dim,n,p,method,k", [(2, 64, 3, "rre", 5), (2, 45, 5, "mpe", 10), (3, 16, 3, "rre", 10)])
+def test_solve_fp32_ir_reaches_fp64_accuracy(pkg, dim, n, p, method, k):
+    import scipy.sparse.linalg as spla
+    coeffs = workloads.random_sine_coeffs(dim, seed=3, modes=8)
+    prob = osolver.Problem(dim, n, p, coeffs)
+    s = pkg.Solver(dim, p, n, k=k)
+    b = s.rhs_sine(coeffs)
+    out = s.solve(b, tol=1e-10, method=method, k=k, prec="fp32_ir", max_cycles=60)
+    assert out["converged"]
+    x = _np(out["x"])
+    res = np.linalg.norm(prob.b - prob.H.finest.A @ x) / np.linalg.norm(prob.b)
+    assert res <= 1.05e-10
+    u = spla.spsolve(prob.H.finest.A.tocsc(), prob.b)
+    assert _rel(x, u) < 1e-6
+    s.close()
+
+
+def test_solve_plain_vcycle_and_graph_free_path(pkg):
+    coeffs = workloads.manufactured_coeffs(2)
+    prob = osolver.Problem(2, 32, 2, coeffs)
+    ref = osolver.solve(prob, "none", tol=1e-10, max_cycles=100)
+    s = pkg.Solver(2, 2, 32, k=5)
+    b = s.rhs_sine(coeffs)
+    for graph in (True, False):
+        out = s.solve(b, tol=1e-10, method="none", max_cycles=100, prec="fp64", graph=graph)
+        assert abs(out["cycles"] - ref["cycles"]) <= 1
+        assert _rel(_np(out["x"]), ref["x"]) < 1e-9 * 10
+    s.close()
+
+
+def test_edge_cases(pkg):
+    s = pkg.Solver(2, 3, 16, k=5)
+    zero = torch.zeros(s.N, dtype=torch.float64, device=DEV)
+    out = s.solve(zero, tol=1e-10)
+    assert out["converged"] and out["cycles"] == 0 and float(out["x"].abs().max()) == 0.0
+    b = s.rhs_sine(workloads.manufactured_coeffs(2))
+    out = s.solve(b, tol=1e-10, max_cycles=0)
+    assert out["status"] == pkg.IGAMG_ENOTCONV and out["cycles"] == 0
+    # warm start from the converged solution converges immediately
+    out = s.solve(b, tol=1e-10)
+    out2 = s.solve(b, x=out["x"].clone(), tol=1e-10, x0_given=True)
+    assert out2["cycles"] == 0
+    nanb = b.clone()
+    nanb[3] = float("nan")
+    with pytest.raises(pkg.IgamgError):
+        s.solve(nanb, tol=1e-10)
+    s.close()
+    # single grid: the 'V-cycle' is the direct solve
+    one = pkg.Solver(2, 2, 8, n_levels=1, k=2)
+    b1 = one.rhs_sine(workloads.manufactured_coeffs(2))
+    out = one.solve(b1, tol=1e-12, method="none", max_cycles=3)
+    assert out["converged"] and out["cycles"] == 1
+    one.close()
+
+
+@pytest.mark.parametrize("p", [2, 5])
+def test_full_size_2d_1024_residual_property(pkg, p):
+    """1024 x 1024 elements: the FP32-refined RRE(5) solution satisfies the
+    oracle's own residual test (oracle operator and load vector, FP64)."""
+    from oracle import galerkin as gk, bspline as bs
+    coeffs = workloads.random_sine_coeffs(2, seed=0, modes=16)
+    s = pkg.Solver(2, p, 1024, k=5)
+    b = s.rhs_sine(coeffs)
+    out = s.solve(b, tol=1e-10, method="rre", k=5, prec="fp32_ir", max_cycles=60)
+    assert out["converged"]
+    x = _np(out["x"])
+    br = bs.uniform_breaks(1024)
+    f = gk.factors_1d(br, p)
+    A = gk.operator([f, f])
+    bo = gk.load_vector([br, br], p, coeffs)
+    assert _rel(_np(b), bo) < 1e-13
+    assert np.linalg.norm(bo - A @ x) / np.linalg.norm(bo) <= 1.05e-10
+    s.close()
