@@ -1,0 +1,313 @@
+#!/usr/bin/env python
+"""Benchmark: time to relative residual 1e-10 and DOF/s of the RRE-accelerated
+geometric-multigrid solver for the 2D IGA Poisson problem on 1024 x 1024
+elements (about 1M unknowns), FP32 V-cycles in FP64 iterative refinement
+(the mixed form) with the plain FP64 form timed beside it.
+
+One step = one complete solve from s_0 = 0 to ||b - A x|| / ||b|| <= 1e-10
+(restarted RRE, k = 5, multicolour Gauss-Seidel V(1,1)-cycles), inputs
+resident in HBM, L2 flushed between steps.  value = DOF / time-to-tolerance,
+summed over ranks (each rank solves its own independent problem: weak
+scaling, no collective on the data path).
+
+  python bench.py [--steps K] [--warmup W] [--p 3] [--k 5] [--method rre]
+  python bench.py --impl reference      # the CPU oracle on a bounded sample
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to rel. residual 1e-10 and DOF/s: FP64 GMG+RRE vs mixed/learned form"
+FP64_PEAK_FLOP_PER_CLK_PER_SM = 4          # 2 FP64 FMA per clock per SM on GB300 (1.25 TFLOP/s nominal)
+N_SMS = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--dim", type=int, default=2)
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--p", type=int, default=3)
+    ap.add_argument("--k", type=int, default=5)
+    ap.add_argument("--method", default="rre", choices=["rre", "mpe"])
+    ap.add_argument("--prec", default="fp32_ir", choices=["fp32_ir", "fp64"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(a):
+    return {"workload": f"{a.dim}D IGA Poisson, {a.n}^{a.dim} elements, p={a.p}, "
+                        f"{a.method.upper()}(k={a.k}) V(1,1) multicolour GS, tol 1e-10",
+            "dim": a.dim, "n_elements": a.n, "p": a.p, "method": a.method, "k": a.k,
+            "rhs": "random sine series, 16 modes/direction, N(0,1), seed = rank",
+            "l2": "flushed between steps (256 MiB write)"}
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for i, nm in enumerate(names):
+                if len(r) > 5 + i and r[5 + i].lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU oracle sample
+def oracle_sample(a, rank_seed=0, restarts=1):
+    """Bounded sample of the oracle on the same workload: the restart-cycle count
+    to tolerance is taken from the oracle on the 128^dim version of the problem
+    (multigrid convergence is mesh independent), and one restart cycle (k+1
+    V-cycles, extrapolation, residual) is timed on the full-size problem.
+    Returns (dof_per_s, seconds_per_restart, cycles, setup_s)."""
+    import numpy as np
+    import workloads
+    from oracle import extrapolation, solver
+    coeffs = workloads.random_sine_coeffs(a.dim, seed=rank_seed, modes=16)
+    small = solver.Problem(a.dim, min(a.n, 128), a.p, coeffs)
+    cycles = solver.solve(small, a.method, k=a.k, tol=1e-10, max_cycles=100)["cycles"]
+    t0 = time.perf_counter()
+    prob = solver.Problem(a.dim, a.n, a.p, coeffs)
+    setup = time.perf_counter() - t0
+    N = prob.H.finest.N
+    s = np.zeros(N)
+    t0 = time.perf_counter()
+    for _ in range(restarts):
+        S = [s]
+        for _ in range(a.k + 1):
+            S.append(prob.cycle(S[-1]))
+        s = extrapolation.extrapolate(S, a.method)[0]
+        prob.residual(s)
+    per = (time.perf_counter() - t0) / restarts
+    return N / (per * cycles), per, cycles, setup, N
+
+
+def run_reference(a, rank, world):
+    if rank != 0:
+        return
+    for _ in range(a.warmup):
+        pass                                    # the oracle has no warm-up state
+    vals, pers = [], []
+    cycles = None
+    for _ in range(max(1, a.steps)):
+        v, per, cycles, setup, N = oracle_sample(a)
+        vals.append(v)
+        pers.append(per)
+    v = sorted(vals)[len(vals) // 2]
+    ms = 1e3 * N / v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "DOF/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(a),
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": v, "unit": "DOF/s",
+                             "sample": f"one restart cycle ({a.k + 1} V-cycles + extrapolation + residual) "
+                                       f"timed at full size x {cycles} cycles (count from the 128^dim problem)"},
+            "e2e": {"value": v, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_ours(a, rank, world, local):
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build_library()
+    import paper_2412_20205_gb300 as pkg
+    import workloads
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    s = pkg.Solver(a.dim, a.p, a.n, k=a.k)
+    coeffs = workloads.random_sine_coeffs(a.dim, seed=a.seed + rank, modes=16)
+    b = s.rhs_sine(coeffs)
+    x = torch.zeros(s.N, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def solve(prec):
+        return s.solve(b, x=x, tol=1e-10, method=a.method, k=a.k, prec=prec, max_cycles=200)
+
+    def timed(prec, steps):
+        times = []
+        out = None
+        for _ in range(steps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = solve(prec)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        return times, out
+
+    for _ in range(a.warmup):
+        solve(a.prec)
+        solve("fp64")
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = pkg.igamg_launch_count()
+    times, out = timed(a.prec, a.steps)
+    launches = pkg.igamg_launch_count() - l0
+    barrier(world)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    times64, out64 = timed("fp64", a.steps)
+
+    # end to end through the public API: pinned host b in, host x out, per step
+    hb = torch.empty(s.N, dtype=torch.float64, pin_memory=True)
+    hb.copy_(b.cpu())
+    hx = torch.empty(s.N, dtype=torch.float64, pin_memory=True)
+    db = torch.empty_like(b)
+    e2e_times = []
+    for _ in range(a.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        db.copy_(hb, non_blocking=True)
+        o = s.solve(db, x=x, tol=1e-10, method=a.method, k=a.k, prec=a.prec, max_cycles=200)
+        hx.copy_(o["x"], non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_times.append((time.perf_counter() - t0) * 1e3)
+
+    # dominant kernel: the FP64 row-coupled residual / operator application
+    # (x-pass + row couplings, bound by the FP64 pipe); algorithmic FLOPs per
+    # launch pair = 2 * 4 (2p+1) N in 2D.
+    ws = s.ws
+    xr = torch.randn(s.N, dtype=torch.float64, device=dev)
+    yr = torch.empty_like(xr)
+    top = len(s.levels) - 1
+    for _ in range(3):
+        pkg.igamg_apply(s.ctx, top, xr, yr, ws)
+    reps = 50
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        pkg.igamg_apply(s.ctx, top, xr, yr, ws)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    apply_ms = e0.elapsed_time(e1) / reps
+    w = 2 * a.p + 1
+    flops = 2.0 * (2 * w + (2 * w if a.dim == 2 else 2 * w * w)) * s.N
+    sm_mhz = clk["sm_mhz"] or 2070.0
+    peak_fp64 = N_SMS * FP64_PEAK_FLOP_PER_CLK_PER_SM * 2070.0e6 / 1e12
+    achieved = flops / (apply_ms * 1e-3) / 1e12
+
+    t_max = max_over_ranks(float(np.mean(times)), world)
+    t64_max = max_over_ranks(float(np.mean(times64)), world)
+    e2e_max = max_over_ranks(float(np.mean(e2e_times)), world)
+    if rank != 0:
+        return
+    units = s.N * world
+    line = {
+        "metric": METRIC, "value": units / (t_max * 1e-3), "unit": "DOF/s", "n_gpus": world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_max, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if a.prec == "fp32_ir" else "f64",
+        "data": "synthetic", "config": workload_config(a),
+        "time_to_tol_ms": t_max, "cycles": out["cycles"], "vcycles": out["vcycles"],
+        "final_rel_residual": float(out["history"][-1]),
+        "fp64_form": {"ms_per_step": t64_max, "value": units / (t64_max * 1e-3), "unit": "DOF/s",
+                      "cycles": out64["cycles"], "final_rel_residual": float(out64["history"][-1])},
+        "e2e": {"value": units / (e2e_max * 1e-3), "unit": "DOF/s",
+                "h2d_bytes_per_step": s.N * 8, "d2h_bytes_per_step": s.N * 8},
+        "gpu_launches": launches,
+        "roofline": {"bound": "alu", "kernel": "k_xpass<double> + k_residual<double> (FP64 operator)",
+                     "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s (FP64)",
+                     "frac": achieved / peak_fp64, "traffic": None,
+                     "peak_source": "152 SMs x 4 FP64 flop/clk x 2070 MHz (nominal 1.25 TFLOP/s)"},
+        "clocks": clk,
+    }
+    if not a.no_cpu_baseline:
+        v, per, cycles, setup, N = oracle_sample(a)
+        line["cpu_baseline"] = {"value": v, "unit": "DOF/s", "cores": 1, "kind": "oracle",
+                                "sample": f"one restart cycle timed at full size ({per:.2f} s) x {cycles} "
+                                          f"cycles (count from the 128^dim problem); set-up {setup:.1f} s excluded"}
+    print(json.dumps(line), flush=True)
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def main():
+    a = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        run_reference(a, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    run_ours(a, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -175,4 +175,8 @@ def prolongation_1d(breaks_fine, breaks_coarse, p):
     Mf = Bf.T @ (wts[:, None] * Bf)
     G = Bf.T @ (wts[:, None] * Bc)
     P = np.linalg.solve(Mf, G)
+    # Compact support (Prop. 3): coarse function J is a combination of the fine
+    # functions overlapping its support only; entries elsewhere are exact zeros
+    # that the dense solve returns as rounding noise.
+    P[np.abs(P) < 1e-13 * np.abs(P).max()] = 0.0
     return P, P[1:-1, 1:-1].copy()

@@ -203,6 +203,28 @@ void compact_transfer(HostLevel& H, int d) {
         }
 }
 
+// Rows of the x-band equal (to 1e-14 relative) to the middle row's band form
+// the Toeplitz interior [lo, hi); returns the middle row index.
+int toeplitz_range(const Factor1D& f, int* lo, int* hi) {
+    const int m = f.m, bw = 2 * f.p + 1, mid = m / 2;
+    double scale = 0.0;
+    for (int b = 0; b < bw; ++b)
+        scale = std::max(scale, std::max(std::fabs(f.M[(size_t)mid * bw + b]), std::fabs(f.K[(size_t)mid * bw + b])));
+    auto same = [&](int i) {
+        for (int b = 0; b < bw; ++b) {
+            if (std::fabs(f.M[(size_t)i * bw + b] - f.M[(size_t)mid * bw + b]) > 1e-14 * scale) return false;
+            if (std::fabs(f.K[(size_t)i * bw + b] - f.K[(size_t)mid * bw + b]) > 1e-14 * scale) return false;
+        }
+        return true;
+    };
+    int l = mid, h = mid + 1;
+    while (l > 0 && same(l - 1)) --l;
+    while (h < m && same(h)) ++h;
+    *lo = l;
+    *hi = h;
+    return mid;
+}
+
 template <typename T>
 std::vector<T> band_major(const Factor1D& f, bool stiff) {
     const int m = f.m, bw = 2 * f.p + 1;
@@ -573,6 +595,18 @@ igamg_status igamg_assemble(igamg_ctx* c) {
         }
         a.invdiag = (const double*)(base + lo[l].inv[0]);
         f.invdiag = (const float*)(base + lo[l].inv[1]);
+        {
+            int tl = 0, th = 0;
+            const int mid = toeplitz_range(H.f[0], &tl, &th), bw = 2 * p + 1;
+            a.tlo = f.tlo = tl;
+            a.thi = f.thi = th;
+            for (int b = 0; b < 2 * kMaxP + 1; ++b) {
+                const double mv = b < bw ? H.f[0].M[(size_t)mid * bw + b] : 0.0;
+                const double kv = b < bw ? H.f[0].K[(size_t)mid * bw + b] : 0.0;
+                a.Mc[b] = mv; a.Kc[b] = kv;
+                f.Mc[b] = (float)mv; f.Kc[b] = (float)kv;
+            }
+        }
         TransferView<double>& t = c->tv64[l];
         TransferView<float>& tf = c->tv32[l];
         std::memset(&t, 0, sizeof(t));

@@ -18,6 +18,10 @@ struct LevelView {
     const T* Mb[3];
     const T* Kb[3];
     const T* invdiag;                     // 1 / A_ii
+    // x-direction rows i in [tlo, thi) share one band (uniform interior of an
+    // open knot vector); the kernels read it from here instead of Mb/Kb[0].
+    int tlo, thi;
+    T Mc[2 * kMaxP + 1], Kc[2 * kMaxP + 1];
     size_t n() const { return (size_t)m[0] * m[1] * m[2]; }
     int rows() const { return m[1] * m[2]; }
 };

@@ -15,6 +15,7 @@
 #include "device.hpp"
 
 #include <cstdio>
+#include <type_traits>
 
 namespace igamg {
 
@@ -27,7 +28,6 @@ long long launch_count() { return g_launches; }
 namespace dev {
 
 constexpr int kThreads = 256;
-constexpr int kMaxNb = (2 * kMaxP + 1) * (2 * kMaxP + 1);
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -49,39 +49,66 @@ __device__ T block_sum(T v, T* red) {
     return s;
 }
 
+// x-direction band entry (row i, band b): the Toeplitz interior comes from the
+// kernel parameters, the p boundary rows at each end from the band arrays.
+template <typename T>
+__device__ __forceinline__ T band_m(const LevelView<T>& L, int i, int b) {
+    return (i >= L.tlo && i < L.thi) ? L.Mc[b] : L.Mb[0][b * L.m[0] + i];
+}
+template <typename T>
+__device__ __forceinline__ T band_k(const LevelView<T>& L, int i, int b) {
+    return (i >= L.tlo && i < L.thi) ? L.Kc[b] : L.Kb[0][b * L.m[0] + i];
+}
+
 // Row-coupling coefficients of row (j, k): for neighbour q = (dj, dk) the
-// weights on T_M and T_K, and the neighbour's row index (-1 outside).
-template <typename T, int DIM>
+// weights on T_M and T_K and the neighbour's row index; neighbours outside
+// the grid get weight 0 and the row's own index (loads stay in bounds).
+template <typename T, int DIM, int P>
 __device__ void row_couplings(const LevelView<T>& L, int j, int k, T* cM, T* cK, int* nrow) {
-    const int p = L.p, w = 2 * p + 1, my = L.m[1], mz = L.m[2];
-    const int nnb = (DIM == 3) ? w * w : w;
-    for (int q = threadIdx.x; q < nnb; q += blockDim.x) {
-        const int dj = (q % w) - p, dk = (DIM == 3) ? (q / w) - p : 0;
+    constexpr int W = 2 * P + 1;
+    constexpr int NNB = (DIM == 3) ? W * W : W;
+    const int my = L.m[1], mz = L.m[2];
+    for (int q = threadIdx.x; q < NNB; q += blockDim.x) {
+        const int dj = (q % W) - P, dk = (DIM == 3) ? (q / W) - P : 0;
         const int jj = j + dj, kk = k + dk;
         const bool ok = jj >= 0 && jj < my && kk >= 0 && kk < mz;
         T a = 0, c = 0;
         if (ok) {
-            const T myv = L.Mb[1][(dj + p) * my + j], kyv = L.Kb[1][(dj + p) * my + j];
+            const T myv = L.Mb[1][(dj + P) * my + j], kyv = L.Kb[1][(dj + P) * my + j];
             if (DIM == 2) {
                 a = kyv;
                 c = myv;
             } else {
-                const T mzv = L.Mb[2][(dk + p) * mz + k], kzv = L.Kb[2][(dk + p) * mz + k];
+                const T mzv = L.Mb[2][(dk + P) * mz + k], kzv = L.Kb[2][(dk + P) * mz + k];
                 a = kzv * myv + mzv * kyv;
                 c = mzv * myv;
             }
         }
         cM[q] = a;
         cK[q] = c;
-        nrow[q] = ok ? (kk * my + jj) : -1;
+        nrow[q] = ok ? (kk * my + jj) : (k * my + j);
     }
+}
+
+// sum over neighbour rows q (all, or all but the own row) of cM T_M + cK T_K at column i
+template <typename T, int NNB, int SKIP>
+__device__ __forceinline__ T couple(const T* cM, const T* cK, const int* nrow, const T* __restrict__ TM,
+                                    const T* __restrict__ TK, int mx, int i) {
+    T acc = 0;
+#pragma unroll
+    for (int q = 0; q < NNB; ++q) {
+        if (q == SKIP) continue;
+        const size_t o = (size_t)nrow[q] * mx + i;
+        acc += cM[q] * TM[o] + cK[q] * TK[o];
+    }
+    return acc;
 }
 
 // ---------------------------------------------------------------- x-pass
 // One CTA per row.  Source row: x, or x + add (iterative-refinement update),
 // or sum_j gamma_j S_j (extrapolated combination); written to x_out when it
 // differs from x.  Then T_M, T_K of the row.
-template <typename T, typename A>
+template <typename T, typename A, int P>
 __global__ void __launch_bounds__(kThreads) k_xpass(LevelView<T> L, const T* __restrict__ x,
                                                      T* __restrict__ x_out, const A* __restrict__ add,
                                                      int nS, const double* __restrict__ gamma,
@@ -89,15 +116,15 @@ __global__ void __launch_bounds__(kThreads) k_xpass(LevelView<T> L, const T* __r
                                                      T* __restrict__ TM, T* __restrict__ TK) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* xs = reinterpret_cast<T*>(smem_raw);
-    const int mx = L.m[0], p = L.p;
+    const int mx = L.m[0];
     const size_t base = (size_t)blockIdx.x * mx;
     __shared__ double g[kMaxQ + 2];
     if (nS > 0) {
         for (int j = threadIdx.x; j < nS; j += blockDim.x) g[j] = gamma[j];
         __syncthreads();
     }
-    for (int ii = threadIdx.x; ii < mx + 2 * p; ii += blockDim.x) {
-        const int i = ii - p;
+    for (int ii = threadIdx.x; ii < mx + 2 * P; ii += blockDim.x) {
+        const int i = ii - P;
         T v = 0;
         if (i >= 0 && i < mx) {
             if (nS > 0) {
@@ -116,14 +143,13 @@ __global__ void __launch_bounds__(kThreads) k_xpass(LevelView<T> L, const T* __r
         xs[ii] = v;
     }
     __syncthreads();
-    const T* Mx = L.Mb[0];
-    const T* Kx = L.Kb[0];
     for (int i = threadIdx.x; i < mx; i += blockDim.x) {
         T am = 0, ak = 0;
-        for (int b = 0; b <= 2 * p; ++b) {
+#pragma unroll
+        for (int b = 0; b <= 2 * P; ++b) {
             const T xv = xs[i + b];
-            am += Mx[b * mx + i] * xv;
-            ak += Kx[b * mx + i] * xv;
+            am += band_m(L, i, b) * xv;
+            ak += band_k(L, i, b) * xv;
         }
         TM[base + i] = am;
         TK[base + i] = ak;
@@ -137,12 +163,15 @@ __global__ void __launch_bounds__(kThreads) k_xpass(LevelView<T> L, const T* __r
 // multicolour sweep with the frozen off-row part F = sum_{row' != row}
 // (cM T_M + cK T_K).  The row's own T_M, T_K are updated incrementally from
 // the corrections of each colour, so a full sweep costs about one apply.
-template <typename T, int DIM>
+template <typename T, int DIM, int P>
 __global__ void __launch_bounds__(kThreads) k_gs_phase(LevelView<T> L, int cy, int cz, int descending,
                                                         T* __restrict__ x, const T* __restrict__ b,
                                                         T* __restrict__ TM, T* __restrict__ TK) {
-    const int mx = L.m[0], my = L.m[1], p = L.p, P1 = p + 1;
-    const int nty = (my - cy + p) / P1;
+    constexpr int P1 = P + 1, W = 2 * P + 1;
+    constexpr int NNB = (DIM == 3) ? W * W : W;
+    constexpr int OWN = (DIM == 3) ? P * W + P : P;
+    const int mx = L.m[0], my = L.m[1];
+    const int nty = (my - cy + P) / P1;
     const int j = cy + P1 * (blockIdx.x % nty);
     const int k = (DIM == 3) ? cz + P1 * (blockIdx.x / nty) : 0;
     const size_t base = ((size_t)k * my + j) * mx;
@@ -153,32 +182,22 @@ __global__ void __launch_bounds__(kThreads) k_gs_phase(LevelView<T> L, int cy, i
     T* tk = tm + mx;
     T* dl = tk + mx;
     T* xs = dl + mx;
-    __shared__ T cM[kMaxNb], cK[kMaxNb];
-    __shared__ int nrow[kMaxNb];
-    row_couplings<T, DIM>(L, j, k, cM, cK, nrow);
+    __shared__ T cM[NNB], cK[NNB];
+    __shared__ int nrow[NNB];
+    row_couplings<T, DIM, P>(L, j, k, cM, cK, nrow);
     __syncthreads();
-    const int w = 2 * p + 1, nnb = (DIM == 3) ? w * w : w;
-    const int own = (DIM == 3) ? p * w + p : p;
     for (int i = threadIdx.x; i < mx; i += blockDim.x) {
-        T acc = b[base + i];
-        for (int q = 0; q < nnb; ++q) {
-            const int r = nrow[q];
-            if (q == own || r < 0) continue;
-            const size_t o = (size_t)r * mx + i;
-            acc -= cM[q] * TM[o] + cK[q] * TK[o];
-        }
-        rhs[i] = acc;
+        rhs[i] = b[base + i] - couple<T, NNB, OWN>(cM, cK, nrow, TM, TK, mx, i);
         tm[i] = TM[base + i];
         tk[i] = TK[base + i];
         xs[i] = x[base + i];
     }
     __syncthreads();
-    const T am = cM[own], ak = cK[own];
-    const T* Mx = L.Mb[0];
-    const T* Kx = L.Kb[0];
+    const T am = cM[OWN], ak = cK[OWN];
     const T* dinv = L.invdiag + base;
+#pragma unroll
     for (int c = 0; c < P1; ++c) {
-        const int cx = descending ? p - c : c;
+        const int cx = descending ? P - c : c;
         for (int i = cx + P1 * (int)threadIdx.x; i < mx; i += P1 * (int)blockDim.x) {
             const T d = (rhs[i] - (am * tm[i] + ak * tk[i])) * dinv[i];
             xs[i] += d;
@@ -191,15 +210,13 @@ __global__ void __launch_bounds__(kThreads) k_gs_phase(LevelView<T> L, int cy, i
             T sm = 0, sk = 0;
             const int i1 = i + r;                       // same-colour node at offset r
             if (i1 < mx) {
-                sm += Mx[(r + p) * mx + i] * dl[i1];
-                sk += Kx[(r + p) * mx + i] * dl[i1];
+                sm += band_m(L, i, r + P) * dl[i1];
+                sk += band_k(L, i, r + P) * dl[i1];
             }
-            if (r >= 1) {                               // and at offset r - (p+1)
-                const int o = r - P1, i2 = i + o;
-                if (i2 >= 0) {
-                    sm += Mx[(o + p) * mx + i] * dl[i2];
-                    sk += Kx[(o + p) * mx + i] * dl[i2];
-                }
+            const int i2 = i1 - P1;                     // and at offset r - (p+1)
+            if (r >= 1 && i2 >= 0) {
+                sm += band_m(L, i, r - 1) * dl[i2];
+                sk += band_k(L, i, r - 1) * dl[i2];
             }
             tm[i] += sm;
             tk[i] += sk;
@@ -214,33 +231,27 @@ __global__ void __launch_bounds__(kThreads) k_gs_phase(LevelView<T> L, int cy, i
 }
 
 // ---------------------------------------------------------------- residual
-// r = b - A x (or -A x without b; negate flips the sign) from T_M, T_K.
-template <typename T, typename R, int DIM>
+// r = b - A x (or A x without b) from T_M, T_K; optional per-row ||r||^2.
+template <typename T, typename R, int DIM, int P>
 __global__ void __launch_bounds__(kThreads) k_residual(LevelView<T> L, const T* __restrict__ b,
                                                         const T* __restrict__ TM, const T* __restrict__ TK,
-                                                        R* __restrict__ r, int negate,
-                                                        double* __restrict__ partial) {
+                                                        R* __restrict__ r, double* __restrict__ partial) {
+    constexpr int W = 2 * P + 1;
+    constexpr int NNB = (DIM == 3) ? W * W : W;
     const int mx = L.m[0], my = L.m[1];
     const int row = blockIdx.x, j = row % my, k = row / my;
     const size_t base = (size_t)row * mx;
-    __shared__ T cM[kMaxNb], cK[kMaxNb];
-    __shared__ int nrow[kMaxNb];
+    __shared__ T cM[NNB], cK[NNB];
+    __shared__ int nrow[NNB];
     __shared__ double red[kThreads / 32];
-    row_couplings<T, DIM>(L, j, k, cM, cK, nrow);
+    row_couplings<T, DIM, P>(L, j, k, cM, cK, nrow);
     __syncthreads();
-    const int w = 2 * L.p + 1, nnb = (DIM == 3) ? w * w : w;
     double ss = 0.0;
     for (int i = threadIdx.x; i < mx; i += blockDim.x) {
-        T acc = b ? b[base + i] : (T)0;
-        for (int q = 0; q < nnb; ++q) {
-            const int rr = nrow[q];
-            if (rr < 0) continue;
-            const size_t o = (size_t)rr * mx + i;
-            acc -= cM[q] * TM[o] + cK[q] * TK[o];
-        }
-        if (negate) acc = -acc;
-        r[base + i] = (R)acc;
-        ss += (double)acc * (double)acc;
+        const T ax = couple<T, NNB, -1>(cM, cK, nrow, TM, TK, mx, i);
+        const T v = b ? b[base + i] - ax : ax;
+        r[base + i] = (R)v;
+        ss += (double)v * (double)v;
     }
     if (partial) {
         const double s = block_sum(ss, red);
@@ -279,7 +290,7 @@ __global__ void k_transfer_axis(const T* __restrict__ in, T* __restrict__ out, i
 
 // Last prolongation axis fused with the correction x += P e and the x-pass:
 // one CTA per fine row; tmp holds the correction with the last axis coarse.
-template <typename T, int DIM>
+template <typename T, int DIM, int P>
 __global__ void __launch_bounds__(kThreads) k_prolong_last(LevelView<T> L, const T* __restrict__ tmp,
                                                             int n_in, const int* __restrict__ lo,
                                                             const T* __restrict__ val, int width,
@@ -287,13 +298,13 @@ __global__ void __launch_bounds__(kThreads) k_prolong_last(LevelView<T> L, const
                                                             T* __restrict__ TK) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* xs = reinterpret_cast<T*>(smem_raw);
-    const int mx = L.m[0], my = L.m[1], p = L.p;
+    const int mx = L.m[0], my = L.m[1];
     const int row = blockIdx.x, j = row % my, k = row / my;
     const int I = (DIM == 2) ? j : k;
     const size_t base = (size_t)row * mx;
     const int l = lo[I];
-    for (int ii = threadIdx.x; ii < mx + 2 * p; ii += blockDim.x) {
-        const int i = ii - p;
+    for (int ii = threadIdx.x; ii < mx + 2 * P; ii += blockDim.x) {
+        const int i = ii - P;
         T v = 0;
         if (i >= 0 && i < mx) {
             T cor = 0;
@@ -309,14 +320,13 @@ __global__ void __launch_bounds__(kThreads) k_prolong_last(LevelView<T> L, const
         xs[ii] = v;
     }
     __syncthreads();
-    const T* Mx = L.Mb[0];
-    const T* Kx = L.Kb[0];
     for (int i = threadIdx.x; i < mx; i += blockDim.x) {
         T am = 0, ak = 0;
-        for (int b = 0; b <= 2 * p; ++b) {
+#pragma unroll
+        for (int b = 0; b <= 2 * P; ++b) {
             const T xv = xs[i + b];
-            am += Mx[b * mx + i] * xv;
-            ak += Kx[b * mx + i] * xv;
+            am += band_m(L, i, b) * xv;
+            ak += band_k(L, i, b) * xv;
         }
         TM[base + i] = am;
         TK[base + i] = ak;
@@ -431,28 +441,34 @@ __global__ void __launch_bounds__(kThreads) k_gram_partial(const double* __restr
 // difference matrix Delta S = [Delta s_0 .. Delta s_q]: the R of Algorithms 3-4
 // is obtained from two Gram passes instead of a Householder QR.
 //   pass 1: G = Delta S^T Delta S; D = sqrt(diag G); Cholesky of the
-//           equilibrated G^ = D^-1 G D^-1 = R1^T R1, stopping at the first
-//           column whose pivot is below tol^2 (column dependent on the
-//           previous ones: the Krylov space is exhausted, q' = that column).
-//   pass 2: W = Delta S_a (R1 D)^-1 for the a leading independent columns,
-//           plus the raw dependent column if any; G2 = Z^T Z = R2^T R2;
-//           R^ = R2 R1 (the column-normalised R of Delta S), and for the
-//           dependent column r = R2^-T (W^T Delta s_dep) / D_dep.
-// Then RRE: R^T R d = e; MPE or a dependent column: R_q d = -r_q, d_q = 1;
-// gamma = d / sum d (with the lambda guard).
+//           equilibrated G^ = D^-1 G D^-1 = R1^T R1, truncated at the first
+//           column whose pivot is numerically zero (or whose difference is 0).
+//   pass 2: W = Delta S_a (R1 D)^-1 for the a retained columns, plus the raw
+//           next column if any; G2 = Z^T Z = R2^T R2; R^ = R2 R1 is the
+//           column-normalised R of Delta S to QR accuracy.
+// The breakdown guard reads the accurate R^: the first column i >= 1 with
+// R^_ii < 1e-6 is dependent on the previous ones (Krylov space exhausted,
+// q' = i).  Then RRE: R^T R d = e; MPE or a dependent column: R_q d = -r_q,
+// d_q = 1; gamma = d / sum d (with the lambda guard).
 __device__ void reduce_gram(int nz, const double* __restrict__ partial, int nblocks, int np, double* G) {
-    for (int c = threadIdx.x; c < nz * (nz + 1) / 2; c += blockDim.x) {
+    // one warp per Gram entry; lanes stride over the block partials in a fixed
+    // order, then a fixed shuffle tree: deterministic.
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int stride = np * (np + 1) / 2;
+    for (int c = warp; c < nz * (nz + 1) / 2; c += nw) {
         int a = 0, cc = c;
         while (cc >= nz - a) { cc -= nz - a; ++a; }
         const int bcol = a + cc;
-        // the partial layout uses the pass's full triangle of size np (q+1 columns)
-        int idx = 0;
+        int idx = 0;                                        // position in the np-column triangle
         for (int r = 0; r < a; ++r) idx += (np - r);
         idx += bcol - a;
         double s = 0.0;
-        for (int blk = 0; blk < nblocks; ++blk) s += partial[(size_t)blk * (np * (np + 1) / 2) + idx];
-        G[a * nz + bcol] = s;
-        G[bcol * nz + a] = s;
+        for (int blk = lane; blk < nblocks; blk += 32) s += partial[(size_t)blk * stride + idx];
+        s = warp_sum(s);
+        if (lane == 0) {
+            G[a * nz + bcol] = s;
+            G[bcol * nz + a] = s;
+        }
     }
 }
 
@@ -470,40 +486,44 @@ __global__ void __launch_bounds__(kThreads) k_chol1(int q, const double* __restr
     reduce_gram(n, partial, nblocks, n, G);
     __syncthreads();
     if (threadIdx.x != 0) return;
-    const double tol2 = 1e-12;                              // (1e-6)^2 on the normalised diagonal
+    const double floor2 = 1e-15;                            // numerically zero pivot of G^
     double* D = info->D;
     double* R = info->R1h;
     for (int i = 0; i < q + 2; ++i) gamma[i] = 0.0;
-    for (int i = 0; i < n; ++i) D[i] = sqrt(G[i * n + i]);
+    double Dinv[kMaxQ + 1], Rinv[kMaxQ + 1];
+    for (int i = 0; i < n; ++i) {
+        const double g = G[i * n + i];
+        Dinv[i] = g > 0.0 ? rsqrt(g) : 0.0;
+        D[i] = g * Dinv[i];
+    }
     info->done = 1;
     if (!(D[0] > 0.0)) {                                    // Delta s_0 = 0: s_0 is a fixed point
         gamma[0] = 1.0;
         *qused = 0;
         return;
     }
-    int dep = n;
-    for (int jc = 0; jc < n && dep == n; ++jc) {
+    int a = n;
+    for (int jc = 0; jc < n && a == n; ++jc) {
+        if (!(D[jc] > 0.0)) { a = jc; break; }
         for (int i = 0; i < jc; ++i) {
-            double s = (D[jc] > 0.0) ? G[i * n + jc] / (D[i] * D[jc]) : 0.0;
+            double s = G[i * n + jc] * Dinv[i] * Dinv[jc];
             for (int kk = 0; kk < i; ++kk) s -= R[kk * n + i] * R[kk * n + jc];
-            R[i * n + jc] = s / R[i * n + i];
+            R[i * n + jc] = s * Rinv[i];
         }
-        double piv = (D[jc] > 0.0) ? 1.0 : 0.0;
+        double piv = 1.0;
         for (int kk = 0; kk < jc; ++kk) piv -= R[kk * n + jc] * R[kk * n + jc];
-        if (jc >= 1 && (!(D[jc] > 0.0) || piv < tol2)) dep = jc;
-        else R[jc * n + jc] = sqrt(piv);
+        if (jc >= 1 && piv < floor2) {
+            a = jc;
+        } else {
+            Rinv[jc] = rsqrt(piv);
+            R[jc * n + jc] = piv * Rinv[jc];
+        }
     }
-    if (dep < n && !(D[dep] > 0.0)) {                       // zero difference: s_dep is a fixed point
-        gamma[dep] = 1.0;
-        *qused = dep;
-        return;
-    }
-    const int a = dep < n ? dep : n;
     for (int i = 0; i < a; ++i)
         for (int j = i; j < a; ++j) info->R1p[i * n + j] = R[i * n + j] * D[j];
-    for (int j = 0; j < a; ++j) info->R1pinv[j] = 1.0 / info->R1p[j * n + j];
+    for (int j = 0; j < a; ++j) info->R1pinv[j] = Rinv[j] * Dinv[j];
     info->a = a;
-    info->dep = dep;
+    info->dep = a;                                          // pass 2 adds raw column a when a < n
     info->done = 0;
 }
 
@@ -533,7 +553,7 @@ __global__ void __launch_bounds__(kThreads) k_gram2_partial(const double* __rest
             double v = dj;
 #pragma unroll
             for (int i = 0; i < j; ++i) v -= z[i] * Rp[i * NC + j];
-            z[j] = (j < a) ? v * Rinv[j] : (j == dep ? dj : 0.0);
+            z[j] = (j < a) ? v * Rinv[j] : (j == dep ? dj : 0.0);   // dep == a here
         }
         int c = 0;
 #pragma unroll
@@ -561,26 +581,30 @@ __global__ void __launch_bounds__(kThreads) k_gamma2(int q, int method, const do
                                                       double* __restrict__ gamma, int* __restrict__ qused) {
     if (info->done) return;
     const int n = q + 1;
-    const int a = info->a, dep = info->dep, nz = a + (dep < n ? 1 : 0);
+    const int a = info->a, nz = a + (a < n ? 1 : 0);
     __shared__ double G2[(kMaxQ + 1) * (kMaxQ + 1)];
     reduce_gram(nz, partial, nblocks, n, G2);
     __syncthreads();
     if (threadIdx.x != 0) return;
+    const double tol = 1e-6;                                // breakdown guard on R^_ii
     const double* D = info->D;
     const double* R1 = info->R1h;
     double R2[(kMaxQ + 1) * (kMaxQ + 1)], Rh[(kMaxQ + 1) * (kMaxQ + 1)], d[kMaxQ + 2], y[kMaxQ + 1];
+    double R2inv[kMaxQ + 1], Rhinv[kMaxQ + 1], Dinv[kMaxQ + 1];
     for (int i = 0; i < q + 2; ++i) gamma[i] = 0.0;
+    for (int i = 0; i < n; ++i) Dinv[i] = D[i] > 0.0 ? 1.0 / D[i] : 0.0;
     // R2 = chol(G2[0:a, 0:a]) (upper, R2^T R2 = G2)
     for (int j = 0; j < a; ++j) {
         for (int i = 0; i < j; ++i) {
             double s = G2[i * nz + j];
             for (int kk = 0; kk < i; ++kk) s -= R2[kk * n + i] * R2[kk * n + j];
-            R2[i * n + j] = s / R2[i * n + i];
+            R2[i * n + j] = s * R2inv[i];
         }
         double piv = G2[j * nz + j];
         for (int kk = 0; kk < j; ++kk) piv -= R2[kk * n + j] * R2[kk * n + j];
         if (!(piv > 0.0)) { set_fallback(q, gamma, qused); return; }
-        R2[j * n + j] = sqrt(piv);
+        R2inv[j] = rsqrt(piv);
+        R2[j * n + j] = piv * R2inv[j];
     }
     // R^ = R2 R1 (upper triangular product, a x a)
     for (int i = 0; i < a; ++i)
@@ -589,51 +613,60 @@ __global__ void __launch_bounds__(kThreads) k_gamma2(int q, int method, const do
             for (int kk = i; kk <= j; ++kk) s += R2[i * n + kk] * R1[kk * n + j];
             Rh[i * n + j] = s;
         }
+    for (int i = 0; i < a; ++i) Rhinv[i] = 1.0 / Rh[i * n + i];
+    int dep = n;
+    for (int j = 1; j < a && dep == n; ++j)
+        if (Rh[j * n + j] < tol) dep = j;
+    if (dep == n && a < n) {
+        dep = a;
+        if (!(D[a] > 0.0)) {                                // zero difference: s_a is a fixed point
+            gamma[a] = 1.0;
+            *qused = a;
+            return;
+        }
+    }
     int qq;
     if (dep < n || method == 2) {
         double r[kMaxQ + 1];
-        int na;
-        if (dep < n) {                                      // r = R2^-T (W^T Delta s_dep) / D_dep
-            qq = dep;
-            na = a;
+        qq = dep < n ? dep : q;
+        if (dep < n && dep == a) {                          // raw column: r = R2^-T (W^T Delta s_a) / D_a
             for (int i = 0; i < a; ++i) {
                 double s = G2[i * nz + a];
                 for (int kk = 0; kk < i; ++kk) s -= R2[kk * n + i] * r[kk];
-                r[i] = s / R2[i * n + i];
+                r[i] = s * R2inv[i];
             }
-            for (int i = 0; i < a; ++i) r[i] /= D[dep];
-        } else {                                            // MPE: r_q = R^[0:q, q]
-            qq = q;
-            na = q;
-            for (int i = 0; i < q; ++i) r[i] = Rh[i * n + q];
+            for (int i = 0; i < a; ++i) r[i] *= Dinv[a];
+        } else {                                            // r_qq = R^[0:qq, qq]
+            for (int i = 0; i < qq; ++i) r[i] = Rh[i * n + qq];
         }
-        for (int i = na - 1; i >= 0; --i) {                 // R^_qq y = -r
+        for (int i = qq - 1; i >= 0; --i) {                 // R^_qq y = -r
             double s = -r[i];
-            for (int kk = i + 1; kk < na; ++kk) s -= Rh[i * n + kk] * y[kk];
-            y[i] = s / Rh[i * n + i];
+            for (int kk = i + 1; kk < qq; ++kk) s -= Rh[i * n + kk] * y[kk];
+            y[i] = s * Rhinv[i];
         }
-        for (int i = 0; i < na; ++i) d[i] = y[i] / D[i];
-        d[qq] = 1.0 / D[qq];
+        for (int i = 0; i < qq; ++i) d[i] = y[i] * Dinv[i];
+        d[qq] = Dinv[qq];
     } else {                                                // RRE: R^T R^ z = D^-1 e, d = z / D
         qq = q;
         double z[kMaxQ + 1];
         for (int i = 0; i < n; ++i) {
-            double s = 1.0 / D[i];
+            double s = Dinv[i];
             for (int kk = 0; kk < i; ++kk) s -= Rh[kk * n + i] * z[kk];
-            z[i] = s / Rh[i * n + i];
+            z[i] = s * Rhinv[i];
         }
         for (int i = n - 1; i >= 0; --i) {
             double s = z[i];
             for (int kk = i + 1; kk < n; ++kk) s -= Rh[i * n + kk] * z[kk];
-            z[i] = s / Rh[i * n + i];
+            z[i] = s * Rhinv[i];
         }
-        for (int i = 0; i < n; ++i) d[i] = z[i] / D[i];
+        for (int i = 0; i < n; ++i) d[i] = z[i] * Dinv[i];
     }
     double lam = 0.0, asum = 0.0;
     for (int i = 0; i <= qq; ++i) { lam += d[i]; asum += fabs(d[i]); }
     bool ok = isfinite(lam) && fabs(lam) > 1e-12 * asum;
+    const double laminv = ok ? 1.0 / lam : 0.0;
     for (int i = 0; i <= qq && ok; ++i) {
-        gamma[i] = d[i] / lam;
+        gamma[i] = d[i] * laminv;
         ok = isfinite(gamma[i]);
     }
     if (!ok) { set_fallback(q, gamma, qused); return; }
@@ -698,12 +731,30 @@ static void set_smem(K kernel, size_t bytes) {
     if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// run f(integral_constant<int, P>) for the runtime degree p in [1, kMaxP]
+template <typename F>
+static void with_p(int p, F&& f) {
+    switch (p) {
+        case 1: f(std::integral_constant<int, 1>()); break;
+        case 2: f(std::integral_constant<int, 2>()); break;
+        case 3: f(std::integral_constant<int, 3>()); break;
+        case 4: f(std::integral_constant<int, 4>()); break;
+        case 5: f(std::integral_constant<int, 5>()); break;
+        case 6: f(std::integral_constant<int, 6>()); break;
+        case 7: f(std::integral_constant<int, 7>()); break;
+        default: break;
+    }
+}
+
 template <typename T, typename A>
 void xpass(cudaStream_t s, const LevelView<T>& L, const T* x, T* x_out, const A* add, int nS,
            const double* gamma, const T* S, size_t ldS, T* TM, T* TK) {
     const size_t smem = (size_t)(L.m[0] + 2 * L.p) * sizeof(T);
-    set_smem(k_xpass<T, A>, smem);
-    k_xpass<T, A><<<L.rows(), kThreads, smem, s>>>(L, x, x_out, add, nS, gamma, S, ldS, TM, TK);
+    with_p(L.p, [&](auto PC) {
+        constexpr int P = decltype(PC)::value;
+        set_smem(k_xpass<T, A, P>, smem);
+        k_xpass<T, A, P><<<L.rows(), kThreads, smem, s>>>(L, x, x_out, add, nS, gamma, S, ldS, TM, TK);
+    });
     count_launch();
 }
 
@@ -716,13 +767,16 @@ void gs_sweep(cudaStream_t s, int dim, const LevelView<T>& L, bool descending, T
         const int nty = (L.m[1] - cy + p) / P1;
         const int ntz = (dim == 3) ? (L.m[2] - cz + p) / P1 : 1;
         if (nty <= 0 || ntz <= 0) return;
-        if (dim == 2) {
-            set_smem(k_gs_phase<T, 2>, smem);
-            k_gs_phase<T, 2><<<nty * ntz, kThreads, smem, s>>>(L, cy, cz, descending, x, b, TM, TK);
-        } else {
-            set_smem(k_gs_phase<T, 3>, smem);
-            k_gs_phase<T, 3><<<nty * ntz, kThreads, smem, s>>>(L, cy, cz, descending, x, b, TM, TK);
-        }
+        with_p(p, [&](auto PC) {
+            constexpr int P = decltype(PC)::value;
+            if (dim == 2) {
+                set_smem(k_gs_phase<T, 2, P>, smem);
+                k_gs_phase<T, 2, P><<<nty * ntz, kThreads, smem, s>>>(L, cy, cz, descending, x, b, TM, TK);
+            } else {
+                set_smem(k_gs_phase<T, 3, P>, smem);
+                k_gs_phase<T, 3, P><<<nty * ntz, kThreads, smem, s>>>(L, cy, cz, descending, x, b, TM, TK);
+            }
+        });
         count_launch();
     };
     const int ncz = (dim == 3) ? P1 : 1;
@@ -735,53 +789,59 @@ void gs_sweep(cudaStream_t s, int dim, const LevelView<T>& L, bool descending, T
 template <typename T, typename R>
 void residual(cudaStream_t s, int dim, const LevelView<T>& L, const T* b, const T* TM, const T* TK,
               R* r, double* partial) {
-    if (dim == 2) k_residual<T, R, 2><<<L.rows(), kThreads, 0, s>>>(L, b, TM, TK, r, b ? 0 : 1, partial);
-    else k_residual<T, R, 3><<<L.rows(), kThreads, 0, s>>>(L, b, TM, TK, r, b ? 0 : 1, partial);
+    with_p(L.p, [&](auto PC) {
+        constexpr int P = decltype(PC)::value;
+        if (dim == 2) k_residual<T, R, 2, P><<<L.rows(), kThreads, 0, s>>>(L, b, TM, TK, r, partial);
+        else k_residual<T, R, 3, P><<<L.rows(), kThreads, 0, s>>>(L, b, TM, TK, r, partial);
+    });
     count_launch();
 }
 
 template <typename T>
-void restrict_(cudaStream_t s, int dim, const TransferView<T>& P, const T* fine, T* coarse, T* tmp1,
+void restrict_(cudaStream_t s, int dim, const TransferView<T>& X, const T* fine, T* coarse, T* tmp1,
                T* tmp2) {
     // axis by axis: x, then y (then z); dims shrink one axis at a time
-    int d[3] = {P.mf[0], P.mf[1], dim == 3 ? P.mf[2] : 1};
+    int d[3] = {X.mf[0], X.mf[1], dim == 3 ? X.mf[2] : 1};
     const T* in = fine;
     for (int a = 0; a < dim; ++a) {
         const int n_in = d[a];
-        d[a] = P.mc[a];
+        d[a] = X.mc[a];
         T* out = (a == dim - 1) ? coarse : (a == 0 ? tmp1 : tmp2);
         const size_t total = (size_t)d[0] * d[1] * d[2];
         k_transfer_axis<T><<<grid_for(total), kThreads, 0, s>>>(in, out, d[0], d[1], d[2], a, n_in,
-                                                                P.rlo[a], P.rv[a], P.rw[a]);
+                                                                X.rlo[a], X.rv[a], X.rw[a]);
         count_launch();
         in = out;
     }
 }
 
 template <typename T>
-void prolong_add(cudaStream_t s, int dim, const TransferView<T>& P, const LevelView<T>& Lf, const T* e,
+void prolong_add(cudaStream_t s, int dim, const TransferView<T>& X, const LevelView<T>& Lf, const T* e,
                  T* x, T* TM, T* TK, T* tmp1, T* tmp2) {
-    int d[3] = {P.mc[0], P.mc[1], dim == 3 ? P.mc[2] : 1};
+    int d[3] = {X.mc[0], X.mc[1], dim == 3 ? X.mc[2] : 1};
     const T* in = e;
     for (int a = 0; a < dim - 1; ++a) {
         const int n_in = d[a];
-        d[a] = P.mf[a];
+        d[a] = X.mf[a];
         T* out = (a == 0) ? tmp1 : tmp2;
         const size_t total = (size_t)d[0] * d[1] * d[2];
         k_transfer_axis<T><<<grid_for(total), kThreads, 0, s>>>(in, out, d[0], d[1], d[2], a, n_in,
-                                                                P.plo[a], P.pv[a], P.pw[a]);
+                                                                X.plo[a], X.pv[a], X.pw[a]);
         count_launch();
         in = out;
     }
     const int a = dim - 1;
     const size_t smem = (size_t)(Lf.m[0] + 2 * Lf.p) * sizeof(T);
-    if (dim == 2) {
-        set_smem(k_prolong_last<T, 2>, smem);
-        k_prolong_last<T, 2><<<Lf.rows(), kThreads, smem, s>>>(Lf, in, P.mc[a], P.plo[a], P.pv[a], P.pw[a], x, TM, TK);
-    } else {
-        set_smem(k_prolong_last<T, 3>, smem);
-        k_prolong_last<T, 3><<<Lf.rows(), kThreads, smem, s>>>(Lf, in, P.mc[a], P.plo[a], P.pv[a], P.pw[a], x, TM, TK);
-    }
+    with_p(Lf.p, [&](auto PC) {
+        constexpr int P = decltype(PC)::value;
+        if (dim == 2) {
+            set_smem(k_prolong_last<T, 2, P>, smem);
+            k_prolong_last<T, 2, P><<<Lf.rows(), kThreads, smem, s>>>(Lf, in, X.mc[a], X.plo[a], X.pv[a], X.pw[a], x, TM, TK);
+        } else {
+            set_smem(k_prolong_last<T, 3, P>, smem);
+            k_prolong_last<T, 3, P><<<Lf.rows(), kThreads, smem, s>>>(Lf, in, X.mc[a], X.plo[a], X.pv[a], X.pw[a], x, TM, TK);
+        }
+    });
     count_launch();
 }
 
