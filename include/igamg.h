@@ -109,7 +109,7 @@ igamg_status igamg_rhs_sine(igamg_ctx* ctx, int modes, const double* h_coeffs, d
  * (Algorithm 3) or MPE (Algorithm 4) through the Gram matrix of the
  * differences, and stops when ||b - A t|| / ||b|| <= tol (or the absolute test
  * with IGAMG_FLAG_ABS_TOL); else s_0 := t.  With IGAMG_EXTRAP_NONE each cycle
- * is a single V-cycle and k is ignored.  k in [1, 16].
+ * is a single V-cycle and k is ignored.  k in [1, 12].
  * d_b: finest right-hand side (read only).  d_x: solution (written; read as
  * s_0 with IGAMG_FLAG_X0_GIVEN).  h_hist (may be NULL) receives max_cycles+1
  * relative residuals: entry 0 for s_0, entry c after cycle c.  h_cycles and
