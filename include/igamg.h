@@ -159,6 +159,23 @@ igamg_status igamg_extrapolate(long n, int q, int method, const double* d_S, lon
                                double* d_t, double* h_gamma, int* h_qused,
                                void* d_ws, size_t ws_bytes, void* stream);
 
+/* Allocation-free igamg_extrapolate, for callers that cannot allocate device
+ * memory where they extrapolate (a host framework that owns all device
+ * allocations and forbids cudaMalloc on its hot path, since cudaMalloc can
+ * block the device and fail on fragmented memory; code under a fixed memory
+ * budget with no allocator to hand scratch through).  The paper has no
+ * counterpart: this is an interface variant only; the arithmetic is that of
+ * igamg_extrapolate.
+ * Scratch is a 240 KiB array built into the library, resident on every GPU
+ * that loads it until the process exits; every restart number q in [1, 12]
+ * fits (larger requests return EINVAL).  The first call on a device looks up
+ * the array's device address, so make it before any stream capture.  All
+ * calls share the array: calls whose GPU work overlaps (e.g. on two streams)
+ * race and must be serialised.  Arguments and results are those of
+ * igamg_extrapolate without (d_ws, ws_bytes); synchronises `stream`. */
+igamg_status igamg_extrapolate_noalloc(long n, int q, int method, const double* d_S, long ld,
+                                       double* d_t, double* h_gamma, int* h_qused, void* stream);
+
 /* ---------------------------------------------------------------- misc */
 
 void igamg_destroy(igamg_ctx* ctx);

@@ -59,6 +59,7 @@ def _load():
         "igamg_vcycle": (c_int, [vp, vp, vp, c_int, vp, c_size, vp]),
         "igamg_extrap_workspace_bytes": (c_size, [c_long, c_int]),
         "igamg_extrapolate": (c_int, [c_long, c_int, c_int, vp, c_long, vp, dp, ip, vp, c_size, vp]),
+        "igamg_extrapolate_noalloc": (c_int, [c_long, c_int, c_int, vp, c_long, vp, dp, ip, vp]),
         "igamg_destroy": (None, [vp]),
         "igamg_status_str": (ctypes.c_char_p, [c_int]),
         "igamg_last_error": (ctypes.c_char_p, []),
@@ -191,6 +192,16 @@ def igamg_extrapolate(n, q, method, S, ld, t, ws, stream=None):
     qused = ctypes.c_int()
     _check(_load().igamg_extrapolate(n, q, method, _ptr(S), ld, _ptr(t), _dbl(gamma), ctypes.byref(qused),
                                      _ptr(ws), ws.numel(), _stream(stream)), "igamg_extrapolate")
+    return gamma, qused.value
+
+
+def igamg_extrapolate_noalloc(n, q, method, S, ld, t, stream=None):
+    """igamg_extrapolate with the library's built-in scratch (no workspace)."""
+    import numpy as np
+    gamma = np.zeros(q + 2)
+    qused = ctypes.c_int()
+    _check(_load().igamg_extrapolate_noalloc(n, q, method, _ptr(S), ld, _ptr(t), _dbl(gamma),
+                                             ctypes.byref(qused), _stream(stream)), "igamg_extrapolate_noalloc")
     return gamma, qused.value
 
 

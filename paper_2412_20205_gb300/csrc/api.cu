@@ -86,6 +86,8 @@ struct Workspace {
 
 }  // namespace
 
+void igamg::set_last_error(const char* msg) { g_err = msg; }
+
 struct igamg_ctx {
     int dim = 2, p = 1, L = 1;
     std::vector<HostLevel> hl;

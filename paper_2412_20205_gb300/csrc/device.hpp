@@ -1,6 +1,7 @@
 // Device-side views and kernel launch wrappers (internal; not part of the C ABI).
 #pragma once
 #include <cstddef>
+#include <string>
 #include <cuda_runtime.h>
 
 namespace igamg {
@@ -56,6 +57,10 @@ struct ExtrapInfo {
     double R1p[(kMaxQ + 1) * (kMaxQ + 1)];
     double R1pinv[kMaxQ + 1];
 };
+
+// Sets the message returned by igamg_last_error() on this thread.
+void set_last_error(const char* msg);
+inline void set_last_error(const std::string& msg) { set_last_error(msg.c_str()); }
 
 // Launch accounting (kernels enqueued by this thread).
 void count_launch(long long n = 1);
