@@ -434,7 +434,7 @@ igamg_status igamg_setup(int dim, int p, const int* n_elems, int n_levels, igamg
                 }
             }
         }
-        if (c->hl.back().m[0] > 5000) { delete c; return fail(IGAMG_EINVAL, "row length above 5000"); }
+        if (c->hl.back().m[0] > 4500) { delete c; return fail(IGAMG_EINVAL, "row length above 4500"); }
         const HostLevel& H0 = c->hl[0];
         const size_t N0 = H0.N();
         if (N0 > 12000) { delete c; return fail(IGAMG_EINVAL, "coarsest grid too large for the direct solve"); }
@@ -561,6 +561,7 @@ igamg_status igamg_assemble(igamg_ctx* c) {
         cLo[0] = add(c->claminv.data(), c->claminv.size() * 8);
         cLo[1] = add(f.data(), f.size() * 4);
     }
+    dev::prepare_kernels();
     void* dm = nullptr;
     if (cudaMalloc(&dm, total) != cudaSuccess) {
         cudaGetLastError();
@@ -597,16 +598,19 @@ igamg_status igamg_assemble(igamg_ctx* c) {
         }
         a.invdiag = (const double*)(base + lo[l].inv[0]);
         f.invdiag = (const float*)(base + lo[l].inv[1]);
-        {
+        for (int d = 0; d < 3; ++d) {
+            a.tlo[d] = f.tlo[d] = 0;
+            a.thi[d] = f.thi[d] = 0;
+            for (int b = 0; b < 2 * kMaxP + 1; ++b) a.Mc[d][b] = a.Kc[d][b] = f.Mc[d][b] = f.Kc[d][b] = 0;
+            if (d >= dim) continue;
             int tl = 0, th = 0;
-            const int mid = toeplitz_range(H.f[0], &tl, &th), bw = 2 * p + 1;
-            a.tlo = f.tlo = tl;
-            a.thi = f.thi = th;
-            for (int b = 0; b < 2 * kMaxP + 1; ++b) {
-                const double mv = b < bw ? H.f[0].M[(size_t)mid * bw + b] : 0.0;
-                const double kv = b < bw ? H.f[0].K[(size_t)mid * bw + b] : 0.0;
-                a.Mc[b] = mv; a.Kc[b] = kv;
-                f.Mc[b] = (float)mv; f.Kc[b] = (float)kv;
+            const int mid = toeplitz_range(H.f[d], &tl, &th), bw = 2 * p + 1;
+            a.tlo[d] = f.tlo[d] = tl;
+            a.thi[d] = f.thi[d] = th;
+            for (int b = 0; b < bw; ++b) {
+                const double mv = H.f[d].M[(size_t)mid * bw + b], kv = H.f[d].K[(size_t)mid * bw + b];
+                a.Mc[d][b] = mv; a.Kc[d][b] = kv;
+                f.Mc[d][b] = (float)mv; f.Kc[d][b] = (float)kv;
             }
         }
         TransferView<double>& t = c->tv64[l];

@@ -4,6 +4,12 @@
 #include <string>
 #include <cuda_runtime.h>
 
+#ifdef __CUDACC__
+#define IGAMG_HD __host__ __device__
+#else
+#define IGAMG_HD
+#endif
+
 namespace igamg {
 
 constexpr int kMaxP = 7;
@@ -19,12 +25,13 @@ struct LevelView {
     const T* Mb[3];
     const T* Kb[3];
     const T* invdiag;                     // 1 / A_ii
-    // x-direction rows i in [tlo, thi) share one band (uniform interior of an
-    // open knot vector); the kernels read it from here instead of Mb/Kb[0].
-    int tlo, thi;
-    T Mc[2 * kMaxP + 1], Kc[2 * kMaxP + 1];
-    size_t n() const { return (size_t)m[0] * m[1] * m[2]; }
-    int rows() const { return m[1] * m[2]; }
+    // per direction d, rows i in [tlo[d], thi[d]) share one band (the uniform
+    // interior of an open knot vector); kernels read it from these parameters
+    // instead of Mb/Kb[d].
+    int tlo[3], thi[3];
+    T Mc[3][2 * kMaxP + 1], Kc[3][2 * kMaxP + 1];
+    IGAMG_HD size_t n() const { return (size_t)m[0] * m[1] * m[2]; }
+    IGAMG_HD int rows() const { return m[1] * m[2]; }
 };
 
 // 1D transfer between a fine level and the next coarser one, direction d.
@@ -67,6 +74,10 @@ void count_launch(long long n = 1);
 long long launch_count();
 
 namespace dev {
+
+// Raise every kernel's dynamic shared-memory limit on the current device
+// (once per device; must run outside stream capture).
+void prepare_kernels();
 
 // T_M = (I (x) M_x) x, T_K = (I (x) K_x) x row by row.  With add != nullptr the
 // row is first replaced by x + add (written to x_out), with nS > 0 by

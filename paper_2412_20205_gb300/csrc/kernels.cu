@@ -53,11 +53,20 @@ __device__ T block_sum(T v, T* red) {
 // kernel parameters, the p boundary rows at each end from the band arrays.
 template <typename T>
 __device__ __forceinline__ T band_m(const LevelView<T>& L, int i, int b) {
-    return (i >= L.tlo && i < L.thi) ? L.Mc[b] : L.Mb[0][b * L.m[0] + i];
+    return (i >= L.tlo[0] && i < L.thi[0]) ? L.Mc[0][b] : L.Mb[0][b * L.m[0] + i];
 }
 template <typename T>
 __device__ __forceinline__ T band_k(const LevelView<T>& L, int i, int b) {
-    return (i >= L.tlo && i < L.thi) ? L.Kc[b] : L.Kb[0][b * L.m[0] + i];
+    return (i >= L.tlo[0] && i < L.thi[0]) ? L.Kc[0][b] : L.Kb[0][b * L.m[0] + i];
+}
+// band entry of direction d (row i, band b) for d = 1, 2
+template <typename T>
+__device__ __forceinline__ T band_md(const LevelView<T>& L, int d, int i, int b) {
+    return (i >= L.tlo[d] && i < L.thi[d]) ? L.Mc[d][b] : L.Mb[d][b * L.m[d] + i];
+}
+template <typename T>
+__device__ __forceinline__ T band_kd(const LevelView<T>& L, int d, int i, int b) {
+    return (i >= L.tlo[d] && i < L.thi[d]) ? L.Kc[d][b] : L.Kb[d][b * L.m[d] + i];
 }
 
 // Row-coupling coefficients of row (j, k): for neighbour q = (dj, dk) the
@@ -74,12 +83,12 @@ __device__ void row_couplings(const LevelView<T>& L, int j, int k, T* cM, T* cK,
         const bool ok = jj >= 0 && jj < my && kk >= 0 && kk < mz;
         T a = 0, c = 0;
         if (ok) {
-            const T myv = L.Mb[1][(dj + P) * my + j], kyv = L.Kb[1][(dj + P) * my + j];
+            const T myv = band_md(L, 1, j, dj + P), kyv = band_kd(L, 1, j, dj + P);
             if (DIM == 2) {
                 a = kyv;
                 c = myv;
             } else {
-                const T mzv = L.Mb[2][(dk + P) * mz + k], kzv = L.Kb[2][(dk + P) * mz + k];
+                const T mzv = band_md(L, 2, k, dk + P), kzv = band_kd(L, 2, k, dk + P);
                 a = kzv * myv + mzv * kyv;
                 c = mzv * myv;
             }
@@ -95,7 +104,8 @@ template <typename T, int NNB, int SKIP>
 __device__ __forceinline__ T couple(const T* cM, const T* cK, const int* nrow, const T* __restrict__ TM,
                                     const T* __restrict__ TK, int mx, int i) {
     T acc = 0;
-#pragma unroll
+    constexpr int U = NNB > 49 ? 9 : NNB;       // bound the loads kept in flight (3D, p >= 4)
+#pragma unroll U
     for (int q = 0; q < NNB; ++q) {
         if (q == SKIP) continue;
         const size_t o = (size_t)nrow[q] * mx + i;
@@ -163,10 +173,47 @@ __global__ void __launch_bounds__(kThreads) k_xpass(LevelView<T> L, const T* __r
 // multicolour sweep with the frozen off-row part F = sum_{row' != row}
 // (cM T_M + cK T_K).  The row's own T_M, T_K are updated incrementally from
 // the corrections of each colour, so a full sweep costs about one apply.
+//
+// Latency layout: one CTA per target row with enough threads to cover the row
+// in one pass; every global load of the phase (neighbour T rows, own T, x, b,
+// inverse diagonal, boundary band entries) is issued in one round, and the
+// p+1 colour steps then touch shared memory only.  Row couplings and the
+// interior x-band come from kernel parameters.
+constexpr int kBandCols = 8 * kMaxP;            // staged non-uniform x-band columns
+
+template <typename T, int P>
+struct RowBand {
+    // x-band entry (row i, band b): parameters in the uniform interior, the
+    // staged table for up to kBandCols boundary columns, memory otherwise
+    const LevelView<T>& L;
+    const T* bm;
+    const T* bk;
+    int nb;
+    __device__ __forceinline__ int slot(int i) const {
+        if (i < L.tlo[0]) return i;
+        return L.tlo[0] + (i - L.thi[0]);
+    }
+    __device__ __forceinline__ T m(int i, int b) const {
+        if (i >= L.tlo[0] && i < L.thi[0]) return L.Mc[0][b];
+        if (nb <= kBandCols) return bm[slot(i) * (2 * P + 1) + b];
+        return L.Mb[0][b * L.m[0] + i];
+    }
+    __device__ __forceinline__ T k(int i, int b) const {
+        if (i >= L.tlo[0] && i < L.thi[0]) return L.Kc[0][b];
+        if (nb <= kBandCols) return bk[slot(i) * (2 * P + 1) + b];
+        return L.Kb[0][b * L.m[0] + i];
+    }
+};
+
+// largest CTA of the row kernels: 3D rows couple to (2p+1)^2 - 1 neighbour
+// rows whose loads are kept in flight together, FP64 needs twice the registers
+template <typename T, int DIM>
+constexpr int row_cta_max() { return DIM == 3 ? 256 : (sizeof(T) == 8 ? 512 : 1024); }
+
 template <typename T, int DIM, int P>
-__global__ void __launch_bounds__(kThreads) k_gs_phase(LevelView<T> L, int cy, int cz, int descending,
-                                                        T* __restrict__ x, const T* __restrict__ b,
-                                                        T* __restrict__ TM, T* __restrict__ TK) {
+__global__ void __launch_bounds__(row_cta_max<T, DIM>()) k_gs_phase(LevelView<T> L, int cy, int cz, int descending,
+                                                    T* __restrict__ x, const T* __restrict__ b,
+                                                    T* __restrict__ TM, T* __restrict__ TK) {
     constexpr int P1 = P + 1, W = 2 * P + 1;
     constexpr int NNB = (DIM == 3) ? W * W : W;
     constexpr int OWN = (DIM == 3) ? P * W + P : P;
@@ -182,24 +229,35 @@ __global__ void __launch_bounds__(kThreads) k_gs_phase(LevelView<T> L, int cy, i
     T* tk = tm + mx;
     T* dl = tk + mx;
     T* xs = dl + mx;
+    T* dv = xs + mx;
     __shared__ T cM[NNB], cK[NNB];
     __shared__ int nrow[NNB];
+    __shared__ T bm[kBandCols * W], bk[kBandCols * W];
     row_couplings<T, DIM, P>(L, j, k, cM, cK, nrow);
+    const int nb = L.tlo[0] + (mx - L.thi[0]);
+    if (nb <= kBandCols)
+        for (int t = threadIdx.x; t < nb * W; t += blockDim.x) {
+            const int sl = t / W, bb = t % W;
+            const int i = sl < L.tlo[0] ? sl : L.thi[0] + (sl - L.tlo[0]);
+            bm[t] = L.Mb[0][bb * mx + i];
+            bk[t] = L.Kb[0][bb * mx + i];
+        }
     __syncthreads();
     for (int i = threadIdx.x; i < mx; i += blockDim.x) {
         rhs[i] = b[base + i] - couple<T, NNB, OWN>(cM, cK, nrow, TM, TK, mx, i);
         tm[i] = TM[base + i];
         tk[i] = TK[base + i];
         xs[i] = x[base + i];
+        dv[i] = L.invdiag[base + i];
     }
     __syncthreads();
+    const RowBand<T, P> band{L, bm, bk, nb};
     const T am = cM[OWN], ak = cK[OWN];
-    const T* dinv = L.invdiag + base;
 #pragma unroll
     for (int c = 0; c < P1; ++c) {
         const int cx = descending ? P - c : c;
         for (int i = cx + P1 * (int)threadIdx.x; i < mx; i += P1 * (int)blockDim.x) {
-            const T d = (rhs[i] - (am * tm[i] + ak * tk[i])) * dinv[i];
+            const T d = (rhs[i] - (am * tm[i] + ak * tk[i])) * dv[i];
             xs[i] += d;
             dl[i] = d;
         }
@@ -210,13 +268,15 @@ __global__ void __launch_bounds__(kThreads) k_gs_phase(LevelView<T> L, int cy, i
             T sm = 0, sk = 0;
             const int i1 = i + r;                       // same-colour node at offset r
             if (i1 < mx) {
-                sm += band_m(L, i, r + P) * dl[i1];
-                sk += band_k(L, i, r + P) * dl[i1];
+                const T d1 = dl[i1];
+                sm += band.m(i, r + P) * d1;
+                sk += band.k(i, r + P) * d1;
             }
             const int i2 = i1 - P1;                     // and at offset r - (p+1)
             if (r >= 1 && i2 >= 0) {
-                sm += band_m(L, i, r - 1) * dl[i2];
-                sk += band_k(L, i, r - 1) * dl[i2];
+                const T d2 = dl[i2];
+                sm += band.m(i, r - 1) * d2;
+                sk += band.k(i, r - 1) * d2;
             }
             tm[i] += sm;
             tk[i] += sk;
@@ -726,9 +786,11 @@ static int grid_for(size_t n, int per = kThreads) {
     return (int)(g < 1 ? 1 : g);
 }
 
-template <typename K>
-static void set_smem(K kernel, size_t bytes) {
-    if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+// threads for a CTA that owns one row of length mx: the whole row in one pass
+// where the kernel's register budget allows
+static int row_threads(int mx, int cap) {
+    int t = ((mx + 31) / 32) * 32;
+    return t < 64 ? 64 : (t > cap ? cap : t);
 }
 
 // run f(integral_constant<int, P>) for the runtime degree p in [1, kMaxP]
@@ -744,6 +806,47 @@ static void with_p(int p, F&& f) {
         case 7: f(std::integral_constant<int, 7>()); break;
         default: break;
     }
+}
+
+// Dynamic shared-memory limits are raised once per device by prepare_kernels()
+// (cudaFuncSetAttribute is not allowed while a stream is being captured).
+template <typename K>
+static void set_smem(K, size_t) {}
+
+template <typename K>
+static void raise_smem(K kernel, int optin) {
+    // the opt-in limit covers static plus dynamic shared memory
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return;
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
+
+void prepare_kernels() {
+    int dev = 0, optin = 48 * 1024;
+    cudaGetDevice(&dev);
+    static bool done[64] = {};
+    if (dev < 0 || dev >= 64 || done[dev]) return;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    auto all_p = [&](auto T_tag) {
+        using T = decltype(T_tag);
+        for (int p = 1; p <= kMaxP; ++p)
+            with_p(p, [&](auto PC) {
+                constexpr int P = decltype(PC)::value;
+                raise_smem(k_xpass<T, T, P>, optin);
+                raise_smem(k_gs_phase<T, 2, P>, optin);
+                raise_smem(k_gs_phase<T, 3, P>, optin);
+                raise_smem(k_prolong_last<T, 2, P>, optin);
+                raise_smem(k_prolong_last<T, 3, P>, optin);
+            });
+        raise_smem(k_coarse_fd<T, 2>, optin);
+        raise_smem(k_coarse_fd<T, 3>, optin);
+    };
+    all_p(0.0);
+    all_p(0.0f);
+    for (int p = 1; p <= kMaxP; ++p)
+        with_p(p, [&](auto PC) { raise_smem(k_xpass<double, float, decltype(PC)::value>, optin); });
+    cudaGetLastError();
+    done[dev] = true;
 }
 
 template <typename T, typename A>
@@ -762,7 +865,8 @@ template <typename T>
 void gs_sweep(cudaStream_t s, int dim, const LevelView<T>& L, bool descending, T* x, const T* b,
               T* TM, T* TK) {
     const int p = L.p, P1 = p + 1;
-    const size_t smem = (size_t)5 * L.m[0] * sizeof(T);
+    const size_t smem = (size_t)6 * L.m[0] * sizeof(T);
+    const int threads = row_threads(L.m[0], dim == 3 ? row_cta_max<T, 3>() : row_cta_max<T, 2>());
     auto launch = [&](int cy, int cz) {
         const int nty = (L.m[1] - cy + p) / P1;
         const int ntz = (dim == 3) ? (L.m[2] - cz + p) / P1 : 1;
@@ -771,10 +875,10 @@ void gs_sweep(cudaStream_t s, int dim, const LevelView<T>& L, bool descending, T
             constexpr int P = decltype(PC)::value;
             if (dim == 2) {
                 set_smem(k_gs_phase<T, 2, P>, smem);
-                k_gs_phase<T, 2, P><<<nty * ntz, kThreads, smem, s>>>(L, cy, cz, descending, x, b, TM, TK);
+                k_gs_phase<T, 2, P><<<nty * ntz, threads, smem, s>>>(L, cy, cz, descending, x, b, TM, TK);
             } else {
                 set_smem(k_gs_phase<T, 3, P>, smem);
-                k_gs_phase<T, 3, P><<<nty * ntz, kThreads, smem, s>>>(L, cy, cz, descending, x, b, TM, TK);
+                k_gs_phase<T, 3, P><<<nty * ntz, threads, smem, s>>>(L, cy, cz, descending, x, b, TM, TK);
             }
         });
         count_launch();

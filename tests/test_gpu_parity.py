@@ -318,3 +318,14 @@ def test_solve_fp64_p7_fixed_cycles(pkg):
     assert _rel(_np(out["x"]), ref["iterates"][-1]) < 1e-7
     assert _hist_ok(out["history"], ref["history"])
     s.close()
+
+
+def test_large_rows_inside_graph_capture(pkg):
+    """Rows whose shared-memory buffers exceed 48 KiB (1026 doubles x 6) launch
+    inside the captured restart graph: the solve must run, FP64 and mixed."""
+    s = pkg.Solver(2, 3, 1024, k=5)
+    b = s.rhs_sine(workloads.random_sine_coeffs(2, seed=2, modes=4))
+    for prec in ("fp64", "fp32_ir"):
+        out = s.solve(b, tol=1e-10, method="rre", k=5, prec=prec, max_cycles=30)
+        assert out["converged"], prec
+    s.close()
