@@ -176,6 +176,32 @@ igamg_status igamg_extrapolate(long n, int q, int method, const double* d_S, lon
 igamg_status igamg_extrapolate_noalloc(long n, int q, int method, const double* d_S, long ld,
                                        double* d_t, double* h_gamma, int* h_qused, void* stream);
 
+/* ---------------------------------------------------------------- batches */
+
+/* Many independent problems of uneven size and degree, solved together.
+ * Problem i: dimension dim, degree p[i], n[i] elements per direction.  The
+ * right-hand sides and solutions are packed back to back in one vector; use
+ * igamg_batch_layout for the offsets (count+1 entries, last = total length).
+ * Each problem runs the restarted extrapolation of igamg_solve with its own
+ * convergence test; problems that converge stop while the others continue.
+ * (The paper treats one problem at a time; batching is an interface
+ * extension of Algorithm 5.) */
+typedef struct igamg_batch igamg_batch;
+igamg_status igamg_batch_create(int count, int dim, const int* p, const int* n, igamg_batch** out);
+igamg_status igamg_batch_layout(const igamg_batch* batch, long* h_offsets);
+size_t igamg_batch_workspace_bytes(const igamg_batch* batch, int k, int prec);
+/* h_coeffs: count blocks of modes^dim sine coefficients (see igamg_rhs_sine). */
+igamg_status igamg_batch_rhs_sine(igamg_batch* batch, int modes, const double* h_coeffs, double* d_b,
+                                  void* stream);
+/* extrap: IGAMG_RRE or IGAMG_MPE.  h_cycles, h_status, h_res (may be NULL):
+ * per problem the restart cycles run, its igamg_status and its final relative
+ * residual.  Returns OK when every problem converged, else the first
+ * non-OK status.  Synchronises `stream`. */
+igamg_status igamg_batch_solve(igamg_batch* batch, const double* d_b, double* d_x, double tol, int extrap,
+                               int k, int max_cycles, int prec, void* d_ws, size_t ws_bytes, void* stream,
+                               int* h_cycles, int* h_status, double* h_res);
+void igamg_batch_destroy(igamg_batch* batch);
+
 /* ---------------------------------------------------------------- misc */
 
 void igamg_destroy(igamg_ctx* ctx);

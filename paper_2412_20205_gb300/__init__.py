@@ -61,6 +61,13 @@ def _load():
         "igamg_extrapolate": (c_int, [c_long, c_int, c_int, vp, c_long, vp, dp, ip, vp, c_size, vp]),
         "igamg_extrapolate_noalloc": (c_int, [c_long, c_int, c_int, vp, c_long, vp, dp, ip, vp]),
         "igamg_destroy": (None, [vp]),
+        "igamg_batch_create": (c_int, [c_int, c_int, ip, ip, ctypes.POINTER(vp)]),
+        "igamg_batch_layout": (c_int, [vp, ctypes.POINTER(c_long)]),
+        "igamg_batch_workspace_bytes": (c_size, [vp, c_int, c_int]),
+        "igamg_batch_rhs_sine": (c_int, [vp, c_int, dp, vp, vp]),
+        "igamg_batch_solve": (c_int, [vp, vp, vp, c_double, c_int, c_int, c_int, c_int, vp, c_size, vp,
+                                      ip, ip, dp]),
+        "igamg_batch_destroy": (None, [vp]),
         "igamg_status_str": (ctypes.c_char_p, [c_int]),
         "igamg_last_error": (ctypes.c_char_p, []),
         "igamg_launch_count": (ctypes.c_longlong, []),
@@ -213,6 +220,50 @@ def igamg_launch_count():
     return int(_load().igamg_launch_count())
 
 
+def igamg_batch_create(dim, ps, ns):
+    count = len(ps)
+    pa = (ctypes.c_int * count)(*[int(v) for v in ps])
+    na = (ctypes.c_int * count)(*[int(v) for v in ns])
+    b = ctypes.c_void_p()
+    _check(_load().igamg_batch_create(count, dim, pa, na, ctypes.byref(b)), "igamg_batch_create")
+    return b
+
+
+def igamg_batch_layout(batch, count):
+    off = (ctypes.c_long * (count + 1))()
+    _check(_load().igamg_batch_layout(batch, off), "igamg_batch_layout")
+    return list(off)
+
+
+def igamg_batch_workspace_bytes(batch, k, prec):
+    return int(_load().igamg_batch_workspace_bytes(batch, k, prec))
+
+
+def igamg_batch_rhs_sine(batch, coeffs, b, stream=None):
+    """coeffs: array of shape (count, modes, ..., modes), one sine series per problem."""
+    import numpy as np
+    c = np.ascontiguousarray(coeffs, dtype=np.float64)
+    _check(_load().igamg_batch_rhs_sine(batch, c.shape[1], _dbl(c), _ptr(b), _stream(stream)),
+           "igamg_batch_rhs_sine")
+
+
+def igamg_batch_solve(batch, count, b, x, tol, extrap, k, max_cycles, prec, ws, stream=None):
+    """Returns (status, cycles[count], statuses[count], residuals[count])."""
+    import numpy as np
+    cyc = (ctypes.c_int * count)()
+    st = (ctypes.c_int * count)()
+    res = np.zeros(count)
+    s = _load().igamg_batch_solve(batch, _ptr(b), _ptr(x), tol, extrap, k, max_cycles, prec, _ptr(ws),
+                                  ws.numel(), _stream(stream), cyc, st, _dbl(res))
+    if s not in (IGAMG_OK, IGAMG_ENOTCONV):
+        _check(s, "igamg_batch_solve")
+    return s, list(cyc), list(st), res
+
+
+def igamg_batch_destroy(batch):
+    _load().igamg_batch_destroy(batch)
+
+
 # ------------------------------------------------------------------ convenience
 class Solver:
     """One problem: context + device workspace (a torch uint8 tensor)."""
@@ -252,6 +303,48 @@ class Solver:
         if self.ctx:
             igamg_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many independent 2D/3D problems (degree p[i], n[i] elements per direction)
+    solved together; vectors are packed back to back (see .offsets)."""
+
+    def __init__(self, dim, ps, ns, k=5, device="cuda"):
+        import torch
+        self.count = len(ps)
+        self.dim = dim
+        self.handle = igamg_batch_create(dim, ps, ns)
+        self.offsets = igamg_batch_layout(self.handle, self.count)
+        self.N = self.offsets[-1]
+        nbytes = max(igamg_batch_workspace_bytes(self.handle, k, PREC["fp32_ir"]),
+                     igamg_batch_workspace_bytes(self.handle, k, PREC["fp64"]))
+        self.ws = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.k_max = k
+
+    def rhs_sine(self, coeffs):
+        import torch
+        b = torch.empty(self.N, dtype=torch.float64, device=self.ws.device)
+        igamg_batch_rhs_sine(self.handle, coeffs, b)
+        return b
+
+    def solve(self, b, x=None, tol=1e-10, method="rre", k=5, max_cycles=200, prec="fp32_ir"):
+        import torch
+        if x is None:
+            x = torch.empty(self.N, dtype=torch.float64, device=self.ws.device)
+        st, cyc, sts, res = igamg_batch_solve(self.handle, self.count, b, x, tol, EXTRAP[method], k, max_cycles,
+                                              PREC[prec], self.ws)
+        return dict(x=x, status=st, cycles=cyc, statuses=sts, residuals=res, converged=st == IGAMG_OK)
+
+    def close(self):
+        if self.handle:
+            igamg_batch_destroy(self.handle)
+            self.handle = None
 
     def __del__(self):
         try:

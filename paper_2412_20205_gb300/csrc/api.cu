@@ -358,6 +358,33 @@ igamg_status check_ws(const igamg_ctx* c, void* ws, size_t bytes, int k, int pre
     return IGAMG_OK;
 }
 
+// Capture one restart cycle of this context into its CUDA graph (cached per
+// right-hand side, workspace, k, method, precision and test).
+igamg_status ensure_graph(igamg_ctx* c, Workspace& w, const double* d_b, void* d_ws, int kk, int extrap,
+                          int prec, const double* denom) {
+    igamg_ctx::Key key;
+    key.b = d_b; key.ws = d_ws; key.k = kk; key.extrap = extrap; key.prec = prec;
+    key.abs_tol = denom == nullptr;
+    if (c->exec && c->key == key) return IGAMG_OK;
+    if (c->exec) { cudaGraphExecDestroy(c->exec); c->exec = nullptr; }
+    cudaGraph_t g = nullptr;
+    const long long before = launch_count();
+    CUDA_TRY(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+    restart_body(c, c->cap, w, extrap, kk, prec, d_b, denom);
+    cudaError_t ce = cudaStreamEndCapture(c->cap, &g);
+    if (ce != cudaSuccess) return fail(IGAMG_ECUDA, std::string("capture: ") + cudaGetErrorString(ce));
+    c->exec_launches = launch_count() - before;
+    count_launch(-c->exec_launches);
+    ce = cudaGraphInstantiate(&c->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) {
+        c->exec = nullptr;
+        return fail(IGAMG_ECUDA, std::string("instantiate: ") + cudaGetErrorString(ce));
+    }
+    c->key = key;
+    return IGAMG_OK;
+}
+
 }  // namespace
 
 // ======================================================================= C ABI
@@ -727,26 +754,8 @@ igamg_status igamg_solve(igamg_ctx* c, const double* d_b, double* d_x, double to
     igamg_status result = IGAMG_ENOTCONV;
     if (res <= tol) result = IGAMG_OK;
     const bool use_graph = !(flags & IGAMG_FLAG_NO_GRAPH);
-    if (use_graph && result != IGAMG_OK && max_cycles > 0) {
-        igamg_ctx::Key key;
-        key.b = d_b; key.ws = d_ws; key.k = kk; key.extrap = extrap; key.prec = prec;
-        key.abs_tol = denom == nullptr;
-        if (!(c->exec && c->key == key)) {
-            if (c->exec) { cudaGraphExecDestroy(c->exec); c->exec = nullptr; }
-            cudaGraph_t g = nullptr;
-            const long long before = launch_count();
-            CUDA_TRY(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
-            restart_body(c, c->cap, w, extrap, kk, prec, d_b, denom);
-            cudaError_t ce = cudaStreamEndCapture(c->cap, &g);
-            if (ce != cudaSuccess) return fail(IGAMG_ECUDA, std::string("capture: ") + cudaGetErrorString(ce));
-            c->exec_launches = launch_count() - before;
-            count_launch(-c->exec_launches);
-            ce = cudaGraphInstantiate(&c->exec, g, 0);
-            cudaGraphDestroy(g);
-            if (ce != cudaSuccess) { c->exec = nullptr; return fail(IGAMG_ECUDA, std::string("instantiate: ") + cudaGetErrorString(ce)); }
-            c->key = key;
-        }
-    }
+    if (use_graph && result != IGAMG_OK && max_cycles > 0)
+        if (igamg_status st = ensure_graph(c, w, d_b, d_ws, kk, extrap, prec, denom)) return st;
     int cyc = 0;
     for (cyc = 1; cyc <= max_cycles && result != IGAMG_OK; ++cyc) {
         if (use_graph) {
@@ -888,6 +897,177 @@ void igamg_destroy(igamg_ctx* c) {
     if (c->h_pin) cudaFreeHost(c->h_pin);
     if (c->dmem) cudaFree(c->dmem);
     delete c;
+}
+
+}  // extern "C"
+
+// ====================================================================== batches
+// Many independent problems of uneven size and degree.  Every problem keeps
+// its own hierarchy, workspace slice and restart-cycle CUDA graph; a round
+// replays one restart cycle of every problem that has not converged, spread
+// over a fixed set of streams so that the latency-bound kernels of different
+// problems overlap on the GPU, then reads every residual at once.
+struct igamg_batch {
+    int count = 0, dim = 2;
+    std::vector<igamg_ctx*> ctx;
+    std::vector<size_t> voff;               // packed-vector offsets, count + 1
+    std::vector<cudaStream_t> streams;
+    cudaEvent_t ev = nullptr;
+    double* h_pin = nullptr;                // 2 per problem: ||b||, last residual
+};
+
+namespace {
+constexpr int kBatchStreams = 16;
+
+std::vector<size_t> batch_ws_offsets(const igamg_batch* B, int k, int prec) {
+    std::vector<size_t> off(B->count + 1, 0);
+    for (int i = 0; i < B->count; ++i)
+        off[i + 1] = off[i] + ((carve(B->ctx[i], nullptr, k, prec).bytes + 255) & ~(size_t)255);
+    return off;
+}
+}  // namespace
+
+extern "C" {
+
+igamg_status igamg_batch_create(int count, int dim, const int* p, const int* n, igamg_batch** out) {
+    if (!out || !p || !n || count < 1) return fail(IGAMG_EINVAL, "bad batch arguments");
+    *out = nullptr;
+    igamg_batch* B = new (std::nothrow) igamg_batch();
+    if (!B) return fail(IGAMG_ENOMEM, "host allocation");
+    B->count = count;
+    B->dim = dim;
+    B->voff.assign(count + 1, 0);
+    for (int i = 0; i < count; ++i) {
+        const int ne[3] = {n[i], n[i], n[i]};
+        igamg_ctx* c = nullptr;
+        igamg_status st = igamg_setup(dim, p[i], ne, 0, &c);
+        if (st == IGAMG_OK) st = igamg_assemble(c);
+        if (st != IGAMG_OK) {
+            if (c) igamg_destroy(c);
+            igamg_batch_destroy(B);
+            return st;
+        }
+        B->ctx.push_back(c);
+        B->voff[i + 1] = B->voff[i] + finestN(c);
+    }
+    B->streams.resize(std::min(count, kBatchStreams));
+    for (auto& s : B->streams) CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    CUDA_TRY(cudaEventCreateWithFlags(&B->ev, cudaEventDisableTiming));
+    CUDA_TRY(cudaMallocHost(&B->h_pin, sizeof(double) * 2 * count));
+    *out = B;
+    return IGAMG_OK;
+}
+
+igamg_status igamg_batch_layout(const igamg_batch* B, long* h_offsets) {
+    if (!B || !h_offsets) return fail(IGAMG_EINVAL, "null batch or offsets");
+    for (int i = 0; i <= B->count; ++i) h_offsets[i] = (long)B->voff[i];
+    return IGAMG_OK;
+}
+
+size_t igamg_batch_workspace_bytes(const igamg_batch* B, int k, int prec) {
+    if (!B || k < 1 || k > kMaxQ || prec < 0 || prec > 1) return 0;
+    return batch_ws_offsets(B, k, prec).back() + 256;
+}
+
+igamg_status igamg_batch_rhs_sine(igamg_batch* B, int modes, const double* h_coeffs, double* d_b, void* stream) {
+    if (!B || !h_coeffs || !d_b || modes < 1) return fail(IGAMG_EINVAL, "bad batch rhs arguments");
+    size_t per = 1;
+    for (int d = 0; d < B->dim; ++d) per *= (size_t)modes;
+    for (int i = 0; i < B->count; ++i)
+        if (igamg_status st = igamg_rhs_sine(B->ctx[i], modes, h_coeffs + per * i, d_b + B->voff[i], stream))
+            return st;
+    return IGAMG_OK;
+}
+
+igamg_status igamg_batch_solve(igamg_batch* B, const double* d_b, double* d_x, double tol, int extrap, int k,
+                               int max_cycles, int prec, void* d_ws, size_t ws_bytes, void* stream,
+                               int* h_cycles, int* h_status, double* h_res) {
+    if (!B || !d_b || !d_x) return fail(IGAMG_EINVAL, "null batch or vector");
+    if (extrap < 1 || extrap > 2 || k < 1 || k > kMaxQ || prec < 0 || prec > 1 || max_cycles < 0 || !(tol >= 0.0))
+        return fail(IGAMG_EINVAL, "bad batch solve arguments");
+    const std::vector<size_t> wo = batch_ws_offsets(B, k, prec);
+    if (!d_ws || ((uintptr_t)d_ws & 255) || ws_bytes < wo.back()) return fail(IGAMG_ENOMEM, "batch workspace too small");
+    const int S = (int)B->streams.size();
+    cudaStream_t caller = (cudaStream_t)stream;
+    CUDA_TRY(cudaEventRecord(B->ev, caller));
+    for (auto s : B->streams) CUDA_TRY(cudaStreamWaitEvent(s, B->ev, 0));
+    std::vector<Workspace> W(B->count);
+    std::vector<int> cyc(B->count, 0), stat(B->count, IGAMG_ENOTCONV);
+    // initial state of every problem: ||b||, s_0 = 0 with its row sums, ||b - A s_0|| / ||b||
+    for (int i = 0; i < B->count; ++i) {
+        igamg_ctx* c = B->ctx[i];
+        cudaStream_t s = B->streams[i % S];
+        W[i] = carve(c, (char*)d_ws + wo[i], k, prec);
+        Workspace& w = W[i];
+        const size_t N = finestN(c);
+        const double* b = d_b + B->voff[i];
+        dev::sumsq_partial(s, b, N, w.partial, 256);
+        dev::norm_final(s, w.partial, 256, nullptr, w.scal, 0);
+        dev::fill_zero<double>(s, w.S, N);
+        dev::xpass<double, double>(s, c->lv64[c->L - 1], w.S, w.S, nullptr, 0, nullptr, nullptr, 0,
+                                   w.d[c->L - 1].TM, w.d[c->L - 1].TK);
+        residual_norm(c, s, w, b, w.scal);
+        CUDA_TRY(cudaMemcpyAsync(B->h_pin + 2 * i, w.scal, 16, cudaMemcpyDeviceToHost, s));
+    }
+    for (int i = 0; i < B->count; ++i)
+        if (igamg_status st = ensure_graph(B->ctx[i], W[i], d_b + B->voff[i], (char*)d_ws + wo[i], k, extrap, prec,
+                                           W[i].scal))
+            return st;
+    for (auto s : B->streams) CUDA_TRY(cudaStreamSynchronize(s));
+    CUDA_TRY(cudaGetLastError());
+    for (int i = 0; i < B->count; ++i) {
+        const double bn = B->h_pin[2 * i], r = B->h_pin[2 * i + 1];
+        if (h_res) h_res[i] = r;
+        if (!std::isfinite(bn)) stat[i] = IGAMG_EBREAKDOWN;
+        else if (bn == 0.0) { stat[i] = IGAMG_OK; if (h_res) h_res[i] = 0.0; }
+        else if (r <= tol) stat[i] = IGAMG_OK;
+    }
+    for (int round = 1; round <= max_cycles; ++round) {
+        int active = 0;
+        for (int i = 0; i < B->count; ++i) {
+            if (stat[i] != IGAMG_ENOTCONV) continue;
+            cudaStream_t s = B->streams[i % S];
+            CUDA_TRY(cudaGraphLaunch(B->ctx[i]->exec, s));
+            count_launch(B->ctx[i]->exec_launches);
+            CUDA_TRY(cudaMemcpyAsync(B->h_pin + 2 * i + 1, W[i].scal + 1, 8, cudaMemcpyDeviceToHost, s));
+            ++active;
+        }
+        if (!active) break;
+        for (auto s : B->streams) CUDA_TRY(cudaStreamSynchronize(s));
+        for (int i = 0; i < B->count; ++i) {
+            if (stat[i] != IGAMG_ENOTCONV) continue;
+            const double r = B->h_pin[2 * i + 1];
+            cyc[i] = round;
+            if (h_res) h_res[i] = r;
+            if (!std::isfinite(r)) stat[i] = IGAMG_EBREAKDOWN;
+            else if (r <= tol) stat[i] = IGAMG_OK;
+        }
+    }
+    for (int i = 0; i < B->count; ++i) {
+        cudaStream_t s = B->streams[i % S];
+        const size_t N = finestN(B->ctx[i]);
+        if (stat[i] == IGAMG_OK && B->h_pin[2 * i] == 0.0) CUDA_TRY(cudaMemsetAsync(d_x + B->voff[i], 0, N * 8, s));
+        else CUDA_TRY(cudaMemcpyAsync(d_x + B->voff[i], W[i].S, N * 8, cudaMemcpyDeviceToDevice, s));
+    }
+    for (auto s : B->streams) CUDA_TRY(cudaStreamSynchronize(s));
+    CUDA_TRY(cudaGetLastError());
+    igamg_status all = IGAMG_OK;
+    for (int i = 0; i < B->count; ++i) {
+        if (h_cycles) h_cycles[i] = cyc[i];
+        if (h_status) h_status[i] = stat[i];
+        if (stat[i] != IGAMG_OK && all == IGAMG_OK) all = (igamg_status)stat[i];
+    }
+    if (all != IGAMG_OK) fail(all, "some problems did not converge");
+    return all;
+}
+
+void igamg_batch_destroy(igamg_batch* B) {
+    if (!B) return;
+    for (auto c : B->ctx) igamg_destroy(c);
+    for (auto s : B->streams) if (s) cudaStreamDestroy(s);
+    if (B->ev) cudaEventDestroy(B->ev);
+    if (B->h_pin) cudaFreeHost(B->h_pin);
+    delete B;
 }
 
 }  // extern "C"
