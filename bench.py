@@ -35,6 +35,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "batch256"],
+                    help="c2: one 1024^2 solve (default); batch256: 256 uneven problems solved together")
     ap.add_argument("--dim", type=int, default=2)
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--p", type=int, default=3)
@@ -274,6 +276,105 @@ def run_ours(a, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(a, rank, world, local):
+    """256 independent 2D problems, n ~ U{32..512}, p ~ U{2,3,4}, random 16-mode
+    right-hand sides; one step = one batched solve of all of them."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build_library()
+    import paper_2412_20205_gb300 as pkg
+    import workloads
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    probs = workloads.batch_problems(256, seed=a.seed + rank)
+    ps = [q["p"] for q in probs]
+    ns = [q["n"] for q in probs]
+    B = pkg.Batch(2, ps, ns, k=a.k)
+    coeffs = np.stack([workloads.random_sine_coeffs(2, seed=q["rhs_seed"], modes=16) for q in probs])
+    b = B.rhs_sine(coeffs)
+    x = torch.empty(B.N, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def timed(prec, steps):
+        times, out = [], None
+        for _ in range(steps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            out = B.solve(b, x=x, tol=1e-10, method=a.method, k=a.k, prec=prec)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        return times, out
+
+    for _ in range(a.warmup):
+        B.solve(b, x=x, tol=1e-10, method=a.method, k=a.k, prec=a.prec)
+        B.solve(b, x=x, tol=1e-10, method=a.method, k=a.k, prec="fp64")
+    barrier(world)
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = pkg.igamg_launch_count()
+    times, out = timed(a.prec, a.steps)
+    launches = pkg.igamg_launch_count() - l0
+    clk = clocks.stop()
+    times64, out64 = timed("fp64", a.steps)
+    hb = b.cpu().pin_memory()
+    hx = torch.empty(B.N, dtype=torch.float64, pin_memory=True)
+    db = torch.empty_like(b)
+    e2e = []
+    for _ in range(a.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        db.copy_(hb, non_blocking=True)
+        o = B.solve(db, x=x, tol=1e-10, method=a.method, k=a.k, prec=a.prec)
+        hx.copy_(o["x"], non_blocking=True)
+        torch.cuda.synchronize()
+        e2e.append((time.perf_counter() - t0) * 1e3)
+    t_max = max_over_ranks(float(np.mean(times)), world)
+    t64 = max_over_ranks(float(np.mean(times64)), world)
+    te = max_over_ranks(float(np.mean(e2e)), world)
+    if rank != 0:
+        return
+    units = B.N * world
+    line = {
+        "metric": METRIC, "value": units / (t_max * 1e-3), "unit": "DOF/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if a.prec == "fp32_ir" else "f64", "data": "synthetic",
+        "config": {"workload": f"256 independent 2D IGA Poisson problems, n ~ U{{32..512}}, p ~ U{{2,3,4}}, "
+                               f"{a.method.upper()}(k={a.k}), tol 1e-10, {B.N} unknowns in total",
+                   "problems": 256, "total_dof": B.N, "method": a.method, "k": a.k,
+                   "rhs": "random sine series, 16 modes/direction, N(0,1), seed 1000 + i",
+                   "l2": "flushed between steps (256 MiB write)"},
+        "converged": bool(out["converged"]), "max_cycles": int(max(out["cycles"])),
+        "max_rel_residual": float(max(out["residuals"])),
+        "fp64_form": {"ms_per_step": t64, "value": units / (t64 * 1e-3), "unit": "DOF/s",
+                      "max_cycles": int(max(out64["cycles"]))},
+        "e2e": {"value": units / (te * 1e-3), "unit": "DOF/s", "h2d_bytes_per_step": B.N * 8,
+                "d2h_bytes_per_step": B.N * 8},
+        "gpu_launches": launches, "clocks": clk,
+    }
+    if not a.no_cpu_baseline:
+        from oracle import solver
+        sample = [q for q in probs if q["n"] <= 96][:6]
+        dof = 0
+        tsum = 0.0
+        for q in sample:
+            prob = solver.Problem(2, q["n"], q["p"], workloads.random_sine_coeffs(2, seed=q["rhs_seed"], modes=16))
+            t1 = time.perf_counter()
+            solver.solve(prob, a.method, k=a.k, tol=1e-10, max_cycles=100)
+            tsum += time.perf_counter() - t1
+            dof += prob.H.finest.N
+        line["cpu_baseline"] = {"value": dof / tsum, "unit": "DOF/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{len(sample)} members with n <= 96 solved to 1e-10 "
+                                          f"({dof} unknowns, {tsum:.1f} s), set-up excluded"}
+    print(json.dumps(line), flush=True)
+    B.close()
+
+
 def barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -303,7 +404,10 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
-    run_ours(a, rank, world, local)
+    if a.workload == "batch256":
+        run_batch(a, rank, world, local)
+    else:
+        run_ours(a, rank, world, local)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
