@@ -176,6 +176,30 @@ igamg_status igamg_extrapolate(long n, int q, int method, const double* d_S, lon
 igamg_status igamg_extrapolate_noalloc(long n, int q, int method, const double* d_S, long ld,
                                        double* d_t, double* h_gamma, int* h_qused, void* stream);
 
+/* ------------------------------------------------------- learned smoother */
+
+/* A small convolutional network used as the finest-level post-smoother of
+ * IGAMG_FP32_IR_LEARNED solves (the paper has no learned component; this is
+ * the build's extension of the smoothing step of Algorithm 2).  Three 3x3
+ * zero-padded convolutions without biases, 1 -> 16 -> 16 -> 1 channels, ReLU
+ * after the first two; BF16 activations, FP32 accumulation, the 16 -> 16
+ * layer on the tensor cores.  Weights: igamg_cnn_num_weights() FP32 values,
+ * W1[co][tap] (144), W2[co][ci][tap] (2304), W3[ci][tap] (144), tap =
+ * 3 (dy+1) + (dx+1) reading pixel (y+dy, x+dx).  Images: batch x H x W FP32,
+ * x fastest. */
+int igamg_cnn_num_weights(void);
+size_t igamg_cnn_workspace_bytes(int batch, int H, int W);
+/* d_y = network(d_r). */
+igamg_status igamg_cnn_forward(int batch, int H, int W, const float* d_r, const float* d_w, float* d_y,
+                               void* d_ws, size_t ws_bytes, void* stream);
+/* d_loss[0] = 0.5 mean((network(d_r) - d_e)^2) and d_grad = its gradient with
+ * respect to the weights (deterministic reductions). */
+igamg_status igamg_cnn_grad(int batch, int H, int W, const float* d_r, const float* d_e, const float* d_w,
+                            float* d_grad, float* d_loss, void* d_ws, size_t ws_bytes, void* stream);
+/* One Adam step (bias-corrected) on n parameters; step counts from 1. */
+igamg_status igamg_adam_step(int n, float* d_w, const float* d_g, float* d_m, float* d_v, int step, float lr,
+                             float b1, float b2, float eps, void* stream);
+
 /* ---------------------------------------------------------------- batches */
 
 /* Many independent problems of uneven size and degree, solved together.

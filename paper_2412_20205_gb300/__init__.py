@@ -61,6 +61,12 @@ def _load():
         "igamg_extrapolate": (c_int, [c_long, c_int, c_int, vp, c_long, vp, dp, ip, vp, c_size, vp]),
         "igamg_extrapolate_noalloc": (c_int, [c_long, c_int, c_int, vp, c_long, vp, dp, ip, vp]),
         "igamg_destroy": (None, [vp]),
+        "igamg_cnn_num_weights": (c_int, []),
+        "igamg_cnn_workspace_bytes": (c_size, [c_int, c_int, c_int]),
+        "igamg_cnn_forward": (c_int, [c_int, c_int, c_int, vp, vp, vp, vp, c_size, vp]),
+        "igamg_cnn_grad": (c_int, [c_int, c_int, c_int, vp, vp, vp, vp, vp, vp, c_size, vp]),
+        "igamg_adam_step": (c_int, [c_int, vp, vp, vp, vp, c_int, ctypes.c_float, ctypes.c_float,
+                                    ctypes.c_float, ctypes.c_float, vp]),
         "igamg_batch_create": (c_int, [c_int, c_int, ip, ip, ctypes.POINTER(vp)]),
         "igamg_batch_layout": (c_int, [vp, ctypes.POINTER(c_long)]),
         "igamg_batch_workspace_bytes": (c_size, [vp, c_int, c_int]),
@@ -218,6 +224,29 @@ def igamg_destroy(ctx):
 
 def igamg_launch_count():
     return int(_load().igamg_launch_count())
+
+
+def igamg_cnn_num_weights():
+    return int(_load().igamg_cnn_num_weights())
+
+
+def igamg_cnn_workspace_bytes(batch, H, W):
+    return int(_load().igamg_cnn_workspace_bytes(batch, H, W))
+
+
+def igamg_cnn_forward(batch, H, W, r, w, y, ws, stream=None):
+    _check(_load().igamg_cnn_forward(batch, H, W, _ptr(r), _ptr(w), _ptr(y), _ptr(ws), ws.numel(),
+                                     _stream(stream)), "igamg_cnn_forward")
+
+
+def igamg_cnn_grad(batch, H, W, r, e, w, grad, loss, ws, stream=None):
+    _check(_load().igamg_cnn_grad(batch, H, W, _ptr(r), _ptr(e), _ptr(w), _ptr(grad), _ptr(loss), _ptr(ws),
+                                  ws.numel(), _stream(stream)), "igamg_cnn_grad")
+
+
+def igamg_adam_step(w, g, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8, stream=None):
+    _check(_load().igamg_adam_step(w.numel(), _ptr(w), _ptr(g), _ptr(m), _ptr(v), step, lr, b1, b2, eps,
+                                   _stream(stream)), "igamg_adam_step")
 
 
 def igamg_batch_create(dim, ps, ns):

@@ -1,0 +1,534 @@
+// Learned post-smoother network: forward, gradient and Adam kernels.
+//
+// Three 3x3 zero-padded convolutions without biases, 1 -> 16 -> 16 -> 1
+// channels, ReLU after the first two.  Images are batch x H x W (x fastest);
+// the hidden activations are stored in BF16, channel-last (16 channels = 32
+// bytes per pixel), arithmetic accumulates in FP32.  Weights are one FP32
+// vector: W1[co][tap] (144), W2[co][ci][tap] (2304), W3[ci][tap] (144), with
+// tap = 3 (dy + 1) + (dx + 1) reading pixel (y + dy, x + dx).
+//
+// The 16 -> 16 layer is the only dense contraction (implicit GEMM with
+// M = pixels, N = 16, K = 144); its forward and input-gradient kernels run on
+// the tensor cores (mma.sync m16n8k16, BF16 in, FP32 accumulate).
+#include "../../include/igamg.h"
+#include "device.hpp"
+
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <string>
+
+namespace igamg {
+namespace cnn {
+
+constexpr int C = 16;
+constexpr int NW1 = C * 9, NW2 = C * C * 9, NW3 = C * 9;
+constexpr int NW = NW1 + NW2 + NW3;
+constexpr int kT = 256;
+
+struct Shape {
+    int B, H, W;
+    __host__ __device__ long long pixels() const { return (long long)B * H * W; }
+};
+
+// A pixel with its row/column, decomposed once; nb(t) is its neighbour
+// through tap t (-1 outside the image).
+struct Pix {
+    long long p;
+    int y, x;
+    __device__ __forceinline__ Pix(const Shape& s, long long q) : p(q) {
+        const long long r = q / s.W;
+        x = (int)(q - r * s.W);
+        y = (int)(r % s.H);
+    }
+    __device__ __forceinline__ long long nb(const Shape& s, int t) const {
+        const int dx = (t % 3) - 1, dy = (t / 3) - 1;
+        const int xx = x + dx, yy = y + dy;
+        if (xx < 0 || xx >= s.W || yy < 0 || yy >= s.H) return -1;
+        return p + (long long)dy * s.W + dx;
+    }
+};
+__device__ __forceinline__ long long neighbour(const Shape& s, long long p, int t) { return Pix(s, p).nb(s, t); }
+
+__device__ __forceinline__ void load16(const __nv_bfloat16* a, long long p, float* v) {
+    const uint4* q = reinterpret_cast<const uint4*>(a + p * C);
+    const uint4 u0 = q[0], u1 = q[1];
+    const __nv_bfloat162* h0 = reinterpret_cast<const __nv_bfloat162*>(&u0);
+    const __nv_bfloat162* h1 = reinterpret_cast<const __nv_bfloat162*>(&u1);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float2 f0 = __bfloat1622float2(h0[i]), f1 = __bfloat1622float2(h1[i]);
+        v[2 * i] = f0.x; v[2 * i + 1] = f0.y;
+        v[8 + 2 * i] = f1.x; v[8 + 2 * i + 1] = f1.y;
+    }
+}
+
+__device__ __forceinline__ void store16(__nv_bfloat16* a, long long p, const float* v) {
+    uint4 u0, u1;
+    __nv_bfloat162* h0 = reinterpret_cast<__nv_bfloat162*>(&u0);
+    __nv_bfloat162* h1 = reinterpret_cast<__nv_bfloat162*>(&u1);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        h0[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+        h1[i] = __floats2bfloat162_rn(v[8 + 2 * i], v[8 + 2 * i + 1]);
+    }
+    uint4* q = reinterpret_cast<uint4*>(a + p * C);
+    q[0] = u0;
+    q[1] = u1;
+}
+
+// ------------------------------------------------------------------ forward
+// a1 = relu(W1 * r)
+__global__ void __launch_bounds__(kT) k_conv1(Shape s, const float* __restrict__ r, const float* __restrict__ w,
+                                              __nv_bfloat16* __restrict__ a1) {
+    __shared__ float W1[NW1];
+    for (int i = threadIdx.x; i < NW1; i += blockDim.x) W1[i] = w[i];
+    __syncthreads();
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < s.pixels();
+         p += (long long)gridDim.x * blockDim.x) {
+        const Pix px(s, p);
+        float nb[9];
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+            const long long q = px.nb(s, t);
+            nb[t] = q >= 0 ? r[q] : 0.f;
+        }
+        float v[C];
+#pragma unroll
+        for (int co = 0; co < C; ++co) {
+            float acc = 0.f;
+#pragma unroll
+            for (int t = 0; t < 9; ++t) acc += W1[co * 9 + t] * nb[t];
+            v[co] = fmaxf(acc, 0.f);
+        }
+        store16(a1, p, v);
+    }
+}
+
+// Tensor-core fragments (mma.sync.m16n8k16, BF16 inputs, FP32 accumulators).
+// Per warp: a strip of 16 consecutive pixels (M) x 16 output channels (two N
+// tiles of 8); K runs over the 9 taps x 16 input channels, one k16 step per
+// tap.  A(m, k) = act[neighbour(pixel m, tap)][k], B(k, n) = weight(tap, k, n).
+__device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, const uint32_t* b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// Implicit-GEMM 16 -> 16 convolution of one 16-pixel strip starting at p0:
+// acc (C fragments of the two 8-channel N tiles) = sum over taps of
+// act[neighbour(pixel, tap)] x Wt[tap].  Wt is the tap-major weight table in
+// shared memory, Wt[t][k][n] (k = contracted channel, n = produced channel);
+// FLIP reads the taps mirrored, which turns the convolution into its adjoint.
+template <bool FLIP>
+__device__ void conv16_strip(const Shape& s, long long p0, const __nv_bfloat16* __restrict__ act,
+                             const float* Wt, float* acc /*[2][4]*/) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc[i] = 0.f;
+    const long long P = s.pixels();
+    const long long pa = p0 + g, pb = p0 + g + 8;
+    const Pix xa(s, pa < P ? pa : 0), xb(s, pb < P ? pb : 0);
+#pragma unroll 1
+    for (int t = 0; t < 9; ++t) {
+        const int tt = FLIP ? 8 - t : t;            // input gradient: flipped taps
+        // A fragment: rows g and g+8 of the strip, columns 2tq, 2tq+1, 2tq+8, 2tq+9
+        uint32_t a[4];
+        {
+            const long long qa = pa < P ? xa.nb(s, t) : -1;
+            const long long qb = pb < P ? xb.nb(s, t) : -1;
+            const __nv_bfloat162 z = __floats2bfloat162_rn(0.f, 0.f);
+            const __nv_bfloat162* ra = qa >= 0 ? reinterpret_cast<const __nv_bfloat162*>(act + qa * C) : nullptr;
+            const __nv_bfloat162* rb = qb >= 0 ? reinterpret_cast<const __nv_bfloat162*>(act + qb * C) : nullptr;
+            __nv_bfloat162 v0 = ra ? ra[tq] : z, v1 = rb ? rb[tq] : z, v2 = ra ? ra[tq + 4] : z, v3 = rb ? rb[tq + 4] : z;
+            a[0] = *reinterpret_cast<uint32_t*>(&v0);
+            a[1] = *reinterpret_cast<uint32_t*>(&v1);
+            a[2] = *reinterpret_cast<uint32_t*>(&v2);
+            a[3] = *reinterpret_cast<uint32_t*>(&v3);
+        }
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+            // B fragment: rows (k) 2tq, 2tq+1 and 2tq+8, 2tq+9; column (n) g of tile nt
+            const float* Wk = Wt + tt * C * C;
+            const int n = nt * 8 + g;
+            uint32_t b[2];
+            b[0] = pack_bf16(Wk[(2 * tq) * C + n], Wk[(2 * tq + 1) * C + n]);
+            b[1] = pack_bf16(Wk[(2 * tq + 8) * C + n], Wk[(2 * tq + 9) * C + n]);
+            mma_bf16(acc + 4 * nt, a, b);
+        }
+    }
+}
+
+// a2 = relu(W2 * a1), tensor cores
+__global__ void __launch_bounds__(kT) k_conv2(Shape s, const __nv_bfloat16* __restrict__ a1,
+                                              const float* __restrict__ w, __nv_bfloat16* __restrict__ a2) {
+    __shared__ float Wt[9 * C * C];                 // [tap][ci][co]
+    for (int i = threadIdx.x; i < NW2; i += blockDim.x) {
+        const int co = i / (C * 9), ci = (i / 9) % C, t = i % 9;
+        Wt[(t * C + ci) * C + co] = w[NW1 + i];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
+    const long long P = s.pixels();
+    const long long strips = (P + 15) / 16;
+    for (long long st = (long long)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); st < strips;
+         st += (long long)gridDim.x * (blockDim.x / 32)) {
+        const long long p0 = st * 16;
+        float acc[8];
+        conv16_strip<false>(s, p0, a1, Wt, acc);
+        // C fragment: rows g / g+8, columns nt*8 + 2tq, 2tq+1
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const long long p = p0 + g + 8 * h;
+            if (p >= P) continue;
+            __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(a2 + p * C);
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt)
+                o[nt * 4 + tq] = __floats2bfloat162_rn(fmaxf(acc[4 * nt + 2 * h], 0.f), fmaxf(acc[4 * nt + 2 * h + 1], 0.f));
+        }
+    }
+}
+
+// y = W3 * a2 (FP32); with accumulate, x += y instead (the solver's correction)
+__global__ void __launch_bounds__(kT) k_conv3(Shape s, const __nv_bfloat16* __restrict__ a2, const float* __restrict__ w,
+                                              float* __restrict__ y, int accumulate) {
+    __shared__ float W3[NW3];
+    for (int i = threadIdx.x; i < NW3; i += blockDim.x) W3[i] = w[NW1 + NW2 + i];
+    __syncthreads();
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < s.pixels();
+         p += (long long)gridDim.x * blockDim.x) {
+        const Pix px(s, p);
+        float acc = 0.f;
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+            const long long q = px.nb(s, t);
+            if (q < 0) continue;
+            float v[C];
+            load16(a2, q, v);
+#pragma unroll
+            for (int c = 0; c < C; ++c) acc += W3[c * 9 + t] * v[c];
+        }
+        if (accumulate) y[p] += acc;
+        else y[p] = acc;
+    }
+}
+
+// ------------------------------------------------------------------ backward
+// gy = (y - e) / n, per-block partial sums of (y - e)^2
+__global__ void __launch_bounds__(kT) k_loss(Shape s, const float* __restrict__ y, const float* __restrict__ e,
+                                             float* __restrict__ gy, double* __restrict__ partial) {
+    __shared__ double red[kT / 32];
+    const long long P = s.pixels();
+    const float inv = 1.0f / (float)P;
+    double ss = 0.0;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+        const float d = y[p] - e[p];
+        gy[p] = d * inv;
+        ss += (double)d * d;
+    }
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < (int)blockDim.x / 32; ++i) t += red[i];
+        partial[blockIdx.x] = t;
+    }
+}
+
+// g2 = (a2 > 0) . (W3^T gy): dL/da2, channel-last BF16
+__global__ void __launch_bounds__(kT) k_conv3_dgrad(Shape s, const float* __restrict__ gy, const float* __restrict__ w,
+                                                    const __nv_bfloat16* __restrict__ a2, __nv_bfloat16* __restrict__ g2) {
+    __shared__ float W3[NW3];
+    for (int i = threadIdx.x; i < NW3; i += blockDim.x) W3[i] = w[NW1 + NW2 + i];
+    __syncthreads();
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < s.pixels();
+         p += (long long)gridDim.x * blockDim.x) {
+        const Pix px(s, p);
+        float v[C] = {};
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+            const long long q = px.nb(s, 8 - t);          // y[q] read a2[p] through tap t
+            if (q < 0) continue;
+            const float gq = gy[q];
+#pragma unroll
+            for (int c = 0; c < C; ++c) v[c] += W3[c * 9 + t] * gq;
+        }
+        float a[C];
+        load16(a2, p, a);
+#pragma unroll
+        for (int c = 0; c < C; ++c) v[c] = a[c] > 0.f ? v[c] : 0.f;
+        store16(g2, p, v);
+    }
+}
+
+// g1 = (a1 > 0) . (W2^T g2): tensor cores with flipped taps and transposed
+// channel roles (contract over the produced channel)
+__global__ void __launch_bounds__(kT) k_conv2_dgrad(Shape s, const __nv_bfloat16* __restrict__ g2,
+                                                    const float* __restrict__ w, const __nv_bfloat16* __restrict__ a1,
+                                                    __nv_bfloat16* __restrict__ g1) {
+    __shared__ float Wt[9 * C * C];                 // [tap][co][ci]: contract over co, produce ci
+    for (int i = threadIdx.x; i < NW2; i += blockDim.x) {
+        const int co = i / (C * 9), ci = (i / 9) % C, t = i % 9;
+        Wt[(t * C + co) * C + ci] = w[NW1 + i];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
+    const long long P = s.pixels();
+    const long long strips = (P + 15) / 16;
+    for (long long st = (long long)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); st < strips;
+         st += (long long)gridDim.x * (blockDim.x / 32)) {
+        const long long p0 = st * 16;
+        float acc[8];
+        conv16_strip<true>(s, p0, g2, Wt, acc);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const long long p = p0 + g + 8 * h;
+            if (p >= P) continue;
+            const __nv_bfloat162* am = reinterpret_cast<const __nv_bfloat162*>(a1 + p * C);
+            __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(g1 + p * C);
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                const float2 m = __bfloat1622float2(am[nt * 4 + tq]);
+                o[nt * 4 + tq] = __floats2bfloat162_rn(m.x > 0.f ? acc[4 * nt + 2 * h] : 0.f,
+                                                       m.y > 0.f ? acc[4 * nt + 2 * h + 1] : 0.f);
+            }
+        }
+    }
+}
+
+// Weight gradients: per-block partial sums over a tile of pixels, one weight
+// per (thread, slot); the final reduction over blocks runs in fixed order.
+// dW1[co][t] = sum_p g1[p][co] r[nb(p,t)]; dW2[co][ci][t] = sum_p g2[p][co] a1[nb(p,t)][ci];
+// dW3[c][t] = sum_p gy[p] a2[nb(p,t)][c]
+constexpr int kTile = 32;                           // pixels per block pass (static smem < 48 KiB)
+
+__global__ void __launch_bounds__(kT) k_wgrad(Shape s, const float* __restrict__ r, const __nv_bfloat16* __restrict__ a1,
+                                              const __nv_bfloat16* __restrict__ a2, const __nv_bfloat16* __restrict__ g1,
+                                              const __nv_bfloat16* __restrict__ g2, const float* __restrict__ gy,
+                                              float* __restrict__ partial) {
+    __shared__ float sg1[kTile][C], sg2[kTile][C], sgy[kTile];
+    __shared__ float sr[kTile][9], sa1[kTile][9][C], sa2[kTile][9][C];
+    float acc[(NW + kT - 1) / kT];
+    constexpr int SLOTS = (NW + kT - 1) / kT;
+#pragma unroll
+    for (int i = 0; i < SLOTS; ++i) acc[i] = 0.f;
+    const long long P = s.pixels();
+    const long long ntiles = (P + kTile - 1) / kTile;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const long long p0 = tile * kTile;
+        __syncthreads();
+        for (int i = threadIdx.x; i < kTile; i += blockDim.x) {
+            const long long p = p0 + i;
+            float v1[C], v2[C];
+            if (p < P) {
+                load16(g1, p, v1);
+                load16(g2, p, v2);
+                sgy[i] = gy[p];
+            } else {
+                for (int c = 0; c < C; ++c) v1[c] = v2[c] = 0.f;
+                sgy[i] = 0.f;
+            }
+            for (int c = 0; c < C; ++c) { sg1[i][c] = v1[c]; sg2[i][c] = v2[c]; }
+        }
+        for (int i = threadIdx.x; i < kTile * 9; i += blockDim.x) {
+            const int pi = i / 9, t = i % 9;
+            const long long p = p0 + pi;
+            const long long q = p < P ? Pix(s, p).nb(s, t) : -1;
+            float v1[C], v2[C];
+            if (q >= 0) {
+                load16(a1, q, v1);
+                load16(a2, q, v2);
+                sr[pi][t] = r[q];
+            } else {
+                for (int c = 0; c < C; ++c) v1[c] = v2[c] = 0.f;
+                sr[pi][t] = 0.f;
+            }
+            for (int c = 0; c < C; ++c) { sa1[pi][t][c] = v1[c]; sa2[pi][t][c] = v2[c]; }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int sl = 0; sl < SLOTS; ++sl) {
+            const int wi = threadIdx.x + sl * kT;
+            if (wi >= NW) continue;
+            float a = 0.f;
+            if (wi < NW1) {
+                const int co = wi / 9, t = wi % 9;
+                for (int i = 0; i < kTile; ++i) a += sg1[i][co] * sr[i][t];
+            } else if (wi < NW1 + NW2) {
+                const int j = wi - NW1, co = j / (C * 9), ci = (j / 9) % C, t = j % 9;
+                for (int i = 0; i < kTile; ++i) a += sg2[i][co] * sa1[i][t][ci];
+            } else {
+                const int j = wi - NW1 - NW2, c = j / 9, t = j % 9;
+                for (int i = 0; i < kTile; ++i) a += sgy[i] * sa2[i][t][c];
+            }
+            acc[sl] += a;
+        }
+    }
+#pragma unroll
+    for (int sl = 0; sl < SLOTS; ++sl) {
+        const int wi = threadIdx.x + sl * kT;
+        if (wi < NW) partial[(size_t)blockIdx.x * NW + wi] = acc[sl];
+    }
+}
+
+__global__ void k_reduce(const float* __restrict__ partial, int nblocks, const double* __restrict__ lpart,
+                         int nl, long long P, float* __restrict__ grad, float* __restrict__ loss) {
+    for (int wi = blockIdx.x * blockDim.x + threadIdx.x; wi < NW; wi += gridDim.x * blockDim.x) {
+        float a = 0.f;
+        for (int b = 0; b < nblocks; ++b) a += partial[(size_t)b * NW + wi];
+        grad[wi] = a;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && loss) {
+        double t = 0.0;
+        for (int i = 0; i < nl; ++i) t += lpart[i];
+        *loss = (float)(0.5 * t / (double)P);
+    }
+}
+
+__global__ void k_adam(int n, float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, float lr, float b1, float b2, float eps, float c1, float c2) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// ------------------------------------------------------------------ host side
+static int grid(long long n, int per) {
+    long long g = (n + per - 1) / per;
+    if (g > 152 * 8) g = 152 * 8;
+    return (int)(g < 1 ? 1 : g);
+}
+constexpr int kWgradBlocks = 304;
+
+size_t workspace_bytes(long long P) {
+    const size_t act = ((size_t)P * C * 2 + 255) / 256 * 256;      // one BF16 channel-last tensor
+    return 4 * act + ((size_t)P * 4 + 255) / 256 * 256 + (size_t)kWgradBlocks * NW * 4 + 8 * 1024 * 8 + 1024;
+}
+
+struct WS {
+    __nv_bfloat16 *a1, *a2, *g1, *g2;
+    float* gy;
+    float* partial;
+    double* lpart;
+};
+
+static WS carve_ws(void* base, long long P) {
+    char* p = (char*)base;
+    const size_t act = ((size_t)P * C * 2 + 255) / 256 * 256;
+    WS w;
+    w.a1 = (__nv_bfloat16*)p; p += act;
+    w.a2 = (__nv_bfloat16*)p; p += act;
+    w.g1 = (__nv_bfloat16*)p; p += act;
+    w.g2 = (__nv_bfloat16*)p; p += act;
+    w.gy = (float*)p; p += ((size_t)P * 4 + 255) / 256 * 256;
+    w.partial = (float*)p; p += (size_t)kWgradBlocks * NW * 4;
+    w.lpart = (double*)p;
+    return w;
+}
+
+void forward(cudaStream_t st, Shape s, const float* r, const float* w, float* y, int accumulate, void* ws) {
+    WS W = carve_ws(ws, s.pixels());
+    const long long P = s.pixels();
+    k_conv1<<<grid(P, kT), kT, 0, st>>>(s, r, w, W.a1);
+    k_conv2<<<grid((P + 15) / 16, kT / 32), kT, 0, st>>>(s, W.a1, w, W.a2);
+    k_conv3<<<grid(P, kT), kT, 0, st>>>(s, W.a2, w, y, accumulate);
+    count_launch(3);
+}
+
+void gradient(cudaStream_t st, Shape s, const float* r, const float* e, const float* w, float* grad, float* loss,
+              float* y, void* ws) {
+    WS W = carve_ws(ws, s.pixels());
+    const long long P = s.pixels();
+    forward(st, s, r, w, y, 0, ws);
+    const int gl = grid(P, kT) > 1024 ? 1024 : grid(P, kT);
+    k_loss<<<gl, kT, 0, st>>>(s, y, e, W.gy, W.lpart);
+    k_conv3_dgrad<<<grid(P, kT), kT, 0, st>>>(s, W.gy, w, W.a2, W.g2);
+    k_conv2_dgrad<<<grid((P + 15) / 16, kT / 32), kT, 0, st>>>(s, W.g2, w, W.a1, W.g1);
+    k_wgrad<<<kWgradBlocks, kT, 0, st>>>(s, r, W.a1, W.a2, W.g1, W.g2, W.gy, W.partial);
+    k_reduce<<<(NW + 255) / 256, 256, 0, st>>>(W.partial, kWgradBlocks, W.lpart, gl, P, grad, loss);
+    count_launch(5);
+}
+
+}  // namespace cnn
+
+size_t cnn_workspace_bytes(long long pixels) { return cnn::workspace_bytes(pixels); }
+void cnn_forward(cudaStream_t st, int B, int H, int W, const float* r, const float* w, float* y, int accumulate,
+                 void* ws) {
+    cnn::forward(st, cnn::Shape{B, H, W}, r, w, y, accumulate, ws);
+}
+
+}  // namespace igamg
+
+using namespace igamg;
+
+extern "C" {
+
+int igamg_cnn_num_weights(void) { return cnn::NW; }
+
+size_t igamg_cnn_workspace_bytes(int batch, int H, int W) {
+    if (batch < 1 || H < 1 || W < 1) return 0;
+    return cnn::workspace_bytes((long long)batch * H * W) + (size_t)batch * H * W * 4 + 256;
+}
+
+igamg_status igamg_cnn_forward(int batch, int H, int W, const float* d_r, const float* d_w, float* d_y, void* d_ws,
+                               size_t ws_bytes, void* stream) {
+    if (batch < 1 || H < 1 || W < 1 || !d_r || !d_w || !d_y || !d_ws) {
+        set_last_error("bad network arguments");
+        return IGAMG_EINVAL;
+    }
+    if (ws_bytes < igamg_cnn_workspace_bytes(batch, H, W) || ((uintptr_t)d_ws & 255)) {
+        set_last_error("network workspace too small or unaligned");
+        return IGAMG_ENOMEM;
+    }
+    cnn::forward((cudaStream_t)stream, cnn::Shape{batch, H, W}, d_r, d_w, d_y, 0, d_ws);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { set_last_error(std::string("network forward: ") + cudaGetErrorString(e)); return IGAMG_ECUDA; }
+    return IGAMG_OK;
+}
+
+igamg_status igamg_cnn_grad(int batch, int H, int W, const float* d_r, const float* d_e, const float* d_w,
+                            float* d_grad, float* d_loss, void* d_ws, size_t ws_bytes, void* stream) {
+    if (batch < 1 || H < 1 || W < 1 || !d_r || !d_e || !d_w || !d_grad || !d_ws) {
+        set_last_error("bad network arguments");
+        return IGAMG_EINVAL;
+    }
+    if (ws_bytes < igamg_cnn_workspace_bytes(batch, H, W) || ((uintptr_t)d_ws & 255)) {
+        set_last_error("network workspace too small or unaligned");
+        return IGAMG_ENOMEM;
+    }
+    const long long P = (long long)batch * H * W;
+    float* y = (float*)((char*)d_ws + cnn::workspace_bytes(P));
+    cnn::gradient((cudaStream_t)stream, cnn::Shape{batch, H, W}, d_r, d_e, d_w, d_grad, d_loss, y, d_ws);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { set_last_error(std::string("network gradient: ") + cudaGetErrorString(e)); return IGAMG_ECUDA; }
+    return IGAMG_OK;
+}
+
+igamg_status igamg_adam_step(int n, float* d_w, const float* d_g, float* d_m, float* d_v, int step, float lr, float b1,
+                             float b2, float eps, void* stream) {
+    if (n < 1 || step < 1 || !d_w || !d_g || !d_m || !d_v) {
+        set_last_error("bad Adam arguments");
+        return IGAMG_EINVAL;
+    }
+    const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
+    cnn::k_adam<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(n, d_w, d_g, d_m, d_v, lr, b1, b2, eps, c1, c2);
+    count_launch();
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { set_last_error(std::string("Adam: ") + cudaGetErrorString(e)); return IGAMG_ECUDA; }
+    return IGAMG_OK;
+}
+
+}  // extern "C"
