@@ -52,8 +52,10 @@ typedef enum { IGAMG_EXTRAP_NONE = 0, IGAMG_RRE = 1, IGAMG_MPE = 2 } igamg_extra
 
 /* Arithmetic of the multigrid cycle.  IGAMG_FP64: everything in FP64.
  * IGAMG_FP32_IR: V-cycles in FP32 inside FP64 iterative refinement; residuals,
- * the extrapolation Gram/least-squares solve and iterate updates in FP64. */
-typedef enum { IGAMG_FP64 = 0, IGAMG_FP32_IR = 1 } igamg_prec;
+ * the extrapolation Gram/least-squares solve and iterate updates in FP64.
+ * IGAMG_FP32_IR_LEARNED: as FP32_IR, with the finest-level post-smoothing
+ * replaced by the learned network (igamg_set_smoother). */
+typedef enum { IGAMG_FP64 = 0, IGAMG_FP32_IR = 1, IGAMG_FP32_IR_LEARNED = 2 } igamg_prec;
 
 /* igamg_solve flags */
 #define IGAMG_FLAG_X0_GIVEN 1u   /* start from d_x instead of s_0 = 0 */
@@ -199,6 +201,23 @@ igamg_status igamg_cnn_grad(int batch, int H, int W, const float* d_r, const flo
 /* One Adam step (bias-corrected) on n parameters; step counts from 1. */
 igamg_status igamg_adam_step(int n, float* d_w, const float* d_g, float* d_m, float* d_v, int step, float lr,
                              float b1, float b2, float eps, void* stream);
+
+/* Use the network with weights d_w (device, caller-owned, must outlive the
+ * solves) as the finest-level post-smoother of IGAMG_FP32_IR_LEARNED solves:
+ * after the coarse correction x += network(b - A x) replaces the Gauss-Seidel
+ * sweep.  When a restart cycle reduces the relative residual by less than
+ * the factor stall_ratio (e.g. 0.9), the solve falls back to plain
+ * Gauss-Seidel post-smoothing for its remaining cycles;
+ * igamg_smoother_fell_back() reports whether the last solve did.  2D
+ * problems only (IGAMG_EINVAL otherwise); d_w = NULL unsets the network. */
+igamg_status igamg_set_smoother(igamg_ctx* ctx, const float* d_w, double stall_ratio);
+int igamg_smoother_fell_back(const igamg_ctx* ctx);
+
+/* One FP64 V-cycle in place on the finest d_x (as igamg_vcycle) that also
+ * copies the iterate at the point just before the finest-level post-smoothing
+ * (after the coarse correction) to d_x_mid: the network's training input. */
+igamg_status igamg_vcycle_probe(igamg_ctx* ctx, double* d_x, const double* d_b, double* d_x_mid,
+                                void* d_ws, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------- batches */
 

@@ -15,11 +15,11 @@ LIB_PATH = os.path.join(_HERE, "libigamg.so")
 
 IGAMG_OK, IGAMG_EINVAL, IGAMG_ENOMEM, IGAMG_ECUDA, IGAMG_ENOTCONV, IGAMG_EBREAKDOWN, IGAMG_ETIMEOUT = range(7)
 IGAMG_EXTRAP_NONE, IGAMG_RRE, IGAMG_MPE = 0, 1, 2
-IGAMG_FP64, IGAMG_FP32_IR = 0, 1
+IGAMG_FP64, IGAMG_FP32_IR, IGAMG_FP32_IR_LEARNED = 0, 1, 2
 IGAMG_FLAG_X0_GIVEN, IGAMG_FLAG_ABS_TOL, IGAMG_FLAG_NO_GRAPH = 1, 2, 4
 
 EXTRAP = {"none": IGAMG_EXTRAP_NONE, "rre": IGAMG_RRE, "mpe": IGAMG_MPE}
-PREC = {"fp64": IGAMG_FP64, "fp32_ir": IGAMG_FP32_IR}
+PREC = {"fp64": IGAMG_FP64, "fp32_ir": IGAMG_FP32_IR, "fp32_ir_learned": IGAMG_FP32_IR_LEARNED}
 
 _lib = None
 
@@ -61,6 +61,9 @@ def _load():
         "igamg_extrapolate": (c_int, [c_long, c_int, c_int, vp, c_long, vp, dp, ip, vp, c_size, vp]),
         "igamg_extrapolate_noalloc": (c_int, [c_long, c_int, c_int, vp, c_long, vp, dp, ip, vp]),
         "igamg_destroy": (None, [vp]),
+        "igamg_set_smoother": (c_int, [vp, vp, c_double]),
+        "igamg_smoother_fell_back": (c_int, [vp]),
+        "igamg_vcycle_probe": (c_int, [vp, vp, vp, vp, vp, c_size, vp]),
         "igamg_cnn_num_weights": (c_int, []),
         "igamg_cnn_workspace_bytes": (c_size, [c_int, c_int, c_int]),
         "igamg_cnn_forward": (c_int, [c_int, c_int, c_int, vp, vp, vp, vp, c_size, vp]),
@@ -226,6 +229,19 @@ def igamg_launch_count():
     return int(_load().igamg_launch_count())
 
 
+def igamg_set_smoother(ctx, w, stall_ratio=0.5):
+    _check(_load().igamg_set_smoother(ctx, _ptr(w), stall_ratio), "igamg_set_smoother")
+
+
+def igamg_smoother_fell_back(ctx):
+    return bool(_load().igamg_smoother_fell_back(ctx))
+
+
+def igamg_vcycle_probe(ctx, x, b, x_mid, ws, stream=None):
+    _check(_load().igamg_vcycle_probe(ctx, _ptr(x), _ptr(b), _ptr(x_mid), _ptr(ws), ws.numel(), _stream(stream)),
+           "igamg_vcycle_probe")
+
+
 def igamg_cnn_num_weights():
     return int(_load().igamg_cnn_num_weights())
 
@@ -305,10 +321,16 @@ class Solver:
         self.levels = igamg_info(self.ctx)
         m = self.levels[-1]
         self.N = m[0] * m[1] * m[2]
-        nbytes = max(igamg_workspace_bytes(self.ctx, k, PREC["fp32_ir"]),
-                     igamg_workspace_bytes(self.ctx, k, PREC["fp64"]))
+        nbytes = max(igamg_workspace_bytes(self.ctx, k, v) for v in PREC.values())
         self.ws = torch.empty(nbytes, dtype=torch.uint8, device=device)
         self.k_max = k
+        self.smoother = None
+
+    def set_smoother(self, w, stall_ratio=0.5):
+        """Use network weights w (device FP32 tensor, kept referenced here) as the
+        learned post-smoother of prec='fp32_ir_learned' solves."""
+        self.smoother = w
+        igamg_set_smoother(self.ctx, w, stall_ratio)
 
     def rhs_sine(self, coeffs, b=None):
         import torch
@@ -326,7 +348,10 @@ class Solver:
                 (0 if graph else IGAMG_FLAG_NO_GRAPH)
         st, hist, cyc, vc = igamg_solve(self.ctx, b, x, tol, EXTRAP[method], k, max_cycles, PREC[prec],
                                         flags, self.ws)
-        return dict(x=x, status=st, history=hist, cycles=cyc, vcycles=vc, converged=st == IGAMG_OK)
+        out = dict(x=x, status=st, history=hist, cycles=cyc, vcycles=vc, converged=st == IGAMG_OK)
+        if prec == "fp32_ir_learned":
+            out["fell_back"] = igamg_smoother_fell_back(self.ctx)
+        return out
 
     def close(self):
         if self.ctx:

@@ -12,6 +12,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 using namespace igamg;
@@ -81,6 +82,7 @@ struct Workspace {
     int* qused = nullptr;
     ExtrapInfo* info = nullptr;
     double* scal = nullptr;   // [0] ||b||, [1] last residual norm, [2..] spare
+    void* cnn = nullptr;      // network workspace (learned post-smoother)
     size_t bytes = 0;
 };
 
@@ -103,17 +105,23 @@ struct igamg_ctx {
     // sine-moment tables for the load vector (finest level)
     cudaStream_t cap = nullptr;             // capture stream
     double* h_pin = nullptr;                // pinned host scalars
-    cudaGraphExec_t exec = nullptr;
-    long long exec_launches = 0;
+    // restart-cycle graphs: slot 0 plain smoothing, slot 1 learned post-smoother
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    long long exec_launches[2] = {0, 0};
     struct Key {
         const void* b = nullptr;
         const void* ws = nullptr;
         int k = -1, extrap = -1, prec = -1, abs_tol = -1;
+        const void* w = nullptr;
         bool operator==(const Key& o) const {
             return b == o.b && ws == o.ws && k == o.k && extrap == o.extrap && prec == o.prec &&
-                   abs_tol == o.abs_tol;
+                   abs_tol == o.abs_tol && w == o.w;
         }
-    } key;
+    } key[2];
+    // learned post-smoother: caller-owned device weights, stall ratio, outcome
+    const float* cnn_w = nullptr;
+    double stall = 0.9;
+    int fell_back = 0;
 };
 
 namespace {
@@ -135,7 +143,7 @@ Workspace carve(const igamg_ctx* c, void* base, int k, int prec) {
         B.tmp1 = cv.take<double>(N);
         B.tmp2 = cv.take<double>(N);
     }
-    if (prec == IGAMG_FP32_IR) {
+    if (prec == IGAMG_FP32_IR || prec == IGAMG_FP32_IR_LEARNED) {
         w.f.resize(L);
         for (int l = 0; l < L; ++l) {
             const size_t N = c->hl[l].N();
@@ -160,6 +168,8 @@ Workspace carve(const igamg_ctx* c, void* base, int k, int prec) {
     w.qused = cv.take<int>(4);
     w.info = cv.take<ExtrapInfo>(1);
     w.scal = cv.take<double>(8);
+    if (prec == IGAMG_FP32_IR_LEARNED)
+        w.cnn = cv.take<unsigned char>(cnn_workspace_bytes((long long)finestN(c)));
     w.bytes = cv.off + 256;
     return w;
 }
@@ -260,7 +270,7 @@ struct Views<float> {
 // top level's TM/TK must match x_top unless top_zero (then x_top = 0 is set).
 template <typename T>
 void vcycle(const igamg_ctx* c, cudaStream_t s, Workspace& w, int top, T* x_top, const T* b_top,
-            bool top_zero) {
+            bool top_zero, bool learned_top = false, T* capture_mid = nullptr) {
     const auto& lv = Views<T>::lv(c);
     const auto& tv = Views<T>::tv(c);
     auto& B = Views<T>::buf(w);
@@ -290,6 +300,15 @@ void vcycle(const igamg_ctx* c, cudaStream_t s, Workspace& w, int top, T* x_top,
         const T* b = (l == top) ? b_top : B[l].b;
         T* e = (l - 1 == top) ? x_top : B[l - 1].x;
         dev::prolong_add<T>(s, dim, tv[l], lv[l], e, x, B[l].TM, B[l].TK, B[l].tmp1, B[l].tmp2);
+        if (l == top && capture_mid)                                                    // state before post-smoothing
+            cudaMemcpyAsync(capture_mid, x, lv[l].n() * sizeof(T), cudaMemcpyDeviceToDevice, s);
+        if constexpr (std::is_same<T, float>::value) {
+            if (l == top && learned_top) {                  // learned post-smoother: x += CNN(b - A x)
+                dev::residual<float, float>(s, dim, lv[l], b, B[l].TM, B[l].TK, B[l].r, nullptr);
+                cnn_forward(s, 1, lv[l].m[1] * lv[l].m[2], lv[l].m[0], B[l].r, c->cnn_w, x, 1, w.cnn);
+                continue;
+            }
+        }
         dev::gs_sweep<T>(s, dim, lv[l], true, x, b, B[l].TM, B[l].TK);                // post-smooth
     }
 }
@@ -311,7 +330,7 @@ void fixed_point_step(const igamg_ctx* c, cudaStream_t s, Workspace& w, int prec
         LevelBuf<float>& G = w.f[top];
         // r = b - A s in FP64, rounded to FP32; e = V32(0; r); s_out = s_in + e (FP64)
         dev::residual<double, float>(s, c->dim, c->lv64[top], d_b, F.TM, F.TK, G.b, nullptr);
-        vcycle<float>(c, s, w, top, G.x, G.b, true);
+        vcycle<float>(c, s, w, top, G.x, G.b, true, prec == IGAMG_FP32_IR_LEARNED);
         dev::xpass<double, float>(s, c->lv64[top], S_in, S_out, G.x, 0, nullptr, nullptr, 0, F.TM, F.TK);
     }
 }
@@ -362,26 +381,28 @@ igamg_status check_ws(const igamg_ctx* c, void* ws, size_t bytes, int k, int pre
 // right-hand side, workspace, k, method, precision and test).
 igamg_status ensure_graph(igamg_ctx* c, Workspace& w, const double* d_b, void* d_ws, int kk, int extrap,
                           int prec, const double* denom) {
+    const int slot = prec == IGAMG_FP32_IR_LEARNED ? 1 : 0;
     igamg_ctx::Key key;
     key.b = d_b; key.ws = d_ws; key.k = kk; key.extrap = extrap; key.prec = prec;
     key.abs_tol = denom == nullptr;
-    if (c->exec && c->key == key) return IGAMG_OK;
-    if (c->exec) { cudaGraphExecDestroy(c->exec); c->exec = nullptr; }
+    key.w = slot ? c->cnn_w : nullptr;
+    if (c->exec[slot] && c->key[slot] == key) return IGAMG_OK;
+    if (c->exec[slot]) { cudaGraphExecDestroy(c->exec[slot]); c->exec[slot] = nullptr; }
     cudaGraph_t g = nullptr;
     const long long before = launch_count();
     CUDA_TRY(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
     restart_body(c, c->cap, w, extrap, kk, prec, d_b, denom);
     cudaError_t ce = cudaStreamEndCapture(c->cap, &g);
     if (ce != cudaSuccess) return fail(IGAMG_ECUDA, std::string("capture: ") + cudaGetErrorString(ce));
-    c->exec_launches = launch_count() - before;
-    count_launch(-c->exec_launches);
-    ce = cudaGraphInstantiate(&c->exec, g, 0);
+    c->exec_launches[slot] = launch_count() - before;
+    count_launch(-c->exec_launches[slot]);
+    ce = cudaGraphInstantiate(&c->exec[slot], g, 0);
     cudaGraphDestroy(g);
     if (ce != cudaSuccess) {
-        c->exec = nullptr;
+        c->exec[slot] = nullptr;
         return fail(IGAMG_ECUDA, std::string("instantiate: ") + cudaGetErrorString(ce));
     }
-    c->key = key;
+    c->key[slot] = key;
     return IGAMG_OK;
 }
 
@@ -714,7 +735,9 @@ igamg_status igamg_solve(igamg_ctx* c, const double* d_b, double* d_x, double to
                          void* stream, double* h_hist, int* h_cycles, int* h_vcycles) {
     if (igamg_status st = check_ctx(c)) return st;
     if (!d_b || !d_x) return fail(IGAMG_EINVAL, "null vector");
-    if (extrap < 0 || extrap > 2 || prec < 0 || prec > 1) return fail(IGAMG_EINVAL, "bad extrap/prec");
+    if (extrap < 0 || extrap > 2 || prec < 0 || prec > 2) return fail(IGAMG_EINVAL, "bad extrap/prec");
+    if (prec == IGAMG_FP32_IR_LEARNED && !c->cnn_w) return fail(IGAMG_EINVAL, "no learned smoother set");
+    c->fell_back = 0;
     if (extrap != IGAMG_EXTRAP_NONE && (k < 1 || k > kMaxQ)) return fail(IGAMG_EINVAL, "k must be in [1, 12]");
     if (max_cycles < 0 || !(tol >= 0.0)) return fail(IGAMG_EINVAL, "bad max_cycles/tol");
     const int kk = (extrap == IGAMG_EXTRAP_NONE) ? 1 : k;
@@ -754,24 +777,34 @@ igamg_status igamg_solve(igamg_ctx* c, const double* d_b, double* d_x, double to
     igamg_status result = IGAMG_ENOTCONV;
     if (res <= tol) result = IGAMG_OK;
     const bool use_graph = !(flags & IGAMG_FLAG_NO_GRAPH);
+    int cur = prec;                                    // the learned form may fall back to plain smoothing
     if (use_graph && result != IGAMG_OK && max_cycles > 0)
-        if (igamg_status st = ensure_graph(c, w, d_b, d_ws, kk, extrap, prec, denom)) return st;
+        if (igamg_status st = ensure_graph(c, w, d_b, d_ws, kk, extrap, cur, denom)) return st;
     int cyc = 0;
     for (cyc = 1; cyc <= max_cycles && result != IGAMG_OK; ++cyc) {
+        const int slot = cur == IGAMG_FP32_IR_LEARNED ? 1 : 0;
         if (use_graph) {
-            CUDA_TRY(cudaGraphLaunch(c->exec, s));
-            count_launch(c->exec_launches);
+            CUDA_TRY(cudaGraphLaunch(c->exec[slot], s));
+            count_launch(c->exec_launches[slot]);
         } else {
-            restart_body(c, s, w, extrap, kk, prec, d_b, denom);
+            restart_body(c, s, w, extrap, kk, cur, d_b, denom);
         }
         CUDA_TRY(cudaMemcpyAsync(c->h_pin, w.scal + 1, 8, cudaMemcpyDeviceToHost, s));
         CUDA_TRY(cudaStreamSynchronize(s));
+        const double prev = res;
         res = c->h_pin[0];
         if (h_hist) h_hist[cyc] = res;
         if (h_cycles) *h_cycles = cyc;
         if (h_vcycles) *h_vcycles = cyc * (extrap == IGAMG_EXTRAP_NONE ? 1 : kk + 1);
         if (!std::isfinite(res)) { result = IGAMG_EBREAKDOWN; fail(result, "non-finite residual"); break; }
-        if (res <= tol) result = IGAMG_OK;
+        if (res <= tol) { result = IGAMG_OK; break; }
+        if (cur == IGAMG_FP32_IR_LEARNED && res > c->stall * prev) {
+            // the network stalled: plain multicolour Gauss-Seidel post-smoothing from here on
+            cur = IGAMG_FP32_IR;
+            c->fell_back = 1;
+            if (use_graph)
+                if (igamg_status st = ensure_graph(c, w, d_b, d_ws, kk, extrap, cur, denom)) return st;
+        }
     }
     CUDA_TRY(cudaMemcpyAsync(d_x, w.S, N * 8, cudaMemcpyDeviceToDevice, s));
     CUDA_TRY(cudaStreamSynchronize(s));
@@ -844,7 +877,8 @@ igamg_status igamg_coarse_solve(igamg_ctx* c, const double* d_r, double* d_e, vo
 igamg_status igamg_vcycle(igamg_ctx* c, double* d_x, const double* d_b, int prec, void* d_ws, size_t ws_bytes,
                           void* stream) {
     if (igamg_status st = check_ctx(c)) return st;
-    if (!d_x || !d_b || prec < 0 || prec > 1) return fail(IGAMG_EINVAL, "bad vcycle arguments");
+    if (!d_x || !d_b || prec < 0 || prec > 2) return fail(IGAMG_EINVAL, "bad vcycle arguments");
+    if (prec == IGAMG_FP32_IR_LEARNED && !c->cnn_w) return fail(IGAMG_EINVAL, "no learned smoother set");
     if (igamg_status st = check_ws(c, d_ws, ws_bytes, 1, prec)) return st;
     Workspace w = carve(c, d_ws, 1, prec);
     cudaStream_t s = (cudaStream_t)stream;
@@ -890,9 +924,36 @@ igamg_status igamg_extrapolate(long n, int q, int method, const double* d_S, lon
     return IGAMG_OK;
 }
 
+igamg_status igamg_set_smoother(igamg_ctx* c, const float* d_w, double stall_ratio) {
+    if (igamg_status st = check_ctx(c)) return st;
+    if (!(stall_ratio > 0.0)) return fail(IGAMG_EINVAL, "stall ratio must be positive");
+    if (d_w && c->dim != 2) return fail(IGAMG_EINVAL, "the learned smoother is a 2D network");
+    c->cnn_w = d_w;
+    c->stall = stall_ratio;
+    return IGAMG_OK;
+}
+
+int igamg_smoother_fell_back(const igamg_ctx* c) { return c ? c->fell_back : 0; }
+
+igamg_status igamg_vcycle_probe(igamg_ctx* c, double* d_x, const double* d_b, double* d_x_mid, void* d_ws,
+                                size_t ws_bytes, void* stream) {
+    if (igamg_status st = check_ctx(c)) return st;
+    if (!d_x || !d_b || !d_x_mid) return fail(IGAMG_EINVAL, "bad probe arguments");
+    if (igamg_status st = check_ws(c, d_ws, ws_bytes, 1, IGAMG_FP64)) return st;
+    Workspace w = carve(c, d_ws, 1, IGAMG_FP64);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int top = c->L - 1;
+    dev::xpass<double, double>(s, c->lv64[top], d_x, nullptr, nullptr, 0, nullptr, nullptr, 0, w.d[top].TM,
+                               w.d[top].TK);
+    vcycle<double>(c, s, w, top, d_x, d_b, false, false, d_x_mid);
+    CUDA_TRY(cudaGetLastError());
+    return IGAMG_OK;
+}
+
 void igamg_destroy(igamg_ctx* c) {
     if (!c) return;
-    if (c->exec) cudaGraphExecDestroy(c->exec);
+    for (int sl = 0; sl < 2; ++sl)
+        if (c->exec[sl]) cudaGraphExecDestroy(c->exec[sl]);
     if (c->cap) cudaStreamDestroy(c->cap);
     if (c->h_pin) cudaFreeHost(c->h_pin);
     if (c->dmem) cudaFree(c->dmem);
@@ -1035,8 +1096,8 @@ igamg_status igamg_batch_solve(igamg_batch* B, const double* d_b, double* d_x, d
         for (int i = 0; i < B->count; ++i) {
             if (stat[i] != IGAMG_ENOTCONV) continue;
             cudaStream_t s = B->streams[B->lane[i]];
-            CUDA_TRY(cudaGraphLaunch(B->ctx[i]->exec, s));
-            count_launch(B->ctx[i]->exec_launches);
+            CUDA_TRY(cudaGraphLaunch(B->ctx[i]->exec[0], s));
+            count_launch(B->ctx[i]->exec_launches[0]);
             CUDA_TRY(cudaMemcpyAsync(B->h_pin + 2 * i + 1, W[i].scal + 1, 8, cudaMemcpyDeviceToHost, s));
             ++active;
         }

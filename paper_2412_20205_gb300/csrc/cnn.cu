@@ -7,9 +7,16 @@
 // vector: W1[co][tap] (144), W2[co][ci][tap] (2304), W3[ci][tap] (144), with
 // tap = 3 (dy + 1) + (dx + 1) reading pixel (y + dy, x + dx).
 //
-// The 16 -> 16 layer is the only dense contraction (implicit GEMM with
-// M = pixels, N = 16, K = 144); its forward and input-gradient kernels run on
-// the tensor cores (mma.sync m16n8k16, BF16 in, FP32 accumulate).
+// Numerics everywhere: the input residual and the weights are rounded to
+// BF16, products accumulate in FP32, hidden activations are stored in BF16.
+//
+// Inference (the solver's post-smoother) runs the whole network in one fused
+// kernel per output tile with the activations in shared memory and all three
+// layers on the tensor cores (implicit GEMMs, M = pixels: 1 -> 16 with K = 9
+// taps, 16 -> 16 with K = 144, 16 -> 1 with K = 144).  Training runs the
+// layers as separate kernels that keep both activations for the backward
+// pass; there the 16 -> 16 forward and input-gradient contractions run on the
+// tensor cores and the rest on the FP32 cores.
 #include "../../include/igamg.h"
 #include "device.hpp"
 
@@ -25,6 +32,8 @@ constexpr int C = 16;
 constexpr int NW1 = C * 9, NW2 = C * C * 9, NW3 = C * 9;
 constexpr int NW = NW1 + NW2 + NW3;
 constexpr int kT = 256;
+
+__device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 
 struct Shape {
     int B, H, W;
@@ -82,7 +91,7 @@ __device__ __forceinline__ void store16(__nv_bfloat16* a, long long p, const flo
 __global__ void __launch_bounds__(kT) k_conv1(Shape s, const float* __restrict__ r, const float* __restrict__ w,
                                               __nv_bfloat16* __restrict__ a1) {
     __shared__ float W1[NW1];
-    for (int i = threadIdx.x; i < NW1; i += blockDim.x) W1[i] = w[i];
+    for (int i = threadIdx.x; i < NW1; i += blockDim.x) W1[i] = bf16r(w[i]);
     __syncthreads();
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < s.pixels();
          p += (long long)gridDim.x * blockDim.x) {
@@ -91,7 +100,7 @@ __global__ void __launch_bounds__(kT) k_conv1(Shape s, const float* __restrict__
 #pragma unroll
         for (int t = 0; t < 9; ++t) {
             const long long q = px.nb(s, t);
-            nb[t] = q >= 0 ? r[q] : 0.f;
+            nb[t] = q >= 0 ? bf16r(r[q]) : 0.f;
         }
         float v[C];
 #pragma unroll
@@ -200,7 +209,7 @@ __global__ void __launch_bounds__(kT) k_conv2(Shape s, const __nv_bfloat16* __re
 __global__ void __launch_bounds__(kT) k_conv3(Shape s, const __nv_bfloat16* __restrict__ a2, const float* __restrict__ w,
                                               float* __restrict__ y, int accumulate) {
     __shared__ float W3[NW3];
-    for (int i = threadIdx.x; i < NW3; i += blockDim.x) W3[i] = w[NW1 + NW2 + i];
+    for (int i = threadIdx.x; i < NW3; i += blockDim.x) W3[i] = bf16r(w[NW1 + NW2 + i]);
     __syncthreads();
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < s.pixels();
          p += (long long)gridDim.x * blockDim.x) {
@@ -217,6 +226,179 @@ __global__ void __launch_bounds__(kT) k_conv3(Shape s, const __nv_bfloat16* __re
         }
         if (accumulate) y[p] += acc;
         else y[p] = acc;
+    }
+}
+
+
+// ------------------------------------------------------------------ fused inference
+// One CTA pass computes the network on a TH x TW output tile: the residual is
+// staged with a 3-pixel halo, layer-1 activations are computed on a 2-pixel
+// halo and layer-2 activations on a 1-pixel halo (the halos are recomputed by
+// the neighbouring tiles), all in shared memory; only r is read and y written
+// in global memory.  The weight fragments live in registers for the whole
+// (persistent, grid-stride) kernel.
+namespace fused {
+constexpr int TH = 16, TW = 32;
+constexpr int RH = TH + 6, RW = TW + 6;
+constexpr int A1H = TH + 4, A1W = TW + 4;
+constexpr int A2H = TH + 2, A2W = TW + 2;
+constexpr int NR = RH * RW, NA1 = A1H * A1W, NA2 = A2H * A2W, NO = TH * TW;
+constexpr int S1 = (NA1 + 15) / 16, S2 = (NA2 + 15) / 16, S3 = NO / 16;
+constexpr int kSmem = NA1 * 32 + NA2 * 32 + NR * 4;
+constexpr int kThreads = 256, kWarps = kThreads / 32;
+constexpr int kBlocks = 152 * 2;
+static_assert(TW % 16 == 0, "output strips of 16 pixels run along x");
+static_assert(kSmem <= 48 * 1024, "within the default dynamic shared-memory limit");
+}  // namespace fused
+
+// Byte offset of half h (channels 8h .. 8h+7) of pixel q in a shared-memory
+// activation tile: 32 bytes per pixel, the two halves swapped when bit 2 of q
+// is set, so that one half of eight consecutive pixels falls in eight distinct
+// 16-byte bank groups (conflict-free ldmatrix phases).
+__device__ __forceinline__ uint32_t act_off(int q, int h) {
+    return (uint32_t)q * 32u + ((uint32_t)(h ^ ((q >> 2) & 1)) << 4);
+}
+
+// Four 8x8 BF16 matrices from shared memory; lanes 8i .. 8i+7 give the row
+// addresses of matrix i, which lands in register i of every lane in the
+// m16n8k16 A-fragment order.
+__device__ __forceinline__ void ldsm_x4(uint32_t* a, uint32_t addr) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3])
+                 : "r"(addr)
+                 : "memory");
+}
+
+// Stores the two 16-row x 16-channel C fragments of a strip (after ReLU) as
+// BF16 activations of pixels q0 + g and q0 + g + 8 of a tile whose pixel
+// (0, 0) is image pixel (y0, x0); pixels outside the image store 0 (the zero
+// padding of the next layer).
+template <int WIDTH, int NPIX>
+__device__ __forceinline__ void store_act(unsigned char* act, int q0, const float (*acc)[4], int y0, int x0,
+                                          const Shape& s) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+        const int q = q0 + g + 8 * hh;
+        if (q >= NPIX) continue;
+        const int yy = y0 + q / WIDTH, xx = x0 + q % WIDTH;
+        const bool in = yy >= 0 && yy < s.H && xx >= 0 && xx < s.W;
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+            const float v0 = in ? fmaxf(acc[nt][2 * hh], 0.f) : 0.f;
+            const float v1 = in ? fmaxf(acc[nt][2 * hh + 1], 0.f) : 0.f;
+            *reinterpret_cast<__nv_bfloat162*>(act + act_off(q, nt) + 4 * tq) = __floats2bfloat162_rn(v0, v1);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(fused::kThreads, 2)
+k_forward_fused(Shape s, const float* __restrict__ r, const float* __restrict__ w, float* __restrict__ y,
+                int accumulate) {
+    using namespace fused;
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char* a1 = smem;
+    unsigned char* a2 = smem + NA1 * 32;
+    float* sr = reinterpret_cast<float*>(smem + (NA1 + NA2) * 32);
+    const uint32_t a1s = (uint32_t)__cvta_generic_to_shared(a1);
+    const uint32_t a2s = (uint32_t)__cvta_generic_to_shared(a2);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, tq = lane & 3;
+
+    // B fragments: B(k, n) = weight of input k (tap or channel) for output n
+    uint32_t b1[2][2], b2[9][2][2], b3[9][2];
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+        const int n = nt * 8 + g;
+        b1[nt][0] = pack_bf16(w[n * 9 + 2 * tq], w[n * 9 + 2 * tq + 1]);
+        b1[nt][1] = pack_bf16(tq == 0 ? w[n * 9 + 8] : 0.f, 0.f);             // taps 9..15 are padding
+    }
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+            const float* Wn = w + NW1 + (nt * 8 + g) * C * 9 + t;              // W2[n][ci][t], ci stride 9
+            b2[t][nt][0] = pack_bf16(Wn[(2 * tq) * 9], Wn[(2 * tq + 1) * 9]);
+            b2[t][nt][1] = pack_bf16(Wn[(2 * tq + 8) * 9], Wn[(2 * tq + 9) * 9]);
+        }
+        const float* W3 = w + NW1 + NW2 + t;                                   // W3[ci][t]; output column 0 only
+        b3[t][0] = g == 0 ? pack_bf16(W3[(2 * tq) * 9], W3[(2 * tq + 1) * 9]) : 0u;
+        b3[t][1] = g == 0 ? pack_bf16(W3[(2 * tq + 8) * 9], W3[(2 * tq + 9) * 9]) : 0u;
+    }
+
+    const int tiles_x = (s.W + TW - 1) / TW, tiles_y = (s.H + TH - 1) / TH;
+    const long long per_img = (long long)tiles_x * tiles_y;
+    const long long ntiles = per_img * s.B;
+    const int lm = (lane & 7) + ((lane >> 3) & 1) * 8, lh = lane >> 4;          // this lane's ldmatrix row
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const long long img = tile / per_img;
+        const int rem = (int)(tile - img * per_img);
+        const int oy = (rem / tiles_x) * TH, ox = (rem % tiles_x) * TW;
+        const long long base = img * s.H * s.W;
+
+        for (int i = threadIdx.x; i < NR; i += kThreads) {                      // residual, 3-pixel halo
+            const int yy = oy - 3 + i / RW, xx = ox - 3 + i % RW;
+            sr[i] = (yy >= 0 && yy < s.H && xx >= 0 && xx < s.W) ? r[base + (long long)yy * s.W + xx] : 0.f;
+        }
+        __syncthreads();
+
+        // layer 1: K = 9 taps (padded to 16), on the 2-pixel halo region
+        for (int st = warp; st < S1; st += kWarps) {
+            uint32_t a[4];
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                const int q = min(st * 16 + g + 8 * hh, NA1 - 1);
+                const float* rp = sr + (q / A1W) * RW + q % A1W;                // tap t reads rp[(t/3) RW + t%3]
+                const int t0 = 2 * tq, t1 = 2 * tq + 1;
+                a[hh] = pack_bf16(rp[(t0 / 3) * RW + t0 % 3], rp[(t1 / 3) * RW + t1 % 3]);
+                a[2 + hh] = pack_bf16(tq == 0 ? rp[2 * RW + 2] : 0.f, 0.f);
+            }
+            float acc[2][4] = {};
+            mma_bf16(acc[0], a, b1[0]);
+            mma_bf16(acc[1], a, b1[1]);
+            store_act<A1W, NA1>(a1, st * 16, acc, oy - 2, ox - 2, s);
+        }
+        __syncthreads();
+
+        // layer 2: K = 9 taps x 16 channels, on the 1-pixel halo region
+        for (int st = warp; st < S2; st += kWarps) {
+            const int qm = min(st * 16 + lm, NA2 - 1);
+            const int q1 = (qm / A2W) * A1W + qm % A2W;                         // a1 pixel under tap (0, 0)
+            float acc[2][4] = {};
+#pragma unroll
+            for (int t = 0; t < 9; ++t) {
+                uint32_t a[4];
+                ldsm_x4(a, a1s + act_off(q1 + (t / 3) * A1W + t % 3, lh));
+                mma_bf16(acc[0], a, b2[t][0]);
+                mma_bf16(acc[1], a, b2[t][1]);
+            }
+            store_act<A2W, NA2>(a2, st * 16, acc, oy - 1, ox - 1, s);
+        }
+        __syncthreads();
+
+        // layer 3: K = 9 taps x 16 channels, N = 8 with only column 0 in use
+        for (int st = warp; st < S3; st += kWarps) {
+            const int q0 = st * 16, oyq = q0 / TW, ox0 = q0 % TW;
+            const int q2 = oyq * A2W + ox0 + lm;                                // a2 pixel under tap (0, 0)
+            float acc[4] = {};
+#pragma unroll
+            for (int t = 0; t < 9; ++t) {
+                uint32_t a[4];
+                ldsm_x4(a, a2s + act_off(q2 + (t / 3) * A2W + t % 3, lh));
+                mma_bf16(acc, a, b3[t]);
+            }
+            if (tq == 0) {
+#pragma unroll
+                for (int hh = 0; hh < 2; ++hh) {
+                    const int yy = oy + oyq, xx = ox + ox0 + g + 8 * hh;
+                    if (yy < s.H && xx < s.W) {
+                        const long long i = base + (long long)yy * s.W + xx;
+                        y[i] = accumulate ? y[i] + acc[2 * hh] : acc[2 * hh];
+                    }
+                }
+            }
+        }
+        // The next pass rewrites sr (read only by layer 1), then a1 and a2,
+        // each after a barrier that every warp reaches only when done here.
     }
 }
 
@@ -247,7 +429,7 @@ __global__ void __launch_bounds__(kT) k_loss(Shape s, const float* __restrict__ 
 __global__ void __launch_bounds__(kT) k_conv3_dgrad(Shape s, const float* __restrict__ gy, const float* __restrict__ w,
                                                     const __nv_bfloat16* __restrict__ a2, __nv_bfloat16* __restrict__ g2) {
     __shared__ float W3[NW3];
-    for (int i = threadIdx.x; i < NW3; i += blockDim.x) W3[i] = w[NW1 + NW2 + i];
+    for (int i = threadIdx.x; i < NW3; i += blockDim.x) W3[i] = bf16r(w[NW1 + NW2 + i]);
     __syncthreads();
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < s.pixels();
          p += (long long)gridDim.x * blockDim.x) {
@@ -346,7 +528,7 @@ __global__ void __launch_bounds__(kT) k_wgrad(Shape s, const float* __restrict__
             if (q >= 0) {
                 load16(a1, q, v1);
                 load16(a2, q, v2);
-                sr[pi][t] = r[q];
+                sr[pi][t] = bf16r(r[q]);
             } else {
                 for (int c = 0; c < C; ++c) v1[c] = v2[c] = 0.f;
                 sr[pi][t] = 0.f;
@@ -439,20 +621,29 @@ static WS carve_ws(void* base, long long P) {
     return w;
 }
 
-void forward(cudaStream_t st, Shape s, const float* r, const float* w, float* y, int accumulate, void* ws) {
+// Forward pass that keeps both hidden activations in the workspace (training).
+void forward_stored(cudaStream_t st, Shape s, const float* r, const float* w, float* y, void* ws) {
     WS W = carve_ws(ws, s.pixels());
     const long long P = s.pixels();
     k_conv1<<<grid(P, kT), kT, 0, st>>>(s, r, w, W.a1);
     k_conv2<<<grid((P + 15) / 16, kT / 32), kT, 0, st>>>(s, W.a1, w, W.a2);
-    k_conv3<<<grid(P, kT), kT, 0, st>>>(s, W.a2, w, y, accumulate);
+    k_conv3<<<grid(P, kT), kT, 0, st>>>(s, W.a2, w, y, 0);
     count_launch(3);
+}
+
+// Inference: y = net(r), or y += net(r) with accumulate; one fused launch.
+void forward(cudaStream_t st, Shape s, const float* r, const float* w, float* y, int accumulate) {
+    const long long tiles = (long long)s.B * ((s.H + fused::TH - 1) / fused::TH) * ((s.W + fused::TW - 1) / fused::TW);
+    const int blocks = (int)(tiles < fused::kBlocks ? tiles : fused::kBlocks);
+    k_forward_fused<<<blocks, fused::kThreads, fused::kSmem, st>>>(s, r, w, y, accumulate);
+    count_launch();
 }
 
 void gradient(cudaStream_t st, Shape s, const float* r, const float* e, const float* w, float* grad, float* loss,
               float* y, void* ws) {
     WS W = carve_ws(ws, s.pixels());
     const long long P = s.pixels();
-    forward(st, s, r, w, y, 0, ws);
+    forward_stored(st, s, r, w, y, ws);
     const int gl = grid(P, kT) > 1024 ? 1024 : grid(P, kT);
     k_loss<<<gl, kT, 0, st>>>(s, y, e, W.gy, W.lpart);
     k_conv3_dgrad<<<grid(P, kT), kT, 0, st>>>(s, W.gy, w, W.a2, W.g2);
@@ -467,7 +658,8 @@ void gradient(cudaStream_t st, Shape s, const float* r, const float* e, const fl
 size_t cnn_workspace_bytes(long long pixels) { return cnn::workspace_bytes(pixels); }
 void cnn_forward(cudaStream_t st, int B, int H, int W, const float* r, const float* w, float* y, int accumulate,
                  void* ws) {
-    cnn::forward(st, cnn::Shape{B, H, W}, r, w, y, accumulate, ws);
+    (void)ws;
+    cnn::forward(st, cnn::Shape{B, H, W}, r, w, y, accumulate);
 }
 
 }  // namespace igamg
@@ -493,7 +685,7 @@ igamg_status igamg_cnn_forward(int batch, int H, int W, const float* d_r, const 
         set_last_error("network workspace too small or unaligned");
         return IGAMG_ENOMEM;
     }
-    cnn::forward((cudaStream_t)stream, cnn::Shape{batch, H, W}, d_r, d_w, d_y, 0, d_ws);
+    cnn::forward((cudaStream_t)stream, cnn::Shape{batch, H, W}, d_r, d_w, d_y, 0);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { set_last_error(std::string("network forward: ") + cudaGetErrorString(e)); return IGAMG_ECUDA; }
     return IGAMG_OK;
