@@ -229,7 +229,7 @@ def igamg_launch_count():
     return int(_load().igamg_launch_count())
 
 
-def igamg_set_smoother(ctx, w, stall_ratio=0.5):
+def igamg_set_smoother(ctx, w, stall_ratio=0.95):
     _check(_load().igamg_set_smoother(ctx, _ptr(w), stall_ratio), "igamg_set_smoother")
 
 
@@ -326,7 +326,7 @@ class Solver:
         self.k_max = k
         self.smoother = None
 
-    def set_smoother(self, w, stall_ratio=0.5):
+    def set_smoother(self, w, stall_ratio=0.95):
         """Use network weights w (device FP32 tensor, kept referenced here) as the
         learned post-smoother of prec='fp32_ir_learned' solves."""
         self.smoother = w
