@@ -213,6 +213,16 @@ igamg_status igamg_adam_step(int n, float* d_w, const float* d_g, float* d_m, fl
 igamg_status igamg_set_smoother(igamg_ctx* ctx, const float* d_w, double stall_ratio);
 int igamg_smoother_fell_back(const igamg_ctx* ctx);
 
+/* Coarse tail of FP32 2D V-cycles (the paper's V-cycle, Algorithm 2, with a
+ * different schedule): levels 0..lc, each with at most 6000 unknowns and
+ * together fitting one CTA's shared memory, run in one kernel launch instead
+ * of one launch per smoothing phase and transfer pass.  Same arithmetic up to
+ * FP32 rounding order.  igamg_coarse_tail_level() returns lc (0: none or
+ * disabled); igamg_set_coarse_tail(ctx, 0) switches it off (on by default),
+ * e.g. to compare both schedules.  FP64 cycles and 3D problems never use it. */
+int igamg_coarse_tail_level(const igamg_ctx* ctx);
+igamg_status igamg_set_coarse_tail(igamg_ctx* ctx, int enable);
+
 /* One FP64 V-cycle in place on the finest d_x (as igamg_vcycle) that also
  * copies the iterate at the point just before the finest-level post-smoothing
  * (after the coarse correction) to d_x_mid: the network's training input. */

@@ -63,6 +63,8 @@ def _load():
         "igamg_destroy": (None, [vp]),
         "igamg_set_smoother": (c_int, [vp, vp, c_double]),
         "igamg_smoother_fell_back": (c_int, [vp]),
+        "igamg_coarse_tail_level": (c_int, [vp]),
+        "igamg_set_coarse_tail": (c_int, [vp, c_int]),
         "igamg_vcycle_probe": (c_int, [vp, vp, vp, vp, vp, c_size, vp]),
         "igamg_cnn_num_weights": (c_int, []),
         "igamg_cnn_workspace_bytes": (c_size, [c_int, c_int, c_int]),
@@ -235,6 +237,14 @@ def igamg_set_smoother(ctx, w, stall_ratio=0.95):
 
 def igamg_smoother_fell_back(ctx):
     return bool(_load().igamg_smoother_fell_back(ctx))
+
+
+def igamg_coarse_tail_level(ctx):
+    return int(_load().igamg_coarse_tail_level(ctx))
+
+
+def igamg_set_coarse_tail(ctx, enable):
+    _check(_load().igamg_set_coarse_tail(ctx, int(bool(enable))), "igamg_set_coarse_tail")
 
 
 def igamg_vcycle_probe(ctx, x, b, x_mid, ws, stream=None):

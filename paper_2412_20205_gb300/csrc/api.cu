@@ -102,6 +102,9 @@ struct igamg_ctx {
     std::vector<TransferView<float>> tv32;
     CoarseView<double> cv64{};
     CoarseView<float> cv32{};
+    // coarse levels of the FP32 2D V-cycle in one CTA (tail32.lc = 0: none)
+    TailView<float> tail32{};
+    bool tail_on = true;
     // sine-moment tables for the load vector (finest level)
     cudaStream_t cap = nullptr;             // capture stream
     double* h_pin = nullptr;                // pinned host scalars
@@ -275,7 +278,11 @@ void vcycle(const igamg_ctx* c, cudaStream_t s, Workspace& w, int top, T* x_top,
     const auto& tv = Views<T>::tv(c);
     auto& B = Views<T>::buf(w);
     const int dim = c->dim;
-    for (int l = top; l >= 1; --l) {
+    // FP32 2D cycles hand levels lc..0 to one CTA when the hierarchy has a tail
+    int lc = 0;
+    if constexpr (std::is_same<T, float>::value)
+        if (c->tail_on && c->tail32.lc > 0 && c->tail32.lc < top) lc = c->tail32.lc;
+    for (int l = top; l >= (lc > 0 ? lc + 1 : 1); --l) {
         T* x = (l == top) ? x_top : B[l].x;
         const T* b = (l == top) ? b_top : B[l].b;
         const size_t N = lv[l].n();
@@ -290,12 +297,15 @@ void vcycle(const igamg_ctx* c, cudaStream_t s, Workspace& w, int top, T* x_top,
         dev::residual<T, T>(s, dim, lv[l], b, B[l].TM, B[l].TK, B[l].r, nullptr);      // r = b - A u
         dev::restrict_<T>(s, dim, tv[l], B[l].r, B[l - 1].b, B[l].tmp1, B[l].tmp2);   // R = P^T
     }
-    {
+    if (lc > 0) {
+        if constexpr (std::is_same<T, float>::value)
+            dev::coarse_tail<float>(s, c->tail32, B[lc].b, B[lc].x);                   // levels lc..0
+    } else {
         T* x0 = (top == 0) ? x_top : B[0].x;
         const T* b0 = (top == 0) ? b_top : B[0].b;
         dev::coarse_solve<T>(s, dim, Views<T>::cv(c), b0, x0);                          // direct
     }
-    for (int l = 1; l <= top; ++l) {
+    for (int l = lc + 1; l <= top; ++l) {
         T* x = (l == top) ? x_top : B[l].x;
         const T* b = (l == top) ? b_top : B[l].b;
         T* e = (l - 1 == top) ? x_top : B[l - 1].x;
@@ -688,6 +698,43 @@ igamg_status igamg_assemble(igamg_ctx* c) {
     }
     c->cv64.laminv = (const double*)(base + cLo[0]);
     c->cv32.laminv = (const float*)(base + cLo[1]);
+    // Coarse tail of the FP32 2D cycle: the highest level below the finest
+    // whose levels 0..lc fit one CTA's shared memory and that one SM handles
+    // faster than a launch per step (kTailMaxN unknowns at most).
+    constexpr size_t kTailMaxN = 6000;
+    c->tail32.lc = 0;
+    if (dim == 2 && L >= 3) {
+        const size_t limit = dev::tail_smem_limit();
+        for (int l = 1; l <= std::min(L - 2, kTailLevels - 1); ++l) {
+            TailView<float> v{};
+            int off = 0;
+            for (int q = 0; q <= l; ++q) {
+                const int n = (int)c->hl[q].N();
+                v.off_x[q] = off; off += (c->hl[q].m[0] + 2 * p) * (c->hl[q].m[1] + 2 * p);   // zero halo of p
+                v.off_b[q] = off; off += n;
+                v.off_inv[q] = off; off += q > 0 ? n : 0;
+                v.off_band[q] = off; off += q > 0 ? 2 * (2 * p + 1) * (c->hl[q].m[0] + c->hl[q].m[1]) : 0;
+            }
+            for (int q = 1; q <= l; ++q) {
+                v.off_tr[q] = off;
+                off += tail_transfer_elems(c->tv32[q]);
+            }
+            v.off_cv = off;
+            off += c->hl[0].m[0] * c->hl[0].m[0] + c->hl[0].m[1] * c->hl[0].m[1] + (int)c->hl[0].N();
+            const int nl = (int)c->hl[l].N();
+            v.off_r = off; off += nl;
+            v.off_t = off; off += nl;
+            v.smem = (size_t)off * sizeof(float);
+            if ((size_t)nl > kTailMaxN || v.smem > limit) break;
+            v.lc = l;
+            for (int q = 0; q <= l; ++q) {
+                v.L[q] = c->lv32[q];
+                v.X[q] = c->tv32[q];
+            }
+            v.C = c->cv32;
+            c->tail32 = v;
+        }
+    }
     CUDA_TRY(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
     CUDA_TRY(cudaMallocHost(&c->h_pin, 64));
     c->assembled = true;
@@ -934,6 +981,24 @@ igamg_status igamg_set_smoother(igamg_ctx* c, const float* d_w, double stall_rat
 }
 
 int igamg_smoother_fell_back(const igamg_ctx* c) { return c ? c->fell_back : 0; }
+
+int igamg_coarse_tail_level(const igamg_ctx* c) {
+    return (c && c->assembled && c->tail_on) ? c->tail32.lc : 0;
+}
+
+igamg_status igamg_set_coarse_tail(igamg_ctx* c, int enable) {
+    if (igamg_status st = check_ctx(c)) return st;
+    const bool on = enable != 0;
+    if (on == c->tail_on) return IGAMG_OK;
+    c->tail_on = on;
+    for (int sl = 0; sl < 2; ++sl)              // recapture with the other form
+        if (c->exec[sl]) {
+            cudaGraphExecDestroy(c->exec[sl]);
+            c->exec[sl] = nullptr;
+            c->key[sl] = igamg_ctx::Key{};
+        }
+    return IGAMG_OK;
+}
 
 igamg_status igamg_vcycle_probe(igamg_ctx* c, double* d_x, const double* d_b, double* d_x_mid, void* d_ws,
                                 size_t ws_bytes, void* stream) {

@@ -56,6 +56,31 @@ struct CoarseView {
     const T* laminv;                      // 1 / (lam_x + lam_y (+ lam_z)), x fastest
 };
 
+// Coarse part of a 2D V-cycle run by one CTA (levels 0..lc): the level views,
+// the transfers X[l] between levels l-1 and l, the coarsest solve, and the
+// shared-memory element offsets of every level's x, b, inverse diagonal and
+// four band arrays (M_x, K_x, M_y, K_y, band-major) and of two scratch
+// vectors.  lc = 0 means the hierarchy has no such tail.
+constexpr int kTailLevels = 6;
+template <typename T>
+struct TailView {
+    int lc;
+    int off_x[kTailLevels], off_b[kTailLevels], off_inv[kTailLevels], off_band[kTailLevels], off_r, off_t;
+    int off_tr[kTailLevels];              // transfer tables of X[l] (see tail_transfer_elems)
+    int off_cv;                           // V_x, V_y, laminv of the coarsest solve
+    size_t smem;                          // dynamic shared memory in bytes
+    LevelView<T> L[kTailLevels];
+    TransferView<T> X[kTailLevels];
+    CoarseView<T> C;
+};
+
+// Shared-memory elements (4-byte) of the staged tables of one 2D transfer:
+// plo/pv and rlo/rv of both directions.
+template <typename T>
+IGAMG_HD inline int tail_transfer_elems(const TransferView<T>& X) {
+    return X.mf[0] * (1 + X.pw[0]) + X.mf[1] * (1 + X.pw[1]) + X.mc[0] * (1 + X.rw[0]) + X.mc[1] * (1 + X.rw[1]);
+}
+
 // Device-side state of one extrapolation (CholeskyQR2 pass-1 results).
 struct ExtrapInfo {
     int done, a, dep, pad;
@@ -84,6 +109,16 @@ namespace dev {
 // Raise every kernel's dynamic shared-memory limit on the current device
 // (once per device; must run outside stream capture).
 void prepare_kernels();
+void prepare_tail_kernels(int optin);
+
+// Largest single-CTA shared-memory size for the coarse tail on this device.
+size_t tail_smem_limit();
+
+// Levels lc..0 of one 2D V-cycle (pre-smoothing, residual, restriction,
+// coarsest solve, prolongation, post-smoothing) in one CTA, starting from
+// x = 0 on every level: reads level lc's right side b, writes its x.
+template <typename T>
+void coarse_tail(cudaStream_t s, const TailView<T>& V, const T* b, T* x);
 
 // T_M = (I (x) M_x) x, T_K = (I (x) K_x) x row by row.  With add != nullptr the
 // row is first replaced by x + add (written to x_out), with nS > 0 by

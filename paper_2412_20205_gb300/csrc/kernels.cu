@@ -13,6 +13,7 @@
 //   2D: (A x)_row = sum_{dj} Ky(j, j+dj) T_M(row+dj) + My(j, j+dj) T_K(row+dj)
 //   3D: coefficients Kz My + Mz Ky on T_M and Mz My on T_K, over (dj, dk).
 #include "device.hpp"
+#include "bands.cuh"
 
 #include <cstdio>
 #include <type_traits>
@@ -47,26 +48,6 @@ __device__ T block_sum(T v, T* red) {
         for (int i = 0; i < (int)(blockDim.x + 31) / 32; ++i) s += red[i];
     __syncthreads();
     return s;
-}
-
-// x-direction band entry (row i, band b): the Toeplitz interior comes from the
-// kernel parameters, the p boundary rows at each end from the band arrays.
-template <typename T>
-__device__ __forceinline__ T band_m(const LevelView<T>& L, int i, int b) {
-    return (i >= L.tlo[0] && i < L.thi[0]) ? L.Mc[0][b] : L.Mb[0][b * L.m[0] + i];
-}
-template <typename T>
-__device__ __forceinline__ T band_k(const LevelView<T>& L, int i, int b) {
-    return (i >= L.tlo[0] && i < L.thi[0]) ? L.Kc[0][b] : L.Kb[0][b * L.m[0] + i];
-}
-// band entry of direction d (row i, band b) for d = 1, 2
-template <typename T>
-__device__ __forceinline__ T band_md(const LevelView<T>& L, int d, int i, int b) {
-    return (i >= L.tlo[d] && i < L.thi[d]) ? L.Mc[d][b] : L.Mb[d][b * L.m[d] + i];
-}
-template <typename T>
-__device__ __forceinline__ T band_kd(const LevelView<T>& L, int d, int i, int b) {
-    return (i >= L.tlo[d] && i < L.thi[d]) ? L.Kc[d][b] : L.Kb[d][b * L.m[d] + i];
 }
 
 // Row-coupling coefficients of row (j, k): for neighbour q = (dj, dk) the
@@ -843,6 +824,7 @@ void prepare_kernels() {
     };
     all_p(0.0);
     all_p(0.0f);
+    prepare_tail_kernels(optin);
     for (int p = 1; p <= kMaxP; ++p)
         with_p(p, [&](auto PC) { raise_smem(k_xpass<double, float, decltype(PC)::value>, optin); });
     cudaGetLastError();

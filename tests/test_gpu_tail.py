@@ -1,0 +1,94 @@
+"""The one-CTA coarse tail of FP32 2D V-cycles, through the C ABI.
+
+The tail changes the schedule of Algorithm 2's coarse levels, not its
+arithmetic: one FP32 refinement step with the tail agrees with the same step
+without it to FP32 round-off (relative 1e-5 on the correction) and with the
+FP64 oracle's V-cycle to FP32 accuracy (2e-5, as for the per-level path);
+whole solves converge in the same number of restart cycles.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from oracle import multigrid as omg  # noqa: E402
+from oracle.galerkin import load_vector  # noqa: E402
+import workloads  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import __graft_entry__ as g
+    g.build_library()
+    import paper_2412_20205_gb300 as p
+    assert torch.cuda.is_available()
+    return p
+
+
+DEV = "cuda"
+
+
+def _t(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
+
+
+def _np(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.mark.parametrize("n,p", [(64, 3), ((40, 27), 2), (130, 5), (100, 7), (33, 1), (70, 4)])
+def test_tail_cycle_matches_per_level_cycle_and_oracle(pkg, n, p):
+    ns = list(n) if isinstance(n, tuple) else [n, n]
+    ctx = pkg.igamg_setup(2, p, ns, 0)
+    pkg.igamg_assemble(ctx)
+    assert pkg.igamg_coarse_tail_level(ctx) >= 1
+    H = omg.Hierarchy(2, ns, p)
+    ws = torch.empty(pkg.igamg_workspace_bytes(ctx, 5, pkg.IGAMG_FP32_IR), dtype=torch.uint8, device=DEV)
+    rng = np.random.default_rng(p)
+    b = load_vector(H.finest.breaks, p, rng.standard_normal((3, 3)))
+    x0 = rng.standard_normal(H.finest.N) * 1e-3
+    ref = omg.cycle(H, x0, b)
+    out = {}
+    for on in (True, False):
+        pkg.igamg_set_coarse_tail(ctx, on)
+        x = _t(x0)
+        pkg.igamg_vcycle(ctx, x, _t(b), pkg.IGAMG_FP32_IR, ws)
+        out[on] = _np(x) - x0
+    assert pkg.igamg_coarse_tail_level(ctx) == 0          # switched off last
+    assert _rel(out[True], out[False]) < 1e-5
+    assert _rel(out[True], ref - x0) < 2e-5
+    pkg.igamg_destroy(ctx)
+
+
+def test_tail_levels(pkg):
+    # 1024^2, p = 3: levels n = 8, 16, 32, 64 ((n+1)^2 <= 6000 unknowns) form the tail
+    ctx = pkg.igamg_setup(2, 3, [1024, 1024], 0)
+    pkg.igamg_assemble(ctx)
+    assert pkg.igamg_coarse_tail_level(ctx) == 3
+    pkg.igamg_destroy(ctx)
+    ctx = pkg.igamg_setup(3, 2, [32, 32, 32], 0)
+    pkg.igamg_assemble(ctx)
+    assert pkg.igamg_coarse_tail_level(ctx) == 0
+    pkg.igamg_destroy(ctx)
+
+
+@pytest.mark.parametrize("p", [2, 3, 5])
+def test_tail_solves_like_per_level_schedule(pkg, p):
+    s = pkg.Solver(2, p, 256, k=5)
+    b = s.rhs_sine(workloads.random_sine_coeffs(2, seed=p))
+    res = {}
+    for on in (False, True):
+        pkg.igamg_set_coarse_tail(s.ctx, on)
+        res[on] = s.solve(b, tol=1e-10, method="rre", k=5, prec="fp32_ir", max_cycles=60)
+        assert res[on]["converged"]
+    assert abs(res[True]["cycles"] - res[False]["cycles"]) <= 1
+    ref = s.solve(b, tol=1e-12, method="rre", k=5, prec="fp64", max_cycles=60)["x"]
+    assert float((res[True]["x"] - ref).norm() / ref.norm()) < 1e-7
+    s.close()
