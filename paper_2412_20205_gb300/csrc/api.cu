@@ -714,6 +714,8 @@ igamg_status igamg_assemble(igamg_ctx* c) {
                 v.off_b[q] = off; off += n;
                 v.off_inv[q] = off; off += q > 0 ? n : 0;
                 v.off_band[q] = off; off += q > 0 ? 2 * (2 * p + 1) * (c->hl[q].m[0] + c->hl[q].m[1]) : 0;
+                v.off_tm[q] = off; off += q > 0 ? 2 * (c->hl[q].m[1] + 2 * p) * c->hl[q].m[0] : 0;
+                v.off_tc[q] = off; off += q > 0 ? 2 * (2 * p + 1) : 0;
             }
             for (int q = 1; q <= l; ++q) {
                 v.off_tr[q] = off;

@@ -58,14 +58,16 @@ struct CoarseView {
 
 // Coarse part of a 2D V-cycle run by one CTA (levels 0..lc): the level views,
 // the transfers X[l] between levels l-1 and l, the coarsest solve, and the
-// shared-memory element offsets of every level's x, b, inverse diagonal and
-// four band arrays (M_x, K_x, M_y, K_y, band-major) and of two scratch
-// vectors.  lc = 0 means the hierarchy has no such tail.
+// shared-memory element offsets of every level's x, b, inverse diagonal,
+// four band arrays (M_x, K_x, M_y, K_y, band-major) and row partial sums, and
+// of two scratch vectors.  lc = 0 means the hierarchy has no such tail.
 constexpr int kTailLevels = 6;
 template <typename T>
 struct TailView {
     int lc;
     int off_x[kTailLevels], off_b[kTailLevels], off_inv[kTailLevels], off_band[kTailLevels], off_r, off_t;
+    int off_tm[kTailLevels];              // T_M then T_K, (m[1] + 2p) x m[0] each
+    int off_tc[kTailLevels];              // Toeplitz interior of M_x then K_x (2p+1 each)
     int off_tr[kTailLevels];              // transfer tables of X[l] (see tail_transfer_elems)
     int off_cv;                           // V_x, V_y, laminv of the coarsest solve
     size_t smem;                          // dynamic shared memory in bytes

@@ -187,9 +187,10 @@ struct RowBand {
 };
 
 // largest CTA of the row kernels: 3D rows couple to (2p+1)^2 - 1 neighbour
-// rows whose loads are kept in flight together, FP64 needs twice the registers
+// rows whose loads are kept in flight together; 2D rows take 512 threads
+// (FP32 at 1024^2: 1024-thread CTAs ran 4% slower, 256 and 128 slower still)
 template <typename T, int DIM>
-constexpr int row_cta_max() { return DIM == 3 ? 256 : (sizeof(T) == 8 ? 512 : 1024); }
+constexpr int row_cta_max() { return DIM == 3 ? 256 : 512; }
 
 template <typename T, int DIM, int P>
 __global__ void __launch_bounds__(row_cta_max<T, DIM>()) k_gs_phase(LevelView<T> L, int cy, int cz, int descending,

@@ -22,14 +22,37 @@ namespace dev {
 
 constexpr int kTailThreads = 512;
 
-// One level's operator data as staged in shared memory: band-major 1D factors
-// (Mx[b * mx + i] = M_x(i, i + b - p), zero outside the matrix) and 1 / A_qq.
-// Iterates x are stored with a zero halo of p nodes on every side (row
-// stride mx + 2p), so that stencil loads need no bounds tests.
+// Staging copies global -> shared with cp.async (4-byte elements): every
+// thread issues all of its copies before waiting once, so the operator data
+// of all tail levels arrives in about one memory round trip.
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+template <typename E>
+__device__ __forceinline__ void stage(E* dst, const E* src, int n) {
+    static_assert(sizeof(E) == 4, "4-byte elements");
+    for (int q = threadIdx.x; q < n; q += blockDim.x) cp_async4(dst + q, src + q);
+}
+
+// One level as the tail sees it, all in shared memory:
+// - band-major 1D factors (Mx[b * mx + i] = M_x(i, i + b - p), zero outside
+//   the matrix) and 1 / A_qq;
+// - the iterate x with a zero halo of p nodes on every side (row stride
+//   mx + 2p), so that x-window loads need no bounds tests;
+// - the row partial sums T_M = (I (x) M_x) x and T_K = (I (x) K_x) x with p
+//   zero rows above and below (row j at (j + p) mx).
+// In the uniform interior of x the x-band comes from the level view's
+// Toeplitz constants (uniform loads), at the p boundary columns from Mx/Kx.
 template <typename T>
 struct TailLevel {
-    int mx, my;
+    int mx, my, tlo, thi;
     const T *Mx, *Kx, *My, *Ky, *inv;
+    T *TM, *TK;
+    const T* Mc;                          // Toeplitz interior of M_x, K_x (2p+1 each)
+    const T* Kc;
 };
 
 template <int P>
@@ -37,49 +60,143 @@ __device__ __forceinline__ int padded(int i, int j, int mx) {
     return (j + P) * (mx + 2 * P) + i + P;
 }
 
-// (A x)_(i, j) for A = K_y (x) M_x + M_y (x) K_x (Sec. 2, Eq. (2)); xp is the
-// padded iterate.
+// sum_b M_x(i, b) x(i + b - p, j) and the K_x sum, from the padded iterate
 template <typename T, int P>
-__device__ __forceinline__ T tail_Ax(const TailLevel<T>& S, const T* xp, int i, int j) {
-    const int mx = S.mx, my = S.my, W = mx + 2 * P;
-    T cm[2 * P + 1], ck[2 * P + 1];
+__device__ __forceinline__ void tail_xsums(const TailLevel<T>& S, const T* xp, int i, int j, T& sM, T& sK) {
+    const T* xr = xp + (j + P) * (S.mx + 2 * P) + i;          // padded (i - p, j)
+    sM = 0;
+    sK = 0;
+    if (i >= S.tlo && i < S.thi) {
 #pragma unroll
-    for (int b = 0; b <= 2 * P; ++b) {
-        cm[b] = S.Mx[b * mx + i];
-        ck[b] = S.Kx[b * mx + i];
+        for (int b = 0; b <= 2 * P; ++b) {
+            const T v = xr[b];
+            sM += S.Mc[b] * v;
+            sK += S.Kc[b] * v;
+        }
+    } else {
+#pragma unroll
+        for (int b = 0; b <= 2 * P; ++b) {
+            const T v = xr[b];
+            sM += S.Mx[b * S.mx + i] * v;
+            sK += S.Kx[b * S.mx + i] * v;
+        }
     }
-    const T* base = xp + j * W + i;                     // padded (i - p, j - p)
+}
+
+// (A x)_(i, j) = sum_bj K_y(j, bj) T_M(i, j + bj - p) + M_y(j, bj) T_K(...),
+// A = K_y (x) M_x + M_y (x) K_x (Sec. 2, Eq. (2)); rows bj != skip only.
+template <typename T, int P>
+__device__ __forceinline__ T tail_couple(const TailLevel<T>& S, int i, int j, int skip) {
     T acc = 0;
 #pragma unroll
     for (int bj = 0; bj <= 2 * P; ++bj) {
-        const T* xr = base + bj * W;
-        T sM = 0, sK = 0;
-#pragma unroll
-        for (int bi = 0; bi <= 2 * P; ++bi) {
-            const T v = xr[bi];
-            sM += cm[bi] * v;
-            sK += ck[bi] * v;
-        }
-        acc += S.Ky[bj * my + j] * sM + S.My[bj * my + j] * sK;
+        if (bj == skip) continue;
+        const int row = (j + bj) * S.mx + i;                      // padded row j + bj - p
+        acc += S.Ky[bj * S.my + j] * S.TM[row] + S.My[bj * S.my + j] * S.TK[row];
     }
     return acc;
 }
 
+// T_M, T_K of every row from x.
+template <typename T, int P>
+__device__ void tail_xpass(const TailLevel<T>& S, const T* xp) {
+    for (int q = threadIdx.x; q < S.mx * S.my; q += blockDim.x) {
+        const int j = q / S.mx, i = q - j * S.mx;
+        T sM, sK;
+        tail_xsums<T, P>(S, xp, i, j, sM, sK);
+        S.TM[(j + P) * S.mx + i] = sM;
+        S.TK[(j + P) * S.mx + i] = sK;
+    }
+    __syncthreads();
+}
+
 // One multicolour GS sweep: colour c = cx + (p+1) cy, ascending (pre) or
 // descending (post); x_q += (b_q - (A x)_q) / A_qq on every node of colour c.
+// Row phases: for fixed cy the rows j = cy mod (p+1) never couple, so each
+// warp takes whole rows and runs their p+1 x-colours with warp barriers only;
+// the CTA synchronises once per row phase.  During a row's colours the other
+// rows' T_M, T_K are frozen and the row's own part is summed from x; the row's
+// T_M, T_K are refreshed when its colours are done.
 template <typename T, int P>
 __device__ void tail_gs(const TailLevel<T>& S, T* xp, const T* b, bool descending) {
     constexpr int NC = P + 1;
-    const int mx = S.mx, my = S.my;
-    for (int cc = 0; cc < NC * NC; ++cc) {
-        const int c = descending ? NC * NC - 1 - cc : cc;
-        const int cx = c % NC, cy = c / NC;
-        const int nx = (mx - cx + NC - 1) / NC, ny = (my - cy + NC - 1) / NC;
-        for (int t = threadIdx.x; t < nx * ny; t += blockDim.x) {
-            const int jt = t / nx;
-            const int i = cx + NC * (t - jt * nx), j = cy + NC * jt;
-            const int q = j * mx + i;
-            xp[padded<P>(i, j, mx)] += (b[q] - tail_Ax<T, P>(S, xp, i, j)) * S.inv[q];
+    const int mx = S.mx, my = S.my, W = mx + 2 * P;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    T mc[2 * P + 1], kc[2 * P + 1];                     // interior x-band, in registers
+#pragma unroll
+    for (int bb = 0; bb <= 2 * P; ++bb) {
+        mc[bb] = S.Mc[bb];
+        kc[bb] = S.Kc[bb];
+    }
+    for (int pc = 0; pc < NC; ++pc) {
+        const int cy = descending ? P - pc : pc;
+        const int nrows = (my - cy + NC - 1) / NC;
+        for (int rr = warp; rr < nrows; rr += nwarps) {
+            const int j = cy + NC * rr;
+            T ky[2 * P + 1], mY[2 * P + 1];             // the row's y-band, in registers
+#pragma unroll
+            for (int bj = 0; bj <= 2 * P; ++bj) {
+                ky[bj] = S.Ky[bj * my + j];
+                mY[bj] = S.My[bj * my + j];
+            }
+            const T* xr0 = xp + (j + P) * W;
+            for (int c = 0; c < NC; ++c) {
+                const int cx = descending ? P - c : c;
+                const int nx = (mx - cx + NC - 1) / NC;
+                for (int s0 = 0; s0 < nx; s0 += 32) {
+                    if (s0 + lane < nx) {
+                        const int i = cx + NC * (s0 + lane);
+                        const int q = j * mx + i;
+                        const T* xr = xr0 + i;                      // padded (i - p, j)
+                        T sM = 0, sK = 0;
+                        if (i >= S.tlo && i < S.thi) {
+#pragma unroll
+                            for (int bb = 0; bb <= 2 * P; ++bb) {
+                                const T v = xr[bb];
+                                sM += mc[bb] * v;
+                                sK += kc[bb] * v;
+                            }
+                        } else {
+#pragma unroll
+                            for (int bb = 0; bb <= 2 * P; ++bb) {
+                                const T v = xr[bb];
+                                sM += S.Mx[bb * mx + i] * v;
+                                sK += S.Kx[bb * mx + i] * v;
+                            }
+                        }
+                        T ax = ky[P] * sM + mY[P] * sK;
+#pragma unroll
+                        for (int bj = 0; bj <= 2 * P; ++bj) {
+                            if (bj == P) continue;
+                            const int row = (j + bj) * mx + i;          // padded T row j + bj - p
+                            ax += ky[bj] * S.TM[row] + mY[bj] * S.TK[row];
+                        }
+                        xp[(j + P) * W + i + P] += (b[q] - ax) * S.inv[q];
+                    }
+                }
+                __syncwarp();
+            }
+            for (int i = lane; i < mx; i += 32) {       // refresh the row's T_M, T_K
+                const T* xr = xr0 + i;
+                T sM = 0, sK = 0;
+                if (i >= S.tlo && i < S.thi) {
+#pragma unroll
+                    for (int bb = 0; bb <= 2 * P; ++bb) {
+                        const T v = xr[bb];
+                        sM += mc[bb] * v;
+                        sK += kc[bb] * v;
+                    }
+                } else {
+#pragma unroll
+                    for (int bb = 0; bb <= 2 * P; ++bb) {
+                        const T v = xr[bb];
+                        sM += S.Mx[bb * mx + i] * v;
+                        sK += S.Kx[bb * mx + i] * v;
+                    }
+                }
+                S.TM[(j + P) * mx + i] = sM;
+                S.TK[(j + P) * mx + i] = sK;
+            }
         }
         __syncthreads();
     }
@@ -87,12 +204,11 @@ __device__ void tail_gs(const TailLevel<T>& S, T* xp, const T* b, bool descendin
 
 // bc = P^T (b - A x): the residual, then the x and y axes of the restriction.
 template <typename T, int P>
-__device__ void tail_restrict(const TailLevel<T>& S, const TransferView<T>& X, const T* xp, const T* b, T* r, T* t,
-                              T* bc) {
+__device__ void tail_restrict(const TailLevel<T>& S, const TransferView<T>& X, const T* b, T* r, T* t, T* bc) {
     const int mx = S.mx, my = S.my;
     for (int q = threadIdx.x; q < mx * my; q += blockDim.x) {
         const int j = q / mx;
-        r[q] = b[q] - tail_Ax<T, P>(S, xp, q - j * mx, j);
+        r[q] = b[q] - tail_couple<T, P>(S, q - j * mx, j, -1);
     }
     __syncthreads();
     const int mcx = X.mc[0], mcy = X.mc[1];
@@ -200,79 +316,74 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_coarse_tail(TailView<T> V, 
     const int lc = V.lc;
     T* r = sm + V.off_r;
     T* t = sm + V.off_t;
-    {
-        const int N = V.L[lc].m[0] * V.L[lc].m[1];
-        T* b = sm + V.off_b[lc];
-        for (int q = threadIdx.x; q < N; q += blockDim.x) b[q] = b_in[q];
-    }
-    for (int l = 0; l <= lc; ++l) {                     // coarse e^0 = 0 on every level, zero halos
-        const int NP = (V.L[l].m[0] + 2 * P) * (V.L[l].m[1] + 2 * P);
-        T* x = sm + V.off_x[l];
-        for (int q = threadIdx.x; q < NP; q += blockDim.x) x[q] = 0;
-    }
-    for (int l = 1; l <= lc; ++l) {                     // stage the operator data
+    stage(sm + V.off_b[lc], b_in, V.L[lc].m[0] * V.L[lc].m[1]);
+    for (int l = 1; l <= lc; ++l) {                     // operator data of the smoothed levels
         const LevelView<T>& L = V.L[l];
-        const int mx = L.m[0], my = L.m[1], N = mx * my;
-        T* inv = sm + V.off_inv[l];
-        for (int q = threadIdx.x; q < N; q += blockDim.x) inv[q] = L.invdiag[q];
+        const int mx = L.m[0], my = L.m[1];
+        stage(sm + V.off_inv[l], L.invdiag, mx * my);
         T* band = sm + V.off_band[l];
-        for (int q = threadIdx.x; q < (2 * P + 1) * mx; q += blockDim.x) {
-            const int b = q / mx, i = q % mx;
-            band[q] = band_m(L, i, b);
-            band[(2 * P + 1) * mx + q] = band_k(L, i, b);
-        }
-        band += 2 * (2 * P + 1) * mx;
-        for (int q = threadIdx.x; q < (2 * P + 1) * my; q += blockDim.x) {
-            const int b = q / my, j = q % my;
-            band[q] = band_md(L, 1, j, b);
-            band[(2 * P + 1) * my + q] = band_kd(L, 1, j, b);
-        }
-    }
-    // transfer tables and the coarsest eigenbasis, read by one pass each
-    for (int l = 1; l <= lc; ++l) {
-        const TransferView<T>& X = V.X[l];
+        stage(band, L.Mb[0], (2 * P + 1) * mx);
+        stage(band + (2 * P + 1) * mx, L.Kb[0], (2 * P + 1) * mx);
+        stage(band + 2 * (2 * P + 1) * mx, L.Mb[1], (2 * P + 1) * my);
+        stage(band + 2 * (2 * P + 1) * mx + (2 * P + 1) * my, L.Kb[1], (2 * P + 1) * my);
+        const TransferView<T>& X = V.X[l];                // transfer tables
         const TransferView<T> Y = staged_transfer(V, l, sm);
         for (int d = 0; d < 2; ++d) {
-            int* plo = const_cast<int*>(Y.plo[d]);
-            int* rlo = const_cast<int*>(Y.rlo[d]);
-            T* pv = const_cast<T*>(Y.pv[d]);
-            T* rv = const_cast<T*>(Y.rv[d]);
-            for (int q = threadIdx.x; q < X.mf[d]; q += blockDim.x) plo[q] = X.plo[d][q];
-            for (int q = threadIdx.x; q < X.mf[d] * X.pw[d]; q += blockDim.x) pv[q] = X.pv[d][q];
-            for (int q = threadIdx.x; q < X.mc[d]; q += blockDim.x) rlo[q] = X.rlo[d][q];
-            for (int q = threadIdx.x; q < X.mc[d] * X.rw[d]; q += blockDim.x) rv[q] = X.rv[d][q];
+            stage(const_cast<int*>(Y.plo[d]), X.plo[d], X.mf[d]);
+            stage(const_cast<T*>(Y.pv[d]), X.pv[d], X.mf[d] * X.pw[d]);
+            stage(const_cast<int*>(Y.rlo[d]), X.rlo[d], X.mc[d]);
+            stage(const_cast<T*>(Y.rv[d]), X.rv[d], X.mc[d] * X.rw[d]);
         }
     }
-    CoarseView<T> Cs = V.C;
+    CoarseView<T> Cs = V.C;                             // coarsest eigenbasis
     {
         T* f = sm + V.off_cv;
         const int m0 = V.C.m[0], m1 = V.C.m[1];
-        for (int q = threadIdx.x; q < m0 * m0; q += blockDim.x) f[q] = V.C.V[0][q];
-        for (int q = threadIdx.x; q < m1 * m1; q += blockDim.x) f[m0 * m0 + q] = V.C.V[1][q];
-        for (int q = threadIdx.x; q < m0 * m1; q += blockDim.x) f[m0 * m0 + m1 * m1 + q] = V.C.laminv[q];
+        stage(f, V.C.V[0], m0 * m0);
+        stage(f + m0 * m0, V.C.V[1], m1 * m1);
+        stage(f + m0 * m0 + m1 * m1, V.C.laminv, m0 * m1);
         Cs.V[0] = f;
         Cs.V[1] = f + m0 * m0;
         Cs.laminv = f + m0 * m0 + m1 * m1;
     }
+    for (int l = 0; l <= lc; ++l) {                     // coarse e^0 = 0 on every level, zero halos
+        const int mx = V.L[l].m[0], my = V.L[l].m[1];
+        T* x = sm + V.off_x[l];
+        for (int q = threadIdx.x; q < (mx + 2 * P) * (my + 2 * P); q += blockDim.x) x[q] = 0;
+        if (l == 0) continue;
+        T* tmk = sm + V.off_tm[l];                      // T_M = T_K = 0 for x = 0
+        for (int q = threadIdx.x; q < 2 * (my + 2 * P) * mx; q += blockDim.x) tmk[q] = 0;
+        T* tc = sm + V.off_tc[l];
+        for (int b = threadIdx.x; b <= 2 * P; b += blockDim.x) {
+            tc[b] = V.L[l].Mc[0][b];
+            tc[2 * P + 1 + b] = V.L[l].Kc[0][b];
+        }
+    }
+    cp_async_wait_all();
     __syncthreads();
     auto level = [&](int l) {
         const int mx = V.L[l].m[0], my = V.L[l].m[1];
         const T* band = sm + V.off_band[l];
-        return TailLevel<T>{mx, my, band, band + (2 * P + 1) * mx, band + 2 * (2 * P + 1) * mx,
-                            band + 2 * (2 * P + 1) * mx + (2 * P + 1) * my, sm + V.off_inv[l]};
+        T* tmk = sm + V.off_tm[l];
+        const T* tc = sm + V.off_tc[l];
+        return TailLevel<T>{mx, my, V.L[l].tlo[0], V.L[l].thi[0], band, band + (2 * P + 1) * mx,
+                            band + 2 * (2 * P + 1) * mx, band + 2 * (2 * P + 1) * mx + (2 * P + 1) * my,
+                            sm + V.off_inv[l], tmk, tmk + (my + 2 * P) * mx, tc, tc + 2 * P + 1};
     };
     for (int l = lc; l >= 1; --l) {
         T* x = sm + V.off_x[l];
         const T* b = sm + V.off_b[l];
         const TailLevel<T> S = level(l);
         tail_gs<T, P>(S, x, b, false);                                           // pre-smooth
-        tail_restrict<T, P>(S, staged_transfer(V, l, sm), x, b, r, t, sm + V.off_b[l - 1]);   // R (b - A x)
+        tail_restrict<T, P>(S, staged_transfer(V, l, sm), b, r, t, sm + V.off_b[l - 1]);   // R (b - A x)
     }
     tail_coarse<T, P>(Cs, sm + V.off_b[0], r, t, sm + V.off_x[0]);              // direct
     for (int l = 1; l <= lc; ++l) {
         T* x = sm + V.off_x[l];
+        const TailLevel<T> S = level(l);
         tail_prolong<T, P>(staged_transfer(V, l, sm), sm + V.off_x[l - 1], t, x);              // x += P e
-        tail_gs<T, P>(level(l), x, sm + V.off_b[l], true);                       // post-smooth
+        tail_xpass<T, P>(S, x);
+        tail_gs<T, P>(S, x, sm + V.off_b[l], true);                              // post-smooth
     }
     const int mx = V.L[lc].m[0], N = mx * V.L[lc].m[1];
     const T* x = sm + V.off_x[lc];
