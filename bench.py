@@ -25,8 +25,18 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "time to rel. residual 1e-10 and DOF/s: FP64 GMG+RRE vs mixed/learned form"
-FP64_PEAK_FLOP_PER_CLK_PER_SM = 4          # 2 FP64 FMA per clock per SM on GB300 (1.25 TFLOP/s nominal)
-N_SMS = 152
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# FP32 GS row-phase kernel on the finest level, from the ncu capture summarised
+# in profiles/k_gs_phase_2d_1024_p3_fp32.md; keyed by (dim, n, p).
+GS_TRAFFIC = {(2, 1024, 3): 11.71e6}
+
+
+def measured_peak(key, fallback):
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)[key])
+    except (OSError, KeyError, ValueError):
+        return fallback
 
 
 def parse():
@@ -220,30 +230,46 @@ def run_ours(a, rank, world, local):
         torch.cuda.synchronize()
         e2e_times.append((time.perf_counter() - t0) * 1e3)
 
-    # dominant kernel: the FP64 row-coupled residual / operator application
-    # (x-pass + row couplings, bound by the FP64 pipe); algorithmic FLOPs per
-    # launch pair = 2 * 4 (2p+1) N in 2D.
-    ws = s.ws
-    xr = torch.randn(s.N, dtype=torch.float64, device=dev)
-    yr = torch.empty_like(xr)
+    # learned form (2D): the stored network as finest post-smoother
+    learned = None
+    if a.dim == 2:
+        wfile = os.path.join(ROOT, "paper_2412_20205_gb300", "weights", "smoother_2d_n256_p3.npy")
+        wnet = torch.tensor(np.load(wfile), dtype=torch.float32, device=dev)
+        s.set_smoother(wnet)
+        for _ in range(a.warmup):
+            solve("fp32_ir_learned")
+        tl, outl = timed("fp32_ir_learned", a.steps)
+        learned = {"ms": float(np.mean(tl)), "cycles": outl["cycles"], "fell_back": outl["fell_back"],
+                   "final_rel_residual": float(outl["history"][-1])}
+
+    # Dominant kernel (ncu launch list of this workload): the FP32 row-phase
+    # Gauss-Seidel kernel.  Timed here on the finest level, same launch
+    # configuration as inside the solve, with CUDA events over `reps` sweeps
+    # ((p+1)^(dim-1) launches each) on this stream.  Algorithmic bytes of a
+    # sweep: read x, b and write x in FP32 = 12 B per DOF; one launch does its
+    # share, 12 N / (p+1)^(dim-1) bytes.
     top = len(s.levels) - 1
+    xg = torch.randn(s.N, dtype=torch.float32, device=dev)
+    bg = torch.randn(s.N, dtype=torch.float32, device=dev)
+    pkg.igamg_smooth_f32(s.ctx, top, xg, bg, 0, s.ws)
     for _ in range(3):
-        pkg.igamg_apply(s.ctx, top, xr, yr, ws)
+        pkg.igamg_smooth_f32(s.ctx, top, xg, bg, 0, s.ws, sums_current=True)
     reps = 50
+    launches_per_sweep = (a.p + 1) ** (a.dim - 1)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
     for _ in range(reps):
-        pkg.igamg_apply(s.ctx, top, xr, yr, ws)
+        pkg.igamg_smooth_f32(s.ctx, top, xg, bg, 0, s.ws, sums_current=True, stream=stream)
     e1.record(stream)
     torch.cuda.synchronize()
-    apply_ms = e0.elapsed_time(e1) / reps
-    w = 2 * a.p + 1
-    flops = 2.0 * (2 * w + (2 * w if a.dim == 2 else 2 * w * w)) * s.N
-    sm_mhz = clk["sm_mhz"] or 2070.0
-    peak_fp64 = N_SMS * FP64_PEAK_FLOP_PER_CLK_PER_SM * 2070.0e6 / 1e12
-    achieved = flops / (apply_ms * 1e-3) / 1e12
+    launch_ms = e0.elapsed_time(e1) / (reps * launches_per_sweep)
+    bytes_per_launch = 12.0 * s.N / launches_per_sweep
+    achieved = bytes_per_launch / (launch_ms * 1e-3) / 1e9
+    peak_hbm = measured_peak("hbm_gbs", 6800.0)
 
+    if learned is not None:
+        learned["ms"] = max_over_ranks(learned["ms"], world)
     t_max = max_over_ranks(float(np.mean(times)), world)
     t64_max = max_over_ranks(float(np.mean(times64)), world)
     e2e_max = max_over_ranks(float(np.mean(e2e_times)), world)
@@ -262,12 +288,19 @@ def run_ours(a, rank, world, local):
         "e2e": {"value": units / (e2e_max * 1e-3), "unit": "DOF/s",
                 "h2d_bytes_per_step": s.N * 8, "d2h_bytes_per_step": s.N * 8},
         "gpu_launches": launches,
-        "roofline": {"bound": "alu", "kernel": "k_xpass<double> + k_residual<double> (FP64 operator)",
-                     "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s (FP64)",
-                     "frac": achieved / peak_fp64, "traffic": None,
-                     "peak_source": "152 SMs x 4 FP64 flop/clk x 2070 MHz (nominal 1.25 TFLOP/s)"},
+        "roofline": {"bound": "hbm", "kernel": f"k_gs_phase<float,{a.dim},{a.p}> (finest level, one row phase)",
+                     "achieved": achieved, "peak": peak_hbm, "unit": "GB/s", "frac": achieved / peak_hbm,
+                     "traffic": GS_TRAFFIC.get((a.dim, a.n, a.p)),
+                     "algorithmic_bytes_per_launch": bytes_per_launch, "launch_us": launch_ms * 1e3,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
         "clocks": clk,
     }
+    if learned is not None:
+        tl_max = learned["ms"]
+        line["learned_form"] = {"ms_per_step": tl_max, "value": units / (tl_max * 1e-3), "unit": "DOF/s",
+                                "cycles": learned["cycles"], "fell_back": learned["fell_back"],
+                                "final_rel_residual": learned["final_rel_residual"],
+                                "network": "3x3 conv 1-16-16-1, BF16/FP32, trained on 257^2 p=3 pairs"}
     if not a.no_cpu_baseline:
         v, per, cycles, setup, N = oracle_sample(a)
         line["cpu_baseline"] = {"value": v, "unit": "DOF/s", "cores": 1, "kind": "oracle",

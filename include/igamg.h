@@ -134,6 +134,14 @@ igamg_status igamg_apply(igamg_ctx* ctx, int level, const double* d_x, double* d
 igamg_status igamg_smooth(igamg_ctx* ctx, int level, double* d_x, const double* d_b,
                           int descending, void* d_ws, size_t ws_bytes, void* stream);
 
+/* The same sweep in FP32 (the smoother of FP32 V-cycles).  The row partial
+ * sums T_M, T_K of d_x live in the workspace (sized for IGAMG_FP32_IR);
+ * sums_current = 1 reuses them as the previous igamg_smooth_f32 call on this
+ * level and workspace left them (valid only if d_x has not changed since),
+ * 0 recomputes them first. */
+igamg_status igamg_smooth_f32(igamg_ctx* ctx, int level, float* d_x, const float* d_b, int descending,
+                              int sums_current, void* d_ws, size_t ws_bytes, void* stream);
+
 /* d_coarse = P_level^T d_fine (restriction from `level` to level-1). */
 igamg_status igamg_restrict(igamg_ctx* ctx, int level, const double* d_fine, double* d_coarse,
                             void* d_ws, size_t ws_bytes, void* stream);

@@ -64,6 +64,7 @@ def _load():
         "igamg_set_smoother": (c_int, [vp, vp, c_double]),
         "igamg_smoother_fell_back": (c_int, [vp]),
         "igamg_coarse_tail_level": (c_int, [vp]),
+        "igamg_smooth_f32": (c_int, [vp, c_int, vp, vp, c_int, c_int, vp, c_size, vp]),
         "igamg_set_coarse_tail": (c_int, [vp, c_int]),
         "igamg_vcycle_probe": (c_int, [vp, vp, vp, vp, vp, c_size, vp]),
         "igamg_cnn_num_weights": (c_int, []),
@@ -237,6 +238,11 @@ def igamg_set_smoother(ctx, w, stall_ratio=0.95):
 
 def igamg_smoother_fell_back(ctx):
     return bool(_load().igamg_smoother_fell_back(ctx))
+
+
+def igamg_smooth_f32(ctx, level, x, b, descending, ws, sums_current=False, stream=None):
+    _check(_load().igamg_smooth_f32(ctx, level, _ptr(x), _ptr(b), int(descending), int(bool(sums_current)),
+                                    _ptr(ws), ws.numel(), _stream(stream)), "igamg_smooth_f32")
 
 
 def igamg_coarse_tail_level(ctx):

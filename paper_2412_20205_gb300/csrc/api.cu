@@ -890,6 +890,21 @@ igamg_status igamg_smooth(igamg_ctx* c, int level, double* d_x, const double* d_
     return IGAMG_OK;
 }
 
+igamg_status igamg_smooth_f32(igamg_ctx* c, int level, float* d_x, const float* d_b, int descending,
+                              int sums_current, void* d_ws, size_t ws_bytes, void* stream) {
+    if (igamg_status st = check_ctx(c)) return st;
+    if (level < 0 || level >= c->L || !d_x || !d_b) return fail(IGAMG_EINVAL, "bad smooth arguments");
+    if (igamg_status st = check_ws(c, d_ws, ws_bytes, 1, IGAMG_FP32_IR)) return st;
+    Workspace w = carve(c, d_ws, 1, IGAMG_FP32_IR);
+    cudaStream_t s = (cudaStream_t)stream;
+    LevelBuf<float>& B = w.f[level];
+    if (!sums_current)
+        dev::xpass<float, float>(s, c->lv32[level], d_x, nullptr, nullptr, 0, nullptr, nullptr, 0, B.TM, B.TK);
+    dev::gs_sweep<float>(s, c->dim, c->lv32[level], descending != 0, d_x, d_b, B.TM, B.TK);
+    CUDA_TRY(cudaGetLastError());
+    return IGAMG_OK;
+}
+
 igamg_status igamg_restrict(igamg_ctx* c, int level, const double* d_fine, double* d_coarse, void* d_ws,
                             size_t ws_bytes, void* stream) {
     if (igamg_status st = check_ctx(c)) return st;

@@ -110,6 +110,23 @@ def test_gs_sweep_every_level_both_orders(pkg, pair):
             assert _rel(_np(x), ref) < 1e-12, (l, desc)
 
 
+def test_gs_sweep_fp32_finest(pkg, pair):
+    """The FP32 sweep (smoother of the FP32 V-cycles) against the FP64 oracle
+    sweep, to FP32 accuracy; two sweeps in a row reuse the kept row sums."""
+    rng = np.random.default_rng(11)
+    lev = pair.H.finest
+    l = len(pair.H.levels) - 1
+    x0 = rng.standard_normal(lev.N)
+    b = rng.standard_normal(lev.N)
+    ref = omg.gs_sweep(lev, omg.gs_sweep(lev, x0, b), b, descending=True)
+    x = torch.tensor(x0, dtype=torch.float32, device=DEV)
+    bf = torch.tensor(b, dtype=torch.float32, device=DEV)
+    pkg.igamg_smooth_f32(pair.ctx, l, x, bf, 0, pair.ws)
+    pkg.igamg_smooth_f32(pair.ctx, l, x, bf, 1, pair.ws, sums_current=True)
+    torch.cuda.synchronize()
+    assert _rel(x.double().cpu().numpy(), ref) < 2e-5
+
+
 def test_restrict_and_prolong_every_level(pkg, pair):
     rng = np.random.default_rng(2)
     for l in range(1, len(pair.H.levels)):
