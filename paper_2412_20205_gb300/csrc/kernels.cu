@@ -152,8 +152,9 @@ __global__ void __launch_bounds__(kThreads) k_xpass(LevelView<T> L, const T* __r
 // fixed (cy, cz) the rows j = cy mod (p+1) (k = cz mod (p+1)) are updated; no
 // two of them couple, and within a row the colours cx = 0..p form a 1D
 // multicolour sweep with the frozen off-row part F = sum_{row' != row}
-// (cM T_M + cK T_K).  The row's own T_M, T_K are updated incrementally from
-// the corrections of each colour, so a full sweep costs about one apply.
+// (cM T_M + cK T_K).  The row's own T_M, T_K at a node are their values at
+// the start of the phase plus the x-band applied to this sweep's corrections,
+// so a full sweep costs about one apply plus 2(2p+1) FMA per node.
 //
 // Latency layout: one CTA per target row with enough threads to cover the row
 // in one pass; every global load of the phase (neighbour T rows, own T, x, b,
@@ -192,7 +193,15 @@ struct RowBand {
 template <typename T, int DIM>
 constexpr int row_cta_max() { return DIM == 3 ? 256 : 512; }
 
+// Which of the two in-row formulations a GS phase uses, by measurement on
+// GB300 (2D 1024^2, RRE(5) solves): the window form (one barrier per colour,
+// 2(2p+1) FMA per node) won for FP32 at p = 2, 4, 5 (by 11-18%) and lost 2%
+// at p = 3 (p = 1, 6, 7 not measured, window form); in FP64 its extra FMAs
+// cost more than the barriers it saves (p = 5: 278 ms against 188 ms).
 template <typename T, int DIM, int P>
+constexpr bool gs_window() { return sizeof(T) == 4 && DIM == 2 && P != 3; }
+
+template <typename T, int DIM, int P, bool WINDOW>
 __global__ void __launch_bounds__(row_cta_max<T, DIM>()) k_gs_phase(LevelView<T> L, int cy, int cz, int descending,
                                                     T* __restrict__ x, const T* __restrict__ b,
                                                     T* __restrict__ TM, T* __restrict__ TK) {
@@ -231,44 +240,98 @@ __global__ void __launch_bounds__(row_cta_max<T, DIM>()) k_gs_phase(LevelView<T>
         tk[i] = TK[base + i];
         xs[i] = x[base + i];
         dv[i] = L.invdiag[base + i];
+        if constexpr (WINDOW) dl[i] = 0;
     }
     __syncthreads();
     const RowBand<T, P> band{L, bm, bk, nb};
     const T am = cM[OWN], ak = cK[OWN];
+    if constexpr (WINDOW) {
+        const int tlo = L.tlo[0], thi = L.thi[0];
+        // sum_b M_x(i, b) dl[i + b - p] (and K_x): the x-band applied to this
+        // sweep's corrections so far (zero for colours not yet done).  In the
+        // uniform interior every neighbour exists and the band comes from the
+        // kernel parameters at compile-time offsets.
+        auto xband_dl = [&](int i, bool skip_own, T& sm, T& sk) {
+            if (i >= tlo && i < thi) {
 #pragma unroll
-    for (int c = 0; c < P1; ++c) {
-        const int cx = descending ? P - c : c;
-        for (int i = cx + P1 * (int)threadIdx.x; i < mx; i += P1 * (int)blockDim.x) {
-            const T d = (rhs[i] - (am * tm[i] + ak * tk[i])) * dv[i];
-            xs[i] += d;
-            dl[i] = d;
+                for (int bb = 0; bb <= 2 * P; ++bb) {
+                    if (skip_own && bb == P) continue;
+                    const T dn = dl[i + bb - P];
+                    sm += L.Mc[0][bb] * dn;
+                    sk += L.Kc[0][bb] * dn;
+                }
+            } else {
+#pragma unroll
+                for (int bb = 0; bb <= 2 * P; ++bb) {
+                    const int n = i + bb - P;
+                    if ((skip_own && bb == P) || n < 0 || n >= mx) continue;
+                    const T dn = dl[n];
+                    sm += band.m(i, bb) * dn;
+                    sk += band.k(i, bb) * dn;
+                }
+            }
+        };
+        // Colour by colour along the row; the row's own partial sums at node i
+        // are tm[i] + xband_dl(i) (its own correction is still zero), so one
+        // barrier per colour suffices.
+#pragma unroll
+        for (int c = 0; c < P1; ++c) {
+            const int cx = descending ? P - c : c;
+            for (int i = cx + P1 * (int)threadIdx.x; i < mx; i += P1 * (int)blockDim.x) {
+                T sm = tm[i], sk = tk[i];
+                xband_dl(i, true, sm, sk);
+                const T d = (rhs[i] - (am * sm + ak * sk)) * dv[i];
+                xs[i] += d;
+                dl[i] = d;
+            }
+            __syncthreads();
         }
-        __syncthreads();
         for (int i = threadIdx.x; i < mx; i += blockDim.x) {
-            int r = (cx - i) % P1;
-            if (r < 0) r += P1;
-            T sm = 0, sk = 0;
-            const int i1 = i + r;                       // same-colour node at offset r
-            if (i1 < mx) {
-                const T d1 = dl[i1];
-                sm += band.m(i, r + P) * d1;
-                sk += band.k(i, r + P) * d1;
-            }
-            const int i2 = i1 - P1;                     // and at offset r - (p+1)
-            if (r >= 1 && i2 >= 0) {
-                const T d2 = dl[i2];
-                sm += band.m(i, r - 1) * d2;
-                sk += band.k(i, r - 1) * d2;
-            }
-            tm[i] += sm;
-            tk[i] += sk;
+            T sm = tm[i], sk = tk[i];
+            xband_dl(i, false, sm, sk);
+            x[base + i] = xs[i];
+            TM[base + i] = sm;
+            TK[base + i] = sk;
         }
-        __syncthreads();
-    }
-    for (int i = threadIdx.x; i < mx; i += blockDim.x) {
-        x[base + i] = xs[i];
-        TM[base + i] = tm[i];
-        TK[base + i] = tk[i];
+    } else {
+        // Incremental form: after each colour the row's T_M, T_K take the
+        // corrections of that colour (a gather of the <= 2 same-colour nodes
+        // within reach), two barriers per colour but 4 FMA per node.
+#pragma unroll
+        for (int c = 0; c < P1; ++c) {
+            const int cx = descending ? P - c : c;
+            for (int i = cx + P1 * (int)threadIdx.x; i < mx; i += P1 * (int)blockDim.x) {
+                const T d = (rhs[i] - (am * tm[i] + ak * tk[i])) * dv[i];
+                xs[i] += d;
+                dl[i] = d;
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < mx; i += blockDim.x) {
+                int r = (cx - i) % P1;
+                if (r < 0) r += P1;
+                T sm = 0, sk = 0;
+                const int i1 = i + r;                       // same-colour node at offset r
+                if (i1 < mx) {
+                    const T d1 = dl[i1];
+                    sm += band.m(i, r + P) * d1;
+                    sk += band.k(i, r + P) * d1;
+                }
+                const int i2 = i1 - P1;                     // and at offset r - (p+1)
+                if (r >= 1 && i2 >= 0) {
+                    const T d2 = dl[i2];
+                    sm += band.m(i, r - 1) * d2;
+                    sk += band.k(i, r - 1) * d2;
+                }
+                tm[i] += sm;
+                tk[i] += sk;
+            }
+            __syncthreads();
+        }
+        for (int i = threadIdx.x; i < mx; i += blockDim.x) {
+            x[base + i] = xs[i];
+            TM[base + i] = tm[i];
+            TK[base + i] = tk[i];
+        }
     }
 }
 
@@ -815,8 +878,8 @@ void prepare_kernels() {
             with_p(p, [&](auto PC) {
                 constexpr int P = decltype(PC)::value;
                 raise_smem(k_xpass<T, T, P>, optin);
-                raise_smem(k_gs_phase<T, 2, P>, optin);
-                raise_smem(k_gs_phase<T, 3, P>, optin);
+                raise_smem(k_gs_phase<T, 2, P, gs_window<T, 2, P>()>, optin);
+                raise_smem(k_gs_phase<T, 3, P, gs_window<T, 3, P>()>, optin);
                 raise_smem(k_prolong_last<T, 2, P>, optin);
                 raise_smem(k_prolong_last<T, 3, P>, optin);
             });
@@ -857,11 +920,13 @@ void gs_sweep(cudaStream_t s, int dim, const LevelView<T>& L, bool descending, T
         with_p(p, [&](auto PC) {
             constexpr int P = decltype(PC)::value;
             if (dim == 2) {
-                set_smem(k_gs_phase<T, 2, P>, smem);
-                k_gs_phase<T, 2, P><<<nty * ntz, threads, smem, s>>>(L, cy, cz, descending, x, b, TM, TK);
+                constexpr bool WIN = gs_window<T, 2, P>();
+                set_smem(k_gs_phase<T, 2, P, WIN>, smem);
+                k_gs_phase<T, 2, P, WIN><<<nty * ntz, threads, smem, s>>>(L, cy, cz, descending, x, b, TM, TK);
             } else {
-                set_smem(k_gs_phase<T, 3, P>, smem);
-                k_gs_phase<T, 3, P><<<nty * ntz, threads, smem, s>>>(L, cy, cz, descending, x, b, TM, TK);
+                constexpr bool WIN = gs_window<T, 3, P>();
+                set_smem(k_gs_phase<T, 3, P, WIN>, smem);
+                k_gs_phase<T, 3, P, WIN><<<nty * ntz, threads, smem, s>>>(L, cy, cz, descending, x, b, TM, TK);
             }
         });
         count_launch();
