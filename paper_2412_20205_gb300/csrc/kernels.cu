@@ -246,10 +246,10 @@ __global__ void __launch_bounds__(row_cta_max<T, DIM>()) k_gs_phase(LevelView<T>
     const RowBand<T, P> band{L, bm, bk, nb};
     const T am = cM[OWN], ak = cK[OWN];
     if constexpr (WINDOW) {
-        const int tlo = L.tlo[0], thi = L.thi[0];
+        const int tlo = max(L.tlo[0], P), thi = min(L.thi[0], mx - P);
         // sum_b M_x(i, b) dl[i + b - p] (and K_x): the x-band applied to this
-        // sweep's corrections so far (zero for colours not yet done).  In the
-        // uniform interior every neighbour exists and the band comes from the
+        // sweep's corrections so far (zero for colours not yet done).  Where
+        // the band is uniform and every neighbour exists it comes from the
         // kernel parameters at compile-time offsets.
         auto xband_dl = [&](int i, bool skip_own, T& sm, T& sk) {
             if (i >= tlo && i < thi) {
