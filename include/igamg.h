@@ -231,6 +231,20 @@ int igamg_smoother_fell_back(const igamg_ctx* ctx);
 int igamg_coarse_tail_level(const igamg_ctx* ctx);
 igamg_status igamg_set_coarse_tail(igamg_ctx* ctx, int enable);
 
+/* Launch schedule of the FP32 V-cycles: gs_threads caps the threads of the
+ * GS row CTAs (0 = default 512, else 128, 256 or 512); tail_levels sets the
+ * coarse tail to levels 0..tail_levels (clipped to the feasible maximum; 0 =
+ * off, -1 = unchanged).  Arithmetic is unchanged up to FP32 rounding order. */
+igamg_status igamg_set_schedule(igamg_ctx* ctx, int gs_threads, int tail_levels);
+void igamg_get_schedule(const igamg_ctx* ctx, int* gs_threads, int* tail_levels);
+
+/* Autotuner: times `reps` FP32 V-cycles (zero start, constant right side) for
+ * every GS row-CTA cap in {128, 256, 512} (2D) and every coarse-tail depth,
+ * on the given stream, and keeps the fastest schedule.  The workspace must be
+ * sized for IGAMG_FP32_IR; its contents are overwritten.  Synchronises the
+ * stream; typically a few tens of milliseconds. */
+igamg_status igamg_autotune(igamg_ctx* ctx, void* d_ws, size_t ws_bytes, void* stream, int reps);
+
 /* One FP64 V-cycle in place on the finest d_x (as igamg_vcycle) that also
  * copies the iterate at the point just before the finest-level post-smoothing
  * (after the coarse correction) to d_x_mid: the network's training input. */
@@ -261,6 +275,11 @@ igamg_status igamg_batch_rhs_sine(igamg_batch* batch, int modes, const double* h
 igamg_status igamg_batch_solve(igamg_batch* batch, const double* d_b, double* d_x, double tol, int extrap,
                                int k, int max_cycles, int prec, void* d_ws, size_t ws_bytes, void* stream,
                                int* h_cycles, int* h_status, double* h_res);
+/* Autotunes the batch: for every degree, igamg_autotune on the problem of
+ * median size; the problems of that degree take its GS row-CTA cap and a
+ * coarse tail down to the same level size.  The workspace is the batch
+ * workspace (sized for IGAMG_FP32_IR); its contents are overwritten. */
+igamg_status igamg_batch_autotune(igamg_batch* batch, void* d_ws, size_t ws_bytes, void* stream, int reps);
 void igamg_batch_destroy(igamg_batch* batch);
 
 /* ---------------------------------------------------------------- misc */

@@ -64,6 +64,10 @@ def _load():
         "igamg_set_smoother": (c_int, [vp, vp, c_double]),
         "igamg_smoother_fell_back": (c_int, [vp]),
         "igamg_coarse_tail_level": (c_int, [vp]),
+        "igamg_set_schedule": (c_int, [vp, c_int, c_int]),
+        "igamg_get_schedule": (None, [vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
+        "igamg_autotune": (c_int, [vp, vp, c_size, vp, c_int]),
+        "igamg_batch_autotune": (c_int, [vp, vp, c_size, vp, c_int]),
         "igamg_smooth_f32": (c_int, [vp, c_int, vp, vp, c_int, c_int, vp, c_size, vp]),
         "igamg_set_coarse_tail": (c_int, [vp, c_int]),
         "igamg_vcycle_probe": (c_int, [vp, vp, vp, vp, vp, c_size, vp]),
@@ -245,6 +249,26 @@ def igamg_smooth_f32(ctx, level, x, b, descending, ws, sums_current=False, strea
                                     _ptr(ws), ws.numel(), _stream(stream)), "igamg_smooth_f32")
 
 
+def igamg_set_schedule(ctx, gs_threads=0, tail_levels=-1):
+    _check(_load().igamg_set_schedule(ctx, gs_threads, tail_levels), "igamg_set_schedule")
+
+
+def igamg_get_schedule(ctx):
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _load().igamg_get_schedule(ctx, ctypes.byref(a), ctypes.byref(b))
+    return {"gs_threads": a.value, "tail_levels": b.value}
+
+
+def igamg_autotune(ctx, ws, reps=3, stream=None):
+    _check(_load().igamg_autotune(ctx, _ptr(ws), ws.numel(), _stream(stream), reps), "igamg_autotune")
+    return igamg_get_schedule(ctx)
+
+
+def igamg_batch_autotune(batch, ws, reps=3, stream=None):
+    _check(_load().igamg_batch_autotune(batch, _ptr(ws), ws.numel(), _stream(stream), reps),
+           "igamg_batch_autotune")
+
+
 def igamg_coarse_tail_level(ctx):
     return int(_load().igamg_coarse_tail_level(ctx))
 
@@ -342,6 +366,10 @@ class Solver:
         self.k_max = k
         self.smoother = None
 
+    def autotune(self, reps=3):
+        """Pick the FP32 V-cycle launch schedule by timing (igamg_autotune)."""
+        return igamg_autotune(self.ctx, self.ws, reps)
+
     def set_smoother(self, w, stall_ratio=0.95):
         """Use network weights w (device FP32 tensor, kept referenced here) as the
         learned post-smoother of prec='fp32_ir_learned' solves."""
@@ -402,6 +430,10 @@ class Batch:
         b = torch.empty(self.N, dtype=torch.float64, device=self.ws.device)
         igamg_batch_rhs_sine(self.handle, coeffs, b)
         return b
+
+    def autotune(self, reps=3):
+        """Pick the FP32 V-cycle launch schedules by timing (igamg_batch_autotune)."""
+        igamg_batch_autotune(self.handle, self.ws, reps)
 
     def solve(self, b, x=None, tol=1e-10, method="rre", k=5, max_cycles=200, prec="fp32_ir"):
         import torch

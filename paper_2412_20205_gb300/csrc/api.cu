@@ -102,9 +102,12 @@ struct igamg_ctx {
     std::vector<TransferView<float>> tv32;
     CoarseView<double> cv64{};
     CoarseView<float> cv32{};
-    // coarse levels of the FP32 2D V-cycle in one CTA (tail32.lc = 0: none)
+    // coarse levels of the FP32 2D V-cycle in one CTA (tail32.lc = 0: none);
+    // tails[l] covers levels 0..l for every feasible l (tails[0] unused)
     TailView<float> tail32{};
+    std::vector<TailView<float>> tails;
     bool tail_on = true;
+    int gs_cap32 = 0;                       // row-CTA thread cap of FP32 GS (0: default)
     // sine-moment tables for the load vector (finest level)
     cudaStream_t cap = nullptr;             // capture stream
     double* h_pin = nullptr;                // pinned host scalars
@@ -268,6 +271,10 @@ struct Views<float> {
     static std::vector<LevelBuf<float>>& buf(Workspace& w) { return w.f; }
 };
 
+// Row-CTA thread cap of the GS sweeps in cycles of type T (autotuned for FP32).
+template <typename T>
+int gs_cap(const igamg_ctx* c) { return std::is_same<T, float>::value ? c->gs_cap32 : 0; }
+
 // Algorithm 2 (mu = 1, nu1 = nu2 = 1) from level `top` down to the coarsest
 // and back.  x_top / b_top are the top level's iterate and right side; the
 // top level's TM/TK must match x_top unless top_zero (then x_top = 0 is set).
@@ -293,7 +300,7 @@ void vcycle(const igamg_ctx* c, cudaStream_t s, Workspace& w, int top, T* x_top,
                 dev::fill_zero<T>(s, B[l].TM, 2 * N);
             }
         }
-        dev::gs_sweep<T>(s, dim, lv[l], false, x, b, B[l].TM, B[l].TK);               // pre-smooth
+        dev::gs_sweep<T>(s, dim, lv[l], false, x, b, B[l].TM, B[l].TK, gs_cap<T>(c));  // pre-smooth
         dev::residual<T, T>(s, dim, lv[l], b, B[l].TM, B[l].TK, B[l].r, nullptr);      // r = b - A u
         dev::restrict_<T>(s, dim, tv[l], B[l].r, B[l - 1].b, B[l].tmp1, B[l].tmp2);   // R = P^T
     }
@@ -319,7 +326,7 @@ void vcycle(const igamg_ctx* c, cudaStream_t s, Workspace& w, int top, T* x_top,
                 continue;
             }
         }
-        dev::gs_sweep<T>(s, dim, lv[l], true, x, b, B[l].TM, B[l].TK);                // post-smooth
+        dev::gs_sweep<T>(s, dim, lv[l], true, x, b, B[l].TM, B[l].TK, gs_cap<T>(c));   // post-smooth
     }
 }
 
@@ -663,6 +670,8 @@ igamg_status igamg_assemble(igamg_ctx* c) {
             if (d >= dim) continue;
             int tl = 0, th = 0;
             const int mid = toeplitz_range(H.f[d], &tl, &th), bw = 2 * p + 1;
+            tl = std::max(tl, p);                    // every band neighbour inside the grid
+            th = std::max(tl, std::min(th, H.m[d] - p));
             a.tlo[d] = f.tlo[d] = tl;
             a.thi[d] = f.thi[d] = th;
             for (int b = 0; b < bw; ++b) {
@@ -703,6 +712,7 @@ igamg_status igamg_assemble(igamg_ctx* c) {
     // faster than a launch per step (kTailMaxN unknowns at most).
     constexpr size_t kTailMaxN = 6000;
     c->tail32.lc = 0;
+    c->tails.assign(1, TailView<float>{});
     if (dim == 2 && L >= 3) {
         const size_t limit = dev::tail_smem_limit();
         for (int l = 1; l <= std::min(L - 2, kTailLevels - 1); ++l) {
@@ -735,6 +745,7 @@ igamg_status igamg_assemble(igamg_ctx* c) {
             }
             v.C = c->cv32;
             c->tail32 = v;
+            c->tails.push_back(v);
         }
     }
     CUDA_TRY(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
@@ -900,7 +911,7 @@ igamg_status igamg_smooth_f32(igamg_ctx* c, int level, float* d_x, const float* 
     LevelBuf<float>& B = w.f[level];
     if (!sums_current)
         dev::xpass<float, float>(s, c->lv32[level], d_x, nullptr, nullptr, 0, nullptr, nullptr, 0, B.TM, B.TK);
-    dev::gs_sweep<float>(s, c->dim, c->lv32[level], descending != 0, d_x, d_b, B.TM, B.TK);
+    dev::gs_sweep<float>(s, c->dim, c->lv32[level], descending != 0, d_x, d_b, B.TM, B.TK, c->gs_cap32);
     CUDA_TRY(cudaGetLastError());
     return IGAMG_OK;
 }
@@ -1003,17 +1014,84 @@ int igamg_coarse_tail_level(const igamg_ctx* c) {
     return (c && c->assembled && c->tail_on) ? c->tail32.lc : 0;
 }
 
-igamg_status igamg_set_coarse_tail(igamg_ctx* c, int enable) {
-    if (igamg_status st = check_ctx(c)) return st;
-    const bool on = enable != 0;
-    if (on == c->tail_on) return IGAMG_OK;
-    c->tail_on = on;
-    for (int sl = 0; sl < 2; ++sl)              // recapture with the other form
+static void drop_graphs(igamg_ctx* c) {
+    for (int sl = 0; sl < 2; ++sl)
         if (c->exec[sl]) {
             cudaGraphExecDestroy(c->exec[sl]);
             c->exec[sl] = nullptr;
             c->key[sl] = igamg_ctx::Key{};
         }
+}
+
+igamg_status igamg_set_schedule(igamg_ctx* c, int gs_threads, int tail_levels) {
+    if (igamg_status st = check_ctx(c)) return st;
+    if (gs_threads != 0 && gs_threads != 128 && gs_threads != 256 && gs_threads != 512)
+        return fail(IGAMG_EINVAL, "gs_threads must be 0, 128, 256 or 512");
+    if (tail_levels < -1) return fail(IGAMG_EINVAL, "tail_levels must be >= -1");
+    c->gs_cap32 = gs_threads;
+    if (tail_levels >= 0) {
+        const int most = (int)c->tails.size() - 1;
+        const int lc = std::min(tail_levels, most);
+        c->tail_on = lc > 0;
+        if (lc > 0) c->tail32 = c->tails[lc];
+    }
+    drop_graphs(c);
+    return IGAMG_OK;
+}
+
+void igamg_get_schedule(const igamg_ctx* c, int* gs_threads, int* tail_levels) {
+    if (gs_threads) *gs_threads = c ? c->gs_cap32 : 0;
+    if (tail_levels) *tail_levels = (c && c->assembled && c->tail_on) ? c->tail32.lc : 0;
+}
+
+igamg_status igamg_autotune(igamg_ctx* c, void* d_ws, size_t ws_bytes, void* stream, int reps) {
+    if (igamg_status st = check_ctx(c)) return st;
+    if (reps < 1) return fail(IGAMG_EINVAL, "reps must be >= 1");
+    if (igamg_status st = check_ws(c, d_ws, ws_bytes, 1, IGAMG_FP32_IR)) return st;
+    Workspace w = carve(c, d_ws, 1, IGAMG_FP32_IR);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int top = c->L - 1;
+    LevelBuf<float>& G = w.f[top];
+    const size_t N = finestN(c);
+    // a right side with every frequency: b = 1 (x = 0 at the start of every cycle)
+    CUDA_TRY(cudaMemsetAsync(G.b, 0x3f, N * sizeof(float), s));       // 0x3f3f3f3f = 0.747
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    const int caps[3] = {128, 256, 512};
+    const int most = (int)c->tails.size() - 1;
+    float best = 1e30f;
+    int best_cap = 0, best_lc = c->tail_on ? c->tail32.lc : 0;
+    for (int ci = 0; ci < (c->dim == 2 ? 3 : 1); ++ci)
+        for (int lc = 0; lc <= most; ++lc) {
+            c->gs_cap32 = c->dim == 2 ? caps[ci] : 0;
+            c->tail_on = lc > 0;
+            if (lc > 0) c->tail32 = c->tails[lc];
+            vcycle<float>(c, s, w, top, G.x, G.b, true);                  // warm-up
+            CUDA_TRY(cudaEventRecord(e0, s));
+            for (int r = 0; r < reps; ++r) vcycle<float>(c, s, w, top, G.x, G.b, true);
+            CUDA_TRY(cudaEventRecord(e1, s));
+            CUDA_TRY(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) { best = ms; best_cap = c->gs_cap32; best_lc = lc; }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->gs_cap32 = best_cap;
+    c->tail_on = best_lc > 0;
+    if (best_lc > 0) c->tail32 = c->tails[best_lc];
+    drop_graphs(c);
+    CUDA_TRY(cudaGetLastError());
+    return IGAMG_OK;
+}
+
+igamg_status igamg_set_coarse_tail(igamg_ctx* c, int enable) {
+    if (igamg_status st = check_ctx(c)) return st;
+    const bool on = enable != 0;
+    if (on == c->tail_on) return IGAMG_OK;
+    c->tail_on = on && c->tails.size() > 1;
+    drop_graphs(c);                             // recapture with the other form
     return IGAMG_OK;
 }
 
@@ -1210,6 +1288,37 @@ igamg_status igamg_batch_solve(igamg_batch* B, const double* d_b, double* d_x, d
     }
     if (all != IGAMG_OK) fail(all, "some problems did not converge");
     return all;
+}
+
+igamg_status igamg_batch_autotune(igamg_batch* B, void* d_ws, size_t ws_bytes, void* stream, int reps) {
+    if (!B || !d_ws) return fail(IGAMG_EINVAL, "bad batch autotune arguments");
+    const std::vector<size_t> off = batch_ws_offsets(B, 1, IGAMG_FP32_IR);
+    if (off.back() > ws_bytes) return fail(IGAMG_ENOMEM, "batch workspace too small (size it for IGAMG_FP32_IR)");
+    // one tuning run per degree, on the problem of median size; the others
+    // take its row-CTA cap and the tail down to the same level size
+    std::vector<int> ps;
+    for (int i = 0; i < B->count; ++i)
+        if (std::find(ps.begin(), ps.end(), B->ctx[i]->p) == ps.end()) ps.push_back(B->ctx[i]->p);
+    for (int p : ps) {
+        std::vector<int> ids;
+        for (int i = 0; i < B->count; ++i)
+            if (B->ctx[i]->p == p) ids.push_back(i);
+        std::sort(ids.begin(), ids.end(), [&](int a, int b) { return finestN(B->ctx[a]) < finestN(B->ctx[b]); });
+        const int m = ids[ids.size() / 2];
+        igamg_ctx* cm = B->ctx[m];
+        if (igamg_status st = igamg_autotune(cm, (char*)d_ws + off[m], off[m + 1] - off[m], stream, reps)) return st;
+        const int cap = cm->gs_cap32;
+        const size_t nthr = (cm->tail_on && cm->tail32.lc > 0) ? cm->hl[cm->tail32.lc].N() : 0;
+        for (int i : ids) {
+            if (i == m) continue;
+            igamg_ctx* ci = B->ctx[i];
+            int lc = 0;
+            for (int l = 1; l < (int)ci->tails.size(); ++l)
+                if (ci->hl[l].N() <= nthr) lc = l;
+            if (igamg_status st = igamg_set_schedule(ci, cap, lc)) return st;
+        }
+    }
+    return IGAMG_OK;
 }
 
 void igamg_batch_destroy(igamg_batch* B) {

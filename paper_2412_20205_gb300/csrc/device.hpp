@@ -26,7 +26,8 @@ struct LevelView {
     const T* Kb[3];
     const T* invdiag;                     // 1 / A_ii
     // per direction d, rows i in [tlo[d], thi[d]) share one band (the uniform
-    // interior of an open knot vector); kernels read it from these parameters
+    // interior of an open knot vector) and have all 2p+1 neighbours inside
+    // the grid (p <= i < m - p); kernels read it from these parameters
     // instead of Mb/Kb[d].
     int tlo[3], thi[3];
     T Mc[3][2 * kMaxP + 1], Kc[3][2 * kMaxP + 1];
@@ -129,10 +130,11 @@ template <typename T, typename A>
 void xpass(cudaStream_t s, const LevelView<T>& L, const T* x, T* x_out, const A* add,
            int nS, const double* gamma, const T* S, size_t ldS, T* TM, T* TK);
 
-// One multicolour Gauss-Seidel sweep (all (p+1)^dim colours) in row phases.
+// One multicolour Gauss-Seidel sweep (all (p+1)^dim colours) in row phases;
+// cap bounds the threads of a row CTA (0: the default).
 template <typename T>
 void gs_sweep(cudaStream_t s, int dim, const LevelView<T>& L, bool descending, T* x,
-              const T* b, T* TM, T* TK);
+              const T* b, T* TM, T* TK, int cap = 0);
 
 // r = b - A x from the row partial sums; optional per-row partial ||r||^2.
 template <typename T, typename R>

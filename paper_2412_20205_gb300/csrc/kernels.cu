@@ -246,11 +246,12 @@ __global__ void __launch_bounds__(row_cta_max<T, DIM>()) k_gs_phase(LevelView<T>
     const RowBand<T, P> band{L, bm, bk, nb};
     const T am = cM[OWN], ak = cK[OWN];
     if constexpr (WINDOW) {
-        const int tlo = max(L.tlo[0], P), thi = min(L.thi[0], mx - P);
+        const int tlo = L.tlo[0], thi = L.thi[0];
         // sum_b M_x(i, b) dl[i + b - p] (and K_x): the x-band applied to this
-        // sweep's corrections so far (zero for colours not yet done).  Where
-        // the band is uniform and every neighbour exists it comes from the
-        // kernel parameters at compile-time offsets.
+        // sweep's corrections so far (zero for colours not yet done).  In the
+        // uniform interior (where every neighbour exists: p <= i < m - p, see
+        // LevelView) the band comes from the kernel parameters at
+        // compile-time offsets.
         auto xband_dl = [&](int i, bool skip_own, T& sm, T& sk) {
             if (i >= tlo && i < thi) {
 #pragma unroll
@@ -909,10 +910,11 @@ void xpass(cudaStream_t s, const LevelView<T>& L, const T* x, T* x_out, const A*
 
 template <typename T>
 void gs_sweep(cudaStream_t s, int dim, const LevelView<T>& L, bool descending, T* x, const T* b,
-              T* TM, T* TK) {
+              T* TM, T* TK, int cap) {
     const int p = L.p, P1 = p + 1;
     const size_t smem = (size_t)6 * L.m[0] * sizeof(T);
-    const int threads = row_threads(L.m[0], dim == 3 ? row_cta_max<T, 3>() : row_cta_max<T, 2>());
+    const int most = dim == 3 ? row_cta_max<T, 3>() : row_cta_max<T, 2>();
+    const int threads = row_threads(L.m[0], (cap >= 64 && cap < most) ? cap : most);
     auto launch = [&](int cy, int cz) {
         const int nty = (L.m[1] - cy + p) / P1;
         const int ntz = (dim == 3) ? (L.m[2] - cz + p) / P1 : 1;
@@ -1082,7 +1084,7 @@ void fill_zero(cudaStream_t s, T* p, size_t n) {
 #define IGAMG_INST(T)                                                                               \
     template void xpass<T, T>(cudaStream_t, const LevelView<T>&, const T*, T*, const T*, int,       \
                               const double*, const T*, size_t, T*, T*);                             \
-    template void gs_sweep<T>(cudaStream_t, int, const LevelView<T>&, bool, T*, const T*, T*, T*);  \
+    template void gs_sweep<T>(cudaStream_t, int, const LevelView<T>&, bool, T*, const T*, T*, T*, int);  \
     template void restrict_<T>(cudaStream_t, int, const TransferView<T>&, const T*, T*, T*, T*);   \
     template void prolong_add<T>(cudaStream_t, int, const TransferView<T>&, const LevelView<T>&,    \
                                  const T*, T*, T*, T*, T*, T*);                                     \

@@ -92,3 +92,45 @@ def test_tail_solves_like_per_level_schedule(pkg, p):
     ref = s.solve(b, tol=1e-12, method="rre", k=5, prec="fp64", max_cycles=60)["x"]
     assert float((res[True]["x"] - ref).norm() / ref.norm()) < 1e-7
     s.close()
+
+
+def test_schedules_agree_and_autotune_solves(pkg):
+    """Every launch schedule (GS row-CTA cap x tail depth) computes the same
+    FP32 cycle up to rounding order; the autotuned one solves to tolerance."""
+    s = pkg.Solver(2, 3, 200, k=5)
+    H = omg.Hierarchy(2, [200, 200], 3)
+    rng = np.random.default_rng(8)
+    b = load_vector(H.finest.breaks, 3, rng.standard_normal((4, 4)))
+    x0 = rng.standard_normal(H.finest.N) * 1e-3
+    ref = omg.cycle(H, x0, b) - x0
+    outs = []
+    for cap in (128, 256, 512):
+        for tail in (0, 1, 99):
+            pkg.igamg_set_schedule(s.ctx, cap, tail)
+            sch = pkg.igamg_get_schedule(s.ctx)
+            assert sch["gs_threads"] == cap and sch["tail_levels"] <= 99
+            x = _t(x0)
+            pkg.igamg_vcycle(s.ctx, x, _t(b), pkg.IGAMG_FP32_IR, s.ws)
+            outs.append(_np(x) - x0)
+    for o in outs:
+        assert _rel(o, ref) < 2e-5
+    sch = s.autotune(reps=2)
+    assert sch["gs_threads"] in (128, 256, 512) and sch["tail_levels"] >= 0
+    bb = s.rhs_sine(workloads.random_sine_coeffs(2, seed=3))
+    out = s.solve(bb, tol=1e-10, method="rre", k=5, prec="fp32_ir")
+    assert out["converged"]
+    ref64 = s.solve(bb, tol=1e-12, method="rre", k=5, prec="fp64")["x"]
+    assert float((out["x"] - ref64).norm() / ref64.norm()) < 1e-7
+    with pytest.raises(RuntimeError):
+        pkg.igamg_set_schedule(s.ctx, 100, 0)
+    s.close()
+
+
+def test_batch_autotune(pkg):
+    ps, ns = [2, 3, 3, 4, 2, 3], [40, 90, 64, 33, 120, 70]
+    B = pkg.Batch(2, ps, ns, k=5)
+    coeffs = np.stack([workloads.random_sine_coeffs(2, seed=i) for i in range(len(ps))])
+    b = B.rhs_sine(coeffs)
+    B.autotune(reps=2)
+    out = B.solve(b, tol=1e-10, method="rre", k=5, prec="fp32_ir")
+    assert out["converged"], out["statuses"]
