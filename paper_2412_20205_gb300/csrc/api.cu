@@ -108,6 +108,7 @@ struct igamg_ctx {
     std::vector<TailView<float>> tails;
     bool tail_on = true;
     int gs_cap32 = 0;                       // row-CTA thread cap of FP32 GS (0: default)
+    DFView dfv{};                           // finest 2D factors as float pairs
     // sine-moment tables for the load vector (finest level)
     cudaStream_t cap = nullptr;             // capture stream
     double* h_pin = nullptr;                // pinned host scalars
@@ -368,6 +369,28 @@ void restart_body(const igamg_ctx* c, cudaStream_t s, Workspace& w, int extrap, 
     const int top = c->L - 1;
     if (extrap == IGAMG_EXTRAP_NONE) {
         fixed_point_step(c, s, w, prec, d_b, w.S, w.S);
+    } else if (prec != IGAMG_FP64 && c->dim == 2) {
+        // FP32 V-cycles with the FP64 residual carried by r <- r - A e in
+        // double-FP32 arithmetic (refine.cu); the restart's first residual and
+        // the one after extrapolation are computed from scratch in FP64.
+        LevelBuf<double>& F = w.d[top];
+        LevelBuf<float>& G = w.f[top];
+        double* r64 = F.b;                                   // unused by FP32 cycles
+        float* tmh = reinterpret_cast<float*>(F.tmp1);
+        float* tml = tmh + N;
+        float* tkh = reinterpret_cast<float*>(F.tmp2);
+        float* tkl = tkh + N;
+        dev::residual<double, float>(s, 2, c->lv64[top], d_b, F.TM, F.TK, G.b, nullptr, r64);
+        for (int i = 0; i <= k; ++i) {
+            vcycle<float>(c, s, w, top, G.x, G.b, true, prec == IGAMG_FP32_IR_LEARNED);
+            dev::refine_xpass_df(s, c->dfv, w.S + (size_t)i * w.ld, w.S + (size_t)(i + 1) * w.ld, G.x, tmh, tml,
+                                 tkh, tkl);
+            if (i < k) dev::refine_residual_df(s, c->dfv, tmh, tml, tkh, tkl, r64, G.b);
+        }
+        const int nb = dev::gram_blocks(N);
+        dev::extrap_gammas(s, k, extrap, w.S, w.ld, N, w.partial, nb, w.info, w.gamma, w.qused);
+        dev::xpass<double, double>(s, c->lv64[top], nullptr, w.S, nullptr, k + 2, w.gamma, w.S, w.ld,
+                                   w.d[top].TM, w.d[top].TK);
     } else {
         for (int i = 0; i <= k; ++i)
             fixed_point_step(c, s, w, prec, d_b, w.S + (size_t)i * w.ld, w.S + (size_t)(i + 1) * w.ld);
@@ -615,6 +638,22 @@ igamg_status igamg_assemble(igamg_ctx* c) {
         lo[l].inv[0] = add(inv.data(), N * 8);
         lo[l].inv[1] = add(inv32.data(), N * 4);
     }
+    // float-pair split of the finest 2D level's factors (double-FP32 refinement update)
+    size_t dfo[2][4] = {};
+    if (dim == 2) {
+        const HostLevel& H = c->hl[L - 1];
+        for (int d = 0; d < 2; ++d)
+            for (int which = 0; which < 2; ++which) {
+                const std::vector<double> v = band_major<double>(H.f[d], which == 1);
+                std::vector<float> hi(v.size()), lw(v.size());
+                for (size_t q = 0; q < v.size(); ++q) {
+                    hi[q] = (float)v[q];
+                    lw[q] = (float)(v[q] - (double)hi[q]);
+                }
+                dfo[d][2 * which] = add(hi.data(), hi.size() * 4);
+                dfo[d][2 * which + 1] = add(lw.data(), lw.size() * 4);
+            }
+    }
     size_t cVo[3][2], cLo[2];
     for (int d = 0; d < dim; ++d) {
         std::vector<float> f(c->cV[d].begin(), c->cV[d].end());
@@ -746,6 +785,27 @@ igamg_status igamg_assemble(igamg_ctx* c) {
             v.C = c->cv32;
             c->tail32 = v;
             c->tails.push_back(v);
+        }
+    }
+    if (dim == 2) {
+        DFView& D = c->dfv;
+        const LevelView<double>& a = c->lv64[L - 1];
+        D.p = p;
+        for (int d = 0; d < 2; ++d) {
+            D.m[d] = a.m[d];
+            D.tlo[d] = a.tlo[d];
+            D.thi[d] = a.thi[d];
+            D.Mh[d] = (const float*)(base + dfo[d][0]);
+            D.Ml[d] = (const float*)(base + dfo[d][1]);
+            D.Kh[d] = (const float*)(base + dfo[d][2]);
+            D.Kl[d] = (const float*)(base + dfo[d][3]);
+            for (int b = 0; b < 2 * kMaxP + 1; ++b) {
+                const double mv = a.Mc[d][b], kv = a.Kc[d][b];
+                D.Mch[d][b] = (float)mv;
+                D.Mcl[d][b] = (float)(mv - (double)D.Mch[d][b]);
+                D.Kch[d][b] = (float)kv;
+                D.Kcl[d][b] = (float)(kv - (double)D.Kch[d][b]);
+            }
         }
     }
     CUDA_TRY(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));

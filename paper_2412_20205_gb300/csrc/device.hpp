@@ -84,6 +84,16 @@ IGAMG_HD inline int tail_transfer_elems(const TransferView<T>& X) {
     return X.mf[0] * (1 + X.pw[0]) + X.mf[1] * (1 + X.pw[1]) + X.mc[0] * (1 + X.rw[0]) + X.mc[1] * (1 + X.rw[1]);
 }
 
+// The finest 2D level's 1D factors with every FP64 entry split into a float
+// pair (hi = float(v), lo = float(v - hi); hi + lo = v to about 2^-48
+// relative), band-major as in LevelView, and the uniform interior's pairs.
+struct DFView {
+    int m[2], p;
+    int tlo[2], thi[2];
+    const float *Mh[2], *Ml[2], *Kh[2], *Kl[2];
+    float Mch[2][2 * kMaxP + 1], Mcl[2][2 * kMaxP + 1], Kch[2][2 * kMaxP + 1], Kcl[2][2 * kMaxP + 1];
+};
+
 // Device-side state of one extrapolation (CholeskyQR2 pass-1 results).
 struct ExtrapInfo {
     int done, a, dep, pad;
@@ -139,7 +149,17 @@ void gs_sweep(cudaStream_t s, int dim, const LevelView<T>& L, bool descending, T
 // r = b - A x from the row partial sums; optional per-row partial ||r||^2.
 template <typename T, typename R>
 void residual(cudaStream_t s, int dim, const LevelView<T>& L, const T* b, const T* TM,
-              const T* TK, R* r, double* partial);
+              const T* TK, R* r, double* partial, double* r64 = nullptr);
+
+// Double-FP32 refinement update on the finest 2D level (refine.cu):
+// S_out = S_in + e and the row sums of e, (I (x) M_x) e and (I (x) K_x) e,
+// each as a float pair (hi + lo) ...
+void refine_xpass_df(cudaStream_t s, const DFView& D, const double* S_in, double* S_out, const float* e,
+                     float* tm_h, float* tm_l, float* tk_h, float* tk_l);
+// ... then r -= A e from those sums in float-pair arithmetic (FP64 r) and
+// rf = float(r), the right side of the next FP32 V-cycle.
+void refine_residual_df(cudaStream_t s, const DFView& D, const float* tm_h, const float* tm_l,
+                        const float* tk_h, const float* tk_l, double* r, float* rf);
 
 // coarse = P^T fine (tmp holds the intermediate axis passes).
 template <typename T>

@@ -337,11 +337,13 @@ __global__ void __launch_bounds__(row_cta_max<T, DIM>()) k_gs_phase(LevelView<T>
 }
 
 // ---------------------------------------------------------------- residual
-// r = b - A x (or A x without b) from T_M, T_K; optional per-row ||r||^2.
+// r = b - A x (or A x without b) from T_M, T_K; optional per-row ||r||^2 and
+// an FP64 copy of r.
 template <typename T, typename R, int DIM, int P>
 __global__ void __launch_bounds__(kThreads) k_residual(LevelView<T> L, const T* __restrict__ b,
                                                         const T* __restrict__ TM, const T* __restrict__ TK,
-                                                        R* __restrict__ r, double* __restrict__ partial) {
+                                                        R* __restrict__ r, double* __restrict__ partial,
+                                                        double* __restrict__ r64) {
     constexpr int W = 2 * P + 1;
     constexpr int NNB = (DIM == 3) ? W * W : W;
     const int mx = L.m[0], my = L.m[1];
@@ -357,6 +359,7 @@ __global__ void __launch_bounds__(kThreads) k_residual(LevelView<T> L, const T* 
         const T ax = couple<T, NNB, -1>(cM, cK, nrow, TM, TK, mx, i);
         const T v = b ? b[base + i] - ax : ax;
         r[base + i] = (R)v;
+        if (r64) r64[base + i] = (double)v;
         ss += (double)v * (double)v;
     }
     if (partial) {
@@ -942,11 +945,11 @@ void gs_sweep(cudaStream_t s, int dim, const LevelView<T>& L, bool descending, T
 
 template <typename T, typename R>
 void residual(cudaStream_t s, int dim, const LevelView<T>& L, const T* b, const T* TM, const T* TK,
-              R* r, double* partial) {
+              R* r, double* partial, double* r64) {
     with_p(L.p, [&](auto PC) {
         constexpr int P = decltype(PC)::value;
-        if (dim == 2) k_residual<T, R, 2, P><<<L.rows(), kThreads, 0, s>>>(L, b, TM, TK, r, partial);
-        else k_residual<T, R, 3, P><<<L.rows(), kThreads, 0, s>>>(L, b, TM, TK, r, partial);
+        if (dim == 2) k_residual<T, R, 2, P><<<L.rows(), kThreads, 0, s>>>(L, b, TM, TK, r, partial, r64);
+        else k_residual<T, R, 3, P><<<L.rows(), kThreads, 0, s>>>(L, b, TM, TK, r, partial, r64);
     });
     count_launch();
 }
@@ -1097,11 +1100,11 @@ template void xpass<double, float>(cudaStream_t, const LevelView<double>&, const
                                    const float*, int, const double*, const double*, size_t, double*,
                                    double*);
 template void residual<double, double>(cudaStream_t, int, const LevelView<double>&, const double*,
-                                       const double*, const double*, double*, double*);
+                                       const double*, const double*, double*, double*, double*);
 template void residual<double, float>(cudaStream_t, int, const LevelView<double>&, const double*,
-                                      const double*, const double*, float*, double*);
+                                      const double*, const double*, float*, double*, double*);
 template void residual<float, float>(cudaStream_t, int, const LevelView<float>&, const float*,
-                                     const float*, const float*, float*, double*);
+                                     const float*, const float*, float*, double*, double*);
 
 }  // namespace dev
 }  // namespace igamg

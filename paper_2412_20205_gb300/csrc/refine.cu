@@ -1,0 +1,157 @@
+// Residual update of the FP32-IR form in double-FP32 arithmetic (2D).
+//
+// Within a restart cycle the FP64 residual of the iterate is carried by the
+// recurrence r_{i+1} = r_i - A e_i, where e_i is the FP32 correction of the
+// i-th V-cycle (x_{i+1} = x_i + e_i).  A e_i is of the size of r_i, so unlike
+// b - A x_{i+1} it involves no cancellation against b; it is evaluated with
+// every FP64 operator entry held as a float pair (hi + lo) and float-pair
+// accumulation (exact products by FMA, two-sum additions), about 2^-46
+// relative per entry of A e, on the FP32 pipe (58x the FP64 rate on GB300).
+// r itself stays in FP64 and every restart starts from a freshly computed
+// FP64 residual b - A x, which is also what the stopping test measures.
+#include "device.hpp"
+
+namespace igamg {
+namespace dev {
+
+constexpr int kRefThreads = 256;
+
+// (sh, sl) += (ch + cl) * (vh + vl), float-pair accumulation
+__device__ __forceinline__ void df_acc(float& sh, float& sl, float ch, float cl, float vh, float vl) {
+    const float p = ch * vh;
+    float pe = fmaf(ch, vh, -p);                  // exact low part of ch * vh
+    pe = fmaf(ch, vl, fmaf(cl, vh, pe));
+    const float t = sh + p;                       // two-sum of the high parts
+    const float bv = t - sh;
+    const float err = (sh - (t - bv)) + (p - bv);
+    sh = t;
+    sl += err + pe;
+}
+
+__device__ __forceinline__ void df_norm(float& sh, float& sl) {
+    const float t = sh + sl;
+    sl = sl - (t - sh);
+    sh = t;
+}
+
+// One CTA per row: S_out = S_in + e; float-pair x-band sums of e.
+template <int P>
+__global__ void __launch_bounds__(kRefThreads) k_xpass_df(DFView D, const double* __restrict__ S_in,
+                                                          double* __restrict__ S_out, const float* __restrict__ e,
+                                                          float* __restrict__ tmh, float* __restrict__ tml,
+                                                          float* __restrict__ tkh, float* __restrict__ tkl) {
+    extern __shared__ float es[];                 // the row of e with a zero halo of p
+    const int mx = D.m[0];
+    const size_t base = (size_t)blockIdx.x * mx;
+    for (int ii = threadIdx.x; ii < mx + 2 * P; ii += blockDim.x) {
+        const int i = ii - P;
+        float v = 0.f;
+        if (i >= 0 && i < mx) {
+            v = e[base + i];
+            S_out[base + i] = S_in[base + i] + (double)v;
+        }
+        es[ii] = v;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < mx; i += blockDim.x) {
+        float mh = 0.f, ml = 0.f, kh = 0.f, kl = 0.f;
+        if (i >= D.tlo[0] && i < D.thi[0]) {
+#pragma unroll
+            for (int b = 0; b <= 2 * P; ++b) {
+                const float v = es[i + b];
+                df_acc(mh, ml, D.Mch[0][b], D.Mcl[0][b], v, 0.f);
+                df_acc(kh, kl, D.Kch[0][b], D.Kcl[0][b], v, 0.f);
+            }
+        } else {
+#pragma unroll
+            for (int b = 0; b <= 2 * P; ++b) {
+                const float v = es[i + b];
+                const int q = b * mx + i;
+                df_acc(mh, ml, D.Mh[0][q], D.Ml[0][q], v, 0.f);
+                df_acc(kh, kl, D.Kh[0][q], D.Kl[0][q], v, 0.f);
+            }
+        }
+        df_norm(mh, ml);
+        df_norm(kh, kl);
+        tmh[base + i] = mh;
+        tml[base + i] = ml;
+        tkh[base + i] = kh;
+        tkl[base + i] = kl;
+    }
+}
+
+// One CTA per row j: r -= sum_dj K_y(j, dj) T_M(e)(j + dj - p) + M_y(j, dj) T_K(e)(...).
+template <int P>
+__global__ void __launch_bounds__(kRefThreads) k_residual_df(DFView D, const float* __restrict__ tmh,
+                                                             const float* __restrict__ tml,
+                                                             const float* __restrict__ tkh,
+                                                             const float* __restrict__ tkl, double* __restrict__ r,
+                                                             float* __restrict__ rf) {
+    const int mx = D.m[0], my = D.m[1], j = blockIdx.x;
+    const bool uni = j >= D.tlo[1] && j < D.thi[1];
+    float kyh[2 * P + 1], kyl[2 * P + 1], myh[2 * P + 1], myl[2 * P + 1];
+#pragma unroll
+    for (int dj = 0; dj <= 2 * P; ++dj) {
+        const int q = dj * my + j;
+        kyh[dj] = uni ? D.Kch[1][dj] : D.Kh[1][q];
+        kyl[dj] = uni ? D.Kcl[1][dj] : D.Kl[1][q];
+        myh[dj] = uni ? D.Mch[1][dj] : D.Mh[1][q];
+        myl[dj] = uni ? D.Mcl[1][dj] : D.Ml[1][q];
+    }
+    const size_t base = (size_t)j * mx;
+    for (int i = threadIdx.x; i < mx; i += blockDim.x) {
+        float ah = 0.f, al = 0.f;
+#pragma unroll
+        for (int dj = 0; dj <= 2 * P; ++dj) {
+            const int jj = j + dj - P;
+            if (jj < 0 || jj >= my) continue;
+            const size_t q = (size_t)jj * mx + i;
+            df_acc(ah, al, kyh[dj], kyl[dj], tmh[q], tml[q]);
+            df_acc(ah, al, myh[dj], myl[dj], tkh[q], tkl[q]);
+        }
+        const double v = r[base + i] - ((double)ah + (double)al);
+        r[base + i] = v;
+        rf[base + i] = (float)v;
+    }
+}
+
+template <typename F>
+static void ref_with_p(int p, F&& f) {
+    switch (p) {
+        case 1: f(std::integral_constant<int, 1>()); break;
+        case 2: f(std::integral_constant<int, 2>()); break;
+        case 3: f(std::integral_constant<int, 3>()); break;
+        case 4: f(std::integral_constant<int, 4>()); break;
+        case 5: f(std::integral_constant<int, 5>()); break;
+        case 6: f(std::integral_constant<int, 6>()); break;
+        case 7: f(std::integral_constant<int, 7>()); break;
+        default: break;
+    }
+}
+
+static int ref_threads(int mx) {
+    const int t = ((mx + 31) / 32) * 32;
+    return t < 64 ? 64 : (t > kRefThreads ? kRefThreads : t);
+}
+
+void refine_xpass_df(cudaStream_t s, const DFView& D, const double* S_in, double* S_out, const float* e,
+                     float* tm_h, float* tm_l, float* tk_h, float* tk_l) {
+    const size_t smem = (size_t)(D.m[0] + 2 * D.p) * sizeof(float);
+    ref_with_p(D.p, [&](auto PC) {
+        constexpr int P = decltype(PC)::value;
+        k_xpass_df<P><<<D.m[1], ref_threads(D.m[0]), smem, s>>>(D, S_in, S_out, e, tm_h, tm_l, tk_h, tk_l);
+    });
+    count_launch();
+}
+
+void refine_residual_df(cudaStream_t s, const DFView& D, const float* tm_h, const float* tm_l, const float* tk_h,
+                        const float* tk_l, double* r, float* rf) {
+    ref_with_p(D.p, [&](auto PC) {
+        constexpr int P = decltype(PC)::value;
+        k_residual_df<P><<<D.m[1], ref_threads(D.m[0]), 0, s>>>(D, tm_h, tm_l, tk_h, tk_l, r, rf);
+    });
+    count_launch();
+}
+
+}  // namespace dev
+}  // namespace igamg
