@@ -134,3 +134,19 @@ def test_batch_autotune(pkg):
     B.autotune(reps=2)
     out = B.solve(b, tol=1e-10, method="rre", k=5, prec="fp32_ir")
     assert out["converged"], out["statuses"]
+
+
+@pytest.mark.parametrize("p", [2, 3, 5])
+def test_fp32_ir_residual_recurrence_reaches_tight_tolerance(pkg, p):
+    """The FP32-IR form carries the FP64 residual by r <- r - A e in
+    double-FP32 arithmetic inside a restart; it must not stall above the
+    FP64 solve's accuracy: relative residual 1e-12 is reached and the
+    solution agrees with an FP64 solve to 1e-10."""
+    s = pkg.Solver(2, p, 256, k=5)
+    b = s.rhs_sine(workloads.random_sine_coeffs(2, seed=11))
+    out = s.solve(b, tol=1e-12, method="rre", k=5, prec="fp32_ir", max_cycles=80)
+    assert out["converged"], out["history"][-4:]
+    ref = s.solve(b, tol=1e-13, method="rre", k=5, prec="fp64", max_cycles=120)
+    assert ref["converged"]
+    assert float((out["x"] - ref["x"]).norm() / ref["x"].norm()) < 1e-10
+    s.close()
