@@ -193,6 +193,91 @@ struct RowBand {
 template <typename T, int DIM>
 constexpr int row_cta_max() { return DIM == 3 ? 256 : 512; }
 
+
+// The p+1 colour steps of one row in the incremental form.  For the partial-
+// sum update the CTA's warps are split into p+1 groups, one per node residue
+// rho = i mod (p+1); with the colours unrolled (DESC fixed) the offsets of the
+// same-colour nodes within reach of a node, r = (cx - rho) mod (p+1) and
+// r - (p+1), are compile-time constants, so in the uniform interior the band
+// entries are kernel parameters at fixed offsets (the group branch is
+// warp-uniform).  CTAs with fewer than p+1 warps take the generic loop.
+template <typename T, int P, bool DESC, bool GROUPS>
+__device__ __forceinline__ void gs_colours_incremental(const LevelView<T>& L, const RowBand<T, P>& band, int mx,
+                                                       T am, T ak, const T* rhs, T* tm, T* tk, T* dl, T* xs,
+                                                       const T* dv) {
+    constexpr int P1 = P + 1;
+    const int per = GROUPS ? ((int)blockDim.x / 32 / P1) * 32 : 0;   // threads per residue group
+    const int rho = per > 0 ? (int)threadIdx.x / per : 0;
+    const int k0 = per > 0 ? (int)threadIdx.x - rho * per : 0;
+    const int tlo = L.tlo[0], thi = L.thi[0];
+#pragma unroll
+    for (int c = 0; c < P1; ++c) {
+        const int cx = DESC ? P - c : c;
+        for (int i = cx + P1 * (int)threadIdx.x; i < mx; i += P1 * (int)blockDim.x) {
+            const T d = (rhs[i] - (am * tm[i] + ak * tk[i])) * dv[i];
+            xs[i] += d;
+            dl[i] = d;
+        }
+        __syncthreads();
+        if (per > 0) {
+#pragma unroll
+            for (int rr = 0; rr < P1; ++rr) {
+                if (rr != rho) continue;
+                const int r = ((cx - rr) % P1 + P1) % P1;
+                for (int i = rr + P1 * k0; i < mx; i += P1 * per) {
+                    T sm = 0, sk = 0;
+                    const int i1 = i + r;                       // same-colour node at offset r
+                    const int i2 = i1 - P1;                     // and at offset r - (p+1)
+                    if (i >= tlo && i < thi) {
+                        const T d1 = dl[i1];
+                        sm = L.Mc[0][r + P] * d1;
+                        sk = L.Kc[0][r + P] * d1;
+                        if (r >= 1) {
+                            const T d2 = dl[i2];
+                            sm += L.Mc[0][r - 1] * d2;
+                            sk += L.Kc[0][r - 1] * d2;
+                        }
+                    } else {
+                        if (i1 < mx) {
+                            const T d1 = dl[i1];
+                            sm += band.m(i, r + P) * d1;
+                            sk += band.k(i, r + P) * d1;
+                        }
+                        if (r >= 1 && i2 >= 0) {
+                            const T d2 = dl[i2];
+                            sm += band.m(i, r - 1) * d2;
+                            sk += band.k(i, r - 1) * d2;
+                        }
+                    }
+                    tm[i] += sm;
+                    tk[i] += sk;
+                }
+            }
+        } else {
+            for (int i = threadIdx.x; i < mx; i += blockDim.x) {
+                int r = (cx - i) % P1;
+                if (r < 0) r += P1;
+                T sm = 0, sk = 0;
+                const int i1 = i + r;
+                if (i1 < mx) {
+                    const T d1 = dl[i1];
+                    sm += band.m(i, r + P) * d1;
+                    sk += band.k(i, r + P) * d1;
+                }
+                const int i2 = i1 - P1;
+                if (r >= 1 && i2 >= 0) {
+                    const T d2 = dl[i2];
+                    sm += band.m(i, r - 1) * d2;
+                    sk += band.k(i, r - 1) * d2;
+                }
+                tm[i] += sm;
+                tk[i] += sk;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // Which of the two in-row formulations a GS phase uses, by measurement on
 // GB300 (2D 1024^2, RRE(5) solves): the window form (one barrier per colour,
 // 2(2p+1) FMA per node) won for FP32 at p = 2, 4, 5 (by 11-18%) and lost 2%
@@ -202,7 +287,7 @@ template <typename T, int DIM, int P>
 constexpr bool gs_window() { return sizeof(T) == 4 && DIM == 2 && P != 3; }
 
 template <typename T, int DIM, int P, bool WINDOW>
-__global__ void __launch_bounds__(row_cta_max<T, DIM>()) k_gs_phase(LevelView<T> L, int cy, int cz, int descending,
+__device__ __forceinline__ void gs_phase_body(const LevelView<T>& L, int cy, int cz, int descending,
                                                     T* __restrict__ x, const T* __restrict__ b,
                                                     T* __restrict__ TM, T* __restrict__ TK) {
     constexpr int P1 = P + 1, W = 2 * P + 1;
@@ -298,42 +383,34 @@ __global__ void __launch_bounds__(row_cta_max<T, DIM>()) k_gs_phase(LevelView<T>
         // Incremental form: after each colour the row's T_M, T_K take the
         // corrections of that colour (a gather of the <= 2 same-colour nodes
         // within reach), two barriers per colour but 4 FMA per node.
-#pragma unroll
-        for (int c = 0; c < P1; ++c) {
-            const int cx = descending ? P - c : c;
-            for (int i = cx + P1 * (int)threadIdx.x; i < mx; i += P1 * (int)blockDim.x) {
-                const T d = (rhs[i] - (am * tm[i] + ak * tk[i])) * dv[i];
-                xs[i] += d;
-                dl[i] = d;
-            }
-            __syncthreads();
-            for (int i = threadIdx.x; i < mx; i += blockDim.x) {
-                int r = (cx - i) % P1;
-                if (r < 0) r += P1;
-                T sm = 0, sk = 0;
-                const int i1 = i + r;                       // same-colour node at offset r
-                if (i1 < mx) {
-                    const T d1 = dl[i1];
-                    sm += band.m(i, r + P) * d1;
-                    sk += band.k(i, r + P) * d1;
-                }
-                const int i2 = i1 - P1;                     // and at offset r - (p+1)
-                if (r >= 1 && i2 >= 0) {
-                    const T d2 = dl[i2];
-                    sm += band.m(i, r - 1) * d2;
-                    sk += band.k(i, r - 1) * d2;
-                }
-                tm[i] += sm;
-                tk[i] += sk;
-            }
-            __syncthreads();
-        }
+        // residue groups measured faster for FP32 2D rows (1024^2 p = 3: 11.75 -> 11.25 ms);
+        // FP64 and 3D rows keep the generic update
+        constexpr bool G = DIM == 2 && sizeof(T) == 4;
+        if (descending) gs_colours_incremental<T, P, true, G>(L, band, mx, am, ak, rhs, tm, tk, dl, xs, dv);
+        else gs_colours_incremental<T, P, false, G>(L, band, mx, am, ak, rhs, tm, tk, dl, xs, dv);
         for (int i = threadIdx.x; i < mx; i += blockDim.x) {
             x[base + i] = xs[i];
             TM[base + i] = tm[i];
             TK[base + i] = tk[i];
         }
     }
+}
+
+// Kernels: one CTA per target row of the phase.  2D rows are compiled for two
+// resident 512-thread CTAs per SM (up to 64 registers; without that hint
+// ptxas settled on 32-40 registers and spilled, and one CTA per SM with 128
+// registers ran slower in FP64); 3D rows keep the compiler's default.
+template <typename T, int P, bool WINDOW>
+__global__ void __launch_bounds__(row_cta_max<T, 2>(), 2)
+    k_gs_phase2(LevelView<T> L, int cy, int cz, int descending, T* __restrict__ x, const T* __restrict__ b,
+                T* __restrict__ TM, T* __restrict__ TK) {
+    gs_phase_body<T, 2, P, WINDOW>(L, cy, cz, descending, x, b, TM, TK);
+}
+template <typename T, int P, bool WINDOW>
+__global__ void __launch_bounds__(row_cta_max<T, 3>())
+    k_gs_phase3(LevelView<T> L, int cy, int cz, int descending, T* __restrict__ x, const T* __restrict__ b,
+                T* __restrict__ TM, T* __restrict__ TK) {
+    gs_phase_body<T, 3, P, WINDOW>(L, cy, cz, descending, x, b, TM, TK);
 }
 
 // ---------------------------------------------------------------- residual
@@ -882,8 +959,8 @@ void prepare_kernels() {
             with_p(p, [&](auto PC) {
                 constexpr int P = decltype(PC)::value;
                 raise_smem(k_xpass<T, T, P>, optin);
-                raise_smem(k_gs_phase<T, 2, P, gs_window<T, 2, P>()>, optin);
-                raise_smem(k_gs_phase<T, 3, P, gs_window<T, 3, P>()>, optin);
+                raise_smem(k_gs_phase2<T, P, gs_window<T, 2, P>()>, optin);
+                raise_smem(k_gs_phase3<T, P, gs_window<T, 3, P>()>, optin);
                 raise_smem(k_prolong_last<T, 2, P>, optin);
                 raise_smem(k_prolong_last<T, 3, P>, optin);
             });
@@ -926,12 +1003,12 @@ void gs_sweep(cudaStream_t s, int dim, const LevelView<T>& L, bool descending, T
             constexpr int P = decltype(PC)::value;
             if (dim == 2) {
                 constexpr bool WIN = gs_window<T, 2, P>();
-                set_smem(k_gs_phase<T, 2, P, WIN>, smem);
-                k_gs_phase<T, 2, P, WIN><<<nty * ntz, threads, smem, s>>>(L, cy, cz, descending, x, b, TM, TK);
+                set_smem(k_gs_phase2<T, P, WIN>, smem);
+                k_gs_phase2<T, P, WIN><<<nty * ntz, threads, smem, s>>>(L, cy, cz, descending, x, b, TM, TK);
             } else {
                 constexpr bool WIN = gs_window<T, 3, P>();
-                set_smem(k_gs_phase<T, 3, P, WIN>, smem);
-                k_gs_phase<T, 3, P, WIN><<<nty * ntz, threads, smem, s>>>(L, cy, cz, descending, x, b, TM, TK);
+                set_smem(k_gs_phase3<T, P, WIN>, smem);
+                k_gs_phase3<T, P, WIN><<<nty * ntz, threads, smem, s>>>(L, cy, cz, descending, x, b, TM, TK);
             }
         });
         count_launch();
