@@ -290,11 +290,12 @@ void vcycle(const igamg_ctx* c, cudaStream_t s, Workspace& w, int top, T* x_top,
     int lc = 0;
     if constexpr (std::is_same<T, float>::value)
         if (c->tail_on && c->tail32.lc > 0 && c->tail32.lc < top) lc = c->tail32.lc;
-    for (int l = top; l >= (lc > 0 ? lc + 1 : 1); --l) {
+    const int lowest = lc > 0 ? lc + 1 : 1;
+    for (int l = top; l >= lowest; --l) {
         T* x = (l == top) ? x_top : B[l].x;
         const T* b = (l == top) ? b_top : B[l].b;
         const size_t N = lv[l].n();
-        if (l != top || top_zero) {
+        if (l == top && top_zero) {                     // coarser levels were cleared by the restriction
             if (x == B[l].x) dev::fill_zero<T>(s, B[l].x, 3 * N);
             else {
                 dev::fill_zero<T>(s, x, N);
@@ -302,8 +303,11 @@ void vcycle(const igamg_ctx* c, cudaStream_t s, Workspace& w, int top, T* x_top,
             }
         }
         dev::gs_sweep<T>(s, dim, lv[l], false, x, b, B[l].TM, B[l].TK, gs_cap<T>(c));  // pre-smooth
-        dev::residual<T, T>(s, dim, lv[l], b, B[l].TM, B[l].TK, B[l].r, nullptr);      // r = b - A u
-        dev::restrict_<T>(s, dim, tv[l], B[l].r, B[l - 1].b, B[l].tmp1, B[l].tmp2);   // R = P^T
+        // b_{l-1} = R (b - A u), R = P^T; the next per-level level's x | T_M | T_K
+        // (coarse e^0 = 0) are cleared in the same pass
+        const bool clear = l - 1 >= lowest;
+        dev::residual_restrict<T>(s, dim, lv[l], tv[l], b, B[l].TM, B[l].TK, B[l].r, B[l - 1].b, B[l].tmp1,
+                                  B[l].tmp2, clear ? B[l - 1].x : nullptr, clear ? 3 * lv[l - 1].n() : 0);
     }
     if (lc > 0) {
         if constexpr (std::is_same<T, float>::value)

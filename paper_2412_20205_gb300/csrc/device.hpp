@@ -164,7 +164,15 @@ void refine_residual_df(cudaStream_t s, const DFView& D, const float* tm_h, cons
 // coarse = P^T fine (tmp holds the intermediate axis passes).
 template <typename T>
 void restrict_(cudaStream_t s, int dim, const TransferView<T>& P, const T* fine, T* coarse,
-               T* tmp1, T* tmp2);
+               T* tmp1, T* tmp2,
+               T* zero = nullptr, size_t nzero = 0);
+
+// coarse = P^T (b - A x) (x given by its row sums T_M, T_K), optionally also
+// clearing zero[0, nzero); 2D fuses the residual with the x-axis pass (r is
+// not written), 3D goes through r.
+template <typename T>
+void residual_restrict(cudaStream_t s, int dim, const LevelView<T>& L, const TransferView<T>& X, const T* b,
+                       const T* TM, const T* TK, T* r, T* coarse, T* tmp1, T* tmp2, T* zero, size_t nzero);
 
 // x += P e, then refresh the row partial sums of x.
 template <typename T>

@@ -445,13 +445,103 @@ __global__ void __launch_bounds__(kThreads) k_residual(LevelView<T> L, const T* 
     }
 }
 
+// 2D: r = b - A x of one row (from T_M, T_K) followed by the x-axis pass of
+// the restriction on that row, t[j][I] = sum_s rv[I rw + s] r[j][rlo[I] + s];
+// r itself never goes to memory.
+template <typename T, int P>
+__global__ void __launch_bounds__(kThreads) k_residual_restrict_x(LevelView<T> L, const T* __restrict__ b,
+                                                                   const T* __restrict__ TM,
+                                                                   const T* __restrict__ TK, int mcx,
+                                                                   const int* __restrict__ rlo,
+                                                                   const T* __restrict__ rv, int rw,
+                                                                   T* __restrict__ t) {
+    constexpr int W = 2 * P + 1;
+    const int mx = L.m[0], j = blockIdx.x;
+    const size_t base = (size_t)j * mx;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* rr = reinterpret_cast<T*>(smem_raw);
+    __shared__ T cM[W], cK[W];
+    __shared__ int nrow[W];
+    row_couplings<T, 2, P>(L, j, 0, cM, cK, nrow);
+    __syncthreads();
+    for (int i = threadIdx.x; i < mx; i += blockDim.x)
+        rr[i] = b[base + i] - couple<T, W, -1>(cM, cK, nrow, TM, TK, mx, i);
+    __syncthreads();
+    for (int I = threadIdx.x; I < mcx; I += blockDim.x) {
+        const int lo = rlo[I];
+        T acc = 0;
+        for (int q = 0; q < rw; ++q) {
+            const int f = lo + q;
+            if (f < 0 || f >= mx) continue;
+            acc += rv[(size_t)I * rw + q] * rr[f];
+        }
+        t[(size_t)j * mcx + I] = acc;
+    }
+}
+
+// 2D: x += P e on one fine row with both prolongation axes in one kernel
+// (the x-axis values of the <= pw1 coarse rows that reach the row are formed
+// on the fly), then the row's T_M, T_K.  Same sums in the same order as the
+// two-pass form.
+template <typename T, int P>
+__global__ void __launch_bounds__(kThreads) k_prolong_fused2(LevelView<T> L, const T* __restrict__ e, int mcx,
+                                                              int mcy, const int* __restrict__ plo0,
+                                                              const T* __restrict__ pv0, int pw0,
+                                                              const int* __restrict__ plo1,
+                                                              const T* __restrict__ pv1, int pw1,
+                                                              T* __restrict__ x, T* __restrict__ TM,
+                                                              T* __restrict__ TK) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* xs = reinterpret_cast<T*>(smem_raw);
+    const int mx = L.m[0], j = blockIdx.x;
+    const size_t base = (size_t)j * mx;
+    const int l1 = plo1[j];
+    for (int ii = threadIdx.x; ii < mx + 2 * P; ii += blockDim.x) {
+        const int i = ii - P;
+        T v = 0;
+        if (i >= 0 && i < mx) {
+            const int l0 = plo0[i];
+            T cor = 0;
+            for (int q1 = 0; q1 < pw1; ++q1) {
+                const int J = l1 + q1;
+                if (J < 0 || J >= mcy) continue;
+                T tJ = 0;                               // (P_x e)(i, J)
+                for (int q0 = 0; q0 < pw0; ++q0) {
+                    const int f = l0 + q0;
+                    if (f < 0 || f >= mcx) continue;
+                    tJ += pv0[(size_t)i * pw0 + q0] * e[(size_t)J * mcx + f];
+                }
+                cor += pv1[(size_t)j * pw1 + q1] * tJ;
+            }
+            v = x[base + i] + cor;
+            x[base + i] = v;
+        }
+        xs[ii] = v;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < mx; i += blockDim.x) {
+        T am = 0, ak = 0;
+#pragma unroll
+        for (int bb = 0; bb <= 2 * P; ++bb) {
+            const T xv = xs[i + bb];
+            am += band_m(L, i, bb) * xv;
+            ak += band_k(L, i, bb) * xv;
+        }
+        TM[base + i] = am;
+        TK[base + i] = ak;
+    }
+}
+
 // ---------------------------------------------------------------- transfer
 // out (dims d0 x d1 x d2, x fastest) along `axis`: out[.., I, ..] =
 // sum_s val[I*width + s] in[.., lo[I] + s, ..], in having n_in along axis.
 template <typename T>
 __global__ void k_transfer_axis(const T* __restrict__ in, T* __restrict__ out, int d0, int d1, int d2,
                                 int axis, int n_in, const int* __restrict__ lo,
-                                const T* __restrict__ val, int width) {
+                                const T* __restrict__ val, int width, T* __restrict__ zero, size_t nzero) {
+    // optionally also clear `zero` (the next level's x | T_M | T_K)
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < nzero; q += (size_t)gridDim.x * blockDim.x)
+        zero[q] = 0;
     const size_t total = (size_t)d0 * d1 * d2;
     for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x) {
@@ -963,6 +1053,8 @@ void prepare_kernels() {
                 raise_smem(k_gs_phase3<T, P, gs_window<T, 3, P>()>, optin);
                 raise_smem(k_prolong_last<T, 2, P>, optin);
                 raise_smem(k_prolong_last<T, 3, P>, optin);
+                raise_smem(k_residual_restrict_x<T, P>, optin);
+                raise_smem(k_prolong_fused2<T, P>, optin);
             });
         raise_smem(k_coarse_fd<T, 2>, optin);
         raise_smem(k_coarse_fd<T, 3>, optin);
@@ -1033,7 +1125,7 @@ void residual(cudaStream_t s, int dim, const LevelView<T>& L, const T* b, const 
 
 template <typename T>
 void restrict_(cudaStream_t s, int dim, const TransferView<T>& X, const T* fine, T* coarse, T* tmp1,
-               T* tmp2) {
+               T* tmp2, T* zero, size_t nzero) {
     // axis by axis: x, then y (then z); dims shrink one axis at a time
     int d[3] = {X.mf[0], X.mf[1], dim == 3 ? X.mf[2] : 1};
     const T* in = fine;
@@ -1043,15 +1135,48 @@ void restrict_(cudaStream_t s, int dim, const TransferView<T>& X, const T* fine,
         T* out = (a == dim - 1) ? coarse : (a == 0 ? tmp1 : tmp2);
         const size_t total = (size_t)d[0] * d[1] * d[2];
         k_transfer_axis<T><<<grid_for(total), kThreads, 0, s>>>(in, out, d[0], d[1], d[2], a, n_in,
-                                                                X.rlo[a], X.rv[a], X.rw[a]);
+                                                                X.rlo[a], X.rv[a], X.rw[a],
+                                                                a == dim - 1 ? zero : nullptr,
+                                                                a == dim - 1 ? nzero : 0);
         count_launch();
         in = out;
     }
 }
 
 template <typename T>
+void residual_restrict(cudaStream_t s, int dim, const LevelView<T>& L, const TransferView<T>& X, const T* b,
+                       const T* TM, const T* TK, T* r, T* coarse, T* tmp1, T* tmp2, T* zero, size_t nzero) {
+    if (dim != 2) {
+        residual<T, T>(s, dim, L, b, TM, TK, r, nullptr);
+        restrict_<T>(s, dim, X, r, coarse, tmp1, tmp2, zero, nzero);
+        return;
+    }
+    const size_t smem = (size_t)L.m[0] * sizeof(T);
+    with_p(L.p, [&](auto PC) {
+        constexpr int P = decltype(PC)::value;
+        k_residual_restrict_x<T, P><<<L.m[1], kThreads, smem, s>>>(L, b, TM, TK, X.mc[0], X.rlo[0], X.rv[0],
+                                                                   X.rw[0], tmp1);
+    });
+    count_launch();
+    const size_t total = (size_t)X.mc[0] * X.mc[1];
+    k_transfer_axis<T><<<grid_for(total), kThreads, 0, s>>>(tmp1, coarse, X.mc[0], X.mc[1], 1, 1, X.mf[1],
+                                                            X.rlo[1], X.rv[1], X.rw[1], zero, nzero);
+    count_launch();
+}
+
+template <typename T>
 void prolong_add(cudaStream_t s, int dim, const TransferView<T>& X, const LevelView<T>& Lf, const T* e,
                  T* x, T* TM, T* TK, T* tmp1, T* tmp2) {
+    if (dim == 2) {
+        const size_t smem = (size_t)(Lf.m[0] + 2 * Lf.p) * sizeof(T);
+        with_p(Lf.p, [&](auto PC) {
+            constexpr int P = decltype(PC)::value;
+            k_prolong_fused2<T, P><<<Lf.m[1], kThreads, smem, s>>>(Lf, e, X.mc[0], X.mc[1], X.plo[0], X.pv[0],
+                                                                   X.pw[0], X.plo[1], X.pv[1], X.pw[1], x, TM, TK);
+        });
+        count_launch();
+        return;
+    }
     int d[3] = {X.mc[0], X.mc[1], dim == 3 ? X.mc[2] : 1};
     const T* in = e;
     for (int a = 0; a < dim - 1; ++a) {
@@ -1060,7 +1185,7 @@ void prolong_add(cudaStream_t s, int dim, const TransferView<T>& X, const LevelV
         T* out = (a == 0) ? tmp1 : tmp2;
         const size_t total = (size_t)d[0] * d[1] * d[2];
         k_transfer_axis<T><<<grid_for(total), kThreads, 0, s>>>(in, out, d[0], d[1], d[2], a, n_in,
-                                                                X.plo[a], X.pv[a], X.pw[a]);
+                                                                X.plo[a], X.pv[a], X.pw[a], nullptr, 0);
         count_launch();
         in = out;
     }
@@ -1165,7 +1290,9 @@ void fill_zero(cudaStream_t s, T* p, size_t n) {
     template void xpass<T, T>(cudaStream_t, const LevelView<T>&, const T*, T*, const T*, int,       \
                               const double*, const T*, size_t, T*, T*);                             \
     template void gs_sweep<T>(cudaStream_t, int, const LevelView<T>&, bool, T*, const T*, T*, T*, int);  \
-    template void restrict_<T>(cudaStream_t, int, const TransferView<T>&, const T*, T*, T*, T*);   \
+    template void restrict_<T>(cudaStream_t, int, const TransferView<T>&, const T*, T*, T*, T*, T*, size_t);  \
+    template void residual_restrict<T>(cudaStream_t, int, const LevelView<T>&, const TransferView<T>&,    \
+                                       const T*, const T*, const T*, T*, T*, T*, T*, T*, size_t);         \
     template void prolong_add<T>(cudaStream_t, int, const TransferView<T>&, const LevelView<T>&,    \
                                  const T*, T*, T*, T*, T*, T*);                                     \
     template void coarse_solve<T>(cudaStream_t, int, const CoarseView<T>&, const T*, T*);          \
