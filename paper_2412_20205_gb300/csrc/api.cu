@@ -112,9 +112,10 @@ struct igamg_ctx {
     // sine-moment tables for the load vector (finest level)
     cudaStream_t cap = nullptr;             // capture stream
     double* h_pin = nullptr;                // pinned host scalars
-    // restart-cycle graphs: slot 0 plain smoothing, slot 1 learned post-smoother
-    cudaGraphExec_t exec[2] = {nullptr, nullptr};
-    long long exec_launches[2] = {0, 0};
+    // restart-cycle graphs, one slot per precision form (igamg_prec), so that
+    // alternating forms do not recapture
+    cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
+    long long exec_launches[3] = {0, 0, 0};
     struct Key {
         const void* b = nullptr;
         const void* ws = nullptr;
@@ -124,7 +125,7 @@ struct igamg_ctx {
             return b == o.b && ws == o.ws && k == o.k && extrap == o.extrap && prec == o.prec &&
                    abs_tol == o.abs_tol && w == o.w;
         }
-    } key[2];
+    } key[3];
     // learned post-smoother: caller-owned device weights, stall ratio, outcome
     const float* cnn_w = nullptr;
     double stall = 0.9;
@@ -425,11 +426,11 @@ igamg_status check_ws(const igamg_ctx* c, void* ws, size_t bytes, int k, int pre
 // right-hand side, workspace, k, method, precision and test).
 igamg_status ensure_graph(igamg_ctx* c, Workspace& w, const double* d_b, void* d_ws, int kk, int extrap,
                           int prec, const double* denom) {
-    const int slot = prec == IGAMG_FP32_IR_LEARNED ? 1 : 0;
+    const int slot = prec;
     igamg_ctx::Key key;
     key.b = d_b; key.ws = d_ws; key.k = kk; key.extrap = extrap; key.prec = prec;
     key.abs_tol = denom == nullptr;
-    key.w = slot ? c->cnn_w : nullptr;
+    key.w = prec == IGAMG_FP32_IR_LEARNED ? c->cnn_w : nullptr;
     if (c->exec[slot] && c->key[slot] == key) return IGAMG_OK;
     if (c->exec[slot]) { cudaGraphExecDestroy(c->exec[slot]); c->exec[slot] = nullptr; }
     cudaGraph_t g = nullptr;
@@ -906,7 +907,7 @@ igamg_status igamg_solve(igamg_ctx* c, const double* d_b, double* d_x, double to
         if (igamg_status st = ensure_graph(c, w, d_b, d_ws, kk, extrap, cur, denom)) return st;
     int cyc = 0;
     for (cyc = 1; cyc <= max_cycles && result != IGAMG_OK; ++cyc) {
-        const int slot = cur == IGAMG_FP32_IR_LEARNED ? 1 : 0;
+        const int slot = cur;
         if (use_graph) {
             CUDA_TRY(cudaGraphLaunch(c->exec[slot], s));
             count_launch(c->exec_launches[slot]);
@@ -1079,7 +1080,7 @@ int igamg_coarse_tail_level(const igamg_ctx* c) {
 }
 
 static void drop_graphs(igamg_ctx* c) {
-    for (int sl = 0; sl < 2; ++sl)
+    for (int sl = 0; sl < 3; ++sl)
         if (c->exec[sl]) {
             cudaGraphExecDestroy(c->exec[sl]);
             c->exec[sl] = nullptr;
@@ -1176,7 +1177,7 @@ igamg_status igamg_vcycle_probe(igamg_ctx* c, double* d_x, const double* d_b, do
 
 void igamg_destroy(igamg_ctx* c) {
     if (!c) return;
-    for (int sl = 0; sl < 2; ++sl)
+    for (int sl = 0; sl < 3; ++sl)
         if (c->exec[sl]) cudaGraphExecDestroy(c->exec[sl]);
     if (c->cap) cudaStreamDestroy(c->cap);
     if (c->h_pin) cudaFreeHost(c->h_pin);
@@ -1320,8 +1321,8 @@ igamg_status igamg_batch_solve(igamg_batch* B, const double* d_b, double* d_x, d
         for (int i = 0; i < B->count; ++i) {
             if (stat[i] != IGAMG_ENOTCONV) continue;
             cudaStream_t s = B->streams[B->lane[i]];
-            CUDA_TRY(cudaGraphLaunch(B->ctx[i]->exec[0], s));
-            count_launch(B->ctx[i]->exec_launches[0]);
+            CUDA_TRY(cudaGraphLaunch(B->ctx[i]->exec[prec], s));
+            count_launch(B->ctx[i]->exec_launches[prec]);
             CUDA_TRY(cudaMemcpyAsync(B->h_pin + 2 * i + 1, W[i].scal + 1, 8, cudaMemcpyDeviceToHost, s));
             ++active;
         }
