@@ -28,7 +28,7 @@ METRIC = "time to rel. residual 1e-10 and DOF/s: FP64 GMG+RRE vs mixed/learned f
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # FP32 GS row-phase kernel on the finest level, from the ncu capture summarised
 # in profiles/k_gs_phase_2d_1024_p3_fp32.md; keyed by (dim, n, p).
-GS_TRAFFIC = {(2, 1024, 3): 11.71e6}
+GS_TRAFFIC = {(2, 1024, 3): 11.77e6}
 
 
 def measured_peak(key, fallback):
