@@ -235,8 +235,8 @@ __global__ void __launch_bounds__(kT) k_conv3(Shape s, const __nv_bfloat16* __re
 // staged with a 3-pixel halo, layer-1 activations are computed on a 2-pixel
 // halo and layer-2 activations on a 1-pixel halo (the halos are recomputed by
 // the neighbouring tiles), all in shared memory; only r is read and y written
-// in global memory.  The weight fragments live in registers for the whole
-// (persistent, grid-stride) kernel.
+// in global memory.  The weight fragments are packed once per CTA of the
+// persistent, grid-stride kernel.
 namespace fused {
 constexpr int TH = 16, TW = 32;
 constexpr int RH = TH + 6, RW = TW + 6;
@@ -244,11 +244,12 @@ constexpr int A1H = TH + 4, A1W = TW + 4;
 constexpr int A2H = TH + 2, A2W = TW + 2;
 constexpr int NR = RH * RW, NA1 = A1H * A1W, NA2 = A2H * A2W, NO = TH * TW;
 constexpr int S1 = (NA1 + 15) / 16, S2 = (NA2 + 15) / 16, S3 = NO / 16;
-constexpr int kSmem = NA1 * 32 + NA2 * 32 + NR * 4;
+constexpr int NB2 = 9 * 2 * 32, NB3 = 9 * 32;     // per-lane B fragments (uint2) of layers 2, 3
+constexpr int kSmem = NA1 * 32 + NA2 * 32 + NR * 4 + (NB2 + NB3) * 8;
 constexpr int kThreads = 256, kWarps = kThreads / 32;
-constexpr int kBlocks = 152 * 2;
+constexpr int kBlocks = 152 * 3;
 static_assert(TW % 16 == 0, "output strips of 16 pixels run along x");
-static_assert(kSmem <= 48 * 1024, "within the default dynamic shared-memory limit");
+static_assert(kSmem <= 64 * 1024, "three CTAs per SM");
 }  // namespace fused
 
 // Byte offset of half h (channels 8h .. 8h+7) of pixel q in a shared-memory
@@ -292,7 +293,7 @@ __device__ __forceinline__ void store_act(unsigned char* act, int q0, const floa
     }
 }
 
-__global__ void __launch_bounds__(fused::kThreads, 2)
+__global__ void __launch_bounds__(fused::kThreads, 3)
 k_forward_fused(Shape s, const float* __restrict__ r, const float* __restrict__ w, float* __restrict__ y,
                 int accumulate) {
     using namespace fused;
@@ -304,25 +305,31 @@ k_forward_fused(Shape s, const float* __restrict__ r, const float* __restrict__ 
     const uint32_t a2s = (uint32_t)__cvta_generic_to_shared(a2);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, tq = lane & 3;
 
-    // B fragments: B(k, n) = weight of input k (tap or channel) for output n
-    uint32_t b1[2][2], b2[9][2][2], b3[9][2];
+    // B fragments: B(k, n) = weight of input k (tap or channel) for output n.
+    // Layer 1's stay in registers; layers 2 and 3 keep one uint2 per (tap,
+    // N tile, lane) in shared memory, which leaves registers for three CTAs
+    // per SM.
+    uint2* Bt2 = reinterpret_cast<uint2*>(smem + (NA1 + NA2) * 32 + NR * 4);
+    uint2* Bt3 = Bt2 + NB2;
+    uint32_t b1[2][2];
 #pragma unroll
     for (int nt = 0; nt < 2; ++nt) {
         const int n = nt * 8 + g;
         b1[nt][0] = pack_bf16(w[n * 9 + 2 * tq], w[n * 9 + 2 * tq + 1]);
         b1[nt][1] = pack_bf16(tq == 0 ? w[n * 9 + 8] : 0.f, 0.f);             // taps 9..15 are padding
     }
-#pragma unroll
-    for (int t = 0; t < 9; ++t) {
-#pragma unroll
-        for (int nt = 0; nt < 2; ++nt) {
-            const float* Wn = w + NW1 + (nt * 8 + g) * C * 9 + t;              // W2[n][ci][t], ci stride 9
-            b2[t][nt][0] = pack_bf16(Wn[(2 * tq) * 9], Wn[(2 * tq + 1) * 9]);
-            b2[t][nt][1] = pack_bf16(Wn[(2 * tq + 8) * 9], Wn[(2 * tq + 9) * 9]);
-        }
+    for (int idx = threadIdx.x; idx < NB2; idx += kThreads) {
+        const int t = idx / 64, nt = (idx / 32) % 2, ln = idx % 32, lg = ln >> 2, lq = ln & 3;
+        const float* Wn = w + NW1 + (nt * 8 + lg) * C * 9 + t;                 // W2[n][ci][t], ci stride 9
+        Bt2[idx] = make_uint2(pack_bf16(Wn[(2 * lq) * 9], Wn[(2 * lq + 1) * 9]),
+                              pack_bf16(Wn[(2 * lq + 8) * 9], Wn[(2 * lq + 9) * 9]));
+    }
+    for (int idx = threadIdx.x; idx < NB3; idx += kThreads) {
+        const int t = idx / 32, ln = idx % 32, lg = ln >> 2, lq = ln & 3;
         const float* W3 = w + NW1 + NW2 + t;                                   // W3[ci][t]; output column 0 only
-        b3[t][0] = g == 0 ? pack_bf16(W3[(2 * tq) * 9], W3[(2 * tq + 1) * 9]) : 0u;
-        b3[t][1] = g == 0 ? pack_bf16(W3[(2 * tq + 8) * 9], W3[(2 * tq + 9) * 9]) : 0u;
+        Bt3[idx] = lg == 0 ? make_uint2(pack_bf16(W3[(2 * lq) * 9], W3[(2 * lq + 1) * 9]),
+                                        pack_bf16(W3[(2 * lq + 8) * 9], W3[(2 * lq + 9) * 9]))
+                           : make_uint2(0u, 0u);
     }
 
     const int tiles_x = (s.W + TW - 1) / TW, tiles_y = (s.H + TH - 1) / TH;
@@ -368,8 +375,10 @@ k_forward_fused(Shape s, const float* __restrict__ r, const float* __restrict__ 
             for (int t = 0; t < 9; ++t) {
                 uint32_t a[4];
                 ldsm_x4(a, a1s + act_off(q1 + (t / 3) * A1W + t % 3, lh));
-                mma_bf16(acc[0], a, b2[t][0]);
-                mma_bf16(acc[1], a, b2[t][1]);
+                const uint2 w0 = Bt2[(t * 2) * 32 + lane], w1 = Bt2[(t * 2 + 1) * 32 + lane];
+                const uint32_t bb0[2] = {w0.x, w0.y}, bb1[2] = {w1.x, w1.y};
+                mma_bf16(acc[0], a, bb0);
+                mma_bf16(acc[1], a, bb1);
             }
             store_act<A2W, NA2>(a2, st * 16, acc, oy - 1, ox - 1, s);
         }
@@ -384,7 +393,9 @@ k_forward_fused(Shape s, const float* __restrict__ r, const float* __restrict__ 
             for (int t = 0; t < 9; ++t) {
                 uint32_t a[4];
                 ldsm_x4(a, a2s + act_off(q2 + (t / 3) * A2W + t % 3, lh));
-                mma_bf16(acc, a, b3[t]);
+                const uint2 w3 = Bt3[t * 32 + lane];
+                const uint32_t bb3[2] = {w3.x, w3.y};
+                mma_bf16(acc, a, bb3);
             }
             if (tq == 0) {
 #pragma unroll
@@ -632,6 +643,18 @@ void forward_stored(cudaStream_t st, Shape s, const float* r, const float* w, fl
 }
 
 // Inference: y = net(r), or y += net(r) with accumulate; one fused launch.
+// The fused kernel needs more than the default 48 KB of dynamic shared memory;
+// the limit is raised once per device, outside any stream capture.
+void prepare(int optin) {
+    (void)optin;
+    static bool done[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || done[dev]) return;
+    cudaFuncSetAttribute(k_forward_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, fused::kSmem);
+    done[dev] = true;
+}
+
 void forward(cudaStream_t st, Shape s, const float* r, const float* w, float* y, int accumulate) {
     const long long tiles = (long long)s.B * ((s.H + fused::TH - 1) / fused::TH) * ((s.W + fused::TW - 1) / fused::TW);
     const int blocks = (int)(tiles < fused::kBlocks ? tiles : fused::kBlocks);
@@ -656,6 +679,7 @@ void gradient(cudaStream_t st, Shape s, const float* r, const float* e, const fl
 }  // namespace cnn
 
 size_t cnn_workspace_bytes(long long pixels) { return cnn::workspace_bytes(pixels); }
+void cnn_prepare() { cnn::prepare(0); }
 void cnn_forward(cudaStream_t st, int B, int H, int W, const float* r, const float* w, float* y, int accumulate,
                  void* ws) {
     (void)ws;
@@ -685,6 +709,7 @@ igamg_status igamg_cnn_forward(int batch, int H, int W, const float* d_r, const 
         set_last_error("network workspace too small or unaligned");
         return IGAMG_ENOMEM;
     }
+    cnn::prepare(0);
     cnn::forward((cudaStream_t)stream, cnn::Shape{batch, H, W}, d_r, d_w, d_y, 0);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { set_last_error(std::string("network forward: ") + cudaGetErrorString(e)); return IGAMG_ECUDA; }

@@ -110,6 +110,8 @@ inline void set_last_error(const std::string& msg) { set_last_error(msg.c_str())
 // Learned post-smoother network (cnn.cu): workspace for an image of `pixels`
 // pixels; y (+)= network(r) for a batch x H x W image.
 size_t cnn_workspace_bytes(long long pixels);
+// raises the network kernels' shared-memory limit on the current device (outside capture)
+void cnn_prepare();
 void cnn_forward(cudaStream_t st, int B, int H, int W, const float* r, const float* w, float* y, int accumulate,
                  void* ws);
 

@@ -1062,6 +1062,7 @@ void prepare_kernels() {
     all_p(0.0);
     all_p(0.0f);
     prepare_tail_kernels(optin);
+    cnn_prepare();
     for (int p = 1; p <= kMaxP; ++p)
         with_p(p, [&](auto PC) { raise_smem(k_xpass<double, float, decltype(PC)::value>, optin); });
     cudaGetLastError();
