@@ -363,7 +363,10 @@ void residual_norm(const igamg_ctx* c, cudaStream_t s, Workspace& w, const doubl
                    const double* denom) {
     const int top = c->L - 1;
     LevelBuf<double>& F = w.d[top];
-    dev::residual<double, double>(s, c->dim, c->lv64[top], d_b, F.TM, F.TK, F.r, w.partial);
+    if (!w.f.empty())           // FP32-IR workspace: also leave r in FP32 for the next V-cycle
+        dev::residual<double, float>(s, c->dim, c->lv64[top], d_b, F.TM, F.TK, w.f[top].b, w.partial, F.r);
+    else
+        dev::residual<double, double>(s, c->dim, c->lv64[top], d_b, F.TM, F.TK, F.r, w.partial);
     dev::norm_final(s, w.partial, c->lv64[top].rows(), denom, w.scal, 1);
 }
 
@@ -378,14 +381,15 @@ void restart_body(const igamg_ctx* c, cudaStream_t s, Workspace& w, int extrap, 
         // FP32 V-cycles with the FP64 residual carried by r <- r - A e in
         // double-FP32 arithmetic (refine.cu); the restart's first residual and
         // the one after extrapolation are computed from scratch in FP64.
+        // r = b - A S_0 in FP64 (F.r) and FP32 (G.b) was left by the residual
+        // norm of the previous restart, or of the solve's start
         LevelBuf<double>& F = w.d[top];
         LevelBuf<float>& G = w.f[top];
-        double* r64 = F.b;                                   // unused by FP32 cycles
+        double* r64 = F.r;
         float* tmh = reinterpret_cast<float*>(F.tmp1);
         float* tml = tmh + N;
         float* tkh = reinterpret_cast<float*>(F.tmp2);
         float* tkl = tkh + N;
-        dev::residual<double, float>(s, 2, c->lv64[top], d_b, F.TM, F.TK, G.b, nullptr, r64);
         for (int i = 0; i <= k; ++i) {
             vcycle<float>(c, s, w, top, G.x, G.b, true, prec == IGAMG_FP32_IR_LEARNED);
             dev::refine_xpass_df(s, c->dfv, w.S + (size_t)i * w.ld, w.S + (size_t)(i + 1) * w.ld, G.x, tmh, tml,
