@@ -279,12 +279,14 @@ __device__ __forceinline__ void gs_colours_incremental(const LevelView<T>& L, co
 }
 
 // Which of the two in-row formulations a GS phase uses, by measurement on
-// GB300 (2D 1024^2, RRE(5) solves): the window form (one barrier per colour,
-// 2(2p+1) FMA per node) won for FP32 at p = 2, 4, 5 (by 11-18%) and lost 2%
-// at p = 3 (p = 1, 6, 7 not measured, window form); in FP64 its extra FMAs
-// cost more than the barriers it saves (p = 5: 278 ms against 188 ms).
+// GB300 (2D 1024^2 and 3D 128^3 RRE solves): the window form (one barrier per
+// colour, 2(2p+1) FMA per node) won for FP32 2D at p = 2, 4, 5 (by 5-18%)
+// and lost at p = 3 to the grouped incremental form; for FP32 3D at p = 3 it
+// won by 6% (332 -> 313 ms; other p not measured, window form); in FP64 its
+// extra FMAs cost more than the barriers it saves (2D p = 5: 278 ms against
+// 226 ms).
 template <typename T, int DIM, int P>
-constexpr bool gs_window() { return sizeof(T) == 4 && DIM == 2 && P != 3; }
+constexpr bool gs_window() { return sizeof(T) == 4 && (DIM == 3 || P != 3); }
 
 template <typename T, int DIM, int P, bool WINDOW>
 __device__ __forceinline__ void gs_phase_body(const LevelView<T>& L, int cy, int cz, int descending,
