@@ -238,6 +238,17 @@ igamg_status igamg_set_coarse_tail(igamg_ctx* ctx, int enable);
 igamg_status igamg_set_schedule(igamg_ctx* ctx, int gs_threads, int tail_levels);
 void igamg_get_schedule(const igamg_ctx* ctx, int* gs_threads, int* tail_levels);
 
+/* Launch overlap (process-wide, on by default): the kernels of the V-cycle,
+ * refinement and extrapolation chain are launched with programmatic stream
+ * serialisation, so that each kernel's CTAs are scheduled while its
+ * predecessor drains and start work the moment the predecessor's writes are
+ * visible.  Same kernels, same order, same results; only the gaps between
+ * launches shrink.  Takes effect for launches enqueued, and restart-cycle
+ * graphs captured, after the call (a context recaptures its graph on its next
+ * solve when the setting differs from the one it was captured with). */
+void igamg_set_launch_overlap(int enable);
+int igamg_get_launch_overlap(void);
+
 /* Autotuner: times `reps` FP32 V-cycles (zero start, constant right side) for
  * every GS row-CTA cap in {128, 256, 512} (2D) and every coarse-tail depth,
  * on the given stream, and keeps the fastest schedule.  The workspace must be

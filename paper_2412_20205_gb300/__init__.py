@@ -66,6 +66,8 @@ def _load():
         "igamg_coarse_tail_level": (c_int, [vp]),
         "igamg_set_schedule": (c_int, [vp, c_int, c_int]),
         "igamg_get_schedule": (None, [vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
+        "igamg_set_launch_overlap": (None, [c_int]),
+        "igamg_get_launch_overlap": (c_int, []),
         "igamg_autotune": (c_int, [vp, vp, c_size, vp, c_int]),
         "igamg_batch_autotune": (c_int, [vp, vp, c_size, vp, c_int]),
         "igamg_smooth_f32": (c_int, [vp, c_int, vp, vp, c_int, c_int, vp, c_size, vp]),
@@ -251,6 +253,15 @@ def igamg_smooth_f32(ctx, level, x, b, descending, ws, sums_current=False, strea
 
 def igamg_set_schedule(ctx, gs_threads=0, tail_levels=-1):
     _check(_load().igamg_set_schedule(ctx, gs_threads, tail_levels), "igamg_set_schedule")
+
+
+def igamg_set_launch_overlap(enable):
+    """Process-wide: launch the V-cycle chain with programmatic stream serialisation."""
+    _load().igamg_set_launch_overlap(1 if enable else 0)
+
+
+def igamg_get_launch_overlap():
+    return bool(_load().igamg_get_launch_overlap())
 
 
 def igamg_get_schedule(ctx):

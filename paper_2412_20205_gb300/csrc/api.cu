@@ -119,11 +119,11 @@ struct igamg_ctx {
     struct Key {
         const void* b = nullptr;
         const void* ws = nullptr;
-        int k = -1, extrap = -1, prec = -1, abs_tol = -1;
+        int k = -1, extrap = -1, prec = -1, abs_tol = -1, overlap = -1;
         const void* w = nullptr;
         bool operator==(const Key& o) const {
             return b == o.b && ws == o.ws && k == o.k && extrap == o.extrap && prec == o.prec &&
-                   abs_tol == o.abs_tol && w == o.w;
+                   abs_tol == o.abs_tol && overlap == o.overlap && w == o.w;
         }
     } key[3];
     // learned post-smoother: caller-owned device weights, stall ratio, outcome
@@ -434,6 +434,7 @@ igamg_status ensure_graph(igamg_ctx* c, Workspace& w, const double* d_b, void* d
     igamg_ctx::Key key;
     key.b = d_b; key.ws = d_ws; key.k = kk; key.extrap = extrap; key.prec = prec;
     key.abs_tol = denom == nullptr;
+    key.overlap = launch_overlap() ? 1 : 0;
     key.w = prec == IGAMG_FP32_IR_LEARNED ? c->cnn_w : nullptr;
     if (c->exec[slot] && c->key[slot] == key) return IGAMG_OK;
     if (c->exec[slot]) { cudaGraphExecDestroy(c->exec[slot]); c->exec[slot] = nullptr; }
@@ -1108,6 +1109,9 @@ igamg_status igamg_set_schedule(igamg_ctx* c, int gs_threads, int tail_levels) {
     return IGAMG_OK;
 }
 
+void igamg_set_launch_overlap(int enable) { set_launch_overlap(enable != 0); }
+int igamg_get_launch_overlap(void) { return launch_overlap() ? 1 : 0; }
+
 void igamg_get_schedule(const igamg_ctx* c, int* gs_threads, int* tail_levels) {
     if (gs_threads) *gs_threads = c ? c->gs_cap32 : 0;
     if (tail_levels) *tail_levels = (c && c->assembled && c->tail_on) ? c->tail32.lc : 0;
@@ -1281,6 +1285,7 @@ igamg_status igamg_batch_rhs_sine(igamg_batch* B, int modes, const double* h_coe
 igamg_status igamg_batch_solve(igamg_batch* B, const double* d_b, double* d_x, double tol, int extrap, int k,
                                int max_cycles, int prec, void* d_ws, size_t ws_bytes, void* stream,
                                int* h_cycles, int* h_status, double* h_res) {
+    const NoOverlapScope serial;                // many streams: no launch overlap (see device.hpp)
     if (!B || !d_b || !d_x) return fail(IGAMG_EINVAL, "null batch or vector");
     if (extrap < 1 || extrap > 2 || k < 1 || k > kMaxQ || prec < 0 || prec > 1 || max_cycles < 0 || !(tol >= 0.0))
         return fail(IGAMG_EINVAL, "bad batch solve arguments");
@@ -1360,6 +1365,7 @@ igamg_status igamg_batch_solve(igamg_batch* B, const double* d_b, double* d_x, d
 }
 
 igamg_status igamg_batch_autotune(igamg_batch* B, void* d_ws, size_t ws_bytes, void* stream, int reps) {
+    const NoOverlapScope serial;                // time the schedules as batched solves run them
     if (!B || !d_ws) return fail(IGAMG_EINVAL, "bad batch autotune arguments");
     const std::vector<size_t> off = batch_ws_offsets(B, 1, IGAMG_FP32_IR);
     if (off.back() > ws_bytes) return fail(IGAMG_ENOMEM, "batch workspace too small (size it for IGAMG_FP32_IR)");

@@ -296,6 +296,7 @@ __device__ __forceinline__ void store_act(unsigned char* act, int q0, const floa
 __global__ void __launch_bounds__(fused::kThreads, 3)
 k_forward_fused(Shape s, const float* __restrict__ r, const float* __restrict__ w, float* __restrict__ y,
                 int accumulate) {
+    pdl_enter();
     using namespace fused;
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char* a1 = smem;
@@ -658,7 +659,7 @@ void prepare(int optin) {
 void forward(cudaStream_t st, Shape s, const float* r, const float* w, float* y, int accumulate) {
     const long long tiles = (long long)s.B * ((s.H + fused::TH - 1) / fused::TH) * ((s.W + fused::TW - 1) / fused::TW);
     const int blocks = (int)(tiles < fused::kBlocks ? tiles : fused::kBlocks);
-    k_forward_fused<<<blocks, fused::kThreads, fused::kSmem, st>>>(s, r, w, y, accumulate);
+    launch_chained(k_forward_fused, blocks, fused::kThreads, fused::kSmem, st, s, r, w, y, accumulate);
     count_launch();
 }
 

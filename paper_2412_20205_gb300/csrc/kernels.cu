@@ -15,6 +15,7 @@
 #include "device.hpp"
 #include "bands.cuh"
 
+#include <atomic>
 #include <cstdio>
 #include <type_traits>
 
@@ -22,9 +23,15 @@ namespace igamg {
 
 namespace {
 thread_local long long g_launches = 0;
+std::atomic<bool> g_overlap{true};
+thread_local int g_no_overlap = 0;
 }
 void count_launch(long long n) { g_launches += n; }
 long long launch_count() { return g_launches; }
+bool launch_overlap() { return g_no_overlap == 0 && g_overlap.load(std::memory_order_relaxed); }
+void set_launch_overlap(bool on) { g_overlap.store(on, std::memory_order_relaxed); }
+NoOverlapScope::NoOverlapScope() { ++g_no_overlap; }
+NoOverlapScope::~NoOverlapScope() { --g_no_overlap; }
 
 namespace dev {
 
@@ -105,6 +112,7 @@ __global__ void __launch_bounds__(kThreads) k_xpass(LevelView<T> L, const T* __r
                                                      int nS, const double* __restrict__ gamma,
                                                      const T* __restrict__ S, size_t ldS,
                                                      T* __restrict__ TM, T* __restrict__ TK) {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* xs = reinterpret_cast<T*>(smem_raw);
     const int mx = L.m[0];
@@ -311,6 +319,7 @@ __device__ __forceinline__ void gs_phase_body(const LevelView<T>& L, int cy, int
     __shared__ T cM[NNB], cK[NNB];
     __shared__ int nrow[NNB];
     __shared__ T bm[kBandCols * W], bk[kBandCols * W];
+    if constexpr (DIM == 3) pdl_enter();
     row_couplings<T, DIM, P>(L, j, k, cM, cK, nrow);
     const int nb = L.tlo[0] + (mx - L.thi[0]);
     if (nb <= kBandCols)
@@ -320,13 +329,21 @@ __device__ __forceinline__ void gs_phase_body(const LevelView<T>& L, int cy, int
             bm[t] = L.Mb[0][bb * mx + i];
             bk[t] = L.Kb[0][bb * mx + i];
         }
+    // 2D rows: everything up to the wait reads operator data that no kernel
+    // writes, so under launch overlap it runs during the previous kernel's
+    // tail (measured 2-9% per solve).  3D rows wait at entry: this order cost
+    // them 27% (128^3, p = 3), with or without overlap.
+    if constexpr (DIM == 2) {
+        for (int i = threadIdx.x; i < mx; i += blockDim.x) dv[i] = L.invdiag[base + i];
+        pdl_enter();
+    }
     __syncthreads();
     for (int i = threadIdx.x; i < mx; i += blockDim.x) {
         rhs[i] = b[base + i] - couple<T, NNB, OWN>(cM, cK, nrow, TM, TK, mx, i);
         tm[i] = TM[base + i];
         tk[i] = TK[base + i];
         xs[i] = x[base + i];
-        dv[i] = L.invdiag[base + i];
+        if constexpr (DIM == 3) dv[i] = L.invdiag[base + i];
         if constexpr (WINDOW) dl[i] = 0;
     }
     __syncthreads();
@@ -431,7 +448,8 @@ __global__ void __launch_bounds__(kThreads) k_residual(LevelView<T> L, const T* 
     __shared__ T cM[NNB], cK[NNB];
     __shared__ int nrow[NNB];
     __shared__ double red[kThreads / 32];
-    row_couplings<T, DIM, P>(L, j, k, cM, cK, nrow);
+    row_couplings<T, DIM, P>(L, j, k, cM, cK, nrow);     // operator data only
+    pdl_enter();
     __syncthreads();
     double ss = 0.0;
     for (int i = threadIdx.x; i < mx; i += blockDim.x) {
@@ -464,7 +482,8 @@ __global__ void __launch_bounds__(kThreads) k_residual_restrict_x(LevelView<T> L
     T* rr = reinterpret_cast<T*>(smem_raw);
     __shared__ T cM[W], cK[W];
     __shared__ int nrow[W];
-    row_couplings<T, 2, P>(L, j, 0, cM, cK, nrow);
+    row_couplings<T, 2, P>(L, j, 0, cM, cK, nrow);       // operator data only
+    pdl_enter();
     __syncthreads();
     for (int i = threadIdx.x; i < mx; i += blockDim.x)
         rr[i] = b[base + i] - couple<T, W, -1>(cM, cK, nrow, TM, TK, mx, i);
@@ -493,6 +512,7 @@ __global__ void __launch_bounds__(kThreads) k_prolong_fused2(LevelView<T> L, con
                                                               const T* __restrict__ pv1, int pw1,
                                                               T* __restrict__ x, T* __restrict__ TM,
                                                               T* __restrict__ TK) {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* xs = reinterpret_cast<T*>(smem_raw);
     const int mx = L.m[0], j = blockIdx.x;
@@ -541,6 +561,7 @@ template <typename T>
 __global__ void k_transfer_axis(const T* __restrict__ in, T* __restrict__ out, int d0, int d1, int d2,
                                 int axis, int n_in, const int* __restrict__ lo,
                                 const T* __restrict__ val, int width, T* __restrict__ zero, size_t nzero) {
+    pdl_enter();
     // optionally also clear `zero` (the next level's x | T_M | T_K)
     for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < nzero; q += (size_t)gridDim.x * blockDim.x)
         zero[q] = 0;
@@ -574,6 +595,7 @@ __global__ void __launch_bounds__(kThreads) k_prolong_last(LevelView<T> L, const
                                                             const T* __restrict__ val, int width,
                                                             T* __restrict__ x, T* __restrict__ TM,
                                                             T* __restrict__ TK) {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* xs = reinterpret_cast<T*>(smem_raw);
     const int mx = L.m[0], my = L.m[1];
@@ -616,6 +638,7 @@ __global__ void __launch_bounds__(kThreads) k_prolong_last(LevelView<T> L, const
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kThreads) k_coarse_fd(CoarseView<T> C, const T* __restrict__ r,
                                                          T* __restrict__ e) {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int m0 = C.m[0], m1 = C.m[1], m2 = (DIM == 3) ? C.m[2] : 1;
     const int N = m0 * m1 * m2;
@@ -656,6 +679,7 @@ __global__ void __launch_bounds__(kThreads) k_coarse_fd(CoarseView<T> C, const T
 // ---------------------------------------------------------------- norms
 __global__ void __launch_bounds__(kThreads) k_sumsq(const double* __restrict__ v, size_t n,
                                                      double* __restrict__ partial) {
+    pdl_enter();
     __shared__ double red[kThreads / 32];
     double s = 0.0;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
@@ -667,6 +691,7 @@ __global__ void __launch_bounds__(kThreads) k_sumsq(const double* __restrict__ v
 __global__ void __launch_bounds__(1024) k_norm_final(const double* __restrict__ partial, int nparts,
                                                       const double* __restrict__ denom,
                                                       double* __restrict__ out, int slot) {
+    pdl_enter();
     __shared__ double red[32];
     double s = 0.0;
     for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += partial[i];
@@ -683,6 +708,7 @@ __global__ void __launch_bounds__(1024) k_norm_final(const double* __restrict__ 
 template <int Q>
 __global__ void __launch_bounds__(kThreads) k_gram_partial(const double* __restrict__ S, size_t ld,
                                                             size_t n, double* __restrict__ partial) {
+    pdl_enter();
     constexpr int NP = (Q + 1) * (Q + 2) / 2;
     double acc[NP];
 #pragma unroll
@@ -759,6 +785,7 @@ __device__ void set_fallback(int q, double* gamma, int* qused) {
 __global__ void __launch_bounds__(kThreads) k_chol1(int q, const double* __restrict__ partial, int nblocks,
                                                      ExtrapInfo* __restrict__ info, double* __restrict__ gamma,
                                                      int* __restrict__ qused) {
+    pdl_enter();
     const int n = q + 1;
     __shared__ double G[(kMaxQ + 1) * (kMaxQ + 1)];
     reduce_gram(n, partial, nblocks, n, G);
@@ -810,6 +837,7 @@ template <int Q>
 __global__ void __launch_bounds__(kThreads) k_gram2_partial(const double* __restrict__ S, size_t ld, size_t n,
                                                              const ExtrapInfo* __restrict__ info,
                                                              double* __restrict__ partial) {
+    pdl_enter();
     constexpr int NC = Q + 1, NP = NC * (NC + 1) / 2;
     if (info->done) return;
     __shared__ double Rp[NC * NC], Rinv[NC];
@@ -857,6 +885,7 @@ __global__ void __launch_bounds__(kThreads) k_gram2_partial(const double* __rest
 __global__ void __launch_bounds__(kThreads) k_gamma2(int q, int method, const double* __restrict__ partial,
                                                       int nblocks, const ExtrapInfo* __restrict__ info,
                                                       double* __restrict__ gamma, int* __restrict__ qused) {
+    pdl_enter();
     if (info->done) return;
     const int n = q + 1;
     const int a = info->a, nz = a + (a < n ? 1 : 0);
@@ -953,6 +982,7 @@ __global__ void __launch_bounds__(kThreads) k_gamma2(int q, int method, const do
 
 __global__ void k_combine(int nS, const double* __restrict__ gamma, const double* __restrict__ S,
                           size_t ld, size_t n, double* __restrict__ t) {
+    pdl_enter();
     __shared__ double g[kMaxQ + 2];
     for (int j = threadIdx.x; j < nS; j += blockDim.x) g[j] = gamma[j];
     __syncthreads();
@@ -993,6 +1023,7 @@ __global__ void k_rhs_sine(int dim, int mx, int my, int mz, int modes, const dou
 
 template <typename T>
 __global__ void k_fill_zero(T* p, size_t n) {
+    pdl_enter();
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         p[i] = (T)0;
 }
@@ -1078,7 +1109,7 @@ void xpass(cudaStream_t s, const LevelView<T>& L, const T* x, T* x_out, const A*
     with_p(L.p, [&](auto PC) {
         constexpr int P = decltype(PC)::value;
         set_smem(k_xpass<T, A, P>, smem);
-        k_xpass<T, A, P><<<L.rows(), kThreads, smem, s>>>(L, x, x_out, add, nS, gamma, S, ldS, TM, TK);
+        launch_chained(k_xpass<T, A, P>, L.rows(), kThreads, smem, s, L, x, x_out, add, nS, gamma, S, ldS, TM, TK);
     });
     count_launch();
 }
@@ -1099,11 +1130,11 @@ void gs_sweep(cudaStream_t s, int dim, const LevelView<T>& L, bool descending, T
             if (dim == 2) {
                 constexpr bool WIN = gs_window<T, 2, P>();
                 set_smem(k_gs_phase2<T, P, WIN>, smem);
-                k_gs_phase2<T, P, WIN><<<nty * ntz, threads, smem, s>>>(L, cy, cz, descending, x, b, TM, TK);
+                launch_chained(k_gs_phase2<T, P, WIN>, nty * ntz, threads, smem, s, L, cy, cz, descending, x, b, TM, TK);
             } else {
                 constexpr bool WIN = gs_window<T, 3, P>();
                 set_smem(k_gs_phase3<T, P, WIN>, smem);
-                k_gs_phase3<T, P, WIN><<<nty * ntz, threads, smem, s>>>(L, cy, cz, descending, x, b, TM, TK);
+                launch_chained(k_gs_phase3<T, P, WIN>, nty * ntz, threads, smem, s, L, cy, cz, descending, x, b, TM, TK);
             }
         });
         count_launch();
@@ -1120,8 +1151,8 @@ void residual(cudaStream_t s, int dim, const LevelView<T>& L, const T* b, const 
               R* r, double* partial, double* r64) {
     with_p(L.p, [&](auto PC) {
         constexpr int P = decltype(PC)::value;
-        if (dim == 2) k_residual<T, R, 2, P><<<L.rows(), kThreads, 0, s>>>(L, b, TM, TK, r, partial, r64);
-        else k_residual<T, R, 3, P><<<L.rows(), kThreads, 0, s>>>(L, b, TM, TK, r, partial, r64);
+        if (dim == 2) launch_chained(k_residual<T, R, 2, P>, L.rows(), kThreads, 0, s, L, b, TM, TK, r, partial, r64);
+        else launch_chained(k_residual<T, R, 3, P>, L.rows(), kThreads, 0, s, L, b, TM, TK, r, partial, r64);
     });
     count_launch();
 }
@@ -1137,7 +1168,7 @@ void restrict_(cudaStream_t s, int dim, const TransferView<T>& X, const T* fine,
         d[a] = X.mc[a];
         T* out = (a == dim - 1) ? coarse : (a == 0 ? tmp1 : tmp2);
         const size_t total = (size_t)d[0] * d[1] * d[2];
-        k_transfer_axis<T><<<grid_for(total), kThreads, 0, s>>>(in, out, d[0], d[1], d[2], a, n_in,
+        launch_chained(k_transfer_axis<T>, grid_for(total), kThreads, 0, s, in, out, d[0], d[1], d[2], a, n_in,
                                                                 X.rlo[a], X.rv[a], X.rw[a],
                                                                 a == dim - 1 ? zero : nullptr,
                                                                 a == dim - 1 ? nzero : 0);
@@ -1157,12 +1188,12 @@ void residual_restrict(cudaStream_t s, int dim, const LevelView<T>& L, const Tra
     const size_t smem = (size_t)L.m[0] * sizeof(T);
     with_p(L.p, [&](auto PC) {
         constexpr int P = decltype(PC)::value;
-        k_residual_restrict_x<T, P><<<L.m[1], kThreads, smem, s>>>(L, b, TM, TK, X.mc[0], X.rlo[0], X.rv[0],
+        launch_chained(k_residual_restrict_x<T, P>, L.m[1], kThreads, smem, s, L, b, TM, TK, X.mc[0], X.rlo[0], X.rv[0],
                                                                    X.rw[0], tmp1);
     });
     count_launch();
     const size_t total = (size_t)X.mc[0] * X.mc[1];
-    k_transfer_axis<T><<<grid_for(total), kThreads, 0, s>>>(tmp1, coarse, X.mc[0], X.mc[1], 1, 1, X.mf[1],
+    launch_chained(k_transfer_axis<T>, grid_for(total), kThreads, 0, s, tmp1, coarse, X.mc[0], X.mc[1], 1, 1, X.mf[1],
                                                             X.rlo[1], X.rv[1], X.rw[1], zero, nzero);
     count_launch();
 }
@@ -1174,7 +1205,7 @@ void prolong_add(cudaStream_t s, int dim, const TransferView<T>& X, const LevelV
         const size_t smem = (size_t)(Lf.m[0] + 2 * Lf.p) * sizeof(T);
         with_p(Lf.p, [&](auto PC) {
             constexpr int P = decltype(PC)::value;
-            k_prolong_fused2<T, P><<<Lf.m[1], kThreads, smem, s>>>(Lf, e, X.mc[0], X.mc[1], X.plo[0], X.pv[0],
+            launch_chained(k_prolong_fused2<T, P>, Lf.m[1], kThreads, smem, s, Lf, e, X.mc[0], X.mc[1], X.plo[0], X.pv[0],
                                                                    X.pw[0], X.plo[1], X.pv[1], X.pw[1], x, TM, TK);
         });
         count_launch();
@@ -1187,7 +1218,7 @@ void prolong_add(cudaStream_t s, int dim, const TransferView<T>& X, const LevelV
         d[a] = X.mf[a];
         T* out = (a == 0) ? tmp1 : tmp2;
         const size_t total = (size_t)d[0] * d[1] * d[2];
-        k_transfer_axis<T><<<grid_for(total), kThreads, 0, s>>>(in, out, d[0], d[1], d[2], a, n_in,
+        launch_chained(k_transfer_axis<T>, grid_for(total), kThreads, 0, s, in, out, d[0], d[1], d[2], a, n_in,
                                                                 X.plo[a], X.pv[a], X.pw[a], nullptr, 0);
         count_launch();
         in = out;
@@ -1198,10 +1229,10 @@ void prolong_add(cudaStream_t s, int dim, const TransferView<T>& X, const LevelV
         constexpr int P = decltype(PC)::value;
         if (dim == 2) {
             set_smem(k_prolong_last<T, 2, P>, smem);
-            k_prolong_last<T, 2, P><<<Lf.rows(), kThreads, smem, s>>>(Lf, in, X.mc[a], X.plo[a], X.pv[a], X.pw[a], x, TM, TK);
+            launch_chained(k_prolong_last<T, 2, P>, Lf.rows(), kThreads, smem, s, Lf, in, X.mc[a], X.plo[a], X.pv[a], X.pw[a], x, TM, TK);
         } else {
             set_smem(k_prolong_last<T, 3, P>, smem);
-            k_prolong_last<T, 3, P><<<Lf.rows(), kThreads, smem, s>>>(Lf, in, X.mc[a], X.plo[a], X.pv[a], X.pw[a], x, TM, TK);
+            launch_chained(k_prolong_last<T, 3, P>, Lf.rows(), kThreads, smem, s, Lf, in, X.mc[a], X.plo[a], X.pv[a], X.pw[a], x, TM, TK);
         }
     });
     count_launch();
@@ -1213,22 +1244,22 @@ void coarse_solve(cudaStream_t s, int dim, const CoarseView<T>& C, const T* r, T
     const size_t smem = (size_t)2 * N * sizeof(T);
     if (dim == 2) {
         set_smem(k_coarse_fd<T, 2>, smem);
-        k_coarse_fd<T, 2><<<1, kThreads, smem, s>>>(C, r, e);
+        launch_chained(k_coarse_fd<T, 2>, 1, kThreads, smem, s, C, r, e);
     } else {
         set_smem(k_coarse_fd<T, 3>, smem);
-        k_coarse_fd<T, 3><<<1, kThreads, smem, s>>>(C, r, e);
+        launch_chained(k_coarse_fd<T, 3>, 1, kThreads, smem, s, C, r, e);
     }
     count_launch();
 }
 
 void sumsq_partial(cudaStream_t s, const double* v, size_t n, double* partial, int nblocks) {
-    k_sumsq<<<nblocks, kThreads, 0, s>>>(v, n, partial);
+    launch_chained(k_sumsq, nblocks, kThreads, 0, s, v, n, partial);
     count_launch();
 }
 
 void norm_final(cudaStream_t s, const double* partial, int nparts, const double* denom, double* out,
                 int slot) {
-    k_norm_final<<<1, 1024, 0, s>>>(partial, nparts, denom, out, slot);
+    launch_chained(k_norm_final, 1, 1024, 0, s, partial, nparts, denom, out, slot);
     count_launch();
 }
 
@@ -1241,7 +1272,7 @@ int gram_blocks(size_t n) {
 void gram_partial(cudaStream_t s, int q, const double* S, size_t ld, size_t n, double* partial, int nblocks) {
     switch (q) {
 #define IGAMG_GRAM_CASE(Q) \
-    case Q: k_gram_partial<Q><<<nblocks, kThreads, 0, s>>>(S, ld, n, partial); break;
+    case Q: launch_chained(k_gram_partial<Q>, nblocks, kThreads, 0, s, S, ld, n, partial); break;
         IGAMG_GRAM_CASE(1) IGAMG_GRAM_CASE(2) IGAMG_GRAM_CASE(3) IGAMG_GRAM_CASE(4)
         IGAMG_GRAM_CASE(5) IGAMG_GRAM_CASE(6) IGAMG_GRAM_CASE(7) IGAMG_GRAM_CASE(8)
         IGAMG_GRAM_CASE(9) IGAMG_GRAM_CASE(10) IGAMG_GRAM_CASE(11) IGAMG_GRAM_CASE(12)
@@ -1254,11 +1285,11 @@ void gram_partial(cudaStream_t s, int q, const double* S, size_t ld, size_t n, d
 void extrap_gammas(cudaStream_t s, int q, int method, const double* S, size_t ld, size_t n,
                    double* partial, int nblocks, ExtrapInfo* info, double* gamma, int* qused) {
     gram_partial(s, q, S, ld, n, partial, nblocks);
-    k_chol1<<<1, kThreads, 0, s>>>(q, partial, nblocks, info, gamma, qused);
+    launch_chained(k_chol1, 1, kThreads, 0, s, q, partial, nblocks, info, gamma, qused);
     count_launch();
     switch (q) {
 #define IGAMG_GRAM2_CASE(Q) \
-    case Q: k_gram2_partial<Q><<<nblocks, kThreads, 0, s>>>(S, ld, n, info, partial); break;
+    case Q: launch_chained(k_gram2_partial<Q>, nblocks, kThreads, 0, s, S, ld, n, info, partial); break;
         IGAMG_GRAM2_CASE(1) IGAMG_GRAM2_CASE(2) IGAMG_GRAM2_CASE(3) IGAMG_GRAM2_CASE(4)
         IGAMG_GRAM2_CASE(5) IGAMG_GRAM2_CASE(6) IGAMG_GRAM2_CASE(7) IGAMG_GRAM2_CASE(8)
         IGAMG_GRAM2_CASE(9) IGAMG_GRAM2_CASE(10) IGAMG_GRAM2_CASE(11) IGAMG_GRAM2_CASE(12)
@@ -1266,12 +1297,12 @@ void extrap_gammas(cudaStream_t s, int q, int method, const double* S, size_t ld
         default: return;
     }
     count_launch();
-    k_gamma2<<<1, kThreads, 0, s>>>(q, method, partial, nblocks, info, gamma, qused);
+    launch_chained(k_gamma2, 1, kThreads, 0, s, q, method, partial, nblocks, info, gamma, qused);
     count_launch();
 }
 
 void combine(cudaStream_t s, int q, const double* gamma, const double* S, size_t ld, size_t n, double* t) {
-    k_combine<<<grid_for(n), kThreads, 0, s>>>(q + 2, gamma, S, ld, n, t);
+    launch_chained(k_combine, grid_for(n), kThreads, 0, s, q + 2, gamma, S, ld, n, t);
     count_launch();
 }
 
@@ -1284,7 +1315,7 @@ void rhs_sine(cudaStream_t s, int dim, const int* m, int modes, const double* H,
 
 template <typename T>
 void fill_zero(cudaStream_t s, T* p, size_t n) {
-    k_fill_zero<T><<<grid_for(n), kThreads, 0, s>>>(p, n);
+    launch_chained(k_fill_zero<T>, grid_for(n), kThreads, 0, s, p, n);
     count_launch();
 }
 

@@ -40,6 +40,7 @@ __global__ void __launch_bounds__(kRefThreads) k_xpass_df(DFView D, const double
                                                           double* __restrict__ S_out, const float* __restrict__ e,
                                                           float* __restrict__ tmh, float* __restrict__ tml,
                                                           float* __restrict__ tkh, float* __restrict__ tkl) {
+    pdl_enter();
     extern __shared__ float es[];                 // the row of e with a zero halo of p
     const int mx = D.m[0];
     const size_t base = (size_t)blockIdx.x * mx;
@@ -98,6 +99,7 @@ __global__ void __launch_bounds__(kRefThreads) k_residual_df(DFView D, const flo
         myh[dj] = uni ? D.Mch[1][dj] : D.Mh[1][q];
         myl[dj] = uni ? D.Mcl[1][dj] : D.Ml[1][q];
     }
+    pdl_enter();                                  // above: operator data only
     const size_t base = (size_t)j * mx;
     for (int i = threadIdx.x; i < mx; i += blockDim.x) {
         float ah = 0.f, al = 0.f;
@@ -139,7 +141,7 @@ void refine_xpass_df(cudaStream_t s, const DFView& D, const double* S_in, double
     const size_t smem = (size_t)(D.m[0] + 2 * D.p) * sizeof(float);
     ref_with_p(D.p, [&](auto PC) {
         constexpr int P = decltype(PC)::value;
-        k_xpass_df<P><<<D.m[1], ref_threads(D.m[0]), smem, s>>>(D, S_in, S_out, e, tm_h, tm_l, tk_h, tk_l);
+        launch_chained(k_xpass_df<P>, D.m[1], ref_threads(D.m[0]), smem, s, D, S_in, S_out, e, tm_h, tm_l, tk_h, tk_l);
     });
     count_launch();
 }
@@ -148,7 +150,7 @@ void refine_residual_df(cudaStream_t s, const DFView& D, const float* tm_h, cons
                         const float* tk_l, double* r, float* rf) {
     ref_with_p(D.p, [&](auto PC) {
         constexpr int P = decltype(PC)::value;
-        k_residual_df<P><<<D.m[1], ref_threads(D.m[0]), 0, s>>>(D, tm_h, tm_l, tk_h, tk_l, r, rf);
+        launch_chained(k_residual_df<P>, D.m[1], ref_threads(D.m[0]), 0, s, D, tm_h, tm_l, tk_h, tk_l, r, rf);
     });
     count_launch();
 }

@@ -311,6 +311,7 @@ __device__ __forceinline__ TransferView<T> staged_transfer(const TailView<T>& V,
 template <typename T, int P>
 __global__ void __launch_bounds__(kTailThreads, 1) k_coarse_tail(TailView<T> V, const T* __restrict__ b_in,
                                                                  T* __restrict__ x_out) {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
     const int lc = V.lc;
@@ -429,7 +430,7 @@ template <typename T>
 void coarse_tail(cudaStream_t s, const TailView<T>& V, const T* b, T* x) {
     tail_with_p(V.L[V.lc].p, [&](auto PC) {
         constexpr int P = decltype(PC)::value;
-        k_coarse_tail<T, P><<<1, kTailThreads, V.smem, s>>>(V, b, x);
+        launch_chained(k_coarse_tail<T, P>, 1, kTailThreads, V.smem, s, V, b, x);
     });
     count_launch();
 }

@@ -150,3 +150,54 @@ def test_fp32_ir_residual_recurrence_reaches_tight_tolerance(pkg, p):
     assert ref["converged"]
     assert float((out["x"] - ref["x"]).norm() / ref["x"].norm()) < 1e-10
     s.close()
+
+
+def test_launch_overlap_is_bitwise_neutral(pkg):
+    """Launch overlap (programmatic dependent launch) changes when a kernel's
+    CTAs are scheduled, never what they compute: every precision form, 2D and
+    3D, single and batched, gives bit-identical solutions and cycle counts with
+    the overlap on and off, inside the restart-cycle graphs and outside them."""
+    import os
+    wfile = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                         "paper_2412_20205_gb300", "weights", "smoother_2d_n256_p3.npy")
+    cases = [(2, 3, 256, ["fp64", "fp32_ir", "fp32_ir_learned"]), (3, 2, 24, ["fp64", "fp32_ir"])]
+    assert pkg.igamg_get_launch_overlap()
+    try:
+        for dim, p, n, precs in cases:
+            s = pkg.Solver(dim, p, n, k=5)
+            if "fp32_ir_learned" in precs:
+                s.set_smoother(torch.tensor(np.load(wfile), dtype=torch.float32, device=DEV))
+            b = s.rhs_sine(workloads.random_sine_coeffs(dim, seed=5))
+            for prec in precs:
+                res = {}
+                for ov in (1, 0, 1):
+                    pkg.igamg_set_launch_overlap(ov)
+                    assert pkg.igamg_get_launch_overlap() == bool(ov)
+                    out = s.solve(b, tol=1e-10, method="rre", k=5, prec=prec)
+                    assert out["converged"]
+                    res.setdefault(ov, []).append((_np(out["x"]).copy(), out["cycles"]))
+                x_on, c_on = res[1][0]
+                for x, c in res[1][1:] + res[0]:
+                    assert c == c_on and np.array_equal(x, x_on), (dim, prec)
+            # the component entry points (no graph) as well
+            x0 = s.rhs_sine(workloads.random_sine_coeffs(dim, seed=6)) * 1e-3
+            outs = []
+            for ov in (1, 0):
+                pkg.igamg_set_launch_overlap(ov)
+                x = x0.clone()
+                pkg.igamg_vcycle(s.ctx, x, b, pkg.IGAMG_FP32_IR, s.ws)
+                outs.append(_np(x))
+            assert np.array_equal(outs[0], outs[1])
+            s.close()
+        ps, ns = [2, 3, 4, 3], [40, 90, 33, 70]
+        B = pkg.Batch(2, ps, ns, k=5)
+        bb = B.rhs_sine(np.stack([workloads.random_sine_coeffs(2, seed=i) for i in range(len(ps))]))
+        xs = []
+        for ov in (1, 0):
+            pkg.igamg_set_launch_overlap(ov)
+            out = B.solve(bb, tol=1e-10, method="rre", k=5, prec="fp32_ir")
+            assert out["converged"]
+            xs.append(_np(out["x"]).copy())
+        assert np.array_equal(xs[0], xs[1])
+    finally:
+        pkg.igamg_set_launch_overlap(1)
