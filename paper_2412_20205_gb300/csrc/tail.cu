@@ -311,13 +311,13 @@ __device__ __forceinline__ TransferView<T> staged_transfer(const TailView<T>& V,
 template <typename T, int P>
 __global__ void __launch_bounds__(kTailThreads, 1) k_coarse_tail(TailView<T> V, const T* __restrict__ b_in,
                                                                  T* __restrict__ x_out) {
-    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
     const int lc = V.lc;
     T* r = sm + V.off_r;
     T* t = sm + V.off_t;
-    stage(sm + V.off_b[lc], b_in, V.L[lc].m[0] * V.L[lc].m[1]);
+    // Operator data (uploaded at assembly, written by no kernel) is staged
+    // before the wait on the previous kernel; the right side b after it.
     for (int l = 1; l <= lc; ++l) {                     // operator data of the smoothed levels
         const LevelView<T>& L = V.L[l];
         const int mx = L.m[0], my = L.m[1];
@@ -360,6 +360,8 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_coarse_tail(TailView<T> V, 
             tc[2 * P + 1 + b] = V.L[l].Kc[0][b];
         }
     }
+    pdl_enter();
+    stage(sm + V.off_b[lc], b_in, V.L[lc].m[0] * V.L[lc].m[1]);
     cp_async_wait_all();
     __syncthreads();
     auto level = [&](int l) {
