@@ -57,6 +57,9 @@ typedef enum { IGAMG_EXTRAP_NONE = 0, IGAMG_RRE = 1, IGAMG_MPE = 2 } igamg_extra
  * replaced by the learned network (igamg_set_smoother). */
 typedef enum { IGAMG_FP64 = 0, IGAMG_FP32_IR = 1, IGAMG_FP32_IR_LEARNED = 2 } igamg_prec;
 
+/* Smoother of the multigrid cycle (igamg_set_cycle). */
+typedef enum { IGAMG_SMOOTH_GS = 0, IGAMG_SMOOTH_JACOBI = 1 } igamg_smoother;
+
 /* igamg_solve flags */
 #define IGAMG_FLAG_X0_GIVEN 1u   /* start from d_x instead of s_0 = 0 */
 #define IGAMG_FLAG_ABS_TOL  2u   /* test ||b - A t|| <= tol instead of ||b - A t|| / ||b|| <= tol */
@@ -237,6 +240,21 @@ igamg_status igamg_set_coarse_tail(igamg_ctx* ctx, int enable);
  * off, -1 = unchanged).  Arithmetic is unchanged up to FP32 rounding order. */
 igamg_status igamg_set_schedule(igamg_ctx* ctx, int gs_threads, int tail_levels);
 void igamg_get_schedule(const igamg_ctx* ctx, int* gs_threads, int* tail_levels);
+
+/* Cycle of Algorithm 2 (Sec. 2.4) used by every solve, cycle and autotune
+ * call of this context.  smoother: IGAMG_SMOOTH_GS (default; multicolour
+ * Gauss-Seidel, (p+1)^dim colours, ascending before and descending after the
+ * coarse correction) or IGAMG_SMOOTH_JACOBI (weighted Jacobi
+ * x += omega D^{-1} (b - A x), the smoother of the paper's experiments in
+ * Sec. 4 with omega = 2/3; omega in (0, 2), ignored for GS).  mu = 1 is the
+ * V-cycle (default), mu = 2 the W-cycle (the coarse problem of every level
+ * above the coarsest is approximated by two cycles from a zero start).
+ * nu1 = nu2 = 1; the coarsest level is solved directly.  Anything but the
+ * default Gauss-Seidel V-cycle runs per-level kernels (no coarse tail), and
+ * IGAMG_FP32_IR_LEARNED solves and igamg_vcycle_probe then return
+ * IGAMG_EINVAL.  Errors: IGAMG_EINVAL for other values. */
+igamg_status igamg_set_cycle(igamg_ctx* ctx, int smoother, int mu, double omega);
+void igamg_get_cycle(const igamg_ctx* ctx, int* smoother, int* mu, double* omega);
 
 /* Launch overlap (process-wide, on by default): the kernels of the V-cycle,
  * refinement and extrapolation chain are launched with programmatic stream

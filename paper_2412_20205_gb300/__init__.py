@@ -17,6 +17,8 @@ IGAMG_OK, IGAMG_EINVAL, IGAMG_ENOMEM, IGAMG_ECUDA, IGAMG_ENOTCONV, IGAMG_EBREAKD
 IGAMG_EXTRAP_NONE, IGAMG_RRE, IGAMG_MPE = 0, 1, 2
 IGAMG_FP64, IGAMG_FP32_IR, IGAMG_FP32_IR_LEARNED = 0, 1, 2
 IGAMG_FLAG_X0_GIVEN, IGAMG_FLAG_ABS_TOL, IGAMG_FLAG_NO_GRAPH = 1, 2, 4
+IGAMG_SMOOTH_GS, IGAMG_SMOOTH_JACOBI = 0, 1
+SMOOTHER = {"gs": IGAMG_SMOOTH_GS, "jacobi": IGAMG_SMOOTH_JACOBI}
 
 EXTRAP = {"none": IGAMG_EXTRAP_NONE, "rre": IGAMG_RRE, "mpe": IGAMG_MPE}
 PREC = {"fp64": IGAMG_FP64, "fp32_ir": IGAMG_FP32_IR, "fp32_ir_learned": IGAMG_FP32_IR_LEARNED}
@@ -66,6 +68,8 @@ def _load():
         "igamg_coarse_tail_level": (c_int, [vp]),
         "igamg_set_schedule": (c_int, [vp, c_int, c_int]),
         "igamg_get_schedule": (None, [vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
+        "igamg_set_cycle": (c_int, [vp, c_int, c_int, c_double]),
+        "igamg_get_cycle": (None, [vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_double)]),
         "igamg_set_launch_overlap": (None, [c_int]),
         "igamg_get_launch_overlap": (c_int, []),
         "igamg_autotune": (c_int, [vp, vp, c_size, vp, c_int]),
@@ -253,6 +257,17 @@ def igamg_smooth_f32(ctx, level, x, b, descending, ws, sums_current=False, strea
 
 def igamg_set_schedule(ctx, gs_threads=0, tail_levels=-1):
     _check(_load().igamg_set_schedule(ctx, gs_threads, tail_levels), "igamg_set_schedule")
+
+
+def igamg_set_cycle(ctx, smoother="gs", mu=1, omega=2.0 / 3.0):
+    """Cycle of Algorithm 2: smoother 'gs' or 'jacobi' (weight omega), mu = 1 (V) or 2 (W)."""
+    _check(_load().igamg_set_cycle(ctx, SMOOTHER[smoother], mu, omega), "igamg_set_cycle")
+
+
+def igamg_get_cycle(ctx):
+    a, b, w = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _load().igamg_get_cycle(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(w))
+    return {"smoother": "jacobi" if a.value == IGAMG_SMOOTH_JACOBI else "gs", "mu": b.value, "omega": w.value}
 
 
 def igamg_set_launch_overlap(enable):

@@ -108,6 +108,10 @@ struct igamg_ctx {
     std::vector<TailView<float>> tails;
     bool tail_on = true;
     int gs_cap32 = 0;                       // row-CTA thread cap of FP32 GS (0: default)
+    // cycle of Algorithm 2: smoother (IGAMG_SMOOTH_GS / IGAMG_SMOOTH_JACOBI),
+    // mu = 1 (V-cycle) or 2 (W-cycle), Jacobi weight
+    int smoother = 0, mu = 1;
+    double omega = 2.0 / 3.0;
     DFView dfv{};                           // finest 2D factors as float pairs
     // sine-moment tables for the load vector (finest level)
     cudaStream_t cap = nullptr;             // capture stream
@@ -277,12 +281,62 @@ struct Views<float> {
 template <typename T>
 int gs_cap(const igamg_ctx* c) { return std::is_same<T, float>::value ? c->gs_cap32 : 0; }
 
+// Algorithm 2 for any mu and either smoother (nu1 = nu2 = 1), recursively:
+// level l pre-smooths, restricts its residual, runs mu cycles on level l - 1
+// from a zero coarse error (one direct solve on the coarsest level: a second
+// one would return the same e), adds the prolonged correction and
+// post-smooths.  Gauss-Seidel colours run ascending before and descending
+// after the coarse correction, as in the V-cycle below.
+template <typename T>
+void mu_cycle(const igamg_ctx* c, cudaStream_t s, Workspace& w, int top, int l, T* x_top, const T* b_top,
+              bool zero) {
+    const auto& lv = Views<T>::lv(c);
+    const auto& tv = Views<T>::tv(c);
+    auto& B = Views<T>::buf(w);
+    const int dim = c->dim;
+    T* x = (l == top) ? x_top : B[l].x;
+    const T* b = (l == top) ? b_top : B[l].b;
+    if (l == 0) {
+        dev::coarse_solve<T>(s, dim, Views<T>::cv(c), b, x);                           // direct
+        return;
+    }
+    const size_t N = lv[l].n();
+    if (zero) {
+        if (x == B[l].x) dev::fill_zero<T>(s, B[l].x, 3 * N);
+        else {
+            dev::fill_zero<T>(s, x, N);
+            dev::fill_zero<T>(s, B[l].TM, 2 * N);
+        }
+    }
+    auto smooth = [&](bool post) {
+        if (c->smoother == IGAMG_SMOOTH_JACOBI)
+            dev::jacobi_sweep<T>(s, dim, lv[l], (T)c->omega, x, b, B[l].TM, B[l].TK);
+        else
+            dev::gs_sweep<T>(s, dim, lv[l], post, x, b, B[l].TM, B[l].TK, gs_cap<T>(c));
+    };
+    smooth(false);
+    const bool clear = l - 1 >= 1;                  // coarse e^0 = 0: x | T_M | T_K of level l - 1
+    dev::residual_restrict<T>(s, dim, lv[l], tv[l], b, B[l].TM, B[l].TK, B[l].r, B[l - 1].b, B[l].tmp1,
+                              B[l].tmp2, clear ? B[l - 1].x : nullptr, clear ? 3 * lv[l - 1].n() : 0);
+    const int reps = (l - 1 == 0) ? 1 : c->mu;
+    for (int i = 0; i < reps; ++i) mu_cycle<T>(c, s, w, top, l - 1, x_top, b_top, false);
+    T* e = (l - 1 == top) ? x_top : B[l - 1].x;
+    dev::prolong_add<T>(s, dim, tv[l], lv[l], e, x, B[l].TM, B[l].TK, B[l].tmp1, B[l].tmp2);
+    smooth(true);
+}
+
+bool default_cycle(const igamg_ctx* c) { return c->smoother == IGAMG_SMOOTH_GS && c->mu == 1; }
+
 // Algorithm 2 (mu = 1, nu1 = nu2 = 1) from level `top` down to the coarsest
 // and back.  x_top / b_top are the top level's iterate and right side; the
 // top level's TM/TK must match x_top unless top_zero (then x_top = 0 is set).
 template <typename T>
 void vcycle(const igamg_ctx* c, cudaStream_t s, Workspace& w, int top, T* x_top, const T* b_top,
             bool top_zero, bool learned_top = false, T* capture_mid = nullptr) {
+    if (!default_cycle(c)) {                        // W-cycle or Jacobi smoothing (callers reject the
+        mu_cycle<T>(c, s, w, top, top, x_top, b_top, top_zero);    // learned form and the probe there)
+        return;
+    }
     const auto& lv = Views<T>::lv(c);
     const auto& tv = Views<T>::tv(c);
     auto& B = Views<T>::buf(w);
@@ -867,6 +921,8 @@ igamg_status igamg_solve(igamg_ctx* c, const double* d_b, double* d_x, double to
     if (!d_b || !d_x) return fail(IGAMG_EINVAL, "null vector");
     if (extrap < 0 || extrap > 2 || prec < 0 || prec > 2) return fail(IGAMG_EINVAL, "bad extrap/prec");
     if (prec == IGAMG_FP32_IR_LEARNED && !c->cnn_w) return fail(IGAMG_EINVAL, "no learned smoother set");
+    if (prec == IGAMG_FP32_IR_LEARNED && !default_cycle(c))
+        return fail(IGAMG_EINVAL, "the learned post-smoother replaces Gauss-Seidel in the V-cycle (igamg_set_cycle)");
     c->fell_back = 0;
     if (extrap != IGAMG_EXTRAP_NONE && (k < 1 || k > kMaxQ)) return fail(IGAMG_EINVAL, "k must be in [1, 12]");
     if (max_cycles < 0 || !(tol >= 0.0)) return fail(IGAMG_EINVAL, "bad max_cycles/tol");
@@ -1024,6 +1080,8 @@ igamg_status igamg_vcycle(igamg_ctx* c, double* d_x, const double* d_b, int prec
     if (igamg_status st = check_ctx(c)) return st;
     if (!d_x || !d_b || prec < 0 || prec > 2) return fail(IGAMG_EINVAL, "bad vcycle arguments");
     if (prec == IGAMG_FP32_IR_LEARNED && !c->cnn_w) return fail(IGAMG_EINVAL, "no learned smoother set");
+    if (prec == IGAMG_FP32_IR_LEARNED && !default_cycle(c))
+        return fail(IGAMG_EINVAL, "the learned post-smoother replaces Gauss-Seidel in the V-cycle (igamg_set_cycle)");
     if (igamg_status st = check_ws(c, d_ws, ws_bytes, 1, prec)) return st;
     Workspace w = carve(c, d_ws, 1, prec);
     cudaStream_t s = (cudaStream_t)stream;
@@ -1109,6 +1167,25 @@ igamg_status igamg_set_schedule(igamg_ctx* c, int gs_threads, int tail_levels) {
     return IGAMG_OK;
 }
 
+igamg_status igamg_set_cycle(igamg_ctx* c, int smoother, int mu, double omega) {
+    if (igamg_status st = check_ctx(c)) return st;
+    if ((smoother != IGAMG_SMOOTH_GS && smoother != IGAMG_SMOOTH_JACOBI) || (mu != 1 && mu != 2))
+        return fail(IGAMG_EINVAL, "smoother must be IGAMG_SMOOTH_GS or IGAMG_SMOOTH_JACOBI, mu 1 or 2");
+    if (smoother == IGAMG_SMOOTH_JACOBI && !(omega > 0.0 && omega < 2.0))
+        return fail(IGAMG_EINVAL, "Jacobi weight must lie in (0, 2)");
+    c->smoother = smoother;
+    c->mu = mu;
+    if (smoother == IGAMG_SMOOTH_JACOBI) c->omega = omega;
+    drop_graphs(c);
+    return IGAMG_OK;
+}
+
+void igamg_get_cycle(const igamg_ctx* c, int* smoother, int* mu, double* omega) {
+    if (smoother) *smoother = c ? c->smoother : 0;
+    if (mu) *mu = c ? c->mu : 1;
+    if (omega) *omega = c ? c->omega : 2.0 / 3.0;
+}
+
 void igamg_set_launch_overlap(int enable) { set_launch_overlap(enable != 0); }
 int igamg_get_launch_overlap(void) { return launch_overlap() ? 1 : 0; }
 
@@ -1170,6 +1247,7 @@ igamg_status igamg_set_coarse_tail(igamg_ctx* c, int enable) {
 
 igamg_status igamg_vcycle_probe(igamg_ctx* c, double* d_x, const double* d_b, double* d_x_mid, void* d_ws,
                                 size_t ws_bytes, void* stream) {
+    if (c && !default_cycle(c)) return fail(IGAMG_EINVAL, "the probe follows the Gauss-Seidel V-cycle");
     if (igamg_status st = check_ctx(c)) return st;
     if (!d_x || !d_b || !d_x_mid) return fail(IGAMG_EINVAL, "bad probe arguments");
     if (igamg_status st = check_ws(c, d_ws, ws_bytes, 1, IGAMG_FP64)) return st;

@@ -150,7 +150,8 @@ __device__ __forceinline__ void pdl_enter() {
 }
 
 // kern<<<grid, block, smem, s>>>(args...), with programmatic stream
-// serialisation when overlap is on.  kern must begin with pdl_enter().
+// serialisation when overlap is on.  kern must call pdl_enter() as described
+// above.
 template <typename... KArgs, typename... Args>
 inline void launch_chained(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                            Args... args) {
@@ -196,6 +197,11 @@ void xpass(cudaStream_t s, const LevelView<T>& L, const T* x, T* x_out, const A*
 template <typename T>
 void gs_sweep(cudaStream_t s, int dim, const LevelView<T>& L, bool descending, T* x,
               const T* b, T* TM, T* TK, int cap = 0);
+
+// One weighted-Jacobi sweep x += omega D^{-1} (b - A x) (the paper's smoother,
+// Sec. 4), then the row partial sums of the new x.
+template <typename T>
+void jacobi_sweep(cudaStream_t s, int dim, const LevelView<T>& L, T omega, T* x, const T* b, T* TM, T* TK);
 
 // r = b - A x from the row partial sums; optional per-row partial ||r||^2.
 template <typename T, typename R>

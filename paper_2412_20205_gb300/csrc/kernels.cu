@@ -465,6 +465,30 @@ __global__ void __launch_bounds__(kThreads) k_residual(LevelView<T> L, const T* 
     }
 }
 
+// Weighted Jacobi (Sec. 4: the paper's smoother, omega = 2/3):
+// x += omega D^{-1} (b - A x), every node from the same x.  A x comes from
+// the row partial sums, which this kernel only reads, so each CTA may
+// overwrite its own row of x; the caller refreshes T_M, T_K afterwards.
+template <typename T, int DIM, int P>
+__global__ void __launch_bounds__(kThreads) k_jacobi(LevelView<T> L, T omega, const T* __restrict__ b,
+                                                      const T* __restrict__ TM, const T* __restrict__ TK,
+                                                      T* __restrict__ x) {
+    constexpr int W = 2 * P + 1;
+    constexpr int NNB = (DIM == 3) ? W * W : W;
+    const int mx = L.m[0], my = L.m[1];
+    const int row = blockIdx.x, j = row % my, k = row / my;
+    const size_t base = (size_t)row * mx;
+    __shared__ T cM[NNB], cK[NNB];
+    __shared__ int nrow[NNB];
+    row_couplings<T, DIM, P>(L, j, k, cM, cK, nrow);     // operator data only
+    pdl_enter();
+    __syncthreads();
+    for (int i = threadIdx.x; i < mx; i += blockDim.x) {
+        const T v = b[base + i] - couple<T, NNB, -1>(cM, cK, nrow, TM, TK, mx, i);
+        x[base + i] += omega * L.invdiag[base + i] * v;
+    }
+}
+
 // 2D: r = b - A x of one row (from T_M, T_K) followed by the x-axis pass of
 // the restriction on that row, t[j][I] = sum_s rv[I rw + s] r[j][rlo[I] + s];
 // r itself never goes to memory.
@@ -1158,6 +1182,17 @@ void residual(cudaStream_t s, int dim, const LevelView<T>& L, const T* b, const 
 }
 
 template <typename T>
+void jacobi_sweep(cudaStream_t s, int dim, const LevelView<T>& L, T omega, T* x, const T* b, T* TM, T* TK) {
+    with_p(L.p, [&](auto PC) {
+        constexpr int P = decltype(PC)::value;
+        if (dim == 2) launch_chained(k_jacobi<T, 2, P>, L.rows(), kThreads, 0, s, L, omega, b, TM, TK, x);
+        else launch_chained(k_jacobi<T, 3, P>, L.rows(), kThreads, 0, s, L, omega, b, TM, TK, x);
+    });
+    count_launch();
+    xpass<T, T>(s, L, x, x, nullptr, 0, nullptr, nullptr, 0, TM, TK);
+}
+
+template <typename T>
 void restrict_(cudaStream_t s, int dim, const TransferView<T>& X, const T* fine, T* coarse, T* tmp1,
                T* tmp2, T* zero, size_t nzero) {
     // axis by axis: x, then y (then z); dims shrink one axis at a time
@@ -1324,6 +1359,7 @@ void fill_zero(cudaStream_t s, T* p, size_t n) {
     template void xpass<T, T>(cudaStream_t, const LevelView<T>&, const T*, T*, const T*, int,       \
                               const double*, const T*, size_t, T*, T*);                             \
     template void gs_sweep<T>(cudaStream_t, int, const LevelView<T>&, bool, T*, const T*, T*, T*, int);  \
+    template void jacobi_sweep<T>(cudaStream_t, int, const LevelView<T>&, T, T*, const T*, T*, T*);  \
     template void restrict_<T>(cudaStream_t, int, const TransferView<T>&, const T*, T*, T*, T*, T*, size_t);  \
     template void residual_restrict<T>(cudaStream_t, int, const LevelView<T>&, const TransferView<T>&,    \
                                        const T*, const T*, const T*, T*, T*, T*, T*, T*, size_t);         \

@@ -1,0 +1,123 @@
+"""Cycle options of Algorithm 2 on the GPU, through the C ABI, against the oracle.
+
+The options are weighted Jacobi with omega = 2/3 (the smoother of the paper's experiments,
+Sec. 4) and the W-cycle (mu = 2, Sec. 2.4). The tolerances are the ones used for the default
+Gauss-Seidel V-cycle:
+- one FP64 cycle agrees with the oracle's cycle to 1e-12 relative;
+- one FP32 refinement step agrees to FP32 accuracy (2e-5 on the correction);
+- whole restarted solves stop within one cycle of the oracle's count;
+- at equal cycle counts the solutions agree to 1e-9.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from oracle import multigrid as omg  # noqa: E402
+from oracle import solver as osolver  # noqa: E402
+from oracle.galerkin import load_vector  # noqa: E402
+import workloads  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import __graft_entry__ as g
+    g.build_library()
+    import paper_2412_20205_gb300 as p
+    assert torch.cuda.is_available()
+    return p
+
+
+DEV = "cuda"
+
+
+def _t(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
+
+
+def _np(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+CYCLES = [("jacobi", 1), ("jacobi", 2), ("gs", 2), ("gs", 1)]
+
+
+@pytest.mark.parametrize("dim,n,p", [(2, 37, 3), (2, (21, 13), 2), (3, 10, 2), (2, 19, 5), (2, 20, 1)])
+def test_one_cycle_matches_oracle(pkg, dim, n, p):
+    ns = list(n) if hasattr(n, "__len__") else [n] * dim
+    ctx = pkg.igamg_setup(dim, p, ns, 0)
+    pkg.igamg_assemble(ctx)
+    H = omg.Hierarchy(dim, ns, p)
+    nb = max(pkg.igamg_workspace_bytes(ctx, 5, pkg.IGAMG_FP32_IR),
+             pkg.igamg_workspace_bytes(ctx, 5, pkg.IGAMG_FP64))
+    ws = torch.empty(nb, dtype=torch.uint8, device=DEV)
+    rng = np.random.default_rng(21)
+    b = load_vector(H.finest.breaks, p, rng.standard_normal((3,) * dim))
+    x0 = rng.standard_normal(H.finest.N) * 1e-3
+    for smoother, mu in CYCLES:
+        pkg.igamg_set_cycle(ctx, smoother, mu)
+        got = pkg.igamg_get_cycle(ctx)
+        assert got["smoother"] == smoother and got["mu"] == mu and abs(got["omega"] - 2.0 / 3.0) < 1e-15
+        ref = omg.cycle(H, x0, b, mu=mu, smoother=smoother)
+        x = _t(x0)
+        pkg.igamg_vcycle(ctx, x, _t(b), pkg.IGAMG_FP64, ws)
+        assert _rel(_np(x), ref) < 1e-12, (smoother, mu)
+        x = _t(x0)
+        pkg.igamg_vcycle(ctx, x, _t(b), pkg.IGAMG_FP32_IR, ws)
+        assert _rel(_np(x) - x0, ref - x0) < 2e-5, (smoother, mu)
+    pkg.igamg_destroy(ctx)
+
+
+SOLVES = [(2, 32, 2, "rre", 5, "jacobi", 1), (2, 24, 3, "mpe", 5, "jacobi", 2),
+          (2, 32, 3, "rre", 5, "gs", 2), (3, 10, 2, "rre", 5, "jacobi", 1),
+          (2, 32, 2, "none", 5, "jacobi", 1), (2, 24, 2, "none", 5, "gs", 2)]
+
+
+@pytest.mark.parametrize("dim,n,p,method,k,smoother,mu", SOLVES)
+def test_solve_matches_oracle(pkg, dim, n, p, method, k, smoother, mu):
+    coeffs = workloads.random_sine_coeffs(dim, seed=13, modes=6)
+    prob = osolver.Problem(dim, n, p, coeffs)
+    ref = osolver.solve(prob, method, k=k, tol=1e-10, max_cycles=150, mu=mu, smoother=smoother,
+                        keep_iterates=True)
+    s = pkg.Solver(dim, p, n, k=k)
+    pkg.igamg_set_cycle(s.ctx, smoother, mu)
+    b = s.rhs_sine(coeffs)
+    out = s.solve(b, tol=1e-10, method=method, k=k, prec="fp64", max_cycles=150)
+    assert out["converged"] and ref["converged"]
+    assert abs(out["cycles"] - ref["cycles"]) <= 1, (out["cycles"], ref["cycles"])
+    c = min(out["cycles"], ref["cycles"])
+    out_c = s.solve(b, tol=0.0, method=method, k=k, prec="fp64", max_cycles=c)
+    assert out_c["cycles"] == c
+    assert _rel(_np(out_c["x"]), ref["iterates"][c - 1]) < 1e-9
+    # the mixed form with the same cycle reaches the same tolerance
+    out32 = s.solve(b, tol=1e-10, method=method, k=k, prec="fp32_ir", max_cycles=150)
+    assert out32["converged"]
+    assert _rel(_np(out32["x"]), ref["x"]) < 1e-7
+    s.close()
+
+
+def test_cycle_options_validated(pkg):
+    s = pkg.Solver(2, 3, 32, k=5)
+    with pytest.raises(RuntimeError):
+        pkg.igamg_set_cycle(s.ctx, "gs", 3)
+    with pytest.raises(RuntimeError):
+        pkg.igamg_set_cycle(s.ctx, "jacobi", 1, omega=2.5)
+    s.set_smoother(torch.zeros(2592, dtype=torch.float32, device=DEV))
+    b = s.rhs_sine(workloads.random_sine_coeffs(2, seed=2, modes=4))
+    pkg.igamg_set_cycle(s.ctx, "jacobi", 1, omega=0.5)
+    assert abs(pkg.igamg_get_cycle(s.ctx)["omega"] - 0.5) < 1e-15
+    pkg.igamg_set_cycle(s.ctx, "jacobi", 1)     # omega = 2/3
+    with pytest.raises(RuntimeError):          # the learned form replaces GS in the V-cycle only
+        s.solve(b, tol=1e-10, prec="fp32_ir_learned")
+    out = s.solve(b, tol=1e-10, prec="fp64")   # a plain solve with the Jacobi cycle still works
+    assert out["converged"]
+    pkg.igamg_set_cycle(s.ctx, "gs", 1)         # back to the default: the learned form runs again
+    assert s.solve(b, tol=1e-10, prec="fp32_ir_learned")["converged"]
+    s.close()
