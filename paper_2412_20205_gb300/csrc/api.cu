@@ -308,21 +308,28 @@ void mu_cycle(const igamg_ctx* c, cudaStream_t s, Workspace& w, int top, int l, 
             dev::fill_zero<T>(s, B[l].TM, 2 * N);
         }
     }
-    auto smooth = [&](bool post) {
-        if (c->smoother == IGAMG_SMOOTH_JACOBI)
-            dev::jacobi_sweep<T>(s, dim, lv[l], (T)c->omega, x, b, B[l].TM, B[l].TK);
-        else
-            dev::gs_sweep<T>(s, dim, lv[l], post, x, b, B[l].TM, B[l].TK, gs_cap<T>(c));
-    };
-    smooth(false);
+    // 2D Jacobi sweeps write the new row sums to a second buffer (the level's
+    // r and tmp2, which the 2D residual-restriction and prolongation kernels
+    // leave untouched): between the two sweeps the sums live there, and the
+    // post-smoothing sweep writes them back to T_M, T_K.
+    const bool alt = c->smoother == IGAMG_SMOOTH_JACOBI && dim == 2;
+    T* tm = alt ? B[l].r : B[l].TM;
+    T* tk = alt ? B[l].tmp2 : B[l].TK;
+    if (c->smoother == IGAMG_SMOOTH_JACOBI)
+        dev::jacobi_sweep<T>(s, dim, lv[l], (T)c->omega, x, b, B[l].TM, B[l].TK, tm, tk);
+    else
+        dev::gs_sweep<T>(s, dim, lv[l], false, x, b, B[l].TM, B[l].TK, gs_cap<T>(c));
     const bool clear = l - 1 >= 1;                  // coarse e^0 = 0: x | T_M | T_K of level l - 1
-    dev::residual_restrict<T>(s, dim, lv[l], tv[l], b, B[l].TM, B[l].TK, B[l].r, B[l - 1].b, B[l].tmp1,
-                              B[l].tmp2, clear ? B[l - 1].x : nullptr, clear ? 3 * lv[l - 1].n() : 0);
+    dev::residual_restrict<T>(s, dim, lv[l], tv[l], b, tm, tk, B[l].r, B[l - 1].b, B[l].tmp1, B[l].tmp2,
+                              clear ? B[l - 1].x : nullptr, clear ? 3 * lv[l - 1].n() : 0);
     const int reps = (l - 1 == 0) ? 1 : c->mu;
     for (int i = 0; i < reps; ++i) mu_cycle<T>(c, s, w, top, l - 1, x_top, b_top, false);
     T* e = (l - 1 == top) ? x_top : B[l - 1].x;
-    dev::prolong_add<T>(s, dim, tv[l], lv[l], e, x, B[l].TM, B[l].TK, B[l].tmp1, B[l].tmp2);
-    smooth(true);
+    dev::prolong_add<T>(s, dim, tv[l], lv[l], e, x, tm, tk, B[l].tmp1, B[l].tmp2);
+    if (c->smoother == IGAMG_SMOOTH_JACOBI)
+        dev::jacobi_sweep<T>(s, dim, lv[l], (T)c->omega, x, b, tm, tk, B[l].TM, B[l].TK);
+    else
+        dev::gs_sweep<T>(s, dim, lv[l], true, x, b, B[l].TM, B[l].TK, gs_cap<T>(c));
 }
 
 bool default_cycle(const igamg_ctx* c) { return c->smoother == IGAMG_SMOOTH_GS && c->mu == 1; }

@@ -199,9 +199,12 @@ void gs_sweep(cudaStream_t s, int dim, const LevelView<T>& L, bool descending, T
               const T* b, T* TM, T* TK, int cap = 0);
 
 // One weighted-Jacobi sweep x += omega D^{-1} (b - A x) (the paper's smoother,
-// Sec. 4), then the row partial sums of the new x.
+// Sec. 4) from the row partial sums TM, TK of x, then the sums of the new x:
+// in 2D written to TMo, TKo (one kernel; must not alias TM, TK), in 3D back
+// to TM, TK (a second kernel; TMo, TKo unused).
 template <typename T>
-void jacobi_sweep(cudaStream_t s, int dim, const LevelView<T>& L, T omega, T* x, const T* b, T* TM, T* TK);
+void jacobi_sweep(cudaStream_t s, int dim, const LevelView<T>& L, T omega, T* x, const T* b, T* TM, T* TK,
+                  T* TMo, T* TKo);
 
 // r = b - A x from the row partial sums; optional per-row partial ||r||^2.
 template <typename T, typename R>

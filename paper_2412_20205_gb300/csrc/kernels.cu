@@ -489,6 +489,50 @@ __global__ void __launch_bounds__(kThreads) k_jacobi(LevelView<T> L, T omega, co
     }
 }
 
+// 2D weighted Jacobi with the row partial sums of the new x in one kernel:
+// a CTA updates its row (b - A x from the old sums T_M, T_K of the 2p+1
+// coupled rows), keeps it in shared memory with a zero halo of p, and writes
+// that row's new sums to TMo, TKo.  The old and new sums live in different
+// buffers, so no CTA reads a row sum another CTA writes.
+template <typename T, int P>
+__global__ void __launch_bounds__(kThreads) k_jacobi2(LevelView<T> L, T omega, const T* __restrict__ b,
+                                                       const T* __restrict__ TM, const T* __restrict__ TK,
+                                                       T* __restrict__ x, T* __restrict__ TMo,
+                                                       T* __restrict__ TKo) {
+    constexpr int W = 2 * P + 1;
+    const int mx = L.m[0], j = blockIdx.x;
+    const size_t base = (size_t)j * mx;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* xs = reinterpret_cast<T*>(smem_raw);
+    __shared__ T cM[W], cK[W];
+    __shared__ int nrow[W];
+    row_couplings<T, 2, P>(L, j, 0, cM, cK, nrow);       // operator data only
+    pdl_enter();
+    __syncthreads();
+    for (int ii = threadIdx.x; ii < mx + 2 * P; ii += blockDim.x) {
+        const int i = ii - P;
+        T v = 0;
+        if (i >= 0 && i < mx) {
+            const T rv = b[base + i] - couple<T, W, -1>(cM, cK, nrow, TM, TK, mx, i);
+            v = x[base + i] + omega * L.invdiag[base + i] * rv;
+            x[base + i] = v;
+        }
+        xs[ii] = v;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < mx; i += blockDim.x) {
+        T am = 0, ak = 0;
+#pragma unroll
+        for (int bb = 0; bb <= 2 * P; ++bb) {
+            const T xv = xs[i + bb];
+            am += band_m(L, i, bb) * xv;
+            ak += band_k(L, i, bb) * xv;
+        }
+        TMo[base + i] = am;
+        TKo[base + i] = ak;
+    }
+}
+
 // 2D: r = b - A x of one row (from T_M, T_K) followed by the x-axis pass of
 // the restriction on that row, t[j][I] = sum_s rv[I rw + s] r[j][rlo[I] + s];
 // r itself never goes to memory.
@@ -1112,6 +1156,7 @@ void prepare_kernels() {
                 raise_smem(k_prolong_last<T, 3, P>, optin);
                 raise_smem(k_residual_restrict_x<T, P>, optin);
                 raise_smem(k_prolong_fused2<T, P>, optin);
+                raise_smem(k_jacobi2<T, P>, optin);
             });
         raise_smem(k_coarse_fd<T, 2>, optin);
         raise_smem(k_coarse_fd<T, 3>, optin);
@@ -1182,11 +1227,21 @@ void residual(cudaStream_t s, int dim, const LevelView<T>& L, const T* b, const 
 }
 
 template <typename T>
-void jacobi_sweep(cudaStream_t s, int dim, const LevelView<T>& L, T omega, T* x, const T* b, T* TM, T* TK) {
+void jacobi_sweep(cudaStream_t s, int dim, const LevelView<T>& L, T omega, T* x, const T* b, T* TM, T* TK,
+                  T* TMo, T* TKo) {
+    if (dim == 2) {
+        const size_t smem = (size_t)(L.m[0] + 2 * L.p) * sizeof(T);
+        with_p(L.p, [&](auto PC) {
+            constexpr int P = decltype(PC)::value;
+            set_smem(k_jacobi2<T, P>, smem);
+            launch_chained(k_jacobi2<T, P>, L.m[1], kThreads, smem, s, L, omega, b, TM, TK, x, TMo, TKo);
+        });
+        count_launch();
+        return;
+    }
     with_p(L.p, [&](auto PC) {
         constexpr int P = decltype(PC)::value;
-        if (dim == 2) launch_chained(k_jacobi<T, 2, P>, L.rows(), kThreads, 0, s, L, omega, b, TM, TK, x);
-        else launch_chained(k_jacobi<T, 3, P>, L.rows(), kThreads, 0, s, L, omega, b, TM, TK, x);
+        launch_chained(k_jacobi<T, 3, P>, L.rows(), kThreads, 0, s, L, omega, b, TM, TK, x);
     });
     count_launch();
     xpass<T, T>(s, L, x, x, nullptr, 0, nullptr, nullptr, 0, TM, TK);
@@ -1359,7 +1414,7 @@ void fill_zero(cudaStream_t s, T* p, size_t n) {
     template void xpass<T, T>(cudaStream_t, const LevelView<T>&, const T*, T*, const T*, int,       \
                               const double*, const T*, size_t, T*, T*);                             \
     template void gs_sweep<T>(cudaStream_t, int, const LevelView<T>&, bool, T*, const T*, T*, T*, int);  \
-    template void jacobi_sweep<T>(cudaStream_t, int, const LevelView<T>&, T, T*, const T*, T*, T*);  \
+    template void jacobi_sweep<T>(cudaStream_t, int, const LevelView<T>&, T, T*, const T*, T*, T*, T*, T*);  \
     template void restrict_<T>(cudaStream_t, int, const TransferView<T>&, const T*, T*, T*, T*, T*, size_t);  \
     template void residual_restrict<T>(cudaStream_t, int, const LevelView<T>&, const TransferView<T>&,    \
                                        const T*, const T*, const T*, T*, T*, T*, T*, T*, size_t);         \
