@@ -300,6 +300,15 @@ void mu_cycle(const igamg_ctx* c, cudaStream_t s, Workspace& w, int top, int l, 
         dev::coarse_solve<T>(s, dim, Views<T>::cv(c), b, x);                           // direct
         return;
     }
+    if constexpr (std::is_same<T, float>::value) {
+        // FP32 2D V-cycles (Jacobi smoothing here) hand levels lc..0 to one
+        // CTA, as the Gauss-Seidel V-cycle does; W-cycles revisit coarse
+        // levels from nonzero iterates, which the tail does not take
+        if (c->mu == 1 && c->tail_on && c->tail32.lc > 0 && l == c->tail32.lc && l < top) {
+            dev::coarse_tail<float>(s, c->tail32, b, x, c->smoother == IGAMG_SMOOTH_JACOBI, (float)c->omega);
+            return;
+        }
+    }
     const size_t N = lv[l].n();
     if (zero) {
         if (x == B[l].x) dev::fill_zero<T>(s, B[l].x, 3 * N);

@@ -182,8 +182,10 @@ size_t tail_smem_limit();
 // Levels lc..0 of one 2D V-cycle (pre-smoothing, residual, restriction,
 // coarsest solve, prolongation, post-smoothing) in one CTA, starting from
 // x = 0 on every level: reads level lc's right side b, writes its x.
+// Smoothing is multicolour Gauss-Seidel, or weighted Jacobi with weight omega
+// when jacobi != 0.
 template <typename T>
-void coarse_tail(cudaStream_t s, const TailView<T>& V, const T* b, T* x);
+void coarse_tail(cudaStream_t s, const TailView<T>& V, const T* b, T* x, int jacobi = 0, T omega = 0);
 
 // T_M = (I (x) M_x) x, T_K = (I (x) K_x) x row by row.  With add != nullptr the
 // row is first replaced by x + add (written to x_out), with nS > 0 by

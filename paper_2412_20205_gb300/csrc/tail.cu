@@ -202,6 +202,25 @@ __device__ void tail_gs(const TailLevel<T>& S, T* xp, const T* b, bool descendin
     }
 }
 
+// One weighted-Jacobi sweep x += omega D^{-1} (b - A x) (Sec. 4) with every
+// node from the same x (A x from T_M, T_K), using the scratch vector d; then
+// T_M, T_K of the new x.
+template <typename T, int P>
+__device__ void tail_jacobi(const TailLevel<T>& S, T* xp, const T* b, T omega, T* d) {
+    const int mx = S.mx, my = S.my;
+    for (int q = threadIdx.x; q < mx * my; q += blockDim.x) {
+        const int j = q / mx, i = q - j * mx;
+        d[q] = omega * (b[q] - tail_couple<T, P>(S, i, j, -1)) * S.inv[q];
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < mx * my; q += blockDim.x) {
+        const int j = q / mx, i = q - j * mx;
+        xp[padded<P>(i, j, mx)] += d[q];
+    }
+    __syncthreads();
+    tail_xpass<T, P>(S, xp);
+}
+
 // bc = P^T (b - A x): the residual, then the x and y axes of the restriction.
 template <typename T, int P>
 __device__ void tail_restrict(const TailLevel<T>& S, const TransferView<T>& X, const T* b, T* r, T* t, T* bc) {
@@ -310,7 +329,7 @@ __device__ __forceinline__ TransferView<T> staged_transfer(const TailView<T>& V,
 
 template <typename T, int P>
 __global__ void __launch_bounds__(kTailThreads, 1) k_coarse_tail(TailView<T> V, const T* __restrict__ b_in,
-                                                                 T* __restrict__ x_out) {
+                                                                 T* __restrict__ x_out, int jacobi, T omega) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
     const int lc = V.lc;
@@ -377,7 +396,8 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_coarse_tail(TailView<T> V, 
         T* x = sm + V.off_x[l];
         const T* b = sm + V.off_b[l];
         const TailLevel<T> S = level(l);
-        tail_gs<T, P>(S, x, b, false);                                           // pre-smooth
+        if (jacobi) tail_jacobi<T, P>(S, x, b, omega, r);                       // pre-smooth
+        else tail_gs<T, P>(S, x, b, false);
         tail_restrict<T, P>(S, staged_transfer(V, l, sm), b, r, t, sm + V.off_b[l - 1]);   // R (b - A x)
     }
     tail_coarse<T, P>(Cs, sm + V.off_b[0], r, t, sm + V.off_x[0]);              // direct
@@ -386,7 +406,8 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_coarse_tail(TailView<T> V, 
         const TailLevel<T> S = level(l);
         tail_prolong<T, P>(staged_transfer(V, l, sm), sm + V.off_x[l - 1], t, x);              // x += P e
         tail_xpass<T, P>(S, x);
-        tail_gs<T, P>(S, x, sm + V.off_b[l], true);                              // post-smooth
+        if (jacobi) tail_jacobi<T, P>(S, x, sm + V.off_b[l], omega, r);        // post-smooth
+        else tail_gs<T, P>(S, x, sm + V.off_b[l], true);
     }
     const int mx = V.L[lc].m[0], N = mx * V.L[lc].m[1];
     const T* x = sm + V.off_x[lc];
@@ -429,15 +450,15 @@ size_t tail_smem_limit() {
 }
 
 template <typename T>
-void coarse_tail(cudaStream_t s, const TailView<T>& V, const T* b, T* x) {
+void coarse_tail(cudaStream_t s, const TailView<T>& V, const T* b, T* x, int jacobi, T omega) {
     tail_with_p(V.L[V.lc].p, [&](auto PC) {
         constexpr int P = decltype(PC)::value;
-        launch_chained(k_coarse_tail<T, P>, 1, kTailThreads, V.smem, s, V, b, x);
+        launch_chained(k_coarse_tail<T, P>, 1, kTailThreads, V.smem, s, V, b, x, jacobi, omega);
     });
     count_launch();
 }
 
-template void coarse_tail<float>(cudaStream_t, const TailView<float>&, const float*, float*);
+template void coarse_tail<float>(cudaStream_t, const TailView<float>&, const float*, float*, int, float);
 
 }  // namespace dev
 }  // namespace igamg

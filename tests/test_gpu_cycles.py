@@ -121,3 +121,35 @@ def test_cycle_options_validated(pkg):
     pkg.igamg_set_cycle(s.ctx, "gs", 1)         # back to the default: the learned form runs again
     assert s.solve(b, tol=1e-10, prec="fp32_ir_learned")["converged"]
     s.close()
+
+
+@pytest.mark.parametrize("n,p", [(130, 3), (64, 2), (100, 5)])
+def test_jacobi_coarse_tail_matches_per_level_cycle(pkg, n, p):
+    """FP32 Jacobi V-cycles run the coarse levels in the one-CTA tail, as the
+    Gauss-Seidel V-cycle does.  One refinement step with the tail agrees with
+    the per-level schedule to FP32 round-off and with the oracle's Jacobi
+    V-cycle to FP32 accuracy."""
+    s = pkg.Solver(2, p, n, k=5)
+    assert pkg.igamg_coarse_tail_level(s.ctx) > 0
+    pkg.igamg_set_cycle(s.ctx, "jacobi", 1)
+    H = omg.Hierarchy(2, [n, n], p)
+    rng = np.random.default_rng(31)
+    b = load_vector(H.finest.breaks, p, rng.standard_normal((4, 4)))
+    x0 = rng.standard_normal(H.finest.N) * 1e-3
+    ref = omg.cycle(H, x0, b, smoother="jacobi") - x0
+    outs = []
+    for tail in (1, 0):
+        pkg.igamg_set_coarse_tail(s.ctx, tail)
+        x = _t(x0)
+        pkg.igamg_vcycle(s.ctx, x, _t(b), pkg.IGAMG_FP32_IR, s.ws)
+        outs.append(_np(x) - x0)
+    assert _rel(outs[0], outs[1]) < 1e-5
+    for o in outs:
+        assert _rel(o, ref) < 2e-5
+    pkg.igamg_set_coarse_tail(s.ctx, 1)
+    bb = s.rhs_sine(workloads.random_sine_coeffs(2, seed=4))
+    out = s.solve(bb, tol=1e-10, method="rre", k=5, prec="fp32_ir")
+    ref64 = s.solve(bb, tol=1e-12, method="rre", k=5, prec="fp64")
+    assert out["converged"] and ref64["converged"]
+    assert float((out["x"] - ref64["x"]).norm() / ref64["x"].norm()) < 1e-7
+    s.close()
