@@ -248,7 +248,9 @@ def run_ours(a, rank, world, local):
     # the paper's own smoother (Sec. 4): weighted Jacobi, omega = 2/3, same V(1,1)-cycle
     pkg.igamg_set_cycle(s.ctx, "jacobi", 1, 2.0 / 3.0)
     for _ in range(a.warmup):
+        torch.cuda.nvtx.range_push("jacobi_warmup_solve")   # marks the solves for profiler filters
         solve(a.prec)
+        torch.cuda.nvtx.range_pop()
         solve("fp64")
     tj, outj = timed(a.prec, a.steps)
     tj64, outj64 = timed("fp64", a.steps)

@@ -153,3 +153,25 @@ def test_jacobi_coarse_tail_matches_per_level_cycle(pkg, n, p):
     assert out["converged"] and ref64["converged"]
     assert float((out["x"] - ref64["x"]).norm() / ref64["x"].norm()) < 1e-7
     s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32_ir", "fp64"])
+def test_full_size_jacobi_solution_passes_oracle_residual_test(pkg, prec):
+    """1024 x 1024 elements, p = 3, the bench's launch configuration with the
+    paper's Jacobi V-cycle: the solution satisfies the oracle's own relative
+    residual test (oracle operator and load vector, FP64)."""
+    from oracle import galerkin as gk, bspline as bs
+    coeffs = workloads.random_sine_coeffs(2, seed=0, modes=16)
+    s = pkg.Solver(2, 3, 1024, k=5)
+    s.autotune(reps=2)
+    pkg.igamg_set_cycle(s.ctx, "jacobi", 1)
+    b = s.rhs_sine(coeffs)
+    out = s.solve(b, tol=1e-10, method="rre", k=5, prec=prec, max_cycles=60)
+    assert out["converged"]
+    x = _np(out["x"])
+    br = bs.uniform_breaks(1024)
+    f = gk.factors_1d(br, 3)
+    A = gk.operator([f, f])
+    bo = gk.load_vector([br, br], 3, coeffs)
+    assert np.linalg.norm(bo - A @ x) / np.linalg.norm(bo) <= 1.05e-10
+    s.close()

@@ -107,3 +107,43 @@ def test_table11_counts_loose():
         m = solver.solve(prob, "mpe", k=int(q), **kw)["cycles"]
         assert v <= 2 * nv and r <= 2 * nr and m <= 2 * nm, (p, v, r, m)
         assert r * (q + 1) < v and m * (q + 1) < v
+
+
+def test_jacobi_sweep_closed_form_p1():
+    """p = 1 in 2D: A = K (x) M + M (x) K with K = tridiag(-1, 2, -1)/h and
+    M = h/6 tridiag(1, 4, 1) on interior nodes.  Every product of sine modes is
+    an eigenvector, eigenvalue kappa_j mu_k + mu_j kappa_k with
+    kappa_j = (2/h)(1 - cos(j pi h)) and mu_j = (h/3)(2 + cos(j pi h)).  The
+    diagonal is 8/3, so one weighted-Jacobi sweep with b = 0 scales the mode
+    by 1 - omega (3/8) lambda."""
+    n = 12
+    h = 1.0 / n
+    lev = mg.Hierarchy(2, n, 1, n_levels=1).finest
+    m = n - 1
+    i = np.arange(1, n)
+    for (j, k) in [(1, 1), (3, 7), (11, 2), (6, 6)]:
+        v = np.outer(np.sin(k * np.pi * i * h), np.sin(j * np.pi * i * h)).ravel()  # x fastest: j on x
+        kap = lambda q: (2.0 / h) * (1 - np.cos(q * np.pi * h))
+        mu = lambda q: (h / 3.0) * (2 + np.cos(q * np.pi * h))
+        lam = kap(j) * mu(k) + mu(j) * kap(k)
+        for omega in (2.0 / 3.0, 0.5):
+            out = mg.jacobi_sweep(lev, v, np.zeros(m * m), omega)
+            assert np.allclose(out, (1 - omega * 3.0 / 8.0 * lam) * v, atol=1e-13)
+
+
+@pytest.mark.parametrize("smoother", ["gs", "jacobi"])
+def test_w_cycle_equals_v_cycle_on_two_levels(smoother):
+    """With two levels the coarse problem is solved exactly, so mu = 2 (a
+    second exact solve from the first one's result) gives the V-cycle; with
+    three levels it differs."""
+    H2 = mg.Hierarchy(2, 16, 2, n_levels=2)
+    b = _rhs(H2, 3)
+    x = np.random.default_rng(4).standard_normal(H2.finest.N)
+    v = mg.cycle(H2, x, b, mu=1, smoother=smoother)
+    w = mg.cycle(H2, x, b, mu=2, smoother=smoother)
+    assert np.allclose(v, w, atol=1e-13 * np.abs(v).max())
+    H3 = mg.Hierarchy(2, 16, 2, n_levels=3)
+    b3 = _rhs(H3, 3)
+    x3 = np.random.default_rng(4).standard_normal(H3.finest.N)
+    assert not np.allclose(mg.cycle(H3, x3, b3, mu=1, smoother=smoother),
+                           mg.cycle(H3, x3, b3, mu=2, smoother=smoother), atol=1e-10)
