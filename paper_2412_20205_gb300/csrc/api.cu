@@ -373,8 +373,7 @@ void vcycle(const igamg_ctx* c, cudaStream_t s, Workspace& w, int top, T* x_top,
                 dev::fill_zero<T>(s, B[l].TM, 2 * N);
             }
         }
-        // pre-smooth; every level below the top starts from the cleared e^0 = 0
-        dev::gs_sweep<T>(s, dim, lv[l], false, x, b, B[l].TM, B[l].TK, gs_cap<T>(c), l != top || top_zero);
+        dev::gs_sweep<T>(s, dim, lv[l], false, x, b, B[l].TM, B[l].TK, gs_cap<T>(c));  // pre-smooth
         // b_{l-1} = R (b - A u), R = P^T; the next per-level level's x | T_M | T_K
         // (coarse e^0 = 0) are cleared in the same pass
         const bool clear = l - 1 >= lowest;

@@ -195,12 +195,10 @@ void xpass(cudaStream_t s, const LevelView<T>& L, const T* x, T* x_out, const A*
            int nS, const double* gamma, const T* S, size_t ldS, T* TM, T* TK);
 
 // One multicolour Gauss-Seidel sweep (all (p+1)^dim colours) in row phases;
-// cap bounds the threads of a row CTA (0: the default).  zero_start: x and
-// its row sums are zero on entry (an ascending sweep from the coarse e^0 = 0),
-// so the first phase reads only b.
+// cap bounds the threads of a row CTA (0: the default).
 template <typename T>
 void gs_sweep(cudaStream_t s, int dim, const LevelView<T>& L, bool descending, T* x,
-              const T* b, T* TM, T* TK, int cap = 0, bool zero_start = false);
+              const T* b, T* TM, T* TK, int cap = 0);
 
 // One weighted-Jacobi sweep x += omega D^{-1} (b - A x) (the paper's smoother,
 // Sec. 4) from the row partial sums TM, TK of x, then the sums of the new x:

@@ -297,7 +297,7 @@ template <typename T, int DIM, int P>
 constexpr bool gs_window() { return sizeof(T) == 4 && (DIM == 3 || P != 3); }
 
 template <typename T, int DIM, int P, bool WINDOW>
-__device__ __forceinline__ void gs_phase_body(const LevelView<T>& L, int cy, int cz, int descending, int zero,
+__device__ __forceinline__ void gs_phase_body(const LevelView<T>& L, int cy, int cz, int descending,
                                                     T* __restrict__ x, const T* __restrict__ b,
                                                     T* __restrict__ TM, T* __restrict__ TK) {
     constexpr int P1 = P + 1, W = 2 * P + 1;
@@ -339,18 +339,10 @@ __device__ __forceinline__ void gs_phase_body(const LevelView<T>& L, int cy, int
     }
     __syncthreads();
     for (int i = threadIdx.x; i < mx; i += blockDim.x) {
-        // 2D only: the same branch in 3D rows cost 128^3, p = 3 28% (262 -> 336 ms)
-        if (DIM == 2 && zero) { // first phase of a sweep from x = 0: every row sum is still zero
-            rhs[i] = b[base + i];
-            tm[i] = 0;
-            tk[i] = 0;
-            xs[i] = 0;
-        } else {
-            rhs[i] = b[base + i] - couple<T, NNB, OWN>(cM, cK, nrow, TM, TK, mx, i);
-            tm[i] = TM[base + i];
-            tk[i] = TK[base + i];
-            xs[i] = x[base + i];
-        }
+        rhs[i] = b[base + i] - couple<T, NNB, OWN>(cM, cK, nrow, TM, TK, mx, i);
+        tm[i] = TM[base + i];
+        tk[i] = TK[base + i];
+        xs[i] = x[base + i];
         if constexpr (DIM == 3) dv[i] = L.invdiag[base + i];
         if constexpr (WINDOW) dl[i] = 0;
     }
@@ -429,15 +421,15 @@ __device__ __forceinline__ void gs_phase_body(const LevelView<T>& L, int cy, int
 // registers ran slower in FP64); 3D rows keep the compiler's default.
 template <typename T, int P, bool WINDOW>
 __global__ void __launch_bounds__(row_cta_max<T, 2>(), 2)
-    k_gs_phase2(LevelView<T> L, int cy, int cz, int descending, int zero, T* __restrict__ x,
-                const T* __restrict__ b, T* __restrict__ TM, T* __restrict__ TK) {
-    gs_phase_body<T, 2, P, WINDOW>(L, cy, cz, descending, zero, x, b, TM, TK);
+    k_gs_phase2(LevelView<T> L, int cy, int cz, int descending, T* __restrict__ x, const T* __restrict__ b,
+                T* __restrict__ TM, T* __restrict__ TK) {
+    gs_phase_body<T, 2, P, WINDOW>(L, cy, cz, descending, x, b, TM, TK);
 }
 template <typename T, int P, bool WINDOW>
 __global__ void __launch_bounds__(row_cta_max<T, 3>())
-    k_gs_phase3(LevelView<T> L, int cy, int cz, int descending, int zero, T* __restrict__ x,
-                const T* __restrict__ b, T* __restrict__ TM, T* __restrict__ TK) {
-    gs_phase_body<T, 3, P, WINDOW>(L, cy, cz, descending, zero, x, b, TM, TK);
+    k_gs_phase3(LevelView<T> L, int cy, int cz, int descending, T* __restrict__ x, const T* __restrict__ b,
+                T* __restrict__ TM, T* __restrict__ TK) {
+    gs_phase_body<T, 3, P, WINDOW>(L, cy, cz, descending, x, b, TM, TK);
 }
 
 // ---------------------------------------------------------------- residual
@@ -1203,12 +1195,12 @@ void xpass(cudaStream_t s, const LevelView<T>& L, const T* x, T* x_out, const A*
 
 template <typename T>
 void gs_sweep(cudaStream_t s, int dim, const LevelView<T>& L, bool descending, T* x, const T* b,
-              T* TM, T* TK, int cap, bool zero_start) {
+              T* TM, T* TK, int cap) {
     const int p = L.p, P1 = p + 1;
     const size_t smem = (size_t)6 * L.m[0] * sizeof(T);
     const int most = dim == 3 ? row_cta_max<T, 3>() : row_cta_max<T, 2>();
     const int threads = row_threads(L.m[0], (cap >= 64 && cap < most) ? cap : most);
-    auto launch = [&](int cy, int cz, int zero) {
+    auto launch = [&](int cy, int cz) {
         const int nty = (L.m[1] - cy + p) / P1;
         const int ntz = (dim == 3) ? (L.m[2] - cz + p) / P1 : 1;
         if (nty <= 0 || ntz <= 0) return;
@@ -1217,13 +1209,11 @@ void gs_sweep(cudaStream_t s, int dim, const LevelView<T>& L, bool descending, T
             if (dim == 2) {
                 constexpr bool WIN = gs_window<T, 2, P>();
                 set_smem(k_gs_phase2<T, P, WIN>, smem);
-                launch_chained(k_gs_phase2<T, P, WIN>, nty * ntz, threads, smem, s, L, cy, cz, descending, zero, x, b,
-                               TM, TK);
+                launch_chained(k_gs_phase2<T, P, WIN>, nty * ntz, threads, smem, s, L, cy, cz, descending, x, b, TM, TK);
             } else {
                 constexpr bool WIN = gs_window<T, 3, P>();
                 set_smem(k_gs_phase3<T, P, WIN>, smem);
-                launch_chained(k_gs_phase3<T, P, WIN>, nty * ntz, threads, smem, s, L, cy, cz, descending, zero, x, b,
-                               TM, TK);
+                launch_chained(k_gs_phase3<T, P, WIN>, nty * ntz, threads, smem, s, L, cy, cz, descending, x, b, TM, TK);
             }
         });
         count_launch();
@@ -1231,7 +1221,7 @@ void gs_sweep(cudaStream_t s, int dim, const LevelView<T>& L, bool descending, T
     const int ncz = (dim == 3) ? P1 : 1;
     for (int c = 0; c < P1 * ncz; ++c) {
         const int cc = descending ? P1 * ncz - 1 - c : c;
-        launch(cc % P1, cc / P1, zero_start && !descending && c == 0);   // phase (0, 0) first
+        launch(cc % P1, cc / P1);
     }
 }
 
@@ -1439,7 +1429,7 @@ void fill_zero(cudaStream_t s, T* p, size_t n) {
 #define IGAMG_INST(T)                                                                               \
     template void xpass<T, T>(cudaStream_t, const LevelView<T>&, const T*, T*, const T*, int,       \
                               const double*, const T*, size_t, T*, T*);                             \
-    template void gs_sweep<T>(cudaStream_t, int, const LevelView<T>&, bool, T*, const T*, T*, T*, int, bool);  \
+    template void gs_sweep<T>(cudaStream_t, int, const LevelView<T>&, bool, T*, const T*, T*, T*, int);  \
     template void jacobi_sweep<T>(cudaStream_t, int, const LevelView<T>&, T, T*, const T*, T*, T*, T*, T*);  \
     template void restrict_<T>(cudaStream_t, int, const TransferView<T>&, const T*, T*, T*, T*, T*, size_t);  \
     template void residual_restrict<T>(cudaStream_t, int, const LevelView<T>&, const TransferView<T>&,    \
