@@ -302,7 +302,7 @@ def test_edge_cases(pkg):
     one.close()
 
 
-@pytest.mark.parametrize("p", [2, 5])
+@pytest.mark.parametrize("p", [2, 3, 5])
 def test_full_size_2d_1024_residual_property(pkg, p):
     """1024 x 1024 elements: the FP32-refined RRE(5) solution satisfies the
     oracle's own residual test (oracle operator and load vector, FP64)."""
