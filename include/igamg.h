@@ -249,10 +249,12 @@ void igamg_get_schedule(const igamg_ctx* ctx, int* gs_threads, int* tail_levels)
  * Sec. 4 with omega = 2/3; omega in (0, 2), ignored for GS).  mu = 1 is the
  * V-cycle (default), mu = 2 the W-cycle (the coarse problem of every level
  * above the coarsest is approximated by two cycles from a zero start).
- * nu1 = nu2 = 1; the coarsest level is solved directly.  Anything but the
- * default Gauss-Seidel V-cycle runs per-level kernels (no coarse tail), and
- * IGAMG_FP32_IR_LEARNED solves and igamg_vcycle_probe then return
- * IGAMG_EINVAL.  Errors: IGAMG_EINVAL for other values. */
+ * nu1 = nu2 = 1; the coarsest level is solved directly.  FP32 2D V-cycles
+ * (either smoother) run their coarse levels in the one-CTA tail
+ * (igamg_set_coarse_tail); W-cycles run per-level kernels throughout.  With
+ * anything but the default Gauss-Seidel V-cycle, IGAMG_FP32_IR_LEARNED solves
+ * and igamg_vcycle_probe return IGAMG_EINVAL.  Errors: IGAMG_EINVAL for other
+ * values. */
 igamg_status igamg_set_cycle(igamg_ctx* ctx, int smoother, int mu, double omega);
 void igamg_get_cycle(const igamg_ctx* ctx, int* smoother, int* mu, double* omega);
 
