@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--prec", default="fp32_ir", choices=["fp32_ir", "fp64"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=256, help="problems in --workload batch256")
+    ap.add_argument("--no-extra-forms", action="store_true",
+                    help="skip the 3D 128^3 and 256-problem batch forms of the default line")
     return ap.parse_args()
 
 
@@ -111,56 +114,169 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# ---------------------------------------------------------------- CPU oracle sample
-def oracle_sample(a, rank_seed=0, restarts=1):
-    """Bounded sample of the oracle on the same workload: the restart-cycle count
-    to tolerance is taken from the oracle on the 128^dim version of the problem
-    (multigrid convergence is mesh independent), and one restart cycle (k+1
-    V-cycles, extrapolation, residual) is timed on the full-size problem.
-    Returns (dof_per_s, seconds_per_restart, cycles, setup_s)."""
-    import numpy as np
+# ---------------------------------------------------------------- CPU oracle
+def host_info():
+    """Host CPU model and core count (the oracle's baseline runs here)."""
+    import platform
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"cpu_model": model or platform.processor() or platform.machine(),
+            "host_cores": os.cpu_count(), "arch": platform.machine()}
+
+
+def _memory_limit_bytes():
+    """Smallest of MemAvailable and the cgroup memory limit."""
+    lim = []
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    lim.append(int(line.split()[1]) * 1024)
+    except OSError:
+        pass
+    for path in ("/sys/fs/cgroup/memory.max", "/sys/fs/cgroup/memory/memory.limit_in_bytes"):
+        try:
+            with open(path) as f:
+                v = f.read().strip()
+            if v.isdigit():
+                lim.append(int(v))
+        except OSError:
+            pass
+    return min(lim) if lim else 8 << 30
+
+
+def _oracle_worker(jobs, barrier, queue):
+    """One oracle process: build its problems (set-up, untimed), wait for the
+    others, then solve each completely to 1e-10 and report the wall times
+    (time.time(): one clock for every process on the host).  jobs: list of
+    (dim, n, p, method, k, seed)."""
     import workloads
-    from oracle import extrapolation, solver
-    coeffs = workloads.random_sine_coeffs(a.dim, seed=rank_seed, modes=16)
-    small = solver.Problem(a.dim, min(a.n, 128), a.p, coeffs)
-    cycles = solver.solve(small, a.method, k=a.k, tol=1e-10, max_cycles=100)["cycles"]
-    t0 = time.perf_counter()
-    prob = solver.Problem(a.dim, a.n, a.p, coeffs)
-    setup = time.perf_counter() - t0
-    N = prob.H.finest.N
-    s = np.zeros(N)
-    t0 = time.perf_counter()
-    for _ in range(restarts):
-        S = [s]
-        for _ in range(a.k + 1):
-            S.append(prob.cycle(S[-1]))
-        s = extrapolation.extrapolate(S, a.method)[0]
-        prob.residual(s)
-    per = (time.perf_counter() - t0) / restarts
-    return N / (per * cycles), per, cycles, setup, N
+    from oracle import solver
+    probs = [(solver.Problem(d, n, p, workloads.random_sine_coeffs(d, seed=sd, modes=16)), m, k)
+             for (d, n, p, m, k, sd) in jobs]
+    barrier.wait(timeout=1800)
+    for prob, method, k in probs:
+        t0 = time.time()
+        out = solver.solve(prob, method, k=k, tol=1e-10, max_cycles=200)
+        t1 = time.time()
+        queue.put((t0, t1, out["cycles"], prob.H.finest.N, bool(out["converged"])))
+
+
+def oracle_bytes_per_dof(dim, p):
+    """Peak RSS of one oracle solve per unknown: its sparse operator and the
+    per-colour row slices hold about 2 x 24 B per non-zero, (2p+1)^dim per row
+    (measured 2D p = 3: 2.75 GB at 1.05 M unknowns)."""
+    return 50.0 * (2 * p + 1) ** dim + 400.0
+
+
+def oracle_run(jobs_per_worker):
+    """Complete oracle solves (the CPU oracle as it stands, FP64, one thread
+    per process), one spawned process per entry of jobs_per_worker, all at
+    once.  Returns the aggregate DOF/s (every solve's N over the wall time
+    from the first start to the last end), the per-solve times and cycles."""
+    import multiprocessing as mp
+    env = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in env:
+        os.environ[k] = "1"                       # one thread per process: cores = processes
+    ctx = mp.get_context("spawn")                 # never fork a process that has touched CUDA
+    workers = len(jobs_per_worker)
+    barrier, queue = ctx.Barrier(workers), ctx.Queue()
+    procs = [ctx.Process(target=_oracle_worker, args=(jobs, barrier, queue)) for jobs in jobs_per_worker]
+    total = sum(len(j) for j in jobs_per_worker)
+    try:
+        for pr in procs:
+            pr.start()
+        res = [queue.get(timeout=3600) for _ in range(total)]
+        for pr in procs:
+            pr.join(timeout=60)
+    finally:
+        for pr in procs:
+            if pr.is_alive():
+                pr.terminate()
+        for k, v in env.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    t0 = min(r[0] for r in res)
+    t1 = max(r[1] for r in res)
+    per = sorted(r[1] - r[0] for r in res)
+    return {"value": sum(r[3] for r in res) / (t1 - t0), "wall_s": t1 - t0, "solve_s": per,
+            "dof": sum(r[3] for r in res), "cycles": sorted({r[2] for r in res}),
+            "converged": all(r[4] for r in res)}
+
+
+def all_core_workers(a, want):
+    """Concurrent oracle processes: one per host core, at most `want`, and as
+    many as the host memory (MemAvailable / cgroup limit) holds with room to spare."""
+    N = (oracle_n(a) + a.p - 2) ** a.dim
+    fit = int(0.5 * _memory_limit_bytes() / (oracle_bytes_per_dof(a.dim, a.p) * N))
+    return max(1, min(os.cpu_count() or 1, want, fit))
+
+
+def oracle_n(a):
+    """Elements per direction of the oracle's sample: the workload's own, except
+    that 3D problems above 64^3 are sampled at 64^3 (same p and k; the oracle's
+    sparse operator holds (2p+1)^3 = 343 non-zeros per row at p = 3, 37 GB at
+    128^3).  Multigrid work is linear in N, so DOF/s carries over."""
+    return min(a.n, 64) if a.dim == 3 else a.n
+
+
+def _job(a, seed):
+    return (a.dim, oracle_n(a), a.p, a.method, a.k, seed)
+
+
+def cpu_baseline(a):
+    """The oracle timed on this host: one complete solve single-threaded, then
+    one complete solve per process on all cores at once."""
+    one = oracle_run([[_job(a, a.seed)]])
+    P = all_core_workers(a, 64)
+    many = oracle_run([[_job(a, a.seed + i)] for i in range(P)]) if P > 1 else one
+    info = host_info()
+    return {"value": many["value"], "unit": "DOF/s", "cores": P, "kind": "oracle",
+            "sample": f"{P} complete solves to 1e-10 of the same workload at {oracle_n(a)}^{a.dim} elements "
+                      f"(seeds {a.seed}..{a.seed + P - 1}), "
+                      f"one per process on {P} cores at once, wall {many['wall_s']:.1f} s; set-up excluded",
+            "time_to_tol_s": {"single_thread": one["solve_s"][0],
+                              "all_cores_median": many["solve_s"][len(many["solve_s"]) // 2]},
+            "single_thread": {"value": one["value"], "unit": "DOF/s", "cores": 1,
+                              "sample": "one complete solve to 1e-10, seed %d" % a.seed},
+            "cycles": many["cycles"], "converged": many["converged"], **info}
 
 
 def run_reference(a, rank, world):
+    """The oracle as the reference arm: `steps` complete solves of this arm's
+    workload, run as concurrent single-threaded processes on the host cores
+    (as many at once as cores and memory allow, in waves); value = DOF of all
+    solves / wall time.  The oracle keeps no state between solves, so the
+    warm-up is its set-up (hierarchy and factors), built before the timed region."""
     if rank != 0:
         return
-    for _ in range(a.warmup):
-        pass                                    # the oracle has no warm-up state
-    vals, pers = [], []
-    cycles = None
-    for _ in range(max(1, a.steps)):
-        v, per, cycles, setup, N = oracle_sample(a)
-        vals.append(v)
-        pers.append(per)
-    v = sorted(vals)[len(vals) // 2]
-    ms = 1e3 * N / v
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "DOF/s", "n_gpus": a.gpus,
+    steps = max(1, a.steps)
+    P = all_core_workers(a, steps)
+    per_worker = (steps + P - 1) // P
+    r = oracle_run([[_job(a, a.seed + i * per_worker + j) for j in range(per_worker)] for i in range(P)])
+    nsolves = P * per_worker
+    ms = 1e3 * r["wall_s"] / nsolves
+    info = host_info()
+    line = {"impl": "reference", "metric": METRIC, "value": r["value"], "unit": "DOF/s", "n_gpus": a.gpus,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(a),
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": v, "unit": "DOF/s",
-                             "sample": f"one restart cycle ({a.k + 1} V-cycles + extrapolation + residual) "
-                                       f"timed at full size x {cycles} cycles (count from the 128^dim problem)"},
-            "e2e": {"value": v, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "time_to_tol_ms": 1e3 * r["solve_s"][len(r["solve_s"]) // 2], "cycles": r["cycles"],
+            "converged": r["converged"],
+            "cpu_baseline": {"kind": "oracle", "cores": P, "value": r["value"], "unit": "DOF/s",
+                             "sample": f"{nsolves} complete solves to 1e-10 at {oracle_n(a)}^{a.dim} elements "
+                                       f"({P} processes x {per_worker}, one "
+                                       f"thread each), wall {r['wall_s']:.1f} s; set-up excluded", **info},
+            "e2e": {"value": r["value"], "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -324,12 +440,78 @@ def run_ours(a, rank, world, local):
                            "cycles": jacobi["cycles"], "final_rel_residual": jacobi["final_rel_residual"],
                            "fp64_ms_per_step": jacobi["ms64"], "fp64_cycles": jacobi["cycles64"],
                            "smoother": "weighted Jacobi, omega = 2/3 (the paper's experiments), V(1,1)"}
+    if not a.no_extra_forms and a.dim == 2 and world == 1:
+        # the other two build workloads, measured in the same run (complete solves)
+        sx = min(a.steps, 5)
+        line["c3_form"] = c3_form(a, pkg, flush, stream, sx, min(a.warmup, 2))
+        line["c4_form"] = c4_form(a, pkg, flush, stream, sx, min(a.warmup, 2))
     if not a.no_cpu_baseline:
-        v, per, cycles, setup, N = oracle_sample(a)
-        line["cpu_baseline"] = {"value": v, "unit": "DOF/s", "cores": 1, "kind": "oracle",
-                                "sample": f"one restart cycle timed at full size ({per:.2f} s) x {cycles} "
-                                          f"cycles (count from the 128^dim problem); set-up {setup:.1f} s excluded"}
+        line["cpu_baseline"] = cpu_baseline(a)
     print(json.dumps(line), flush=True)
+
+
+def _timed_solves(fn, steps, flush, stream):
+    """CUDA-event times (ms) of `steps` calls of fn(), L2 flushed before each."""
+    import torch
+    times, out = [], None
+    for _ in range(steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return times, out
+
+
+def c3_form(a, pkg, flush, stream, steps, warmup):
+    """3D Poisson, 128^3 elements, p = 3, RRE(10), manufactured right side: the
+    mixed and FP64 forms, complete solves to 1e-10."""
+    import numpy as np
+    import workloads
+    s = pkg.Solver(3, 3, 128, k=10)
+    b = s.rhs_sine(workloads.manufactured_coeffs(3))
+    res = {"workload": "3D IGA Poisson, 128^3 elements, p=3, RRE(k=10), V(1,1) multicolour GS (64 colours), "
+                       "f = 3 pi^2 prod sin(pi x_d), tol 1e-10", "dof": s.N}
+    for prec in ("fp32_ir", "fp64"):
+        fn = lambda: s.solve(b, tol=1e-10, method="rre", k=10, prec=prec, max_cycles=100)
+        for _ in range(warmup):
+            fn()
+        t, out = _timed_solves(fn, steps, flush, stream)
+        ms = float(np.mean(t))
+        res[prec] = {"ms_per_step": ms, "value": s.N / (ms * 1e-3), "unit": "DOF/s", "cycles": out["cycles"],
+                     "vcycles": out["vcycles"], "final_rel_residual": float(out["history"][-1])}
+    s.close()
+    return res
+
+
+def c4_form(a, pkg, flush, stream, steps, warmup):
+    """256 independent 2D problems, n ~ U{32..512}, p ~ U{2,3,4}, random 16-mode
+    right sides, RRE(5): the mixed and FP64 forms of one batched solve."""
+    import numpy as np
+    import workloads
+    probs = workloads.batch_problems(256, seed=0)
+    B = pkg.Batch(2, [q["p"] for q in probs], [q["n"] for q in probs], k=5)
+    coeffs = np.stack([workloads.random_sine_coeffs(2, seed=q["rhs_seed"], modes=16) for q in probs])
+    b = B.rhs_sine(coeffs)
+    B.autotune()
+    res = {"workload": "256 independent 2D IGA Poisson problems, n ~ U{32..512}, p ~ U{2,3,4}, RRE(k=5), "
+                       "tol 1e-10", "dof": B.N}
+    for prec in ("fp32_ir", "fp64"):
+        fn = lambda: B.solve(b, tol=1e-10, method="rre", k=5, prec=prec)
+        for _ in range(warmup):
+            fn()
+        l0 = pkg.igamg_launch_count()
+        t, out = _timed_solves(fn, steps, flush, stream)
+        ms = float(np.mean(t))
+        res[prec] = {"ms_per_step": ms, "value": B.N / (ms * 1e-3), "unit": "DOF/s",
+                     "max_cycles": int(max(out["cycles"])), "converged": bool(out["converged"]),
+                     "max_rel_residual": float(max(out["residuals"])),
+                     "gpu_launches_per_solve": (pkg.igamg_launch_count() - l0) // max(1, steps)}
+    B.close()
+    return res
 
 
 def run_batch(a, rank, world, local):
@@ -344,7 +526,7 @@ def run_batch(a, rank, world, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    probs = workloads.batch_problems(256, seed=a.seed + rank)
+    probs = workloads.batch_problems(a.batch_count, seed=a.seed + rank)
     ps = [q["p"] for q in probs]
     ns = [q["n"] for q in probs]
     B = pkg.Batch(2, ps, ns, k=a.k)
@@ -391,8 +573,6 @@ def run_batch(a, rank, world, local):
         hx.copy_(o["x"], non_blocking=True)
         torch.cuda.synchronize()
         e2e.append((time.perf_counter() - t0) * 1e3)
-    jacobi["ms"] = max_over_ranks(jacobi["ms"], world)
-    jacobi["ms64"] = max_over_ranks(jacobi["ms64"], world)
     t_max = max_over_ranks(float(np.mean(times)), world)
     t64 = max_over_ranks(float(np.mean(times64)), world)
     te = max_over_ranks(float(np.mean(e2e)), world)
@@ -403,9 +583,9 @@ def run_batch(a, rank, world, local):
         "metric": METRIC, "value": units / (t_max * 1e-3), "unit": "DOF/s", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if a.prec == "fp32_ir" else "f64", "data": "synthetic",
-        "config": {"workload": f"256 independent 2D IGA Poisson problems, n ~ U{{32..512}}, p ~ U{{2,3,4}}, "
+        "config": {"workload": f"{len(probs)} independent 2D IGA Poisson problems, n ~ U{{32..512}}, p ~ U{{2,3,4}}, "
                                f"{a.method.upper()}(k={a.k}), tol 1e-10, {B.N} unknowns in total",
-                   "problems": 256, "total_dof": B.N, "method": a.method, "k": a.k,
+                   "problems": len(probs), "total_dof": B.N, "method": a.method, "k": a.k,
                    "rhs": "random sine series, 16 modes/direction, N(0,1), seed 1000 + i",
                    "schedule": "autotuned per degree (igamg_batch_autotune)",
                    "l2": "flushed between steps (256 MiB write)"},
@@ -418,19 +598,18 @@ def run_batch(a, rank, world, local):
         "gpu_launches": launches, "clocks": clk,
     }
     if not a.no_cpu_baseline:
-        from oracle import solver
-        sample = [q for q in probs if q["n"] <= 96][:6]
-        dof = 0
-        tsum = 0.0
-        for q in sample:
-            prob = solver.Problem(2, q["n"], q["p"], workloads.random_sine_coeffs(2, seed=q["rhs_seed"], modes=16))
-            t1 = time.perf_counter()
-            solver.solve(prob, a.method, k=a.k, tol=1e-10, max_cycles=100)
-            tsum += time.perf_counter() - t1
-            dof += prob.H.finest.N
-        line["cpu_baseline"] = {"value": dof / tsum, "unit": "DOF/s", "cores": 1, "kind": "oracle",
-                                "sample": f"{len(sample)} members with n <= 96 solved to 1e-10 "
-                                          f"({dof} unknowns, {tsum:.1f} s), set-up excluded"}
+        # the batch's first members, each solved completely, one per process on
+        # all cores at once (every worker gets the same count; memory-bounded)
+        P = max(1, min(os.cpu_count() or 1, 16,
+                       int(0.5 * _memory_limit_bytes() / (oracle_bytes_per_dof(2, 4) * 513 ** 2))))
+        per = 2
+        jobs = [[(2, q["n"], q["p"], a.method, a.k, q["rhs_seed"]) for q in probs[i * per:(i + 1) * per]]
+                for i in range(P)]
+        r = oracle_run(jobs)
+        line["cpu_baseline"] = {"value": r["value"], "unit": "DOF/s", "cores": P, "kind": "oracle",
+                                "sample": f"batch members 0..{P * per - 1} ({r['dof']} unknowns) solved "
+                                          f"completely to 1e-10, {per} per process on {P} cores at once, "
+                                          f"wall {r['wall_s']:.1f} s; set-up excluded", **host_info()}
     print(json.dumps(line), flush=True)
     B.close()
 

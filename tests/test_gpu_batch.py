@@ -60,3 +60,28 @@ def test_batch_zero_rhs_member(pkg):
     x = out["x"].cpu().numpy()
     assert np.all(x[B.offsets[1]:B.offsets[2]] == 0.0)
     B.close()
+
+
+def test_bench_batch_path_runs(pkg):
+    """bench.py's batched workload end to end on a 4-problem batch: one JSON
+    line with every problem converged (guards the bench path itself)."""
+    import io
+    import json
+    import sys
+    import contextlib
+    import bench
+    old = sys.argv
+    sys.argv = ["bench.py", "--workload", "batch256", "--batch-count", "4", "--steps", "1", "--warmup", "1",
+                "--no-cpu-baseline"]
+    try:
+        a = bench.parse()
+    finally:
+        sys.argv = old
+    buf = io.StringIO()
+    with contextlib.redirect_stdout(buf):
+        bench.run_batch(a, 0, 1, 0)
+    lines = [l for l in buf.getvalue().splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["converged"] and line["value"] > 0 and line["config"]["problems"] == 4
+    assert line["gpu_launches"] > 0 and line["e2e"]["h2d_bytes_per_step"] == 8 * line["config"]["total_dof"]

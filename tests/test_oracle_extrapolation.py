@@ -105,3 +105,32 @@ def test_restarted_solver_reaches_tolerance_and_the_discrete_solution(method):
     assert out["vcycles"] == 6 * out["cycles"]
     u = spla.spsolve(prob.H.finest.A.tocsc(), prob.b)
     assert np.linalg.norm(out["x"] - u) <= 1e-6 * np.linalg.norm(u)
+
+
+@pytest.mark.parametrize("method,krylov_step", [("rre", krylov.gmres), ("mpe", krylov.fom)])
+@pytest.mark.parametrize("q", [2, 4])
+def test_restarted_extrapolation_is_restarted_krylov(method, krylov_step, q):
+    """Algorithm 5 restarts from the extrapolant t (s_0 := t).  Each restart
+    cycle from s_0 is one RRE (MPE) step, i.e. GMRES(q) (FOM(q)) from x_0 = s_0
+    on the V-cycle-preconditioned system, so three restart cycles of the oracle
+    equal three cycles of restarted GMRES(q) (FOM(q)), iterate by iterate.  An
+    oracle that restarted from the last V-cycle iterate s_{q+1}, or ran q
+    instead of q+1 V-cycles per restart, fails this."""
+    H = mg.Hierarchy(2, 16, 3)
+    b = load_vector(H.finest.breaks, 3, np.random.default_rng(6).standard_normal((3, 3)))
+    N = H.finest.N
+    G = lambda x: mg.cycle(H, x, b)
+    c = G(np.zeros(N))
+    F = lambda v: v - (G(v) - c)
+    A = H.finest.A
+    res = lambda x: float(np.linalg.norm(b - A @ x))
+    out = ex.restarted(G, res, np.zeros(N), q, method, tol=0.0, max_cycles=3, keep_iterates=True)
+    assert out["cycles"] == 3 and out["vcycles"] == 3 * (q + 1)
+    x = np.zeros(N)
+    for cyc in range(3):
+        x = krylov_step(F, c, x, q)
+        t = out["iterates"][cyc]
+        assert np.linalg.norm(t - x) < 1e-10 * np.linalg.norm(x), cyc
+        # the history holds ||b - A t|| of the same iterate (cancellation in b - A t
+        # limits the agreement of two nearby iterates' residuals to about cond(A) eps)
+        assert abs(out["history"][cyc + 1] - res(x)) < 1e-5 * res(x), cyc
