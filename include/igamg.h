@@ -189,6 +189,37 @@ igamg_status igamg_extrapolate(long n, int q, int method, const double* d_S, lon
 igamg_status igamg_extrapolate_noalloc(long n, int q, int method, const double* d_S, long ld,
                                        double* d_t, double* h_gamma, int* h_qused, void* stream);
 
+/* ------------------------------------------- Gauss-Seidel sweep schedule */
+
+/* Form of the multicolour Gauss-Seidel sweep (Sec. 2.4; the same colours,
+ * order and arithmetic either way, so the results are identical).  The
+ * single-launch form runs a whole sweep in one kernel launch, each row
+ * starting as soon as the rows within reach of earlier colours are done
+ * (persistent CTAs claim rows in colour order and wait on per-row flags in
+ * the workspace); the other form runs one launch per row phase ((p+1)^(dim-1)
+ * per sweep).  Per precision of the cycle (FP32 V-cycles of the mixed forms,
+ * FP64 cycles): 0 = row phases on every level, 1 = one launch on every level,
+ * N >= 2 = one launch on levels with at least N rows (m_y m_z), -1 =
+ * unchanged.  Defaults: 2D row phases; 3D one launch from 8192 rows.
+ * igamg_autotune picks the threshold by timing.  Errors: EINVAL. */
+igamg_status igamg_set_sweep_form(igamg_ctx* ctx, int single_launch_fp32, int single_launch_fp64);
+void igamg_get_sweep_form(const igamg_ctx* ctx, int* single_launch_fp32, int* single_launch_fp64);
+
+/* Bound of every device-side wait of the single-launch sweeps, in seconds
+ * (process-wide, default 1; read when work is enqueued or a restart graph is
+ * captured).  A wait that runs out sets an error word in the workspace and
+ * the kernel finishes normally; igamg_solve and igamg_batch_solve then return
+ * IGAMG_ETIMEOUT (the iterate is not meaningful), and igamg_device_status
+ * reports it after component calls.  test_unset_flag = 1 makes every sweep
+ * CTA first wait on a word that nothing sets, so that the wait runs out: it
+ * exists to test this path and slows every sweep by the limit. */
+void igamg_set_wait_limit(double seconds, int test_unset_flag);
+
+/* Synchronises `stream` and returns IGAMG_ETIMEOUT (clearing the word) when
+ * a bounded device-side wait of a call that used workspace d_ws gave up
+ * since the word was last cleared, else IGAMG_OK. */
+igamg_status igamg_device_status(const igamg_ctx* ctx, void* d_ws, size_t ws_bytes, void* stream);
+
 /* ------------------------------------------------------- learned smoother */
 
 /* A small convolutional network used as the finest-level post-smoother of

@@ -70,6 +70,10 @@ def _load():
         "igamg_get_schedule": (None, [vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
         "igamg_set_cycle": (c_int, [vp, c_int, c_int, c_double]),
         "igamg_get_cycle": (None, [vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_double)]),
+        "igamg_set_sweep_form": (c_int, [vp, c_int, c_int]),
+        "igamg_get_sweep_form": (None, [vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
+        "igamg_set_wait_limit": (None, [c_double, c_int]),
+        "igamg_device_status": (c_int, [vp, vp, c_size, vp]),
         "igamg_set_launch_overlap": (None, [c_int]),
         "igamg_get_launch_overlap": (c_int, []),
         "igamg_autotune": (c_int, [vp, vp, c_size, vp, c_int]),
@@ -268,6 +272,31 @@ def igamg_get_cycle(ctx):
     a, b, w = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
     _load().igamg_get_cycle(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(w))
     return {"smoother": "jacobi" if a.value == IGAMG_SMOOTH_JACOBI else "gs", "mu": b.value, "omega": w.value}
+
+
+def igamg_set_sweep_form(ctx, single_launch_fp32=-1, single_launch_fp64=-1):
+    """GS sweep form per precision: 1 one launch per sweep, 0 one per row phase, -1 unchanged."""
+    _check(_load().igamg_set_sweep_form(ctx, int(single_launch_fp32), int(single_launch_fp64)),
+           "igamg_set_sweep_form")
+
+
+def igamg_get_sweep_form(ctx):
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _load().igamg_get_sweep_form(ctx, ctypes.byref(a), ctypes.byref(b))
+    return {"fp32": a.value, "fp64": b.value}
+
+
+def igamg_set_wait_limit(seconds=1.0, test_unset_flag=False):
+    """Process-wide bound of the device-side waits (test_unset_flag: make them run out)."""
+    _load().igamg_set_wait_limit(float(seconds), 1 if test_unset_flag else 0)
+
+
+def igamg_device_status(ctx, ws, stream=None):
+    """IGAMG_OK, or IGAMG_ETIMEOUT if a bounded device wait gave up (returned, not raised)."""
+    st = _load().igamg_device_status(ctx, _ptr(ws), ws.numel(), _stream(stream))
+    if st not in (IGAMG_OK, IGAMG_ETIMEOUT):
+        _check(st, "igamg_device_status")
+    return st
 
 
 def igamg_set_launch_overlap(enable):

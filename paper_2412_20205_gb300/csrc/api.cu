@@ -83,12 +83,24 @@ struct Workspace {
     ExtrapInfo* info = nullptr;
     double* scal = nullptr;   // [0] ||b||, [1] last residual norm, [2..] spare
     void* cnn = nullptr;      // network workspace (learned post-smoother)
+    // synchronisation words of the single-launch GS sweeps: per level the row
+    // flags and two counters, then the error word and a word nothing sets;
+    // cleared when a call takes the workspace into use (every sweep leaves
+    // them zero)
+    unsigned* sync = nullptr;
+    size_t nsync = 0;
+    std::vector<unsigned*> done, ctr;
+    unsigned* err = nullptr;
+    unsigned* never = nullptr;
     size_t bytes = 0;
 };
 
 }  // namespace
 
 void igamg::set_last_error(const char* msg) { g_err = msg; }
+
+// Default row threshold of one-launch GS sweeps on 3D levels (igamg_ctx::flow32).
+constexpr int kFlowRows3D = 8192;
 
 struct igamg_ctx {
     int dim = 2, p = 1, L = 1;
@@ -108,6 +120,15 @@ struct igamg_ctx {
     std::vector<TailView<float>> tails;
     bool tail_on = true;
     int gs_cap32 = 0;                       // row-CTA thread cap of FP32 GS (0: default)
+    // GS sweep form per precision: levels with at least this many rows run a
+    // sweep in one launch (rows wait on their earlier-phase neighbours), the
+    // others one launch per row phase.  Measured on GB300: one launch won
+    // where a sweep has many rows per phase (3D 128^3 finest level, 16641
+    // rows: 185 us against 828 us per FP32 sweep) and lost where the phase
+    // chain's latency dominates (2D 1024^2: 49 against 34 us; 3D 64^3, 4225
+    // rows: 185 against 142 us).  kNever: never.
+    static constexpr int kNever = 1 << 30;
+    int flow32 = kNever, flow64 = kNever;
     // cycle of Algorithm 2: smoother (IGAMG_SMOOTH_GS / IGAMG_SMOOTH_JACOBI),
     // mu = 1 (V-cycle) or 2 (W-cycle), Jacobi weight
     int smoother = 0, mu = 1;
@@ -123,11 +144,11 @@ struct igamg_ctx {
     struct Key {
         const void* b = nullptr;
         const void* ws = nullptr;
-        int k = -1, extrap = -1, prec = -1, abs_tol = -1, overlap = -1;
+        int k = -1, extrap = -1, prec = -1, abs_tol = -1, overlap = -1, sync = -1;
         const void* w = nullptr;
         bool operator==(const Key& o) const {
             return b == o.b && ws == o.ws && k == o.k && extrap == o.extrap && prec == o.prec &&
-                   abs_tol == o.abs_tol && overlap == o.overlap && w == o.w;
+                   abs_tol == o.abs_tol && overlap == o.overlap && sync == o.sync && w == o.w;
         }
     } key[3];
     // learned post-smoother: caller-owned device weights, stall ratio, outcome
@@ -139,6 +160,7 @@ struct igamg_ctx {
 namespace {
 
 size_t finestN(const igamg_ctx* c) { return c->hl.back().N(); }
+size_t lv64_n(const igamg_ctx* c, int l) { return c->hl[l].N(); }
 
 Workspace carve(const igamg_ctx* c, void* base, int k, int prec) {
     Workspace w;
@@ -180,6 +202,21 @@ Workspace carve(const igamg_ctx* c, void* base, int k, int prec) {
     w.qused = cv.take<int>(4);
     w.info = cv.take<ExtrapInfo>(1);
     w.scal = cv.take<double>(8);
+    w.nsync = 2;
+    for (int l = 0; l < L; ++l) w.nsync += 2 + (size_t)c->hl[l].m[1] * c->hl[l].m[2];
+    w.sync = cv.take<unsigned>(w.nsync);
+    w.done.resize(L);
+    w.ctr.resize(L);
+    if (w.sync) {
+        unsigned* q = w.sync;
+        w.err = q++;
+        w.never = q++;
+        for (int l = 0; l < L; ++l) {
+            w.ctr[l] = q;
+            w.done[l] = q + 2;
+            q += 2 + (size_t)c->hl[l].m[1] * c->hl[l].m[2];
+        }
+    }
     if (prec == IGAMG_FP32_IR_LEARNED)
         w.cnn = cv.take<unsigned char>(cnn_workspace_bytes((long long)finestN(c)));
     w.bytes = cv.off + 256;
@@ -281,6 +318,26 @@ struct Views<float> {
 template <typename T>
 int gs_cap(const igamg_ctx* c) { return std::is_same<T, float>::value ? c->gs_cap32 : 0; }
 
+// One GS sweep on level l in the context's form for precision T.
+template <typename T>
+void sweep(const igamg_ctx* c, cudaStream_t s, const Workspace& w, int l, bool descending, T* x, const T* b,
+           T* TM, T* TK) {
+    const auto& lv = Views<T>::lv(c);
+    const bool flow = lv[l].rows() >= (std::is_same<T, float>::value ? c->flow32 : c->flow64);
+    if (flow && w.sync) {
+        const SweepSync sy{w.done[l], w.ctr[l], w.err, w.never, wait_limit_ns(), wait_test_unset()};
+        dev::gs_sweep<T>(s, c->dim, lv[l], descending, x, b, TM, TK, gs_cap<T>(c), &sy);
+    } else {
+        dev::gs_sweep<T>(s, c->dim, lv[l], descending, x, b, TM, TK, gs_cap<T>(c));
+    }
+}
+
+// Clears the workspace's synchronisation words (the first use of a workspace
+// in a call; sweeps leave them zero).
+cudaError_t clear_sync(const Workspace& w, cudaStream_t s) {
+    return cudaMemsetAsync(w.sync, 0, w.nsync * sizeof(unsigned), s);
+}
+
 // Algorithm 2 for any mu and either smoother (nu1 = nu2 = 1), recursively:
 // level l pre-smooths, restricts its residual, runs mu cycles on level l - 1
 // from a zero coarse error (one direct solve on the coarsest level: a second
@@ -327,7 +384,7 @@ void mu_cycle(const igamg_ctx* c, cudaStream_t s, Workspace& w, int top, int l, 
     if (c->smoother == IGAMG_SMOOTH_JACOBI)
         dev::jacobi_sweep<T>(s, dim, lv[l], (T)c->omega, x, b, B[l].TM, B[l].TK, tm, tk);
     else
-        dev::gs_sweep<T>(s, dim, lv[l], false, x, b, B[l].TM, B[l].TK, gs_cap<T>(c));
+        sweep<T>(c, s, w, l, false, x, b, B[l].TM, B[l].TK);
     const bool clear = l - 1 >= 1;                  // coarse e^0 = 0: x | T_M | T_K of level l - 1
     dev::residual_restrict<T>(s, dim, lv[l], tv[l], b, tm, tk, B[l].r, B[l - 1].b, B[l].tmp1, B[l].tmp2,
                               clear ? B[l - 1].x : nullptr, clear ? 3 * lv[l - 1].n() : 0);
@@ -338,7 +395,7 @@ void mu_cycle(const igamg_ctx* c, cudaStream_t s, Workspace& w, int top, int l, 
     if (c->smoother == IGAMG_SMOOTH_JACOBI)
         dev::jacobi_sweep<T>(s, dim, lv[l], (T)c->omega, x, b, tm, tk, B[l].TM, B[l].TK);
     else
-        dev::gs_sweep<T>(s, dim, lv[l], true, x, b, B[l].TM, B[l].TK, gs_cap<T>(c));
+        sweep<T>(c, s, w, l, true, x, b, B[l].TM, B[l].TK);
 }
 
 bool default_cycle(const igamg_ctx* c) { return c->smoother == IGAMG_SMOOTH_GS && c->mu == 1; }
@@ -373,7 +430,7 @@ void vcycle(const igamg_ctx* c, cudaStream_t s, Workspace& w, int top, T* x_top,
                 dev::fill_zero<T>(s, B[l].TM, 2 * N);
             }
         }
-        dev::gs_sweep<T>(s, dim, lv[l], false, x, b, B[l].TM, B[l].TK, gs_cap<T>(c));  // pre-smooth
+        sweep<T>(c, s, w, l, false, x, b, B[l].TM, B[l].TK);                            // pre-smooth
         // b_{l-1} = R (b - A u), R = P^T; the next per-level level's x | T_M | T_K
         // (coarse e^0 = 0) are cleared in the same pass
         const bool clear = l - 1 >= lowest;
@@ -402,7 +459,7 @@ void vcycle(const igamg_ctx* c, cudaStream_t s, Workspace& w, int top, T* x_top,
                 continue;
             }
         }
-        dev::gs_sweep<T>(s, dim, lv[l], true, x, b, B[l].TM, B[l].TK, gs_cap<T>(c));   // post-smooth
+        sweep<T>(c, s, w, l, true, x, b, B[l].TM, B[l].TK);                             // post-smooth
     }
 }
 
@@ -505,6 +562,7 @@ igamg_status ensure_graph(igamg_ctx* c, Workspace& w, const double* d_b, void* d
     key.b = d_b; key.ws = d_ws; key.k = kk; key.extrap = extrap; key.prec = prec;
     key.abs_tol = denom == nullptr;
     key.overlap = launch_overlap() ? 1 : 0;
+    key.sync = sync_generation();
     key.w = prec == IGAMG_FP32_IR_LEARNED ? c->cnn_w : nullptr;
     if (c->exec[slot] && c->key[slot] == key) return IGAMG_OK;
     if (c->exec[slot]) { cudaGraphExecDestroy(c->exec[slot]); c->exec[slot] = nullptr; }
@@ -619,6 +677,8 @@ igamg_status igamg_setup(int dim, int p, const int* n_elems, int n_levels, igamg
         delete c;
         return fail(IGAMG_EINVAL, std::string("setup: ") + e.what());
     }
+    // one-launch sweeps on 3D levels with many rows (see igamg_ctx::flow32)
+    if (dim == 3) c->flow32 = c->flow64 = kFlowRows3D;
     *out = c;
     return IGAMG_OK;
 }
@@ -948,6 +1008,7 @@ igamg_status igamg_solve(igamg_ctx* c, const double* d_b, double* d_x, double to
     cudaStream_t s = (cudaStream_t)stream;
     const size_t N = finestN(c);
     const int top = c->L - 1;
+    CUDA_TRY(clear_sync(w, s));
     if (h_cycles) *h_cycles = 0;
     if (h_vcycles) *h_vcycles = 0;
     // ||b|| (denominator of the relative test)
@@ -992,9 +1053,16 @@ igamg_status igamg_solve(igamg_ctx* c, const double* d_b, double* d_x, double to
             restart_body(c, s, w, extrap, kk, cur, d_b, denom);
         }
         CUDA_TRY(cudaMemcpyAsync(c->h_pin, w.scal + 1, 8, cudaMemcpyDeviceToHost, s));
+        unsigned* h_err = reinterpret_cast<unsigned*>(c->h_pin + 2);
+        CUDA_TRY(cudaMemcpyAsync(h_err, w.err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
         CUDA_TRY(cudaStreamSynchronize(s));
         const double prev = res;
         res = c->h_pin[0];
+        if (*h_err) {
+            result = IGAMG_ETIMEOUT;
+            fail(result, "a bounded device-side wait of a Gauss-Seidel sweep gave up");
+            break;
+        }
         if (h_hist) h_hist[cyc] = res;
         if (h_cycles) *h_cycles = cyc;
         if (h_vcycles) *h_vcycles = cyc * (extrap == IGAMG_EXTRAP_NONE ? 1 : kk + 1);
@@ -1013,6 +1081,46 @@ igamg_status igamg_solve(igamg_ctx* c, const double* d_b, double* d_x, double to
     CUDA_TRY(cudaGetLastError());
     if (result == IGAMG_ENOTCONV) fail(result, "max_cycles reached");
     return result;
+}
+
+igamg_status igamg_device_status(const igamg_ctx* c, void* d_ws, size_t ws_bytes, void* stream) {
+    if (igamg_status st = check_ctx(c)) return st;
+    if (!d_ws || ((uintptr_t)d_ws & 255)) return fail(IGAMG_EINVAL, "bad workspace");
+    const Workspace w = carve(c, d_ws, 1, IGAMG_FP64);
+    if (ws_bytes < (size_t)((char*)(w.sync + w.nsync) - (char*)d_ws)) return fail(IGAMG_EINVAL, "workspace too small");
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned* h_err = reinterpret_cast<unsigned*>(c->h_pin + 2);
+    CUDA_TRY(cudaMemcpyAsync(h_err, w.err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (*h_err) {
+        CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(unsigned), s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        return fail(IGAMG_ETIMEOUT, "a bounded device-side wait of a Gauss-Seidel sweep gave up");
+    }
+    return IGAMG_OK;
+}
+
+void igamg_set_wait_limit(double seconds, int test_unset_flag) {
+    set_wait_limit(seconds > 0 ? (long long)(seconds * 1e9) : 0, test_unset_flag);
+}
+
+static void drop_graphs(igamg_ctx* c);
+
+igamg_status igamg_set_sweep_form(igamg_ctx* c, int single_launch_fp32, int single_launch_fp64) {
+    if (igamg_status st = check_ctx(c, false)) return st;
+    if (single_launch_fp32 < -1 || single_launch_fp64 < -1)
+        return fail(IGAMG_EINVAL, "sweep form: -1 unchanged, 0 never, 1 always, N >= 2 on levels of >= N rows");
+    auto rows = [](int v) { return v == 0 ? igamg_ctx::kNever : v; };
+    if (single_launch_fp32 >= 0) c->flow32 = rows(single_launch_fp32);
+    if (single_launch_fp64 >= 0) c->flow64 = rows(single_launch_fp64);
+    drop_graphs(c);
+    return IGAMG_OK;
+}
+
+void igamg_get_sweep_form(const igamg_ctx* c, int* single_launch_fp32, int* single_launch_fp64) {
+    auto v = [](int r) { return r >= igamg_ctx::kNever ? 0 : r; };
+    if (single_launch_fp32) *single_launch_fp32 = c ? v(c->flow32) : 0;
+    if (single_launch_fp64) *single_launch_fp64 = c ? v(c->flow64) : 0;
 }
 
 igamg_status igamg_apply(igamg_ctx* c, int level, const double* d_x, double* d_y, void* d_ws,
@@ -1038,7 +1146,8 @@ igamg_status igamg_smooth(igamg_ctx* c, int level, double* d_x, const double* d_
     cudaStream_t s = (cudaStream_t)stream;
     LevelBuf<double>& B = w.d[level];
     dev::xpass<double, double>(s, c->lv64[level], d_x, nullptr, nullptr, 0, nullptr, nullptr, 0, B.TM, B.TK);
-    dev::gs_sweep<double>(s, c->dim, c->lv64[level], descending != 0, d_x, d_b, B.TM, B.TK);
+    CUDA_TRY(clear_sync(w, s));
+    sweep<double>(c, s, w, level, descending != 0, d_x, d_b, B.TM, B.TK);
     CUDA_TRY(cudaGetLastError());
     return IGAMG_OK;
 }
@@ -1051,9 +1160,11 @@ igamg_status igamg_smooth_f32(igamg_ctx* c, int level, float* d_x, const float* 
     Workspace w = carve(c, d_ws, 1, IGAMG_FP32_IR);
     cudaStream_t s = (cudaStream_t)stream;
     LevelBuf<float>& B = w.f[level];
-    if (!sums_current)
+    if (!sums_current) {
+        CUDA_TRY(clear_sync(w, s));
         dev::xpass<float, float>(s, c->lv32[level], d_x, nullptr, nullptr, 0, nullptr, nullptr, 0, B.TM, B.TK);
-    dev::gs_sweep<float>(s, c->dim, c->lv32[level], descending != 0, d_x, d_b, B.TM, B.TK, c->gs_cap32);
+    }
+    sweep<float>(c, s, w, level, descending != 0, d_x, d_b, B.TM, B.TK);
     CUDA_TRY(cudaGetLastError());
     return IGAMG_OK;
 }
@@ -1102,6 +1213,7 @@ igamg_status igamg_vcycle(igamg_ctx* c, double* d_x, const double* d_b, int prec
     Workspace w = carve(c, d_ws, 1, prec);
     cudaStream_t s = (cudaStream_t)stream;
     const int top = c->L - 1;
+    CUDA_TRY(clear_sync(w, s));
     dev::xpass<double, double>(s, c->lv64[top], d_x, nullptr, nullptr, 0, nullptr, nullptr, 0, w.d[top].TM,
                                w.d[top].TK);
     fixed_point_step(c, s, w, prec, d_b, d_x, d_x);
@@ -1219,36 +1331,82 @@ igamg_status igamg_autotune(igamg_ctx* c, void* d_ws, size_t ws_bytes, void* str
     const int top = c->L - 1;
     LevelBuf<float>& G = w.f[top];
     const size_t N = finestN(c);
+    CUDA_TRY(clear_sync(w, s));
     // a right side with every frequency: b = 1 (x = 0 at the start of every cycle)
     CUDA_TRY(cudaMemsetAsync(G.b, 0x3f, N * sizeof(float), s));       // 0x3f3f3f3f = 0.747
-    cudaEvent_t e0, e1;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    // on any error: the schedule found on entry, no leaked events, no graphs
+    // captured with a trial schedule
+    struct Restore {
+        igamg_ctx* c;
+        cudaEvent_t *e0, *e1;
+        int cap, flow32, flow64;
+        bool tail_on;
+        TailView<float> tail;
+        bool armed = true;
+        ~Restore() {
+            if (*e0) cudaEventDestroy(*e0);
+            if (*e1) cudaEventDestroy(*e1);
+            if (!armed) return;
+            c->gs_cap32 = cap;
+            c->flow32 = flow32;
+            c->flow64 = flow64;
+            c->tail_on = tail_on;
+            c->tail32 = tail;
+            drop_graphs(c);
+        }
+    } restore{c, &e0, &e1, c->gs_cap32, c->flow32, c->flow64, c->tail_on, c->tail32};
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
     const int caps[3] = {128, 256, 512};
+    // one-launch sweep thresholds tried (rows per level; kNever = row phases only)
+    const int flows[3] = {igamg_ctx::kNever, 16384, 4096};
     const int most = (int)c->tails.size() - 1;
+    auto time_cycles = [&](auto tag, float* ms) -> igamg_status {
+        using T = decltype(tag);
+        auto& B = Views<T>::buf(w);
+        T* x = B[top].x;
+        const T* b = B[top].b;
+        if constexpr (std::is_same<T, double>::value)     // FP64 cycles: a constant right side too
+            CUDA_TRY(cudaMemsetAsync(B[top].b, 0x3f, lv64_n(c, top) * sizeof(double), s));
+        vcycle<T>(c, s, w, top, x, b, true);                               // warm-up
+        CUDA_TRY(cudaEventRecord(e0, s));
+        for (int r = 0; r < reps; ++r) vcycle<T>(c, s, w, top, x, b, true);
+        CUDA_TRY(cudaEventRecord(e1, s));
+        CUDA_TRY(cudaEventSynchronize(e1));
+        CUDA_TRY(cudaEventElapsedTime(ms, e0, e1));
+        return IGAMG_OK;
+    };
     float best = 1e30f;
-    int best_cap = 0, best_lc = c->tail_on ? c->tail32.lc : 0;
-    for (int ci = 0; ci < (c->dim == 2 ? 3 : 1); ++ci)
-        for (int lc = 0; lc <= most; ++lc) {
-            c->gs_cap32 = c->dim == 2 ? caps[ci] : 0;
-            c->tail_on = lc > 0;
-            if (lc > 0) c->tail32 = c->tails[lc];
-            vcycle<float>(c, s, w, top, G.x, G.b, true);                  // warm-up
-            CUDA_TRY(cudaEventRecord(e0, s));
-            for (int r = 0; r < reps; ++r) vcycle<float>(c, s, w, top, G.x, G.b, true);
-            CUDA_TRY(cudaEventRecord(e1, s));
-            CUDA_TRY(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-            if (ms < best) { best = ms; best_cap = c->gs_cap32; best_lc = lc; }
-        }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    int best_cap = 0, best_lc = c->tail_on ? c->tail32.lc : 0, best_flow = c->flow32;
+    for (int fi = 0; fi < 3; ++fi)
+        for (int ci = 0; ci < (c->dim == 2 ? 3 : 1); ++ci)
+            for (int lc = 0; lc <= most; ++lc) {
+                c->flow32 = flows[fi];
+                c->gs_cap32 = c->dim == 2 ? caps[ci] : 0;
+                c->tail_on = lc > 0;
+                if (lc > 0) c->tail32 = c->tails[lc];
+                float ms = 0.f;
+                if (igamg_status st = time_cycles(0.0f, &ms)) return st;
+                if (ms < best) { best = ms; best_cap = c->gs_cap32; best_lc = lc; best_flow = c->flow32; }
+            }
     c->gs_cap32 = best_cap;
     c->tail_on = best_lc > 0;
     if (best_lc > 0) c->tail32 = c->tails[best_lc];
-    drop_graphs(c);
+    c->flow32 = best_flow;
+    // FP64 cycles: the sweep form only (on the same workspace; b = the FP32 b in FP64)
+    float best64 = 1e30f;
+    int best_flow64 = c->flow64;
+    for (int fi = 0; fi < 3; ++fi) {
+        c->flow64 = flows[fi];
+        float ms = 0.f;
+        if (igamg_status st = time_cycles(0.0, &ms)) return st;
+        if (ms < best64) { best64 = ms; best_flow64 = c->flow64; }
+    }
+    c->flow64 = best_flow64;
     CUDA_TRY(cudaGetLastError());
+    restore.armed = false;
+    drop_graphs(c);
     return IGAMG_OK;
 }
 
@@ -1270,6 +1428,7 @@ igamg_status igamg_vcycle_probe(igamg_ctx* c, double* d_x, const double* d_b, do
     Workspace w = carve(c, d_ws, 1, IGAMG_FP64);
     cudaStream_t s = (cudaStream_t)stream;
     const int top = c->L - 1;
+    CUDA_TRY(clear_sync(w, s));
     dev::xpass<double, double>(s, c->lv64[top], d_x, nullptr, nullptr, 0, nullptr, nullptr, 0, w.d[top].TM,
                                w.d[top].TK);
     vcycle<double>(c, s, w, top, d_x, d_b, false, false, d_x_mid);
@@ -1303,6 +1462,7 @@ struct igamg_batch {
     std::vector<cudaStream_t> streams;
     cudaEvent_t ev = nullptr;
     double* h_pin = nullptr;                // 2 per problem: ||b||, last residual
+    unsigned* h_err = nullptr;              // per problem: its workspace's device-wait error word
 };
 
 namespace {
@@ -1351,6 +1511,7 @@ igamg_status igamg_batch_create(int count, int dim, const int* p, const int* n, 
     for (int i = 0; i < count; ++i) B->lane[i] = i % (int)B->streams.size();
     CUDA_TRY(cudaEventCreateWithFlags(&B->ev, cudaEventDisableTiming));
     CUDA_TRY(cudaMallocHost(&B->h_pin, sizeof(double) * 2 * count));
+    CUDA_TRY(cudaMallocHost(&B->h_err, sizeof(unsigned) * count));
     *out = B;
     return IGAMG_OK;
 }
@@ -1398,6 +1559,7 @@ igamg_status igamg_batch_solve(igamg_batch* B, const double* d_b, double* d_x, d
         Workspace& w = W[i];
         const size_t N = finestN(c);
         const double* b = d_b + B->voff[i];
+        CUDA_TRY(clear_sync(w, s));
         dev::sumsq_partial(s, b, N, w.partial, 256);
         dev::norm_final(s, w.partial, 256, nullptr, w.scal, 0);
         dev::fill_zero<double>(s, w.S, N);
@@ -1445,9 +1607,12 @@ igamg_status igamg_batch_solve(igamg_batch* B, const double* d_b, double* d_x, d
         const size_t N = finestN(B->ctx[i]);
         if (stat[i] == IGAMG_OK && B->h_pin[2 * i] == 0.0) CUDA_TRY(cudaMemsetAsync(d_x + B->voff[i], 0, N * 8, s));
         else CUDA_TRY(cudaMemcpyAsync(d_x + B->voff[i], W[i].S, N * 8, cudaMemcpyDeviceToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(B->h_err + i, W[i].err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     }
     for (auto s : B->streams) CUDA_TRY(cudaStreamSynchronize(s));
     CUDA_TRY(cudaGetLastError());
+    for (int i = 0; i < B->count; ++i)
+        if (B->h_err[i]) stat[i] = IGAMG_ETIMEOUT;
     igamg_status all = IGAMG_OK;
     for (int i = 0; i < B->count; ++i) {
         if (h_cycles) h_cycles[i] = cyc[i];
@@ -1496,6 +1661,7 @@ void igamg_batch_destroy(igamg_batch* B) {
     for (auto s : B->streams) if (s) cudaStreamDestroy(s);
     if (B->ev) cudaEventDestroy(B->ev);
     if (B->h_pin) cudaFreeHost(B->h_pin);
+    if (B->h_err) cudaFreeHost(B->h_err);
     delete B;
 }
 

@@ -94,6 +94,28 @@ struct DFView {
     float Mch[2][2 * kMaxP + 1], Mcl[2][2 * kMaxP + 1], Kch[2][2 * kMaxP + 1], Kcl[2][2 * kMaxP + 1];
 };
 
+// Synchronisation words of a single-launch Gauss-Seidel sweep on one level
+// (in the caller's workspace).  They are zero before a sweep and every sweep
+// leaves them zero, so they are cleared once when a workspace is taken into
+// use.  Every wait on them is bounded: after limit_ns the kernel sets bit 0
+// of *err and carries on.
+struct SweepSync {
+    unsigned* done;          // one flag per row of the level
+    unsigned* ctr;           // [0] next row claim, [1] CTAs finished
+    unsigned* err;           // bit 0: a bounded wait gave up
+    const unsigned* never;   // a word nothing sets (tests of the bounded wait)
+    long long limit_ns;      // bound of every wait
+    int test_unset;          // 1: every CTA first waits on *never
+};
+
+// Process-wide bound of the device-side waits and the test switch that makes
+// every single-launch sweep wait on a flag nothing sets (read when a sweep is
+// enqueued or a graph captured); sync_generation() changes with either.
+void set_wait_limit(long long ns, int test_unset);
+long long wait_limit_ns();
+int wait_test_unset();
+int sync_generation();
+
 // Device-side state of one extrapolation (CholeskyQR2 pass-1 results).
 struct ExtrapInfo {
     int done, a, dep, pad;
@@ -194,11 +216,13 @@ template <typename T, typename A>
 void xpass(cudaStream_t s, const LevelView<T>& L, const T* x, T* x_out, const A* add,
            int nS, const double* gamma, const T* S, size_t ldS, T* TM, T* TK);
 
-// One multicolour Gauss-Seidel sweep (all (p+1)^dim colours) in row phases;
-// cap bounds the threads of a row CTA (0: the default).
+// One multicolour Gauss-Seidel sweep (all (p+1)^dim colours): with sy ==
+// nullptr as (p+1)^(dim-1) row-phase launches, else in one launch whose rows
+// wait on their earlier-phase neighbours through *sy (same results); cap
+// bounds the threads of a row CTA (0: the default).
 template <typename T>
 void gs_sweep(cudaStream_t s, int dim, const LevelView<T>& L, bool descending, T* x,
-              const T* b, T* TM, T* TK, int cap = 0);
+              const T* b, T* TM, T* TK, int cap = 0, const SweepSync* sy = nullptr);
 
 // One weighted-Jacobi sweep x += omega D^{-1} (b - A x) (the paper's smoother,
 // Sec. 4) from the row partial sums TM, TK of x, then the sums of the new x:

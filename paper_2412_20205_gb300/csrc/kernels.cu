@@ -25,7 +25,18 @@ namespace {
 thread_local long long g_launches = 0;
 std::atomic<bool> g_overlap{true};
 thread_local int g_no_overlap = 0;
+std::atomic<long long> g_wait_ns{1000000000LL};      // one second
+std::atomic<int> g_wait_test{0};
+std::atomic<int> g_sync_gen{0};
 }
+void set_wait_limit(long long ns, int test_unset) {
+    g_wait_ns.store(ns < 0 ? 0 : ns);
+    g_wait_test.store(test_unset ? 1 : 0);
+    g_sync_gen.fetch_add(1);
+}
+long long wait_limit_ns() { return g_wait_ns.load(); }
+int wait_test_unset() { return g_wait_test.load(); }
+int sync_generation() { return g_sync_gen.load(); }
 void count_launch(long long n) { g_launches += n; }
 long long launch_count() { return g_launches; }
 bool launch_overlap() { return g_no_overlap == 0 && g_overlap.load(std::memory_order_relaxed); }
@@ -87,8 +98,16 @@ __device__ void row_couplings(const LevelView<T>& L, int j, int k, T* cM, T* cK,
     }
 }
 
+// Global load of data that other CTAs of the same grid write (CG = true):
+// through L2 only (.cg), never from a stale L1 line.  CG = false: a plain load.
+template <bool CG, typename T>
+__device__ __forceinline__ T ldv(const T* p) {
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
+}
+
 // sum over neighbour rows q (all, or all but the own row) of cM T_M + cK T_K at column i
-template <typename T, int NNB, int SKIP>
+template <typename T, int NNB, int SKIP, bool CG = false>
 __device__ __forceinline__ T couple(const T* cM, const T* cK, const int* nrow, const T* __restrict__ TM,
                                     const T* __restrict__ TK, int mx, int i) {
     T acc = 0;
@@ -97,7 +116,7 @@ __device__ __forceinline__ T couple(const T* cM, const T* cK, const int* nrow, c
     for (int q = 0; q < NNB; ++q) {
         if (q == SKIP) continue;
         const size_t o = (size_t)nrow[q] * mx + i;
-        acc += cM[q] * TM[o] + cK[q] * TK[o];
+        acc += cM[q] * ldv<CG>(TM + o) + cK[q] * ldv<CG>(TK + o);
     }
     return acc;
 }
@@ -296,31 +315,50 @@ __device__ __forceinline__ void gs_colours_incremental(const LevelView<T>& L, co
 template <typename T, int DIM, int P>
 constexpr bool gs_window() { return sizeof(T) == 4 && (DIM == 3 || P != 3); }
 
-template <typename T, int DIM, int P, bool WINDOW>
-__device__ __forceinline__ void gs_phase_body(const LevelView<T>& L, int cy, int cz, int descending,
-                                                    T* __restrict__ x, const T* __restrict__ b,
-                                                    T* __restrict__ TM, T* __restrict__ TK) {
-    constexpr int P1 = P + 1, W = 2 * P + 1;
-    constexpr int NNB = (DIM == 3) ? W * W : W;
-    constexpr int OWN = (DIM == 3) ? P * W + P : P;
-    const int mx = L.m[0], my = L.m[1];
-    const int nty = (my - cy + P) / P1;
-    const int j = cy + P1 * (blockIdx.x % nty);
-    const int k = (DIM == 3) ? cz + P1 * (blockIdx.x / nty) : 0;
-    const size_t base = ((size_t)k * my + j) * mx;
+// Shared-memory rows of one GS row update: right side minus the frozen
+// off-row part, the row's own partial sums, this sweep's corrections, x and
+// the inverse diagonal (6 rows of m_x), then the row couplings and the staged
+// boundary x-band columns.
+template <typename T, int DIM, int P>
+struct GsSmem {
+    static constexpr int W = 2 * P + 1;
+    static constexpr int NNB = (DIM == 3) ? W * W : W;
+    T *rhs, *tm, *tk, *dl, *xs, *dv;
+    T* cM;
+    T* cK;
+    int* nrow;
+    T* bm;
+    T* bk;
+};
 
+template <typename T, int DIM, int P>
+__device__ __forceinline__ GsSmem<T, DIM, P> gs_smem(int mx) {
+    using S = GsSmem<T, DIM, P>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* rhs = reinterpret_cast<T*>(smem_raw);
-    T* tm = rhs + mx;
-    T* tk = tm + mx;
-    T* dl = tk + mx;
-    T* xs = dl + mx;
-    T* dv = xs + mx;
-    __shared__ T cM[NNB], cK[NNB];
-    __shared__ int nrow[NNB];
-    __shared__ T bm[kBandCols * W], bk[kBandCols * W];
-    if constexpr (DIM == 3) pdl_enter();
-    row_couplings<T, DIM, P>(L, j, k, cM, cK, nrow);
+    __shared__ T cM[S::NNB], cK[S::NNB];
+    __shared__ int nrow[S::NNB];
+    __shared__ T bm[kBandCols * S::W], bk[kBandCols * S::W];
+    S g;
+    g.rhs = reinterpret_cast<T*>(smem_raw);
+    g.tm = g.rhs + mx;
+    g.tk = g.tm + mx;
+    g.dl = g.tk + mx;
+    g.xs = g.dl + mx;
+    g.dv = g.xs + mx;
+    g.cM = cM;
+    g.cK = cK;
+    g.nrow = nrow;
+    g.bm = bm;
+    g.bk = bk;
+    return g;
+}
+
+// The x-band's boundary columns (row independent) into shared memory; returns
+// their count (the RowBand falls back to memory above kBandCols).
+template <typename T, int P>
+__device__ __forceinline__ int gs_stage_band(const LevelView<T>& L, T* bm, T* bk) {
+    constexpr int W = 2 * P + 1;
+    const int mx = L.m[0];
     const int nb = L.tlo[0] + (mx - L.thi[0]);
     if (nb <= kBandCols)
         for (int t = threadIdx.x; t < nb * W; t += blockDim.x) {
@@ -329,26 +367,37 @@ __device__ __forceinline__ void gs_phase_body(const LevelView<T>& L, int cy, int
             bm[t] = L.Mb[0][bb * mx + i];
             bk[t] = L.Kb[0][bb * mx + i];
         }
-    // 2D rows: everything up to the wait reads operator data that no kernel
-    // writes, so under launch overlap it runs during the previous kernel's
-    // tail (measured 2-9% per solve).  3D rows wait at entry: this order cost
-    // them 27% (128^3, p = 3), with or without overlap.
-    if constexpr (DIM == 2) {
-        for (int i = threadIdx.x; i < mx; i += blockDim.x) dv[i] = L.invdiag[base + i];
-        pdl_enter();
-    }
-    __syncthreads();
+    return nb;
+}
+
+// One target row's p+1 colour steps from its loads to its stores, after the
+// row couplings (cM, cK, nrow) and, in 2D, the inverse diagonal (dv) are in
+// shared memory and a barrier has made them visible.  CG: x, T_M and T_K are
+// read through L2 (they are written by other CTAs of the same launch).
+template <typename T, int DIM, int P, bool WINDOW, bool CG>
+__device__ __forceinline__ void gs_row(const LevelView<T>& L, const GsSmem<T, DIM, P>& g, const RowBand<T, P>& band,
+                                       size_t base, int descending, T* __restrict__ x, const T* __restrict__ b,
+                                       T* __restrict__ TM, T* __restrict__ TK) {
+    constexpr int P1 = P + 1, W = 2 * P + 1;
+    constexpr int NNB = (DIM == 3) ? W * W : W;
+    constexpr int OWN = (DIM == 3) ? P * W + P : P;
+    const int mx = L.m[0];
+    T* rhs = g.rhs;
+    T* tm = g.tm;
+    T* tk = g.tk;
+    T* dl = g.dl;
+    T* xs = g.xs;
+    T* dv = g.dv;
     for (int i = threadIdx.x; i < mx; i += blockDim.x) {
-        rhs[i] = b[base + i] - couple<T, NNB, OWN>(cM, cK, nrow, TM, TK, mx, i);
-        tm[i] = TM[base + i];
-        tk[i] = TK[base + i];
-        xs[i] = x[base + i];
+        rhs[i] = b[base + i] - couple<T, NNB, OWN, CG>(g.cM, g.cK, g.nrow, TM, TK, mx, i);
+        tm[i] = ldv<CG>(TM + base + i);
+        tk[i] = ldv<CG>(TK + base + i);
+        xs[i] = ldv<CG>(x + base + i);
         if constexpr (DIM == 3) dv[i] = L.invdiag[base + i];
         if constexpr (WINDOW) dl[i] = 0;
     }
     __syncthreads();
-    const RowBand<T, P> band{L, bm, bk, nb};
-    const T am = cM[OWN], ak = cK[OWN];
+    const T am = g.cM[OWN], ak = g.cK[OWN];
     if constexpr (WINDOW) {
         const int tlo = L.tlo[0], thi = L.thi[0];
         // sum_b M_x(i, b) dl[i + b - p] (and K_x): the x-band applied to this
@@ -415,6 +464,157 @@ __device__ __forceinline__ void gs_phase_body(const LevelView<T>& L, int cy, int
     }
 }
 
+template <typename T, int DIM, int P, bool WINDOW>
+__device__ __forceinline__ void gs_phase_body(const LevelView<T>& L, int cy, int cz, int descending,
+                                              T* __restrict__ x, const T* __restrict__ b,
+                                              T* __restrict__ TM, T* __restrict__ TK) {
+    constexpr int P1 = P + 1;
+    const int mx = L.m[0], my = L.m[1];
+    const int nty = (my - cy + P) / P1;
+    const int j = cy + P1 * (blockIdx.x % nty);
+    const int k = (DIM == 3) ? cz + P1 * (blockIdx.x / nty) : 0;
+    const size_t base = ((size_t)k * my + j) * mx;
+    const GsSmem<T, DIM, P> g = gs_smem<T, DIM, P>(mx);
+    if constexpr (DIM == 3) pdl_enter();
+    row_couplings<T, DIM, P>(L, j, k, g.cM, g.cK, g.nrow);
+    const int nb = gs_stage_band<T, P>(L, g.bm, g.bk);
+    // 2D rows: everything up to the wait reads operator data that no kernel
+    // writes, so under launch overlap it runs during the previous kernel's
+    // tail (measured 2-9% per solve).  3D rows wait at entry: this order cost
+    // them 27% (128^3, p = 3), with or without overlap.
+    if constexpr (DIM == 2) {
+        for (int i = threadIdx.x; i < mx; i += blockDim.x) g.dv[i] = L.invdiag[base + i];
+        pdl_enter();
+    }
+    __syncthreads();
+    const RowBand<T, P> band{L, g.bm, g.bk, nb};
+    gs_row<T, DIM, P, WINDOW, false>(L, g, band, base, descending, x, b, TM, TK);
+}
+
+// ---------------------------------------------------------------- single-launch sweep
+// Cross-CTA waits of a single-launch sweep.  ld.acquire / st.release at GPU
+// scope order a row's published data before and after its flag.
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ long long global_ns() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Waits until *f != 0; false when limit_ns has passed, or at once when an
+// earlier wait already gave up (*err != 0), so that a sweep whose waits run
+// out ends within about one limit in all.
+__device__ __noinline__ bool wait_flag(const unsigned* f, long long limit_ns, const unsigned* err) {
+    if (ld_acquire_gpu(f)) return true;
+    const long long t0 = global_ns();
+    for (;;) {
+        if (*(volatile const unsigned*)err) return false;
+        __nanosleep(32);
+        if (ld_acquire_gpu(f)) return true;
+        if (global_ns() - t0 >= limit_ns) return false;
+    }
+}
+
+// One whole multicolour Gauss-Seidel sweep ((p+1)^dim colours) in ONE launch.
+// The colour order is the row-phase order of gs_phase_body: for 2D phases
+// ph = 0..p over rows j = cy mod (p+1), cy = ph (descending: p - ph); in 3D
+// ph runs over (cy, cz) with cz slowest.  Within a phase no two rows couple,
+// and a row reads the T rows of the 2p (3D: (2p+1)^2 - 1) rows within reach.
+// Those of earlier phases must hold this sweep's values and those of later
+// phases the previous ones; so a row may start as soon as its earlier-phase
+// neighbours are done, and a later-phase neighbour cannot overwrite what it
+// reads because that neighbour waits for it in turn.  The result is exactly
+// that of the phase-by-phase launches (same arithmetic, same order per row).
+//
+// Work distribution: persistent CTAs claim rows from a counter in phase
+// order, so every row a CTA waits on was claimed earlier by a CTA that is
+// running; the unfinished row of smallest claim index never waits, which
+// rules out deadlock whatever the number of resident CTAs.  Each CTA
+// prefetches its next claim.  Every wait is bounded (SweepSync::limit_ns):
+// on expiry the kernel records it in *err, goes on and returns normally (the
+// host reports IGAMG_ETIMEOUT).  The last CTA to finish clears the row flags
+// and counters for the next sweep.
+template <typename T, int DIM, int P, bool WINDOW>
+__device__ __forceinline__ void gs_sweep_body(const LevelView<T>& L, int descending, T* x, const T* __restrict__ b,
+                                              T* TM, T* TK, const SweepSync& sy) {
+    constexpr int P1 = P + 1, W = 2 * P + 1;
+    constexpr int NPH = (DIM == 3) ? P1 * P1 : P1;
+    const int mx = L.m[0], my = L.m[1], mz = (DIM == 3) ? L.m[2] : 1;
+    const int rows = my * mz;
+    const GsSmem<T, DIM, P> g = gs_smem<T, DIM, P>(mx);
+    __shared__ int s_task[2];
+    __shared__ int s_last;
+    const int nb = gs_stage_band<T, P>(L, g.bm, g.bk);      // operator data: before the wait
+    const RowBand<T, P> band{L, g.bm, g.bk, nb};
+    pdl_enter();
+    if (threadIdx.x == 0) {
+        s_task[0] = (int)atomicAdd(&sy.ctr[0], 1u);
+        if (sy.test_unset && !wait_flag(sy.never, sy.limit_ns, sy.err)) atomicOr(sy.err, 1u);
+    }
+    __syncthreads();
+    for (int it = 0;; ++it) {
+        const int t = s_task[it & 1];
+        if (t >= rows) break;
+        if (threadIdx.x == 0) s_task[(it + 1) & 1] = (int)atomicAdd(&sy.ctr[0], 1u);
+        // claim index -> phase and row, phases in sweep order
+        int ph = 0, rem = t, cy = 0, cz = 0, nty = 0;
+        for (; ph < NPH; ++ph) {
+            const int c = descending ? NPH - 1 - ph : ph;
+            cy = c % P1;
+            cz = c / P1;
+            nty = (my - cy + P) / P1;
+            const int ntz = (DIM == 3) ? (mz - cz + P) / P1 : 1;
+            const int cnt = (nty > 0 && ntz > 0) ? nty * ntz : 0;
+            if (rem < cnt) break;
+            rem -= cnt;
+        }
+        const int j = cy + P1 * (rem % nty);
+        const int k = (DIM == 3) ? cz + P1 * (rem / nty) : 0;
+        const int row = k * my + j;
+        const size_t base = (size_t)row * mx;
+        row_couplings<T, DIM, P>(L, j, k, g.cM, g.cK, g.nrow);
+        if constexpr (DIM == 2)
+            for (int i = threadIdx.x; i < mx; i += blockDim.x) g.dv[i] = L.invdiag[base + i];
+        // wait for the neighbours of earlier phases (one thread each)
+        constexpr int NQ = (DIM == 3) ? W * W : W;
+        for (int q = threadIdx.x; q < NQ; q += blockDim.x) {
+            const int dj = (q % W) - P, dk = (DIM == 3) ? (q / W) - P : 0;
+            const int jj = j + dj, kk = k + dk;
+            if ((dj == 0 && dk == 0) || jj < 0 || jj >= my || kk < 0 || kk >= mz) continue;
+            const int c = (jj % P1) + P1 * (kk % P1);
+            const int phn = descending ? NPH - 1 - c : c;
+            if (phn < ph && !wait_flag(&sy.done[kk * my + jj], sy.limit_ns, sy.err)) atomicOr(sy.err, 1u);
+        }
+        __syncthreads();
+        gs_row<T, DIM, P, WINDOW, true>(L, g, band, base, descending, x, b, TM, TK);
+        __syncthreads();                            // every store of the row issued
+        if (threadIdx.x == 0) {
+            __threadfence();
+            st_release_gpu(&sy.done[row], 1u);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&sy.ctr[1], 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last) {                                   // every row is done: reset for the next sweep
+        __threadfence();
+        for (int r = threadIdx.x; r < rows; r += blockDim.x) sy.done[r] = 0u;
+        if (threadIdx.x == 0) {
+            sy.ctr[0] = 0u;
+            sy.ctr[1] = 0u;
+        }
+    }
+}
+
 // Kernels: one CTA per target row of the phase.  2D rows are compiled for two
 // resident 512-thread CTAs per SM (up to 64 registers; without that hint
 // ptxas settled on 32-40 registers and spilled, and one CTA per SM with 128
@@ -430,6 +630,16 @@ __global__ void __launch_bounds__(row_cta_max<T, 3>())
     k_gs_phase3(LevelView<T> L, int cy, int cz, int descending, T* __restrict__ x, const T* __restrict__ b,
                 T* __restrict__ TM, T* __restrict__ TK) {
     gs_phase_body<T, 3, P, WINDOW>(L, cy, cz, descending, x, b, TM, TK);
+}
+template <typename T, int P, bool WINDOW>
+__global__ void __launch_bounds__(row_cta_max<T, 2>(), 2)
+    k_gs_sweep2(LevelView<T> L, int descending, T* x, const T* __restrict__ b, T* TM, T* TK, SweepSync sy) {
+    gs_sweep_body<T, 2, P, WINDOW>(L, descending, x, b, TM, TK, sy);
+}
+template <typename T, int P, bool WINDOW>
+__global__ void __launch_bounds__(row_cta_max<T, 3>())
+    k_gs_sweep3(LevelView<T> L, int descending, T* x, const T* __restrict__ b, T* TM, T* TK, SweepSync sy) {
+    gs_sweep_body<T, 3, P, WINDOW>(L, descending, x, b, TM, TK, sy);
 }
 
 // ---------------------------------------------------------------- residual
@@ -1162,6 +1372,8 @@ void prepare_kernels() {
                 raise_smem(k_xpass<T, T, P>, optin);
                 raise_smem(k_gs_phase2<T, P, gs_window<T, 2, P>()>, optin);
                 raise_smem(k_gs_phase3<T, P, gs_window<T, 3, P>()>, optin);
+                raise_smem(k_gs_sweep2<T, P, gs_window<T, 2, P>()>, optin);
+                raise_smem(k_gs_sweep3<T, P, gs_window<T, 3, P>()>, optin);
                 raise_smem(k_prolong_last<T, 2, P>, optin);
                 raise_smem(k_prolong_last<T, 3, P>, optin);
                 raise_smem(k_residual_restrict_x<T, P>, optin);
@@ -1193,13 +1405,42 @@ void xpass(cudaStream_t s, const LevelView<T>& L, const T* x, T* x_out, const A*
     count_launch();
 }
 
+// CTAs of a single-launch sweep: as many as fit on the device at once (more
+// would only claim nothing and exit), at most one per row.
+template <typename K>
+static int resident_grid(K kernel, int threads, size_t smem, int rows) {
+    int dev = 0, nsm = 1, per = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem) != cudaSuccess || per < 1) per = 1;
+    const long long g = (long long)per * nsm;
+    return (int)(g < rows ? g : rows);
+}
+
 template <typename T>
 void gs_sweep(cudaStream_t s, int dim, const LevelView<T>& L, bool descending, T* x, const T* b,
-              T* TM, T* TK, int cap) {
+              T* TM, T* TK, int cap, const SweepSync* sy) {
     const int p = L.p, P1 = p + 1;
     const size_t smem = (size_t)6 * L.m[0] * sizeof(T);
     const int most = dim == 3 ? row_cta_max<T, 3>() : row_cta_max<T, 2>();
     const int threads = row_threads(L.m[0], (cap >= 64 && cap < most) ? cap : most);
+    if (sy) {
+        const int rows = L.rows();
+        with_p(p, [&](auto PC) {
+            constexpr int P = decltype(PC)::value;
+            if (dim == 2) {
+                constexpr bool WIN = gs_window<T, 2, P>();
+                const int grid = resident_grid(k_gs_sweep2<T, P, WIN>, threads, smem, rows);
+                launch_chained(k_gs_sweep2<T, P, WIN>, grid, threads, smem, s, L, (int)descending, x, b, TM, TK, *sy);
+            } else {
+                constexpr bool WIN = gs_window<T, 3, P>();
+                const int grid = resident_grid(k_gs_sweep3<T, P, WIN>, threads, smem, rows);
+                launch_chained(k_gs_sweep3<T, P, WIN>, grid, threads, smem, s, L, (int)descending, x, b, TM, TK, *sy);
+            }
+        });
+        count_launch();
+        return;
+    }
     auto launch = [&](int cy, int cz) {
         const int nty = (L.m[1] - cy + p) / P1;
         const int ntz = (dim == 3) ? (L.m[2] - cz + p) / P1 : 1;
@@ -1429,7 +1670,8 @@ void fill_zero(cudaStream_t s, T* p, size_t n) {
 #define IGAMG_INST(T)                                                                               \
     template void xpass<T, T>(cudaStream_t, const LevelView<T>&, const T*, T*, const T*, int,       \
                               const double*, const T*, size_t, T*, T*);                             \
-    template void gs_sweep<T>(cudaStream_t, int, const LevelView<T>&, bool, T*, const T*, T*, T*, int);  \
+    template void gs_sweep<T>(cudaStream_t, int, const LevelView<T>&, bool, T*, const T*, T*, T*, int,   \
+                              const SweepSync*);                                                     \
     template void jacobi_sweep<T>(cudaStream_t, int, const LevelView<T>&, T, T*, const T*, T*, T*, T*, T*);  \
     template void restrict_<T>(cudaStream_t, int, const TransferView<T>&, const T*, T*, T*, T*, T*, size_t);  \
     template void residual_restrict<T>(cudaStream_t, int, const LevelView<T>&, const TransferView<T>&,    \

@@ -141,17 +141,25 @@ def test_gs_sweep_fp32_finest(pkg, pair):
 
 
 def test_restrict_and_prolong_every_level(pkg, pair):
+    """The GPU's knot-insertion transfer against the oracle's L2-projection P =
+    M_f^{-1} G.  The oracle's P comes from a solve with the fine mass matrix,
+    so it is exact only to about cond(M_f) eps (cond(M_f) grows with p: 27 at
+    p = 3, 1.3e3 at p = 7); the tolerance is the larger of 1e-13 and twice that."""
     rng = np.random.default_rng(2)
     for l in range(1, len(pair.H.levels)):
         Nf, Nc = pair.H.levels[l].N, pair.H.levels[l - 1].N
+        kappa = max(np.linalg.cond(M) for M, _ in pair.H.levels[l].factors)
+        tol = max(1e-13, 2.0 * kappa * np.finfo(float).eps)
         r = rng.standard_normal(Nf)
         rc = torch.empty(Nc, dtype=torch.float64, device=DEV)
         pkg.igamg_restrict(pair.ctx, l, _t(r), rc, pair.ws)
-        assert _close(_np(rc), pair.H.P[l].T @ r, 1e-13)
+        ref = pair.H.P[l].T @ r
+        assert _close(_np(rc), ref, tol), (l, _rel(_np(rc), ref), _relmax(_np(rc), ref), tol)
         e, x0 = rng.standard_normal(Nc), rng.standard_normal(Nf)
         x = _t(x0)
         pkg.igamg_prolong(pair.ctx, l, _t(e), x, pair.ws)
-        assert _close(_np(x), x0 + pair.H.P[l] @ e, 1e-13)
+        ref = x0 + pair.H.P[l] @ e
+        assert _close(_np(x), ref, tol), (l, _rel(_np(x), ref), _relmax(_np(x), ref), tol)
 
 
 def test_coarse_solve(pkg, pair):
