@@ -64,6 +64,9 @@ typedef enum { IGAMG_SMOOTH_GS = 0, IGAMG_SMOOTH_JACOBI = 1 } igamg_smoother;
 #define IGAMG_FLAG_X0_GIVEN 1u   /* start from d_x instead of s_0 = 0 */
 #define IGAMG_FLAG_ABS_TOL  2u   /* test ||b - A t|| <= tol instead of ||b - A t|| / ||b|| <= tol */
 #define IGAMG_FLAG_NO_GRAPH 4u   /* enqueue kernels directly instead of replaying a CUDA graph */
+#define IGAMG_FLAG_HOST_LOOP 8u  /* test the residual on the host after every restart cycle (one graph
+                                    launch and one synchronisation per cycle) instead of running the
+                                    restart loop on the GPU */
 
 typedef struct igamg_ctx igamg_ctx;
 
@@ -119,8 +122,16 @@ igamg_status igamg_rhs_sine(igamg_ctx* ctx, int modes, const double* h_coeffs, d
  * s_0 with IGAMG_FLAG_X0_GIVEN).  h_hist (may be NULL) receives max_cycles+1
  * relative residuals: entry 0 for s_0, entry c after cycle c.  h_cycles and
  * h_vcycles receive the restart cycles and V-cycles run.
+ * The restart loop runs on the GPU: one CUDA graph holds a conditional WHILE
+ * node around the restart cycle, whose last kernel applies the accuracy test
+ * to the residual and sets the loop condition, so a solve is one graph launch
+ * and one host synchronisation (not with IGAMG_FLAG_HOST_LOOP or
+ * IGAMG_FLAG_NO_GRAPH, for IGAMG_FP32_IR_LEARNED, whose stall fallback
+ * switches smoothers between cycles, or for max_cycles >= 2047: then the
+ * host tests the residual after every cycle).  Same arithmetic either way.
  * Returns OK on convergence, ENOTCONV after max_cycles (d_x = last iterate),
- * EBREAKDOWN on a non-finite residual.  Synchronises `stream`. */
+ * EBREAKDOWN on a non-finite residual, ETIMEOUT when a bounded device wait of
+ * a single-launch sweep gave up.  Synchronises `stream`. */
 igamg_status igamg_solve(igamg_ctx* ctx, const double* d_b, double* d_x, double tol,
                          int extrap, int k, int max_cycles, int prec, unsigned flags,
                          void* d_ws, size_t ws_bytes, void* stream,
@@ -337,6 +348,15 @@ igamg_status igamg_batch_rhs_sine(igamg_batch* batch, int modes, const double* h
 igamg_status igamg_batch_solve(igamg_batch* batch, const double* d_b, double* d_x, double tol, int extrap,
                                int k, int max_cycles, int prec, void* d_ws, size_t ws_bytes, void* stream,
                                int* h_cycles, int* h_status, double* h_res);
+/* Where the batch's restart loops run.  enable = 1 (default): on the GPU, in
+ * one CUDA graph whose independent branches hold, per problem, a kernel that
+ * starts its loop (unless it converged at s_0 = 0) and a conditional WHILE
+ * node around its restart cycle, ended on the device by its own accuracy
+ * test; a batched solve is then one graph launch and one host
+ * synchronisation.  enable = 0: rounds of per-problem restart-cycle graphs on
+ * 128 streams, the host testing every residual after each round.  Same
+ * arithmetic either way.  Errors: EINVAL for a null batch. */
+igamg_status igamg_batch_set_device_loop(igamg_batch* batch, int enable);
 /* Autotunes the batch: for every degree, igamg_autotune on the problem of
  * median size; the problems of that degree take its GS row-CTA cap and a
  * coarse tail down to the same level size.  The workspace is the batch

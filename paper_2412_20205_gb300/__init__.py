@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libigamg.so")
 IGAMG_OK, IGAMG_EINVAL, IGAMG_ENOMEM, IGAMG_ECUDA, IGAMG_ENOTCONV, IGAMG_EBREAKDOWN, IGAMG_ETIMEOUT = range(7)
 IGAMG_EXTRAP_NONE, IGAMG_RRE, IGAMG_MPE = 0, 1, 2
 IGAMG_FP64, IGAMG_FP32_IR, IGAMG_FP32_IR_LEARNED = 0, 1, 2
-IGAMG_FLAG_X0_GIVEN, IGAMG_FLAG_ABS_TOL, IGAMG_FLAG_NO_GRAPH = 1, 2, 4
+IGAMG_FLAG_X0_GIVEN, IGAMG_FLAG_ABS_TOL, IGAMG_FLAG_NO_GRAPH, IGAMG_FLAG_HOST_LOOP = 1, 2, 4, 8
 IGAMG_SMOOTH_GS, IGAMG_SMOOTH_JACOBI = 0, 1
 SMOOTHER = {"gs": IGAMG_SMOOTH_GS, "jacobi": IGAMG_SMOOTH_JACOBI}
 
@@ -94,6 +94,7 @@ def _load():
         "igamg_batch_solve": (c_int, [vp, vp, vp, c_double, c_int, c_int, c_int, c_int, vp, c_size, vp,
                                       ip, ip, dp]),
         "igamg_batch_destroy": (None, [vp]),
+        "igamg_batch_set_device_loop": (c_int, [vp, c_int]),
         "igamg_status_str": (ctypes.c_char_p, [c_int]),
         "igamg_last_error": (ctypes.c_char_p, []),
         "igamg_launch_count": (ctypes.c_longlong, []),
@@ -400,6 +401,11 @@ def igamg_batch_solve(batch, count, b, x, tol, extrap, k, max_cycles, prec, ws, 
     return s, list(cyc), list(st), res
 
 
+def igamg_batch_set_device_loop(batch, enable):
+    """Batched restart loops on the GPU in one graph (True) or as host-driven rounds (False)."""
+    _check(_load().igamg_batch_set_device_loop(batch, 1 if enable else 0), "igamg_batch_set_device_loop")
+
+
 def igamg_batch_destroy(batch):
     _load().igamg_batch_destroy(batch)
 
@@ -439,12 +445,12 @@ class Solver:
         return b
 
     def solve(self, b, x=None, tol=1e-10, method="rre", k=5, max_cycles=200, prec="fp64",
-              x0_given=False, absolute=False, graph=True):
+              x0_given=False, absolute=False, graph=True, host_loop=False):
         import torch
         if x is None:
             x = torch.zeros(self.N, dtype=torch.float64, device=self.ws.device)
         flags = (IGAMG_FLAG_X0_GIVEN if x0_given else 0) | (IGAMG_FLAG_ABS_TOL if absolute else 0) | \
-                (0 if graph else IGAMG_FLAG_NO_GRAPH)
+                (0 if graph else IGAMG_FLAG_NO_GRAPH) | (IGAMG_FLAG_HOST_LOOP if host_loop else 0)
         st, hist, cyc, vc = igamg_solve(self.ctx, b, x, tol, EXTRAP[method], k, max_cycles, PREC[prec],
                                         flags, self.ws)
         out = dict(x=x, status=st, history=hist, cycles=cyc, vcycles=vc, converged=st == IGAMG_OK)

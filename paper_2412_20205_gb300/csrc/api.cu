@@ -92,6 +92,8 @@ struct Workspace {
     std::vector<unsigned*> done, ctr;
     unsigned* err = nullptr;
     unsigned* never = nullptr;
+    LoopState* loop = nullptr;   // device-side restart loop: state and residual history
+    double* hist = nullptr;
     size_t bytes = 0;
 };
 
@@ -151,6 +153,14 @@ struct igamg_ctx {
                    abs_tol == o.abs_tol && overlap == o.overlap && sync == o.sync && w == o.w;
         }
     } key[3];
+    // device-side restart loops (a conditional WHILE node around one restart
+    // cycle), one per precision form, keyed like exec[]; body_launches =
+    // kernels per cycle; h_loop / h_hist: pinned staging of state and history
+    cudaGraphExec_t loop_exec[3] = {nullptr, nullptr, nullptr};
+    long long loop_body_launches[3] = {0, 0, 0};
+    Key loop_key[3];
+    LoopState* h_loop = nullptr;
+    double* h_hist = nullptr;
     // learned post-smoother: caller-owned device weights, stall ratio, outcome
     const float* cnn_w = nullptr;
     double stall = 0.9;
@@ -202,6 +212,8 @@ Workspace carve(const igamg_ctx* c, void* base, int k, int prec) {
     w.qused = cv.take<int>(4);
     w.info = cv.take<ExtrapInfo>(1);
     w.scal = cv.take<double>(8);
+    w.loop = cv.take<LoopState>(1);
+    w.hist = cv.take<double>(kLoopHist);
     w.nsync = 2;
     for (int l = 0; l < L; ++l) w.nsync += 2 + (size_t)c->hl[l].m[1] * c->hl[l].m[2];
     w.sync = cv.take<unsigned>(w.nsync);
@@ -584,6 +596,53 @@ igamg_status ensure_graph(igamg_ctx* c, Workspace& w, const double* d_b, void* d
     return IGAMG_OK;
 }
 
+// Capture the device-side restart loop of this context: a graph holding one
+// conditional WHILE node (condition 1 at launch) whose body is one restart
+// cycle followed by loop_step, which records the residual and clears the
+// condition once the accuracy test passes, max_cycles is reached, the
+// residual is not finite or a device wait gave up.  Cached like ensure_graph.
+igamg_status ensure_loop_graph(igamg_ctx* c, Workspace& w, const double* d_b, void* d_ws, int kk, int extrap,
+                               int prec, const double* denom) {
+    const int slot = prec;
+    igamg_ctx::Key key;
+    key.b = d_b; key.ws = d_ws; key.k = kk; key.extrap = extrap; key.prec = prec;
+    key.abs_tol = denom == nullptr;
+    key.overlap = launch_overlap() ? 1 : 0;
+    key.sync = sync_generation();
+    if (c->loop_exec[slot] && c->loop_key[slot] == key) return IGAMG_OK;
+    if (c->loop_exec[slot]) { cudaGraphExecDestroy(c->loop_exec[slot]); c->loop_exec[slot] = nullptr; }
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(cudaGraphCreate(&g, 0));
+    struct GraphGuard { cudaGraph_t g; ~GraphGuard() { if (g) cudaGraphDestroy(g); } } guard{g};
+    cudaGraphConditionalHandle h;
+    CUDA_TRY(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    CUDA_TRY(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    const long long before = launch_count();
+    CUDA_TRY(cudaStreamBeginCaptureToGraph(c->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    restart_body(c, c->cap, w, extrap, kk, prec, d_b, denom);
+    dev::loop_step(c->cap, h, w.loop, w.scal + 1, w.err, w.hist);
+    cudaGraph_t got = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(c->cap, &got);
+    const long long body_launches = launch_count() - before;
+    count_launch(-body_launches);
+    if (ce != cudaSuccess) return fail(IGAMG_ECUDA, std::string("loop capture: ") + cudaGetErrorString(ce));
+    ce = cudaGraphInstantiate(&c->loop_exec[slot], g, 0);
+    if (ce != cudaSuccess) {
+        c->loop_exec[slot] = nullptr;
+        return fail(IGAMG_ECUDA, std::string("loop instantiate: ") + cudaGetErrorString(ce));
+    }
+    c->loop_body_launches[slot] = body_launches;
+    c->loop_key[slot] = key;
+    return IGAMG_OK;
+}
+
 }  // namespace
 
 // ======================================================================= C ABI
@@ -950,6 +1009,8 @@ igamg_status igamg_assemble(igamg_ctx* c) {
     }
     CUDA_TRY(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
     CUDA_TRY(cudaMallocHost(&c->h_pin, 64));
+    CUDA_TRY(cudaMallocHost(&c->h_loop, sizeof(LoopState)));
+    CUDA_TRY(cudaMallocHost(&c->h_hist, sizeof(double) * kLoopHist));
     c->assembled = true;
     return IGAMG_OK;
 }
@@ -1040,6 +1101,41 @@ igamg_status igamg_solve(igamg_ctx* c, const double* d_b, double* d_x, double to
     igamg_status result = IGAMG_ENOTCONV;
     if (res <= tol) result = IGAMG_OK;
     const bool use_graph = !(flags & IGAMG_FLAG_NO_GRAPH);
+    // The restart loop of Algorithm 5 runs on the GPU (one graph launch and one
+    // synchronisation per solve) unless the caller asks for the host loop, the
+    // graph is off, or the learned form may switch smoothers between cycles.
+    const bool device_loop = use_graph && !(flags & IGAMG_FLAG_HOST_LOOP) && prec != IGAMG_FP32_IR_LEARNED &&
+                             max_cycles < kLoopHist;
+    if (device_loop && result != IGAMG_OK && max_cycles > 0) {
+        if (igamg_status st = ensure_loop_graph(c, w, d_b, d_ws, kk, extrap, prec, denom)) return st;
+        LoopState* hs = c->h_loop;
+        hs->cyc = 0;
+        hs->max_cycles = max_cycles;
+        hs->code = kLoopRunning;
+        hs->pad = 0;
+        hs->tol = tol;
+        hs->res = res;
+        CUDA_TRY(cudaMemcpyAsync(w.loop, hs, sizeof(LoopState), cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaGraphLaunch(c->loop_exec[prec], s));
+        CUDA_TRY(cudaMemcpyAsync(hs, w.loop, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaMemcpyAsync(c->h_hist, w.hist, sizeof(double) * (max_cycles + 1), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        const int n = hs->cyc;
+        count_launch((long long)n * c->loop_body_launches[prec]);
+        if (h_hist)
+            for (int i = 1; i <= n; ++i) h_hist[i] = c->h_hist[i];
+        if (h_cycles) *h_cycles = n;
+        if (h_vcycles) *h_vcycles = n * (extrap == IGAMG_EXTRAP_NONE ? 1 : kk + 1);
+        switch (hs->code) {
+            case kLoopConverged: result = IGAMG_OK; break;
+            case kLoopBreakdown: result = fail(IGAMG_EBREAKDOWN, "non-finite residual"); break;
+            case kLoopTimeout:
+                result = fail(IGAMG_ETIMEOUT, "a bounded device-side wait of a Gauss-Seidel sweep gave up");
+                break;
+            default: result = IGAMG_ENOTCONV; break;
+        }
+        max_cycles = 0;                                // the host loop below has nothing left to do
+    }
     int cur = prec;                                    // the learned form may fall back to plain smoothing
     if (use_graph && result != IGAMG_OK && max_cycles > 0)
         if (igamg_status st = ensure_graph(c, w, d_b, d_ws, kk, extrap, cur, denom)) return st;
@@ -1271,12 +1367,18 @@ int igamg_coarse_tail_level(const igamg_ctx* c) {
 }
 
 static void drop_graphs(igamg_ctx* c) {
-    for (int sl = 0; sl < 3; ++sl)
+    for (int sl = 0; sl < 3; ++sl) {
         if (c->exec[sl]) {
             cudaGraphExecDestroy(c->exec[sl]);
             c->exec[sl] = nullptr;
             c->key[sl] = igamg_ctx::Key{};
         }
+        if (c->loop_exec[sl]) {
+            cudaGraphExecDestroy(c->loop_exec[sl]);
+            c->loop_exec[sl] = nullptr;
+            c->loop_key[sl] = igamg_ctx::Key{};
+        }
+    }
 }
 
 igamg_status igamg_set_schedule(igamg_ctx* c, int gs_threads, int tail_levels) {
@@ -1442,6 +1544,10 @@ void igamg_destroy(igamg_ctx* c) {
         if (c->exec[sl]) cudaGraphExecDestroy(c->exec[sl]);
     if (c->cap) cudaStreamDestroy(c->cap);
     if (c->h_pin) cudaFreeHost(c->h_pin);
+    for (int sl = 0; sl < 3; ++sl)
+        if (c->loop_exec[sl]) cudaGraphExecDestroy(c->loop_exec[sl]);
+    if (c->h_loop) cudaFreeHost(c->h_loop);
+    if (c->h_hist) cudaFreeHost(c->h_hist);
     if (c->dmem) cudaFree(c->dmem);
     delete c;
 }
@@ -1463,6 +1569,15 @@ struct igamg_batch {
     cudaEvent_t ev = nullptr;
     double* h_pin = nullptr;                // 2 per problem: ||b||, last residual
     unsigned* h_err = nullptr;              // per problem: its workspace's device-wait error word
+    // device-side loops: one graph whose independent branches are, per
+    // problem, an init kernel and a conditional WHILE node around that
+    // problem's restart cycle; d_state / h_state: per-problem loop states
+    bool device_loop = true;
+    LoopState* d_state = nullptr;
+    LoopState* h_state = nullptr;
+    cudaGraphExec_t loop_exec[2] = {nullptr, nullptr};
+    igamg_ctx::Key loop_key[2];
+    std::vector<long long> body_launches[2];
 };
 
 namespace {
@@ -1479,6 +1594,56 @@ std::vector<size_t> batch_ws_offsets(const igamg_batch* B, int k, int prec) {
     for (int i = 0; i < B->count; ++i)
         off[i + 1] = off[i] + ((carve(B->ctx[i], nullptr, k, prec).bytes + 255) & ~(size_t)255);
     return off;
+}
+
+// The batch's device-side loops in one graph (see igamg_batch::device_loop):
+// problem i contributes a root init kernel (condition = state i running) and
+// a WHILE node after it whose body is its restart cycle and loop_step.
+igamg_status ensure_batch_loop_graph(igamg_batch* B, std::vector<Workspace>& W, const std::vector<size_t>& wo,
+                                     const double* d_b, void* d_ws, int k, int extrap, int prec) {
+    igamg_ctx::Key key;
+    key.b = d_b; key.ws = d_ws; key.k = k; key.extrap = extrap; key.prec = prec;
+    key.abs_tol = 0;
+    key.overlap = launch_overlap() ? 1 : 0;
+    key.sync = sync_generation();
+    if (B->loop_exec[prec] && B->loop_key[prec] == key) return IGAMG_OK;
+    if (B->loop_exec[prec]) { cudaGraphExecDestroy(B->loop_exec[prec]); B->loop_exec[prec] = nullptr; }
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(cudaGraphCreate(&g, 0));
+    struct GraphGuard { cudaGraph_t g; ~GraphGuard() { if (g) cudaGraphDestroy(g); } } guard{g};
+    B->body_launches[prec].assign(B->count, 0);
+    cudaStream_t cap = B->ctx[0]->cap;
+    for (int i = 0; i < B->count; ++i) {
+        igamg_ctx* c = B->ctx[i];
+        cudaGraphConditionalHandle h;
+        CUDA_TRY(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
+        cudaGraphNode_t init;
+        CUDA_TRY(dev::add_loop_init_node(g, h, B->d_state + i, &init));
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        CUDA_TRY(cudaGraphAddNode(&node, g, &init, nullptr, 1, &np));
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        const long long before = launch_count();
+        CUDA_TRY(cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        restart_body(c, cap, W[i], extrap, k, prec, d_b + B->voff[i], W[i].scal);
+        dev::loop_step(cap, h, B->d_state + i, W[i].scal + 1, W[i].err, nullptr);
+        cudaGraph_t got = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(cap, &got);
+        B->body_launches[prec][i] = launch_count() - before;
+        count_launch(-B->body_launches[prec][i]);
+        if (ce != cudaSuccess) return fail(IGAMG_ECUDA, std::string("batch loop capture: ") + cudaGetErrorString(ce));
+    }
+    const cudaError_t ce = cudaGraphInstantiate(&B->loop_exec[prec], g, 0);
+    if (ce != cudaSuccess) {
+        B->loop_exec[prec] = nullptr;
+        return fail(IGAMG_ECUDA, std::string("batch loop instantiate: ") + cudaGetErrorString(ce));
+    }
+    B->loop_key[prec] = key;
+    return IGAMG_OK;
 }
 }  // namespace
 
@@ -1512,6 +1677,8 @@ igamg_status igamg_batch_create(int count, int dim, const int* p, const int* n, 
     CUDA_TRY(cudaEventCreateWithFlags(&B->ev, cudaEventDisableTiming));
     CUDA_TRY(cudaMallocHost(&B->h_pin, sizeof(double) * 2 * count));
     CUDA_TRY(cudaMallocHost(&B->h_err, sizeof(unsigned) * count));
+    CUDA_TRY(cudaMallocHost(&B->h_state, sizeof(LoopState) * count));
+    CUDA_TRY(cudaMalloc(&B->d_state, sizeof(LoopState) * count));
     *out = B;
     return IGAMG_OK;
 }
@@ -1568,10 +1735,15 @@ igamg_status igamg_batch_solve(igamg_batch* B, const double* d_b, double* d_x, d
         residual_norm(c, s, w, b, w.scal);
         CUDA_TRY(cudaMemcpyAsync(B->h_pin + 2 * i, w.scal, 16, cudaMemcpyDeviceToHost, s));
     }
-    for (int i = 0; i < B->count; ++i)
-        if (igamg_status st = ensure_graph(B->ctx[i], W[i], d_b + B->voff[i], (char*)d_ws + wo[i], k, extrap, prec,
-                                           W[i].scal))
-            return st;
+    const bool device_loop = B->device_loop;
+    if (device_loop) {
+        if (igamg_status st = ensure_batch_loop_graph(B, W, wo, d_b, d_ws, k, extrap, prec)) return st;
+    } else {
+        for (int i = 0; i < B->count; ++i)
+            if (igamg_status st = ensure_graph(B->ctx[i], W[i], d_b + B->voff[i], (char*)d_ws + wo[i], k, extrap,
+                                               prec, W[i].scal))
+                return st;
+    }
     for (auto s : B->streams) CUDA_TRY(cudaStreamSynchronize(s));
     CUDA_TRY(cudaGetLastError());
     for (int i = 0; i < B->count; ++i) {
@@ -1580,6 +1752,39 @@ igamg_status igamg_batch_solve(igamg_batch* B, const double* d_b, double* d_x, d
         if (!std::isfinite(bn)) stat[i] = IGAMG_EBREAKDOWN;
         else if (bn == 0.0) { stat[i] = IGAMG_OK; if (h_res) h_res[i] = 0.0; }
         else if (r <= tol) stat[i] = IGAMG_OK;
+    }
+    if (device_loop && max_cycles > 0) {
+        // every problem's restart loop on the GPU: one graph launch
+        for (int i = 0; i < B->count; ++i) {
+            LoopState& ls = B->h_state[i];
+            ls.cyc = 0;
+            ls.max_cycles = max_cycles;
+            ls.code = stat[i] == IGAMG_ENOTCONV ? kLoopRunning : kLoopConverged;
+            ls.pad = 0;
+            ls.tol = tol;
+            ls.res = B->h_pin[2 * i + 1];
+        }
+        CUDA_TRY(cudaMemcpyAsync(B->d_state, B->h_state, sizeof(LoopState) * B->count, cudaMemcpyHostToDevice,
+                                 caller));
+        CUDA_TRY(cudaGraphLaunch(B->loop_exec[prec], caller));
+        CUDA_TRY(cudaMemcpyAsync(B->h_state, B->d_state, sizeof(LoopState) * B->count, cudaMemcpyDeviceToHost,
+                                 caller));
+        CUDA_TRY(cudaStreamSynchronize(caller));
+        CUDA_TRY(cudaGetLastError());
+        for (int i = 0; i < B->count; ++i) {
+            if (stat[i] != IGAMG_ENOTCONV) continue;
+            const LoopState& ls = B->h_state[i];
+            cyc[i] = ls.cyc;
+            count_launch((long long)ls.cyc * B->body_launches[prec][i]);
+            if (h_res) h_res[i] = ls.res;
+            stat[i] = ls.code == kLoopConverged ? IGAMG_OK
+                      : ls.code == kLoopBreakdown ? IGAMG_EBREAKDOWN
+                      : ls.code == kLoopTimeout ? IGAMG_ETIMEOUT
+                                                : IGAMG_ENOTCONV;
+        }
+        CUDA_TRY(cudaEventRecord(B->ev, caller));
+        for (auto s : B->streams) CUDA_TRY(cudaStreamWaitEvent(s, B->ev, 0));
+        max_cycles = 0;                             // the per-round host loop below has nothing left to do
     }
     for (int round = 1; round <= max_cycles; ++round) {
         int active = 0;
@@ -1623,9 +1828,21 @@ igamg_status igamg_batch_solve(igamg_batch* B, const double* d_b, double* d_x, d
     return all;
 }
 
+igamg_status igamg_batch_set_device_loop(igamg_batch* B, int enable) {
+    if (!B) return fail(IGAMG_EINVAL, "null batch");
+    B->device_loop = enable != 0;
+    return IGAMG_OK;
+}
+
 igamg_status igamg_batch_autotune(igamg_batch* B, void* d_ws, size_t ws_bytes, void* stream, int reps) {
     const NoOverlapScope serial;                // time the schedules as batched solves run them
     if (!B || !d_ws) return fail(IGAMG_EINVAL, "bad batch autotune arguments");
+    for (int sl = 0; sl < 2; ++sl)              // members' schedules change: recapture the loops
+        if (B->loop_exec[sl]) {
+            cudaGraphExecDestroy(B->loop_exec[sl]);
+            B->loop_exec[sl] = nullptr;
+            B->loop_key[sl] = igamg_ctx::Key{};
+        }
     const std::vector<size_t> off = batch_ws_offsets(B, 1, IGAMG_FP32_IR);
     if (off.back() > ws_bytes) return fail(IGAMG_ENOMEM, "batch workspace too small (size it for IGAMG_FP32_IR)");
     // one tuning run per degree, on the problem of median size; the others
@@ -1662,6 +1879,10 @@ void igamg_batch_destroy(igamg_batch* B) {
     if (B->ev) cudaEventDestroy(B->ev);
     if (B->h_pin) cudaFreeHost(B->h_pin);
     if (B->h_err) cudaFreeHost(B->h_err);
+    if (B->h_state) cudaFreeHost(B->h_state);
+    if (B->d_state) cudaFree(B->d_state);
+    for (auto& e : B->loop_exec)
+        if (e) cudaGraphExecDestroy(e);
     delete B;
 }
 

@@ -498,6 +498,209 @@ __global__ void __launch_bounds__(kT) k_conv2_dgrad(Shape s, const __nv_bfloat16
     }
 }
 
+// ------------------------------------------------------------------ training on the tensor cores
+// The remaining contractions of the training step as implicit GEMMs on
+// mma.sync.m16n8k16 (BF16 operands, FP32 accumulation), one warp per strip
+// of 16 consecutive pixels.
+
+// BF16 bits of channel c of pixel q of a channel-last activation (0 outside).
+__device__ __forceinline__ uint32_t act_bits(const __nv_bfloat16* a, long long q, int c) {
+    return q >= 0 ? (uint32_t)__bfloat16_as_ushort(a[q * C + c]) : 0u;
+}
+__device__ __forceinline__ uint32_t f_bits(float v) { return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v)); }
+__device__ __forceinline__ uint32_t pk(uint32_t lo, uint32_t hi) { return lo | (hi << 16); }
+
+// Nine-tap layers with one input channel: out[p][c] = sum_t w9[c][t] in[q(p, t)],
+// M = the strip's pixels, N = 16 channels (two n-tiles), K = 9 taps padded to
+// 16.  FLIP reads in[] through the mirrored tap (the adjoint of a 16 -> 1
+// layer).  MODE 0 (layer 1 forward): out = relu(.); MODE 1 (layer 3 input
+// gradient): out = . where mask[p][c] > 0, else 0.
+template <bool FLIP, int MODE>
+__global__ void __launch_bounds__(kT) k_tap9_tc(Shape s, const float* __restrict__ in, const float* __restrict__ w9,
+                                                const __nv_bfloat16* __restrict__ mask, __nv_bfloat16* __restrict__ out) {
+    __shared__ float W[C * 9];
+    for (int i = threadIdx.x; i < C * 9; i += blockDim.x) W[i] = w9[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
+    // B fragments (k = tap, n = channel), fixed for the kernel
+    uint32_t b[2][2];
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+        const int c = nt * 8 + g;
+        b[nt][0] = pk(f_bits(W[c * 9 + 2 * tq]), f_bits(W[c * 9 + 2 * tq + 1]));
+        b[nt][1] = tq == 0 ? pk(f_bits(W[c * 9 + 8]), 0u) : 0u;
+    }
+    const long long P = s.pixels();
+    const long long strips = (P + 15) / 16;
+    for (long long st = (long long)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); st < strips;
+         st += (long long)gridDim.x * (blockDim.x / 32)) {
+        const long long p0 = st * 16;
+        const long long pa = p0 + g, pb = p0 + g + 8;
+        const Pix xa(s, pa < P ? pa : 0), xb(s, pb < P ? pb : 0);
+        auto v = [&](const Pix& x, long long p, int t) -> uint32_t {
+            if (p >= P || t > 8) return 0u;
+            const long long q = x.nb(s, FLIP ? 8 - t : t);
+            return q >= 0 ? f_bits(in[q]) : 0u;
+        };
+        uint32_t a[4];
+        a[0] = pk(v(xa, pa, 2 * tq), v(xa, pa, 2 * tq + 1));
+        a[1] = pk(v(xb, pb, 2 * tq), v(xb, pb, 2 * tq + 1));
+        a[2] = pk(v(xa, pa, 2 * tq + 8), 0u);
+        a[3] = pk(v(xb, pb, 2 * tq + 8), 0u);
+        float acc[2][4] = {};
+        mma_bf16(acc[0], a, b[0]);
+        mma_bf16(acc[1], a, b[1]);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const long long p = p0 + g + 8 * h;
+            if (p >= P) continue;
+            __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(out + p * C);
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                float v0 = acc[nt][2 * h], v1 = acc[nt][2 * h + 1];
+                if (MODE == 0) {
+                    v0 = fmaxf(v0, 0.f);
+                    v1 = fmaxf(v1, 0.f);
+                } else {
+                    const float2 m = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162*>(mask + p * C)[nt * 4 + tq]);
+                    v0 = m.x > 0.f ? v0 : 0.f;
+                    v1 = m.y > 0.f ? v1 : 0.f;
+                }
+                o[nt * 4 + tq] = __floats2bfloat162_rn(v0, v1);
+            }
+        }
+    }
+}
+
+// y = W3 * a2 (layer 3, 16 -> 1) with the 16 -> 16 strip contraction: the
+// weight table holds W3 in output column 0 and zeros elsewhere.
+__global__ void __launch_bounds__(kT) k_conv3_tc(Shape s, const __nv_bfloat16* __restrict__ a2, const float* __restrict__ w,
+                                                 float* __restrict__ y) {
+    __shared__ float Wt[9 * C * C];                 // [tap][ci][n], n = 0 only
+    for (int i = threadIdx.x; i < 9 * C * C; i += blockDim.x) {
+        const int t = i / (C * C), ci = (i / C) % C, n = i % C;
+        Wt[i] = n == 0 ? w[NW1 + NW2 + ci * 9 + t] : 0.f;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
+    const long long P = s.pixels();
+    const long long strips = (P + 15) / 16;
+    for (long long st = (long long)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); st < strips;
+         st += (long long)gridDim.x * (blockDim.x / 32)) {
+        const long long p0 = st * 16;
+        float acc[8];
+        conv16_strip<false>(s, p0, a2, Wt, acc);
+        if (tq == 0) {                              // column 0 of n-tile 0: rows g and g + 8
+            if (p0 + g < P) y[p0 + g] = acc[0];
+            if (p0 + g + 8 < P) y[p0 + g + 8] = acc[2];
+        }
+    }
+}
+
+// Weight gradients on the tensor cores, K = pixels.  Per strip of 16 pixels:
+//   dW2[co][ci][t] += sum_p g2[p][co] a1[q(p,t)][ci]   (M = co, N = (t, ci): 18 n-tiles)
+//   dW1[co][t]     += sum_p g1[p][co] r[q(p,t)]        (M = co, N = t: 2 n-tiles)
+//   dW3[c][t]      += sum_q a2[q][c] gy[q(q,8-t)]      (the same sum as sum_p gy[p] a2[q(p,t)][c],
+//                                                        indexed by the pixel a2 is read at)
+// The A operands (channel x pixel) are the transposed channel-last tensors.
+// Each warp keeps its sums over a fixed sequence of strips and writes them to
+// its own row of `partial`; k_reduce adds the rows in fixed order, so the
+// gradient is deterministic.
+constexpr int kWgradWarpsPerBlock = kT / 32;
+
+__global__ void __launch_bounds__(kT) k_wgrad_tc(Shape s, const float* __restrict__ r, const __nv_bfloat16* __restrict__ a1,
+                                                 const __nv_bfloat16* __restrict__ a2, const __nv_bfloat16* __restrict__ g1,
+                                                 const __nv_bfloat16* __restrict__ g2, const float* __restrict__ gy,
+                                                 float* __restrict__ partial) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
+    const int warp = blockIdx.x * kWgradWarpsPerBlock + (threadIdx.x >> 5);
+    const int nwarps = gridDim.x * kWgradWarpsPerBlock;
+    float acc2[18][4] = {}, acc1[2][4] = {}, acc3[2][4] = {};
+    const long long P = s.pixels();
+    const long long strips = (P + 15) / 16;
+    for (long long st = warp; st < strips; st += nwarps) {
+        const long long p0 = st * 16;
+        long long pk4[4] = {p0 + 2 * tq, p0 + 2 * tq + 1, p0 + 2 * tq + 8, p0 + 2 * tq + 9};
+        Pix px[4] = {Pix(s, 0), Pix(s, 0), Pix(s, 0), Pix(s, 0)};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (pk4[i] < P) px[i] = Pix(s, pk4[i]);
+            else pk4[i] = -1;
+        }
+        // A fragments (m = channel g / g + 8, k = pixels 2tq, 2tq+1 / 2tq+8, 2tq+9)
+        auto afrag = [&](const __nv_bfloat16* x, uint32_t* a) {
+            a[0] = pk(act_bits(x, pk4[0], g), act_bits(x, pk4[1], g));
+            a[1] = pk(act_bits(x, pk4[0], g + 8), act_bits(x, pk4[1], g + 8));
+            a[2] = pk(act_bits(x, pk4[2], g), act_bits(x, pk4[3], g));
+            a[3] = pk(act_bits(x, pk4[2], g + 8), act_bits(x, pk4[3], g + 8));
+        };
+        uint32_t A2[4], A1[4], A3[4];
+        afrag(g2, A2);
+        afrag(g1, A1);
+        afrag(a2, A3);
+        auto nbq = [&](int i, int t) -> long long { return pk4[i] >= 0 ? px[i].nb(s, t) : -1; };
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+            long long q[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) q[i] = nbq(i, t);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                uint32_t b[2];
+                b[0] = pk(act_bits(a1, q[0], 8 * h + g), act_bits(a1, q[1], 8 * h + g));
+                b[1] = pk(act_bits(a1, q[2], 8 * h + g), act_bits(a1, q[3], 8 * h + g));
+                mma_bf16(acc2[2 * t + h], A2, b);
+            }
+        }
+        // dW1 and dW3: n = tap (g in n-tile 0, tap 8 at column 0 of n-tile 1)
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+            const int tap = nt == 0 ? g : (g == 0 ? 8 : -1);
+            uint32_t b1[2] = {0u, 0u}, b3[2] = {0u, 0u};
+            if (tap >= 0) {
+                long long q1[4], q3[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    q1[i] = nbq(i, tap);
+                    q3[i] = nbq(i, 8 - tap);
+                }
+                auto rv = [&](long long q) { return q >= 0 ? f_bits(r[q]) : 0u; };
+                auto gv = [&](long long q) { return q >= 0 ? f_bits(gy[q]) : 0u; };
+                b1[0] = pk(rv(q1[0]), rv(q1[1]));
+                b1[1] = pk(rv(q1[2]), rv(q1[3]));
+                b3[0] = pk(gv(q3[0]), gv(q3[1]));
+                b3[1] = pk(gv(q3[2]), gv(q3[3]));
+            }
+            mma_bf16(acc1[nt], A1, b1);
+            mma_bf16(acc3[nt], A3, b3);
+        }
+    }
+    // C fragments: rows (co / c) g and g + 8, columns 2tq, 2tq + 1 of each n-tile
+    float* row = partial + (size_t)warp * NW;
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+        const int co = g + 8 * hh;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+#pragma unroll
+            for (int t = 0; t < 9; ++t)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int ci = 8 * h + 2 * tq + j;
+                    row[NW1 + (co * C + ci) * 9 + t] = acc2[2 * t + h][2 * hh + j];
+                }
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                const int tap = nt * 8 + 2 * tq + j;
+                if (tap < 9) {
+                    row[co * 9 + tap] = acc1[nt][2 * hh + j];
+                    row[NW1 + NW2 + co * 9 + tap] = acc3[nt][2 * hh + j];
+                }
+            }
+        }
+    }
+}
+
 // Weight gradients: per-block partial sums over a tile of pixels, one weight
 // per (thread, slot); the final reduction over blocks runs in fixed order.
 // dW1[co][t] = sum_p g1[p][co] r[nb(p,t)]; dW2[co][ci][t] = sum_p g2[p][co] a1[nb(p,t)][ci];
@@ -605,11 +808,12 @@ static int grid(long long n, int per) {
     if (g > 152 * 8) g = 152 * 8;
     return (int)(g < 1 ? 1 : g);
 }
-constexpr int kWgradBlocks = 304;
+constexpr int kWgradBlocks = 152;
+constexpr int kWgradRows = kWgradBlocks * kWgradWarpsPerBlock;      // partial-sum rows (one per warp)
 
 size_t workspace_bytes(long long P) {
     const size_t act = ((size_t)P * C * 2 + 255) / 256 * 256;      // one BF16 channel-last tensor
-    return 4 * act + ((size_t)P * 4 + 255) / 256 * 256 + (size_t)kWgradBlocks * NW * 4 + 8 * 1024 * 8 + 1024;
+    return 4 * act + ((size_t)P * 4 + 255) / 256 * 256 + (size_t)kWgradRows * NW * 4 + 8 * 1024 * 8 + 1024;
 }
 
 struct WS {
@@ -628,7 +832,7 @@ static WS carve_ws(void* base, long long P) {
     w.g1 = (__nv_bfloat16*)p; p += act;
     w.g2 = (__nv_bfloat16*)p; p += act;
     w.gy = (float*)p; p += ((size_t)P * 4 + 255) / 256 * 256;
-    w.partial = (float*)p; p += (size_t)kWgradBlocks * NW * 4;
+    w.partial = (float*)p; p += (size_t)kWgradRows * NW * 4;
     w.lpart = (double*)p;
     return w;
 }
@@ -637,9 +841,10 @@ static WS carve_ws(void* base, long long P) {
 void forward_stored(cudaStream_t st, Shape s, const float* r, const float* w, float* y, void* ws) {
     WS W = carve_ws(ws, s.pixels());
     const long long P = s.pixels();
-    k_conv1<<<grid(P, kT), kT, 0, st>>>(s, r, w, W.a1);
-    k_conv2<<<grid((P + 15) / 16, kT / 32), kT, 0, st>>>(s, W.a1, w, W.a2);
-    k_conv3<<<grid(P, kT), kT, 0, st>>>(s, W.a2, w, y, 0);
+    const int gs = grid((P + 15) / 16, kT / 32);
+    k_tap9_tc<false, 0><<<gs, kT, 0, st>>>(s, r, w, nullptr, W.a1);
+    k_conv2<<<gs, kT, 0, st>>>(s, W.a1, w, W.a2);
+    k_conv3_tc<<<gs, kT, 0, st>>>(s, W.a2, w, y);
     count_launch(3);
 }
 
@@ -670,10 +875,11 @@ void gradient(cudaStream_t st, Shape s, const float* r, const float* e, const fl
     forward_stored(st, s, r, w, y, ws);
     const int gl = grid(P, kT) > 1024 ? 1024 : grid(P, kT);
     k_loss<<<gl, kT, 0, st>>>(s, y, e, W.gy, W.lpart);
-    k_conv3_dgrad<<<grid(P, kT), kT, 0, st>>>(s, W.gy, w, W.a2, W.g2);
-    k_conv2_dgrad<<<grid((P + 15) / 16, kT / 32), kT, 0, st>>>(s, W.g2, w, W.a1, W.g1);
-    k_wgrad<<<kWgradBlocks, kT, 0, st>>>(s, r, W.a1, W.a2, W.g1, W.g2, W.gy, W.partial);
-    k_reduce<<<(NW + 255) / 256, 256, 0, st>>>(W.partial, kWgradBlocks, W.lpart, gl, P, grad, loss);
+    const int gs = grid((P + 15) / 16, kT / 32);
+    k_tap9_tc<true, 1><<<gs, kT, 0, st>>>(s, W.gy, w + NW1 + NW2, W.a2, W.g2);
+    k_conv2_dgrad<<<gs, kT, 0, st>>>(s, W.g2, w, W.a1, W.g1);
+    k_wgrad_tc<<<kWgradBlocks, kT, 0, st>>>(s, r, W.a1, W.a2, W.g1, W.g2, W.gy, W.partial);
+    k_reduce<<<(NW + 255) / 256, 256, 0, st>>>(W.partial, kWgradRows, W.lpart, gl, P, grad, loss);
     count_launch(5);
 }
 

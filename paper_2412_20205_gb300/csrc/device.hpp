@@ -116,6 +116,19 @@ long long wait_limit_ns();
 int wait_test_unset();
 int sync_generation();
 
+// Device-side state of the restart loop of Algorithm 5 when the loop runs on
+// the GPU (a conditional WHILE node of a CUDA graph around the restart cycle).
+enum LoopCode { kLoopRunning = 0, kLoopConverged = 1, kLoopMaxCycles = 2, kLoopBreakdown = 3, kLoopTimeout = 4 };
+struct LoopState {
+    int cyc;              // restart cycles run
+    int max_cycles;
+    int code;             // LoopCode
+    int pad;
+    double tol;           // the accuracy test: residual <= tol
+    double res;           // the last residual
+};
+constexpr int kLoopHist = 2048;           // residual history capacity of a device-side loop
+
 // Device-side state of one extrapolation (CholeskyQR2 pass-1 results).
 struct ExtrapInfo {
     int done, a, dep, pad;
@@ -268,6 +281,18 @@ void prolong_add(cudaStream_t s, int dim, const TransferView<T>& P, const LevelV
 // e = A_0^{-1} r on the coarsest grid.
 template <typename T>
 void coarse_solve(cudaStream_t s, int dim, const CoarseView<T>& C, const T* r, T* e);
+
+// End of one restart cycle of a device-side loop: cyc += 1, the residual
+// res[0] into hist[cyc] (hist may be null) and st->res, the accuracy test,
+// and the WHILE condition (1 = run another cycle).  A set error word ends the
+// loop with kLoopTimeout.
+void loop_step(cudaStream_t s, cudaGraphConditionalHandle h, LoopState* st, const double* res,
+               const unsigned* err, double* hist);
+// Sets the WHILE condition from st->code (1 while kLoopRunning).
+void loop_init(cudaStream_t s, cudaGraphConditionalHandle h, const LoopState* st);
+// The same kernel added to graph g as a root node.
+cudaError_t add_loop_init_node(cudaGraph_t g, cudaGraphConditionalHandle h, const LoopState* st,
+                               cudaGraphNode_t* node);
 
 // Partial sums of squares of v (deterministic): nblocks partials.
 void sumsq_partial(cudaStream_t s, const double* v, size_t n, double* partial, int nblocks);

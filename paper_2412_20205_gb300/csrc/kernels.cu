@@ -991,6 +991,30 @@ __global__ void __launch_bounds__(1024) k_norm_final(const double* __restrict__ 
     }
 }
 
+// ---------------------------------------------------------------- device-side restart loop
+__global__ void k_loop_step(cudaGraphConditionalHandle h, LoopState* st, const double* __restrict__ res,
+                            const unsigned* __restrict__ err, double* __restrict__ hist) {
+    pdl_enter();
+    if (threadIdx.x != 0) return;
+    const int cyc = st->cyc + 1;
+    const double r = res[0];
+    st->cyc = cyc;
+    st->res = r;
+    if (hist && cyc < kLoopHist) hist[cyc] = r;
+    int code = kLoopRunning;
+    if (!isfinite(r)) code = kLoopBreakdown;
+    else if (*err) code = kLoopTimeout;
+    else if (r <= st->tol) code = kLoopConverged;
+    else if (cyc >= st->max_cycles) code = kLoopMaxCycles;
+    st->code = code;
+    cudaGraphSetConditional(h, code == kLoopRunning ? 1u : 0u);
+}
+
+__global__ void k_loop_init(cudaGraphConditionalHandle h, const LoopState* st) {
+    pdl_enter();
+    if (threadIdx.x == 0) cudaGraphSetConditional(h, st->code == kLoopRunning ? 1u : 0u);
+}
+
 // ---------------------------------------------------------------- extrapolation
 // Gram partials of Delta s_a = s_{a+1} - s_a (a = 0..Q), upper triangle.
 template <int Q>
@@ -1602,6 +1626,30 @@ void coarse_solve(cudaStream_t s, int dim, const CoarseView<T>& C, const T* r, T
 void sumsq_partial(cudaStream_t s, const double* v, size_t n, double* partial, int nblocks) {
     launch_chained(k_sumsq, nblocks, kThreads, 0, s, v, n, partial);
     count_launch();
+}
+
+void loop_step(cudaStream_t s, cudaGraphConditionalHandle h, LoopState* st, const double* res,
+               const unsigned* err, double* hist) {
+    launch_chained(k_loop_step, 1, 32, 0, s, h, st, res, err, hist);
+    count_launch();
+}
+
+void loop_init(cudaStream_t s, cudaGraphConditionalHandle h, const LoopState* st) {
+    launch_chained(k_loop_init, 1, 32, 0, s, h, st);
+    count_launch();
+}
+
+cudaError_t add_loop_init_node(cudaGraph_t g, cudaGraphConditionalHandle h, const LoopState* st,
+                               cudaGraphNode_t* node) {
+    void* args[2] = {&h, &st};
+    cudaKernelNodeParams kp = {};
+    kp.func = (void*)k_loop_init;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(32);
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    return cudaGraphAddKernelNode(node, g, nullptr, 0, &kp);
 }
 
 void norm_final(cudaStream_t s, const double* partial, int nparts, const double* denom, double* out,

@@ -172,3 +172,37 @@ def test_fused_forward_large_image(pkg):
     got = _np(y)
     assert _rel(got, ref) < 2e-2
     assert np.dot(got.ravel(), ref.ravel()) / (np.linalg.norm(got) * np.linalg.norm(ref)) > 0.999
+
+
+def test_stored_network_saves_restarts_at_1024_p4(pkg):
+    """What the trained network gains: with the stored weights (trained on
+    257^2, p = 3 pairs), 1024^2 elements at p = 4 -- where multicolour
+    Gauss-Seidel smooths worse -- the learned post-smoother needs fewer RRE(5)
+    restart cycles than the plain mixed form on every right-hand side, without
+    falling back, and its solution passes the oracle's residual test (the
+    oracle's operator and load vector, FP64)."""
+    import os
+    from oracle import bspline as bs, galerkin as gk
+    wfile = os.path.join(os.path.dirname(pkg.__file__), "weights", "smoother_2d_n256_p3.npy")
+    w = torch.tensor(np.load(wfile), dtype=torch.float32, device=DEV)
+    n, p = 1024, 4
+    s = pkg.Solver(2, p, n, k=5)
+    s.set_smoother(w)
+    br = bs.uniform_breaks(n)
+    f = gk.factors_1d(br, p)
+    A = gk.operator([f, f])
+    total_plain = total_learned = 0
+    for seed in (10000, 10001, 10002):
+        coeffs = workloads.random_sine_coeffs(2, seed=seed, modes=16)
+        b = s.rhs_sine(coeffs)
+        plain = s.solve(b, tol=1e-10, method="rre", k=5, prec="fp32_ir", max_cycles=60)
+        learned = s.solve(b, tol=1e-10, method="rre", k=5, prec="fp32_ir_learned", max_cycles=60)
+        assert plain["converged"] and learned["converged"] and not learned["fell_back"]
+        assert learned["cycles"] <= plain["cycles"], (seed, learned["cycles"], plain["cycles"])
+        total_plain += plain["cycles"]
+        total_learned += learned["cycles"]
+        bo = gk.load_vector([br, br], p, coeffs)
+        x = _np(learned["x"])
+        assert np.linalg.norm(bo - A @ x) / np.linalg.norm(bo) <= 1.05e-10
+    assert total_learned < total_plain, (total_learned, total_plain)
+    s.close()

@@ -80,6 +80,7 @@ def test_single_launch_solves_are_bitwise_equal(pkg, dim, n, p, k):
 
 def test_bounded_wait_runs_out_and_is_reported(pkg):
     s = pkg.Solver(2, 3, 64, k=5)
+    pkg.igamg_set_sweep_form(s.ctx, 1, 1)           # single-launch sweeps on every level
     b = s.rhs_sine(workloads.random_sine_coeffs(2, seed=5, modes=6))
     ref = s.solve(b, tol=1e-10, method="rre", k=5, prec="fp32_ir")
     assert ref["converged"]
