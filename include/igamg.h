@@ -324,6 +324,23 @@ igamg_status igamg_autotune(igamg_ctx* ctx, void* d_ws, size_t ws_bytes, void* s
 igamg_status igamg_vcycle_probe(igamg_ctx* ctx, double* d_x, const double* d_b, double* d_x_mid,
                                 void* d_ws, size_t ws_bytes, void* stream);
 
+/* Training pairs of the learned post-smoother, generated by the solver
+ * itself: restarted RRE(k) (Algorithm 5 with Algorithm 3) in FP64 from s_0 =
+ * 0 on right side d_b, every V-cycle probed as in igamg_vcycle_probe.  For
+ * each V-cycle (in order, up to max_pairs) with probed iterate x_mid it
+ * writes the pair r = b - A x_mid, e = u_h - x_mid (d_uh: the discrete
+ * solution, e.g. an igamg_solve to 1e-13), both scaled by the same c > 0 so
+ * that e has unit root-mean-square, as FP32 rows of length N into d_R and d_E
+ * (pair i at offset i N).  Stops after the restart whose extrapolant passes
+ * ||b - A t|| / ||b|| <= tol, or after max_restarts.  h_pairs receives the
+ * number of pairs written.  Workspace: igamg_training_workspace_bytes(ctx,
+ * k).  Synchronises `stream` once per restart.  Errors: EINVAL (also for a
+ * context whose cycle is not the Gauss-Seidel V-cycle), ENOMEM, EBREAKDOWN. */
+size_t igamg_training_workspace_bytes(const igamg_ctx* ctx, int k);
+igamg_status igamg_training_pairs(igamg_ctx* ctx, const double* d_b, const double* d_uh, int k, double tol,
+                                  int max_restarts, float* d_R, float* d_E, int max_pairs, void* d_ws,
+                                  size_t ws_bytes, void* stream, int* h_pairs);
+
 /* ---------------------------------------------------------------- batches */
 
 /* Many independent problems of uneven size and degree, solved together.

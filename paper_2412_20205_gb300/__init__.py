@@ -81,6 +81,8 @@ def _load():
         "igamg_smooth_f32": (c_int, [vp, c_int, vp, vp, c_int, c_int, vp, c_size, vp]),
         "igamg_set_coarse_tail": (c_int, [vp, c_int]),
         "igamg_vcycle_probe": (c_int, [vp, vp, vp, vp, vp, c_size, vp]),
+        "igamg_training_workspace_bytes": (c_size, [vp, c_int]),
+        "igamg_training_pairs": (c_int, [vp, vp, vp, c_int, c_double, c_int, vp, vp, c_int, vp, c_size, vp, ip]),
         "igamg_cnn_num_weights": (c_int, []),
         "igamg_cnn_workspace_bytes": (c_size, [c_int, c_int, c_int]),
         "igamg_cnn_forward": (c_int, [c_int, c_int, c_int, vp, vp, vp, vp, c_size, vp]),
@@ -336,6 +338,20 @@ def igamg_set_coarse_tail(ctx, enable):
 def igamg_vcycle_probe(ctx, x, b, x_mid, ws, stream=None):
     _check(_load().igamg_vcycle_probe(ctx, _ptr(x), _ptr(b), _ptr(x_mid), _ptr(ws), ws.numel(), _stream(stream)),
            "igamg_vcycle_probe")
+
+
+def igamg_training_workspace_bytes(ctx, k):
+    return int(_load().igamg_training_workspace_bytes(ctx, k))
+
+
+def igamg_training_pairs(ctx, b, uh, k, tol, max_restarts, R, E, ws, stream=None):
+    """Writes scaled (r, e) training pairs into the FP32 tensors R, E (pairs x N); returns the count."""
+    n = ctypes.c_int()
+    max_pairs = min(R.shape[0], E.shape[0])
+    _check(_load().igamg_training_pairs(ctx, _ptr(b), _ptr(uh), k, tol, max_restarts, _ptr(R), _ptr(E), max_pairs,
+                                        _ptr(ws), ws.numel(), _stream(stream), ctypes.byref(n)),
+           "igamg_training_pairs")
+    return n.value
 
 
 def igamg_cnn_num_weights():

@@ -1538,6 +1538,71 @@ igamg_status igamg_vcycle_probe(igamg_ctx* c, double* d_x, const double* d_b, do
     return IGAMG_OK;
 }
 
+size_t igamg_training_workspace_bytes(const igamg_ctx* c, int k) {
+    if (!c || k < 1 || k > kMaxQ) return 0;
+    return carve(c, nullptr, k, IGAMG_FP64).bytes + 3 * (((finestN(c) * sizeof(double)) + 255) & ~(size_t)255) + 256;
+}
+
+igamg_status igamg_training_pairs(igamg_ctx* c, const double* d_b, const double* d_uh, int k, double tol,
+                                  int max_restarts, float* d_R, float* d_E, int max_pairs, void* d_ws,
+                                  size_t ws_bytes, void* stream, int* h_pairs) {
+    if (c && !default_cycle(c)) return fail(IGAMG_EINVAL, "the probe follows the Gauss-Seidel V-cycle");
+    if (igamg_status st = check_ctx(c)) return st;
+    if (!d_b || !d_uh || !d_R || !d_E || !h_pairs || k < 1 || k > kMaxQ || max_restarts < 1 || max_pairs < 0 ||
+        !(tol >= 0.0))
+        return fail(IGAMG_EINVAL, "bad training-pair arguments");
+    if (!d_ws || ((uintptr_t)d_ws & 255)) return fail(IGAMG_EINVAL, "bad workspace");
+    if (ws_bytes < igamg_training_workspace_bytes(c, k)) return fail(IGAMG_ENOMEM, "training workspace too small");
+    Workspace w = carve(c, d_ws, k, IGAMG_FP64);
+    const size_t N = finestN(c);
+    const size_t vb = ((N * sizeof(double)) + 255) & ~(size_t)255;
+    char* extra = (char*)d_ws + ((w.bytes + 255) & ~(size_t)255);
+    double* mid = (double*)extra;                   // iterate before the finest post-smoothing
+    double* r64 = (double*)(extra + vb);            // b - A mid
+    double* e64 = (double*)(extra + 2 * vb);        // u_h - mid
+    cudaStream_t s = (cudaStream_t)stream;
+    const int top = c->L - 1;
+    LevelBuf<double>& F = w.d[top];
+    *h_pairs = 0;
+    CUDA_TRY(clear_sync(w, s));
+    // ||b||, s_0 = 0 and its row sums
+    dev::sumsq_partial(s, d_b, N, w.partial, 256);
+    dev::norm_final(s, w.partial, 256, nullptr, w.scal, 0);
+    dev::fill_zero<double>(s, w.S, N);
+    dev::xpass<double, double>(s, c->lv64[top], w.S, w.S, nullptr, 0, nullptr, nullptr, 0, F.TM, F.TK);
+    int pairs = 0;
+    for (int rs = 0; rs < max_restarts; ++rs) {
+        for (int j = 0; j <= k; ++j) {
+            double* Sj = w.S + (size_t)j * w.ld;
+            double* Sn = w.S + (size_t)(j + 1) * w.ld;
+            CUDA_TRY(cudaMemcpyAsync(Sn, Sj, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            vcycle<double>(c, s, w, top, Sn, d_b, false, false, mid);            // s_{j+1} = G(s_j), probed
+            if (pairs < max_pairs) {
+                // e = u_h - mid, r = b - A mid (row sums of mid in F.r / F.tmp2), unit RMS of e
+                dev::diff_sumsq(s, d_uh, mid, N, e64, w.partial, 256);
+                dev::norm_final(s, w.partial, 256, nullptr, w.scal, 2);
+                dev::xpass<double, double>(s, c->lv64[top], mid, nullptr, nullptr, 0, nullptr, nullptr, 0, F.r,
+                                           F.tmp2);
+                dev::residual<double, double>(s, c->dim, c->lv64[top], d_b, F.r, F.tmp2, r64, nullptr);
+                dev::scale_pair(s, r64, e64, w.scal + 2, N, d_R + (size_t)pairs * N, d_E + (size_t)pairs * N);
+                ++pairs;
+            }
+        }
+        // t = RRE(s_0..s_{k+1}) (Algorithm 3), s_0 := t, ||b - A t|| / ||b||
+        const int nb = dev::gram_blocks(N);
+        dev::extrap_gammas(s, k, IGAMG_RRE, w.S, w.ld, N, w.partial, nb, w.info, w.gamma, w.qused);
+        dev::xpass<double, double>(s, c->lv64[top], nullptr, w.S, nullptr, k + 2, w.gamma, w.S, w.ld, F.TM, F.TK);
+        residual_norm(c, s, w, d_b, w.scal);
+        CUDA_TRY(cudaMemcpyAsync(c->h_pin, w.scal + 1, 8, cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        CUDA_TRY(cudaGetLastError());
+        if (!std::isfinite(c->h_pin[0])) return fail(IGAMG_EBREAKDOWN, "non-finite residual");
+        if (c->h_pin[0] <= tol) break;
+    }
+    *h_pairs = pairs;
+    return IGAMG_OK;
+}
+
 void igamg_destroy(igamg_ctx* c) {
     if (!c) return;
     for (int sl = 0; sl < 3; ++sl)

@@ -294,6 +294,12 @@ void loop_init(cudaStream_t s, cudaGraphConditionalHandle h, const LoopState* st
 cudaError_t add_loop_init_node(cudaGraph_t g, cudaGraphConditionalHandle h, const LoopState* st,
                                cudaGraphNode_t* node);
 
+// Training pairs of the learned smoother: e = u - v with nblocks partial sums
+// of e^2; then R = float(c r), E = float(c e), c = sqrt(n) / *enorm.
+void diff_sumsq(cudaStream_t s, const double* u, const double* v, size_t n, double* e, double* partial,
+                int nblocks);
+void scale_pair(cudaStream_t s, const double* r, const double* e, const double* enorm, size_t n, float* R, float* E);
+
 // Partial sums of squares of v (deterministic): nblocks partials.
 void sumsq_partial(cudaStream_t s, const double* v, size_t n, double* partial, int nblocks);
 // out[slot] = sqrt(sum partial) / (*denom), and non-finite flag.

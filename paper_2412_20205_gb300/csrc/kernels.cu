@@ -976,6 +976,33 @@ __global__ void __launch_bounds__(kThreads) k_sumsq(const double* __restrict__ v
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
+// e = u - v (written to e) with per-block partial sums of e^2.
+__global__ void __launch_bounds__(kThreads) k_diff_sumsq(const double* __restrict__ u, const double* __restrict__ v,
+                                                         size_t n, double* __restrict__ e, double* __restrict__ partial) {
+    pdl_enter();
+    __shared__ double red[kThreads / 32];
+    double s = 0.0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const double d = u[i] - v[i];
+        e[i] = d;
+        s += d * d;
+    }
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// R = float(c r), E = float(c e) with c = sqrt(n) / enorm[0] (unit RMS of E).
+__global__ void __launch_bounds__(kThreads) k_scale_pair(const double* __restrict__ r, const double* __restrict__ e,
+                                                         const double* __restrict__ enorm, size_t n,
+                                                         float* __restrict__ R, float* __restrict__ E) {
+    pdl_enter();
+    const double c = sqrt((double)n) / fmax(enorm[0], 1e-300);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        R[i] = (float)(c * r[i]);
+        E[i] = (float)(c * e[i]);
+    }
+}
+
 __global__ void __launch_bounds__(1024) k_norm_final(const double* __restrict__ partial, int nparts,
                                                       const double* __restrict__ denom,
                                                       double* __restrict__ out, int slot) {
@@ -1625,6 +1652,17 @@ void coarse_solve(cudaStream_t s, int dim, const CoarseView<T>& C, const T* r, T
 
 void sumsq_partial(cudaStream_t s, const double* v, size_t n, double* partial, int nblocks) {
     launch_chained(k_sumsq, nblocks, kThreads, 0, s, v, n, partial);
+    count_launch();
+}
+
+void diff_sumsq(cudaStream_t s, const double* u, const double* v, size_t n, double* e, double* partial,
+                int nblocks) {
+    launch_chained(k_diff_sumsq, nblocks, kThreads, 0, s, u, v, n, e, partial);
+    count_launch();
+}
+
+void scale_pair(cudaStream_t s, const double* r, const double* e, const double* enorm, size_t n, float* R, float* E) {
+    launch_chained(k_scale_pair, grid_for(n), kThreads, 0, s, r, e, enorm, n, R, E);
     count_launch();
 }
 

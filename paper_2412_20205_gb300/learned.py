@@ -2,10 +2,9 @@
 
 Data: for seeded random smooth right-hand sides on one grid, the discrete
 solution u_h is computed by the solver itself (FP64, relative residual
-1e-13).  Then restarted RRE runs (Algorithm 5) are replayed from s_0 = 0 with
-the library's components: every V-cycle is igamg_vcycle_probe, which also
-captures the iterate x_mid just before the finest-level post-smoothing, and
-every restart ends with igamg_extrapolate.  Each V-cycle yields one pair
+1e-13).  Then igamg_training_pairs runs restarted RRE (Algorithm 5) from
+s_0 = 0 in the library, probing every V-cycle at the iterate x_mid just
+before the finest-level post-smoothing; each V-cycle yields one pair
 (r, e) = (b - A x_mid, u_h - x_mid).  The network has no biases, so it is
 positively homogeneous (net(c r) = c net(r) for c > 0): a pair scaled by any
 positive c is an equally valid example, and each pair is scaled to unit RMS
@@ -26,9 +25,8 @@ import time
 import numpy as np
 import torch
 
-from . import (IGAMG_RRE, Solver, igamg_adam_step, igamg_apply, igamg_cnn_grad, igamg_cnn_num_weights,
-               igamg_cnn_workspace_bytes, igamg_extrap_workspace_bytes, igamg_extrapolate,
-               igamg_vcycle_probe)
+from . import (Solver, igamg_adam_step, igamg_cnn_grad, igamg_cnn_num_weights, igamg_cnn_workspace_bytes,
+               igamg_training_pairs, igamg_training_workspace_bytes)
 
 
 def _coeffs(seed, modes):
@@ -38,39 +36,26 @@ def _coeffs(seed, modes):
 
 def generate_pairs(n=256, p=3, problems=420, k=5, seed0=0, modes=16, tol=1e-10, max_restarts=20,
                    device="cuda"):
-    """Returns (R, E) float32 tensors of shape (pairs, m, m), m = n + p - 2."""
+    """Returns (R, E) float32 tensors of shape (pairs, m, m), m = n + p - 2:
+    per problem the discrete solution by an FP64 solve to 1e-13, then the
+    pairs of its restarted RRE run from igamg_training_pairs."""
     s = Solver(2, p, n, k=k, device=device)
     m = s.levels[-1][0]
     N = s.N
-    top = len(s.levels) - 1
-    S = torch.empty((k + 2, N), dtype=torch.float64, device=device)
-    t = torch.empty(N, dtype=torch.float64, device=device)
-    mid = torch.empty(N, dtype=torch.float64, device=device)
-    ax = torch.empty(N, dtype=torch.float64, device=device)
-    ews = torch.empty(igamg_extrap_workspace_bytes(N, k), dtype=torch.uint8, device=device)
+    per = (k + 1) * max_restarts                    # most pairs one problem can give
+    Rb = torch.empty((per, N), dtype=torch.float32, device=device)
+    Eb = torch.empty_like(Rb)
+    ws = torch.empty(igamg_training_workspace_bytes(s.ctx, k), dtype=torch.uint8, device=device)
     R, E = [], []
     for i in range(problems):
         b = s.rhs_sine(_coeffs(seed0 + i, modes))
-        bn = float(b.norm())
         uh = s.solve(b, tol=1e-13, method="rre", k=k, prec="fp64", max_cycles=100)["x"].clone()
-        S[0].zero_()
-        for _ in range(max_restarts):
-            for j in range(k + 1):
-                S[j + 1].copy_(S[j])
-                igamg_vcycle_probe(s.ctx, S[j + 1], b, mid, s.ws)
-                igamg_apply(s.ctx, top, mid, ax, s.ws)
-                r = b - ax
-                e = uh - mid
-                c = 1.0 / max(float(e.norm()) / math.sqrt(N), 1e-300)
-                R.append((r * c).float().view(m, m))
-                E.append((e * c).float().view(m, m))
-            igamg_extrapolate(N, k, IGAMG_RRE, S, N, t, ews)
-            S[0].copy_(t)
-            igamg_apply(s.ctx, top, t, ax, s.ws)
-            if float((b - ax).norm()) <= tol * bn:
-                break
+        c = igamg_training_pairs(s.ctx, b, uh, k, tol, max_restarts, Rb, Eb, ws)
+        R.append(Rb[:c].clone())
+        E.append(Eb[:c].clone())
     s.close()
-    return torch.stack(R), torch.stack(E)
+    R, E = torch.cat(R), torch.cat(E)
+    return R.view(-1, m, m), E.view(-1, m, m)
 
 
 def init_weights(seed=0, device="cuda"):

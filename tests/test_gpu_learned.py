@@ -206,3 +206,36 @@ def test_stored_network_saves_restarts_at_1024_p4(pkg):
         assert np.linalg.norm(bo - A @ x) / np.linalg.norm(bo) <= 1.05e-10
     assert total_learned < total_plain, (total_learned, total_plain)
     s.close()
+
+
+def test_training_pairs_match_oracle(pkg):
+    """igamg_training_pairs against the oracle: the first two V-cycles of the
+    restarted RRE run from s_0 = 0, probed before the finest post-smoothing
+    (composed from oracle steps), give pairs (b - A x_mid, u_h - x_mid) scaled
+    to unit RMS error; FP32 storage, relative 1e-5."""
+    import scipy.sparse.linalg as spla
+    from oracle import solver as osolver
+    n, p, k = 40, 3, 3
+    coeffs = workloads.random_sine_coeffs(2, seed=12, modes=6)
+    prob = osolver.Problem(2, n, p, coeffs)
+    H, b = prob.H, prob.b
+    A = H.finest.A
+    uh = spla.spsolve(A.tocsc(), b)
+    s = pkg.Solver(2, p, n, k=k)
+    bt = s.rhs_sine(coeffs)
+    uht = s.solve(bt, tol=1e-13, method="rre", k=k, prec="fp64", max_cycles=100)["x"]
+    per = (k + 1) * 4
+    R = torch.empty((per, s.N), dtype=torch.float32, device=DEV)
+    E = torch.empty_like(R)
+    ws = torch.empty(pkg.igamg_training_workspace_bytes(s.ctx, k), dtype=torch.uint8, device=DEV)
+    cnt = pkg.igamg_training_pairs(s.ctx, bt, uht, k, 1e-10, 4, R, E, ws)
+    assert cnt % (k + 1) == 0 and cnt >= k + 1
+    x = np.zeros(H.finest.N)
+    for i in range(2):
+        mid = _oracle_mid(H, x, b)
+        e = uh - mid
+        c = np.sqrt(H.finest.N) / np.linalg.norm(e)
+        assert _rel(E[i].double().cpu().numpy(), c * e) < 1e-5, i
+        assert _rel(R[i].double().cpu().numpy(), c * (b - A @ mid)) < 1e-5, i
+        x = omg.cycle(H, x, b)
+    s.close()
