@@ -77,6 +77,10 @@ class Hierarchy:
     def finest(self):
         return self.levels[-1]
 
+    def solve_coarsest(self, b):
+        """A_0^{-1} b by the Cholesky factor (A_0 is SPD)."""
+        return sla.cho_solve(self.coarse_chol, b)
+
 
 def gs_sweep(level, x, b, descending=False):
     """One multicolour Gauss-Seidel sweep: for each colour c in order,
@@ -109,7 +113,7 @@ def smooth(level, x, b, nu, smoother, pre, omega=2.0 / 3.0):
 def mu_cycle(H, l, x, b, mu=1, nu1=1, nu2=1, smoother="gs", omega=2.0 / 3.0):
     """Algorithm 2 on level l (0 = coarsest) with initial guess x and right side b."""
     if l == 0:
-        return sla.cho_solve(H.coarse_chol, b)                 # direct coarsest solve
+        return H.solve_coarsest(b)                              # direct coarsest solve
     lev = H.levels[l]
     u = smooth(lev, x, b, nu1, smoother, pre=True, omega=omega)  # pre-smooth
     r = b - lev.A @ u                                           # residual

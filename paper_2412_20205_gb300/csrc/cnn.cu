@@ -15,8 +15,8 @@
 // layers on the tensor cores (implicit GEMMs, M = pixels: 1 -> 16 with K = 9
 // taps, 16 -> 16 with K = 144, 16 -> 1 with K = 144).  Training runs the
 // layers as separate kernels that keep both activations for the backward
-// pass; there the 16 -> 16 forward and input-gradient contractions run on the
-// tensor cores and the rest on the FP32 cores.
+// pass, every contraction on the tensor cores as well: the layer forwards,
+// the input gradients and the weight gradients (implicit GEMMs over pixels).
 #include "../../include/igamg.h"
 #include "device.hpp"
 
@@ -87,33 +87,6 @@ __device__ __forceinline__ void store16(__nv_bfloat16* a, long long p, const flo
 }
 
 // ------------------------------------------------------------------ forward
-// a1 = relu(W1 * r)
-__global__ void __launch_bounds__(kT) k_conv1(Shape s, const float* __restrict__ r, const float* __restrict__ w,
-                                              __nv_bfloat16* __restrict__ a1) {
-    __shared__ float W1[NW1];
-    for (int i = threadIdx.x; i < NW1; i += blockDim.x) W1[i] = bf16r(w[i]);
-    __syncthreads();
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < s.pixels();
-         p += (long long)gridDim.x * blockDim.x) {
-        const Pix px(s, p);
-        float nb[9];
-#pragma unroll
-        for (int t = 0; t < 9; ++t) {
-            const long long q = px.nb(s, t);
-            nb[t] = q >= 0 ? bf16r(r[q]) : 0.f;
-        }
-        float v[C];
-#pragma unroll
-        for (int co = 0; co < C; ++co) {
-            float acc = 0.f;
-#pragma unroll
-            for (int t = 0; t < 9; ++t) acc += W1[co * 9 + t] * nb[t];
-            v[co] = fmaxf(acc, 0.f);
-        }
-        store16(a1, p, v);
-    }
-}
-
 // Tensor-core fragments (mma.sync.m16n8k16, BF16 inputs, FP32 accumulators).
 // Per warp: a strip of 16 consecutive pixels (M) x 16 output channels (two N
 // tiles of 8); K runs over the 9 taps x 16 input channels, one k16 step per
@@ -202,30 +175,6 @@ __global__ void __launch_bounds__(kT) k_conv2(Shape s, const __nv_bfloat16* __re
             for (int nt = 0; nt < 2; ++nt)
                 o[nt * 4 + tq] = __floats2bfloat162_rn(fmaxf(acc[4 * nt + 2 * h], 0.f), fmaxf(acc[4 * nt + 2 * h + 1], 0.f));
         }
-    }
-}
-
-// y = W3 * a2 (FP32); with accumulate, x += y instead (the solver's correction)
-__global__ void __launch_bounds__(kT) k_conv3(Shape s, const __nv_bfloat16* __restrict__ a2, const float* __restrict__ w,
-                                              float* __restrict__ y, int accumulate) {
-    __shared__ float W3[NW3];
-    for (int i = threadIdx.x; i < NW3; i += blockDim.x) W3[i] = bf16r(w[NW1 + NW2 + i]);
-    __syncthreads();
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < s.pixels();
-         p += (long long)gridDim.x * blockDim.x) {
-        const Pix px(s, p);
-        float acc = 0.f;
-#pragma unroll
-        for (int t = 0; t < 9; ++t) {
-            const long long q = px.nb(s, t);
-            if (q < 0) continue;
-            float v[C];
-            load16(a2, q, v);
-#pragma unroll
-            for (int c = 0; c < C; ++c) acc += W3[c * 9 + t] * v[c];
-        }
-        if (accumulate) y[p] += acc;
-        else y[p] = acc;
     }
 }
 
@@ -434,32 +383,6 @@ __global__ void __launch_bounds__(kT) k_loss(Shape s, const float* __restrict__ 
         double t = 0.0;
         for (int i = 0; i < (int)blockDim.x / 32; ++i) t += red[i];
         partial[blockIdx.x] = t;
-    }
-}
-
-// g2 = (a2 > 0) . (W3^T gy): dL/da2, channel-last BF16
-__global__ void __launch_bounds__(kT) k_conv3_dgrad(Shape s, const float* __restrict__ gy, const float* __restrict__ w,
-                                                    const __nv_bfloat16* __restrict__ a2, __nv_bfloat16* __restrict__ g2) {
-    __shared__ float W3[NW3];
-    for (int i = threadIdx.x; i < NW3; i += blockDim.x) W3[i] = bf16r(w[NW1 + NW2 + i]);
-    __syncthreads();
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < s.pixels();
-         p += (long long)gridDim.x * blockDim.x) {
-        const Pix px(s, p);
-        float v[C] = {};
-#pragma unroll
-        for (int t = 0; t < 9; ++t) {
-            const long long q = px.nb(s, 8 - t);          // y[q] read a2[p] through tap t
-            if (q < 0) continue;
-            const float gq = gy[q];
-#pragma unroll
-            for (int c = 0; c < C; ++c) v[c] += W3[c * 9 + t] * gq;
-        }
-        float a[C];
-        load16(a2, p, a);
-#pragma unroll
-        for (int c = 0; c < C; ++c) v[c] = a[c] > 0.f ? v[c] : 0.f;
-        store16(g2, p, v);
     }
 }
 
@@ -698,81 +621,6 @@ __global__ void __launch_bounds__(kT) k_wgrad_tc(Shape s, const float* __restric
                 }
             }
         }
-    }
-}
-
-// Weight gradients: per-block partial sums over a tile of pixels, one weight
-// per (thread, slot); the final reduction over blocks runs in fixed order.
-// dW1[co][t] = sum_p g1[p][co] r[nb(p,t)]; dW2[co][ci][t] = sum_p g2[p][co] a1[nb(p,t)][ci];
-// dW3[c][t] = sum_p gy[p] a2[nb(p,t)][c]
-constexpr int kTile = 32;                           // pixels per block pass (static smem < 48 KiB)
-
-__global__ void __launch_bounds__(kT) k_wgrad(Shape s, const float* __restrict__ r, const __nv_bfloat16* __restrict__ a1,
-                                              const __nv_bfloat16* __restrict__ a2, const __nv_bfloat16* __restrict__ g1,
-                                              const __nv_bfloat16* __restrict__ g2, const float* __restrict__ gy,
-                                              float* __restrict__ partial) {
-    __shared__ float sg1[kTile][C], sg2[kTile][C], sgy[kTile];
-    __shared__ float sr[kTile][9], sa1[kTile][9][C], sa2[kTile][9][C];
-    float acc[(NW + kT - 1) / kT];
-    constexpr int SLOTS = (NW + kT - 1) / kT;
-#pragma unroll
-    for (int i = 0; i < SLOTS; ++i) acc[i] = 0.f;
-    const long long P = s.pixels();
-    const long long ntiles = (P + kTile - 1) / kTile;
-    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const long long p0 = tile * kTile;
-        __syncthreads();
-        for (int i = threadIdx.x; i < kTile; i += blockDim.x) {
-            const long long p = p0 + i;
-            float v1[C], v2[C];
-            if (p < P) {
-                load16(g1, p, v1);
-                load16(g2, p, v2);
-                sgy[i] = gy[p];
-            } else {
-                for (int c = 0; c < C; ++c) v1[c] = v2[c] = 0.f;
-                sgy[i] = 0.f;
-            }
-            for (int c = 0; c < C; ++c) { sg1[i][c] = v1[c]; sg2[i][c] = v2[c]; }
-        }
-        for (int i = threadIdx.x; i < kTile * 9; i += blockDim.x) {
-            const int pi = i / 9, t = i % 9;
-            const long long p = p0 + pi;
-            const long long q = p < P ? Pix(s, p).nb(s, t) : -1;
-            float v1[C], v2[C];
-            if (q >= 0) {
-                load16(a1, q, v1);
-                load16(a2, q, v2);
-                sr[pi][t] = bf16r(r[q]);
-            } else {
-                for (int c = 0; c < C; ++c) v1[c] = v2[c] = 0.f;
-                sr[pi][t] = 0.f;
-            }
-            for (int c = 0; c < C; ++c) { sa1[pi][t][c] = v1[c]; sa2[pi][t][c] = v2[c]; }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int sl = 0; sl < SLOTS; ++sl) {
-            const int wi = threadIdx.x + sl * kT;
-            if (wi >= NW) continue;
-            float a = 0.f;
-            if (wi < NW1) {
-                const int co = wi / 9, t = wi % 9;
-                for (int i = 0; i < kTile; ++i) a += sg1[i][co] * sr[i][t];
-            } else if (wi < NW1 + NW2) {
-                const int j = wi - NW1, co = j / (C * 9), ci = (j / 9) % C, t = j % 9;
-                for (int i = 0; i < kTile; ++i) a += sg2[i][co] * sa1[i][t][ci];
-            } else {
-                const int j = wi - NW1 - NW2, c = j / 9, t = j % 9;
-                for (int i = 0; i < kTile; ++i) a += sgy[i] * sa2[i][t][c];
-            }
-            acc[sl] += a;
-        }
-    }
-#pragma unroll
-    for (int sl = 0; sl < SLOTS; ++sl) {
-        const int wi = threadIdx.x + sl * kT;
-        if (wi < NW) partial[(size_t)blockIdx.x * NW + wi] = acc[sl];
     }
 }
 
