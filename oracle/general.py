@@ -20,9 +20,8 @@ evaluated at the mapped points (J^{-T} grad^ = grad).  The unit square itself is
 F = identity.  Quadrature: p+1 Gauss points per element and direction, the
 rule of the Poisson path.
 
-The map of the quarter annulus (Sec. 4.3: "approximated by the B-spline
-approach") is a tensor B-spline surface on the same knot vectors as the
-discretisation (isoparametric), whose control points the caller gives.
+The map F is given as a function of the parameter point returning the
+physical point and J (the quarter annulus of Sec. 4.3 uses its polar map).
 
 Coarse operators: the Galerkin product A_{2h} = P^T A_h P of Eq. (4) with the
 oracle's L2-projection P (the coefficients vary, so re-discretisation is no
@@ -33,8 +32,7 @@ import numpy as np
 import scipy.linalg as sla
 import scipy.sparse as sp
 
-from .bspline import (basis, basis_derivative, coarsen_breaks, element_quadrature, open_knot_vector,
-                      uniform_breaks)
+from .bspline import basis, basis_derivative, coarsen_breaks, element_quadrature, open_knot_vector, uniform_breaks
 from .galerkin import kron_list, n_interior, prolongation_1d
 
 
@@ -45,11 +43,6 @@ def quadrature_1d(breaks, p):
     return x, w, basis(knots, p, x)[:, 1:-1], basis_derivative(knots, p, x)[:, 1:-1]
 
 
-def full_basis_1d(breaks, p, x):
-    knots = open_knot_vector(breaks, p)
-    return basis(knots, p, x), basis_derivative(knots, p, x)
-
-
 def parametric_points(breaks_x, breaks_y, p):
     """The tensor quadrature points (xi, eta), weights w (x fastest, flat)."""
     xq, wx, _, _ = quadrature_1d(breaks_x, p)
@@ -58,32 +51,16 @@ def parametric_points(breaks_x, breaks_y, p):
     return XI.ravel(), ETA.ravel(), np.outer(wy, wx).ravel()
 
 
-def geometry_at_points(breaks_x, breaks_y, p, ctrl):
-    """Map F and Jacobian J = DF at the quadrature points for the B-spline
-    surface F(xi, eta) = sum_ij ctrl[:, j, i] N_i(xi) N_j(eta) on the full open
-    knot vectors (ctrl: 2 x (n_y+p) x (n_x+p)); ctrl = None is the identity.
-    Returns (x, y, J) with J of shape (nq, 2, 2), J[q, a, b] = d F_a / d xi_b."""
-    xq, _, _, _ = quadrature_1d(breaks_x, p)
-    yq, _, _, _ = quadrature_1d(breaks_y, p)
-    if ctrl is None:
-        XI, ETA = np.meshgrid(xq, yq)
-        J = np.zeros((XI.size, 2, 2))
+def geometry_at_points(breaks_x, breaks_y, p, geometry):
+    """Physical points and Jacobian J = DF at the quadrature points of the unit
+    square for the map geometry(xi, eta) -> (x, y, J) (J: nq x 2 x 2,
+    J[q, a, b] = d F_a / d xi_b); geometry = None is the identity."""
+    xi, eta, _ = parametric_points(breaks_x, breaks_y, p)
+    if geometry is None:
+        J = np.zeros((xi.size, 2, 2))
         J[:, 0, 0] = J[:, 1, 1] = 1.0
-        return XI.ravel(), ETA.ravel(), J
-    Bx, Dx = full_basis_1d(breaks_x, p, xq)
-    By, Dy = full_basis_1d(breaks_y, p, yq)
-    out = []
-    for a in range(2):
-        C = np.asarray(ctrl[a], dtype=np.float64)            # [j][i]
-        val = By @ C @ Bx.T                                   # [eta][xi]
-        dxi = By @ C @ Dx.T
-        deta = Dy @ C @ Bx.T
-        out.append((val.ravel(), dxi.ravel(), deta.ravel()))
-    J = np.empty((out[0][0].size, 2, 2))
-    for a in range(2):
-        J[:, a, 0] = out[a][1]
-        J[:, a, 1] = out[a][2]
-    return out[0][0], out[1][0], J
+        return xi, eta, J
+    return geometry(xi, eta)
 
 
 def transformed_coefficients(J, A, B, c):
@@ -106,9 +83,9 @@ def assemble(breaks_x, breaks_y, p, Ah, Bh, ch):
     _, wx, Bx, Dx = quadrature_1d(breaks_x, p)
     _, wy, By, Dy = quadrature_1d(breaks_y, p)
     w = np.outer(wy, wx).ravel()
-    V = sp.csr_matrix(sp.kron(By, Bx))                # phi at points
-    GX = sp.csr_matrix(sp.kron(By, Dx))               # d phi / d xi
-    GY = sp.csr_matrix(sp.kron(Dy, Bx))               # d phi / d eta
+    V = sp.csr_matrix(sp.kron(sp.csr_matrix(By), sp.csr_matrix(Bx)))                # phi at points
+    GX = sp.csr_matrix(sp.kron(sp.csr_matrix(By), sp.csr_matrix(Dx)))               # d phi / d xi
+    GY = sp.csr_matrix(sp.kron(sp.csr_matrix(Dy), sp.csr_matrix(Bx)))               # d phi / d eta
     G = [GX, GY]
 
     def wdiag(v):
@@ -133,7 +110,7 @@ def load_vector(breaks_x, breaks_y, p, fh):
     _, wx, Bx, _ = quadrature_1d(breaks_x, p)
     _, wy, By, _ = quadrature_1d(breaks_y, p)
     w = np.outer(wy, wx).ravel()
-    return sp.csr_matrix(sp.kron(By, Bx)).T @ (w * fh)
+    return sp.csr_matrix(sp.kron(sp.csr_matrix(By), sp.csr_matrix(Bx))).T @ (w * fh)
 
 
 class GeneralLevel:
@@ -191,12 +168,12 @@ class GeneralHierarchy:
 class GeneralProblem:
     """Hierarchy + load vector of one problem: coefficient functions of the
     physical point, A(x, y) -> (nq, 2, 2), B(x, y) -> (nq, 2), c(x, y), f(x, y),
-    on the unit square or the image of the control net ctrl."""
+    on the unit square or the image of geometry(xi, eta) -> (x, y, J)."""
 
-    def __init__(self, n, p, A, B, c, f, ctrl=None, coarsest=8):
+    def __init__(self, n, p, A, B, c, f, geometry=None, coarsest=8):
         ns = list(n) if np.ndim(n) else [int(n)] * 2
         bx, by = uniform_breaks(ns[0]), uniform_breaks(ns[1])
-        x, y, J = geometry_at_points(bx, by, p, ctrl)
+        x, y, J = geometry_at_points(bx, by, p, geometry)
         self.x, self.y, self.J = x, y, J
         Ah, Bh, ch, det = transformed_coefficients(J, A(x, y), B(x, y), c(x, y))
         self.det = det
@@ -208,12 +185,6 @@ class GeneralProblem:
 
     def residual(self, x):
         return float(np.linalg.norm(self.b - self.A_fine @ x))
-
-
-def greville(breaks, p):
-    """Greville abscissae of the full open knot vector (averages of p consecutive inner knots)."""
-    t = open_knot_vector(breaks, p)
-    return np.array([t[i + 1:i + p + 1].mean() for i in range(len(t) - p - 1)])
 
 
 def solution_at_points(breaks_x, breaks_y, p, u_h):
