@@ -108,6 +108,46 @@ size_t igamg_workspace_bytes(const igamg_ctx* ctx, int k, int prec);
 igamg_status igamg_rhs_sine(igamg_ctx* ctx, int modes, const double* h_coeffs, double* d_b,
                             void* stream);
 
+/* --------------------------------------- general operator (Sec. 4.3) */
+
+/* The full elliptic problem of Sec. 4.3, Eq. (fullelliptic):
+ *   -div(A grad u) + B . grad u + c u = f,  u = 0 on the boundary,
+ * A SPD, on the image of the unit square under a map F (the unit square
+ * itself, or e.g. the quarter annulus of Table 15), 2D.  Galerkin
+ * discretisation on the tensor B-spline space of igamg_setup (degree p,
+ * n_elems[2] uniform elements, at most 1024 per direction), (p+1)-point Gauss
+ * quadrature per element and direction; the map enters as the transformed
+ * coefficients |J| J^{-1} A J^{-T}, |J| J^{-1} B, |J| c and |J| f on the unit
+ * square (J = DF).  Coarse operators: the Galerkin product P^T A P of Eq. (4)
+ * with the knot-insertion P; the coarsest level is solved with its dense
+ * inverse.  igamg_solve then runs Algorithm 5 (RRE or MPE; A is not
+ * symmetric, so RRE is GMRES-like and MPE FOM-like) around Algorithm 2 with
+ * the context's cycle (igamg_set_cycle: multicolour Gauss-Seidel, (p+1)^2
+ * colours, or weighted Jacobi; V or W), FP64 only (IGAMG_FP64); igamg_apply,
+ * igamg_smooth and igamg_vcycle act on the stencil levels.  The calls that
+ * only exist for the Poisson problem (igamg_rhs_sine, igamg_smooth_f32,
+ * igamg_autotune, the learned smoother, the probe) return IGAMG_EINVAL.
+ * Order: igamg_setup_general -> igamg_quadrature_points -> evaluate the
+ * problem's functions there -> igamg_assemble_general -> igamg_rhs_points ->
+ * igamg_solve.
+ * Errors: EINVAL (sizes, a Jacobian with det <= 0, a singular coarsest
+ * operator), ECUDA, ENOMEM. */
+igamg_status igamg_setup_general(int p, const int* n_elems, int n_levels, igamg_ctx** out);
+/* Number of quadrature points nq = (n_x (p+1)) (n_y (p+1)) and their
+ * parameter coordinates (xi, eta) in [0,1]^2, x fastest: h_xi, h_eta hold nq
+ * doubles each.  The caller maps them by F and evaluates A, B, c, f there. */
+long igamg_quadrature_count(const igamg_ctx* ctx);
+igamg_status igamg_quadrature_points(const igamg_ctx* ctx, double* h_xi, double* h_eta);
+/* Assembles every level on the host and uploads it (may be called again with
+ * new coefficients).  h_coef: 6 nq doubles, A11, A12, A22, B1, B2, c at the
+ * mapped points (coefficient-major: h_coef[k nq + q]); h_jac: 4 nq doubles,
+ * dF1/dxi, dF1/deta, dF2/dxi, dF2/deta at the points, or NULL for the unit
+ * square (F = identity). */
+igamg_status igamg_assemble_general(igamg_ctx* ctx, const double* h_coef, const double* h_jac);
+/* Load vector b_I = int f phi_I (with |J|) from h_f: nq values of f at the
+ * mapped points; writes d_b (finest N) and synchronises `stream`. */
+igamg_status igamg_rhs_points(igamg_ctx* ctx, const double* h_f, double* d_b, void* stream);
+
 /* ---------------------------------------------------------------- solve */
 
 /* Restarted extrapolation (Algorithm 5) around the V-cycle (Algorithm 2, mu=1,

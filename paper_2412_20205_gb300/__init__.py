@@ -51,6 +51,11 @@ def _load():
         "igamg_get_factor": (c_int, [vp, c_int, c_int, c_int, dp, ip, ip]),
         "igamg_workspace_bytes": (c_size, [vp, c_int, c_int]),
         "igamg_rhs_sine": (c_int, [vp, c_int, dp, vp, vp]),
+        "igamg_setup_general": (c_int, [c_int, ip, c_int, ctypes.POINTER(vp)]),
+        "igamg_quadrature_count": (c_long, [vp]),
+        "igamg_quadrature_points": (c_int, [vp, dp, dp]),
+        "igamg_assemble_general": (c_int, [vp, dp, dp]),
+        "igamg_rhs_points": (c_int, [vp, dp, vp, vp]),
         "igamg_solve": (c_int, [vp, vp, vp, c_double, c_int, c_int, c_int, c_int, ctypes.c_uint,
                                 vp, c_size, vp, dp, ip, ip]),
         "igamg_apply": (c_int, [vp, c_int, vp, vp, vp, c_size, vp]),
@@ -174,6 +179,38 @@ def igamg_rhs_sine(ctx, coeffs, b, stream=None):
     import numpy as np
     c = np.ascontiguousarray(coeffs, dtype=np.float64)
     _check(_load().igamg_rhs_sine(ctx, c.shape[0], _dbl(c), _ptr(b), _stream(stream)), "igamg_rhs_sine")
+
+
+def igamg_setup_general(p, n_elems, n_levels=0):
+    n = list(n_elems) if hasattr(n_elems, "__len__") else [int(n_elems)] * 2
+    arr = (ctypes.c_int * 3)(*(n + [1]))
+    ctx = ctypes.c_void_p()
+    _check(_load().igamg_setup_general(p, arr, n_levels, ctypes.byref(ctx)), "igamg_setup_general")
+    return ctx
+
+
+def igamg_quadrature_points(ctx):
+    """(xi, eta) arrays of the finest level's quadrature points (x fastest)."""
+    import numpy as np
+    nq = int(_load().igamg_quadrature_count(ctx))
+    xi, eta = np.zeros(nq), np.zeros(nq)
+    _check(_load().igamg_quadrature_points(ctx, _dbl(xi), _dbl(eta)), "igamg_quadrature_points")
+    return xi, eta
+
+
+def igamg_assemble_general(ctx, coef, jac=None):
+    """coef: (6, nq) A11, A12, A22, B1, B2, c at the mapped points; jac: (4, nq) or None."""
+    import numpy as np
+    cf = np.ascontiguousarray(coef, dtype=np.float64)
+    jc = None if jac is None else np.ascontiguousarray(jac, dtype=np.float64)
+    _check(_load().igamg_assemble_general(ctx, _dbl(cf), None if jc is None else _dbl(jc)),
+           "igamg_assemble_general")
+
+
+def igamg_rhs_points(ctx, f, b, stream=None):
+    import numpy as np
+    fv = np.ascontiguousarray(f, dtype=np.float64)
+    _check(_load().igamg_rhs_points(ctx, _dbl(fv), _ptr(b), _stream(stream)), "igamg_rhs_points")
 
 
 def igamg_solve(ctx, b, x, tol, extrap, k, max_cycles, prec, flags, ws, stream=None):
@@ -484,6 +521,42 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+class GeneralSolver(Solver):
+    """The full elliptic problem of Sec. 4.3 on a (mapped) unit square: the
+    problem's functions are evaluated at the library's quadrature points
+    (mapped by `geometry`, which returns (x, y, J)) and passed to the
+    assembly; solves run in FP64."""
+
+    def __init__(self, p, n, A, B, c, geometry=None, n_levels=0, k=10, device="cuda"):
+        import numpy as np
+        import torch
+        self.dim, self.p = 2, p
+        self.ctx = igamg_setup_general(p, n, n_levels)
+        xi, eta = igamg_quadrature_points(self.ctx)
+        if geometry is None:
+            x, y, J = xi, eta, None
+        else:
+            x, y, J = geometry(xi, eta)
+        self.points = (x, y)
+        Av, Bv = A(x, y), B(x, y)
+        coef = np.stack([Av[:, 0, 0], Av[:, 0, 1], Av[:, 1, 1], Bv[:, 0], Bv[:, 1], c(x, y)])
+        jac = None if J is None else np.stack([J[:, 0, 0], J[:, 0, 1], J[:, 1, 0], J[:, 1, 1]])
+        igamg_assemble_general(self.ctx, coef, jac)
+        self.levels = igamg_info(self.ctx)
+        m = self.levels[-1]
+        self.N = m[0] * m[1] * m[2]
+        self.ws = torch.empty(igamg_workspace_bytes(self.ctx, k, IGAMG_FP64), dtype=torch.uint8, device=device)
+        self.k_max = k
+        self.smoother = None
+
+    def rhs(self, f):
+        """Load vector of f (a function of the physical point)."""
+        import torch
+        b = torch.empty(self.N, dtype=torch.float64, device=self.ws.device)
+        igamg_rhs_points(self.ctx, f(*self.points), b)
+        return b
 
 
 class Batch:

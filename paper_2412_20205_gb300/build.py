@@ -17,7 +17,8 @@ NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE,
            "--expt-relaxed-constexpr"]
-SOURCES = ["kernels.cu", "api.cu", "noalloc.cu", "cnn.cu", "tail.cu", "refine.cu", "host_setup.cpp"]
+SOURCES = ["kernels.cu", "api.cu", "noalloc.cu", "cnn.cu", "tail.cu", "refine.cu", "general.cu", "host_setup.cpp",
+           "general_setup.cpp"]
 
 
 def _cmd(src, obj):

@@ -161,6 +161,16 @@ struct igamg_ctx {
     Key loop_key[3];
     LoopState* h_loop = nullptr;
     double* h_hist = nullptr;
+    // general operator of Sec. 4.3 (igamg_setup_general): quadrature data of
+    // the finest level, |J| at its points, and per level the stencil
+    // operator (device memory gmem, views sv) and the coarsest dense inverse
+    bool general = false, gen_ready = false;
+    Quad1D gqx, gqy;
+    std::vector<double> gdet;
+    void* gmem = nullptr;
+    std::vector<StencilView> sv;
+    double* A0inv = nullptr;
+    int n0 = 0;
     // learned post-smoother: caller-owned device weights, stall ratio, outcome
     const float* cnn_w = nullptr;
     double stall = 0.9;
@@ -475,6 +485,41 @@ void vcycle(const igamg_ctx* c, cudaStream_t s, Workspace& w, int top, T* x_top,
     }
 }
 
+// ---------------------------------------------------------------- general operator
+// Algorithm 2 (any mu; nu1 = nu2 = 1) on the stencil levels of a general
+// context: multicolour Gauss-Seidel (ascending before, descending after the
+// coarse correction) or weighted Jacobi, residual on the stencil, restriction
+// R = P^T and prolongation P of the Poisson path, Galerkin coarse operators,
+// dense coarsest solve.  Level l's r holds its residual; x | TM of a coarse
+// level are its iterate.
+void gen_mu_cycle(const igamg_ctx* c, cudaStream_t s, Workspace& w, int top, int l, double* x_top,
+                  const double* b_top, bool zero) {
+    auto& B = w.d;
+    double* x = (l == top) ? x_top : B[l].x;
+    const double* b = (l == top) ? b_top : B[l].b;
+    const StencilView& V = c->sv[l];
+    if (l == 0) {
+        dev::gen_dense_apply(s, c->A0inv, c->n0, b, x);
+        return;
+    }
+    if (zero) dev::fill_zero<double>(s, x, V.n());
+    auto smooth = [&](bool descending) {
+        if (c->smoother == IGAMG_SMOOTH_JACOBI) {
+            dev::gen_residual(s, V, x, b, B[l].r, nullptr);
+            dev::gen_jacobi_update(s, V, c->omega, B[l].r, x);
+        } else {
+            dev::gen_gs_sweep(s, V, descending, x, b);
+        }
+    };
+    smooth(false);
+    dev::gen_residual(s, V, x, b, B[l].r, nullptr);
+    dev::restrict_<double>(s, 2, c->tv64[l], B[l].r, B[l - 1].b, B[l].tmp1, B[l].tmp2);
+    const int reps = (l - 1 == 0) ? 1 : c->mu;
+    for (int i = 0; i < reps; ++i) gen_mu_cycle(c, s, w, top, l - 1, x_top, b_top, i == 0);
+    dev::gen_prolong_add(s, c->tv64[l], B[l - 1].x, x);
+    smooth(true);
+}
+
 // One V-cycle (fixed-point step s_{i+1} = G(s_i), Eq. fixedpoint) from S_in to
 // S_out on the finest level; the finest FP64 TM/TK match S_in on entry and
 // S_out on exit.
@@ -483,6 +528,11 @@ void fixed_point_step(const igamg_ctx* c, cudaStream_t s, Workspace& w, int prec
     const int top = c->L - 1;
     const size_t N = finestN(c);
     LevelBuf<double>& F = w.d[top];
+    if (c->general) {                               // FP64 only (checked by the callers)
+        if (S_out != S_in) cudaMemcpyAsync(S_out, S_in, N * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        gen_mu_cycle(c, s, w, top, top, S_out, d_b, false);
+        return;
+    }
     if (prec == IGAMG_FP64) {
         if (S_out != S_in) cudaMemcpyAsync(S_out, S_in, N * sizeof(double), cudaMemcpyDeviceToDevice, s);
         vcycle<double>(c, s, w, top, S_out, d_b, false);
@@ -502,6 +552,11 @@ void residual_norm(const igamg_ctx* c, cudaStream_t s, Workspace& w, const doubl
                    const double* denom) {
     const int top = c->L - 1;
     LevelBuf<double>& F = w.d[top];
+    if (c->general) {
+        dev::gen_residual(s, c->sv[top], w.S, d_b, F.r, w.partial);
+        dev::norm_final(s, w.partial, dev::gen_blocks(c->sv[top].n()), denom, w.scal, 1);
+        return;
+    }
     if (!w.f.empty())           // FP32-IR workspace: also leave r in FP32 for the next V-cycle
         dev::residual<double, float>(s, c->dim, c->lv64[top], d_b, F.TM, F.TK, w.f[top].b, w.partial, F.r);
     else
@@ -516,6 +571,13 @@ void restart_body(const igamg_ctx* c, cudaStream_t s, Workspace& w, int extrap, 
     const int top = c->L - 1;
     if (extrap == IGAMG_EXTRAP_NONE) {
         fixed_point_step(c, s, w, prec, d_b, w.S, w.S);
+    } else if (c->general) {
+        // general operator: FP64 cycles; t = sum_j gamma_j s_j -> S_0 (no row sums)
+        for (int i = 0; i <= k; ++i)
+            fixed_point_step(c, s, w, prec, d_b, w.S + (size_t)i * w.ld, w.S + (size_t)(i + 1) * w.ld);
+        const int nb = dev::gram_blocks(N);
+        dev::extrap_gammas(s, k, extrap, w.S, w.ld, N, w.partial, nb, w.info, w.gamma, w.qused);
+        dev::combine(s, k, w.gamma, w.S, w.ld, N, w.S);
     } else if (prec != IGAMG_FP64 && c->dim == 2) {
         // FP32 V-cycles with the FP64 residual carried by r <- r - A e in
         // double-FP32 arithmetic (refine.cu); the restart's first residual and
@@ -1020,7 +1082,132 @@ size_t igamg_workspace_bytes(const igamg_ctx* c, int k, int prec) {
     return carve(c, nullptr, std::max(k, 1), prec).bytes;
 }
 
+static void drop_graphs(igamg_ctx* c);
+
+igamg_status igamg_setup_general(int p, const int* n_elems, int n_levels, igamg_ctx** out) {
+    if (igamg_status st = igamg_setup(2, p, n_elems, n_levels, out)) return st;
+    igamg_ctx* c = *out;
+    if (n_elems[0] > 1024 || n_elems[1] > 1024) {
+        igamg_destroy(c);
+        *out = nullptr;
+        return fail(IGAMG_EINVAL, "general operator: at most 1024 elements per direction");
+    }
+    c->general = true;
+    c->gqx = quadrature_1d(c->hl.back().breaks[0], p);
+    c->gqy = quadrature_1d(c->hl.back().breaks[1], p);
+    return IGAMG_OK;
+}
+
+long igamg_quadrature_count(const igamg_ctx* c) {
+    return (c && c->general) ? (long)c->gqx.nq * c->gqy.nq : 0;
+}
+
+igamg_status igamg_quadrature_points(const igamg_ctx* c, double* h_xi, double* h_eta) {
+    if (!c || !c->general || !h_xi || !h_eta) return fail(IGAMG_EINVAL, "general context and two arrays needed");
+    for (int qy = 0; qy < c->gqy.nq; ++qy)
+        for (int qx = 0; qx < c->gqx.nq; ++qx) {
+            const size_t q = (size_t)qy * c->gqx.nq + qx;
+            h_xi[q] = c->gqx.x[qx];
+            h_eta[q] = c->gqy.x[qy];
+        }
+    return IGAMG_OK;
+}
+
+igamg_status igamg_assemble_general(igamg_ctx* c, const double* h_coef, const double* h_jac) {
+    if (!c || !c->general || !h_coef) return fail(IGAMG_EINVAL, "general context and coefficients needed");
+    if (!c->assembled)
+        if (igamg_status st = igamg_assemble(c)) return st;
+    const size_t nq = (size_t)c->gqx.nq * c->gqy.nq;
+    // transformed coefficients on the unit square: |J| J^{-1} A J^{-T}, |J| J^{-1} B, |J| c
+    std::vector<double> co(6 * nq);
+    c->gdet.assign(nq, 1.0);
+    for (size_t q = 0; q < nq; ++q) {
+        const double a11 = h_coef[q], a12 = h_coef[nq + q], a22 = h_coef[2 * nq + q];
+        const double b1 = h_coef[3 * nq + q], b2 = h_coef[4 * nq + q], cc = h_coef[5 * nq + q];
+        double j11 = 1, j12 = 0, j21 = 0, j22 = 1;
+        if (h_jac) { j11 = h_jac[q]; j12 = h_jac[nq + q]; j21 = h_jac[2 * nq + q]; j22 = h_jac[3 * nq + q]; }
+        const double det = j11 * j22 - j12 * j21;
+        if (!(det > 0.0) || !std::isfinite(det)) return fail(IGAMG_EINVAL, "geometry Jacobian not positive");
+        // K = J^{-1} = adj(J) / det
+        const double k11 = j22 / det, k12 = -j12 / det, k21 = -j21 / det, k22 = j11 / det;
+        // K A K^T
+        const double t11 = k11 * a11 + k12 * a12, t12 = k11 * a12 + k12 * a22;
+        const double t21 = k21 * a11 + k22 * a12, t22 = k21 * a12 + k22 * a22;
+        co[q] = det * (t11 * k11 + t12 * k12);
+        co[nq + q] = det * (t11 * k21 + t12 * k22);
+        co[2 * nq + q] = det * (t21 * k21 + t22 * k22);
+        co[3 * nq + q] = det * (k11 * b1 + k12 * b2);
+        co[4 * nq + q] = det * (k21 * b1 + k22 * b2);
+        co[5 * nq + q] = det * cc;
+        c->gdet[q] = det;
+    }
+    const int L = c->L, p = c->p, W = 2 * p + 1;
+    std::vector<Stencil2D> ops(L);
+    std::vector<double> A0inv;
+    try {
+        ops[L - 1] = assemble_general(c->gqx, c->gqy, co.data());
+        for (int l = L - 1; l >= 1; --l)
+            ops[l - 1] = galerkin_coarse(ops[l], c->hl[l].P[0], c->hl[l - 1].m[0], c->hl[l].P[1], c->hl[l - 1].m[1]);
+        if (!dense_inverse(ops[0], A0inv)) return fail(IGAMG_EINVAL, "singular coarsest operator");
+    } catch (const std::exception& e) {
+        return fail(IGAMG_EINVAL, std::string("general assembly: ") + e.what());
+    }
+    // one device allocation: per level the stencil and the inverse diagonal, then the coarsest inverse
+    std::vector<size_t> off(2 * L + 1);
+    size_t total = 0;
+    for (int l = 0; l < L; ++l) {
+        off[2 * l] = total;
+        total = (total + ops[l].S.size() * 8 + 255) & ~(size_t)255;
+        off[2 * l + 1] = total;
+        total = (total + ops[l].N() * 8 + 255) & ~(size_t)255;
+    }
+    off[2 * L] = total;
+    total += A0inv.size() * 8;
+    if (c->gmem) { cudaFree(c->gmem); c->gmem = nullptr; }
+    c->gen_ready = false;
+    CUDA_TRY(cudaMalloc(&c->gmem, total));
+    char* base = (char*)c->gmem;
+    c->sv.assign(L, StencilView{});
+    for (int l = 0; l < L; ++l) {
+        const size_t N = ops[l].N();
+        std::vector<double> inv(N);
+        for (size_t I = 0; I < N; ++I) {
+            const double d = ops[l].S[(size_t)(p * W + p) * N + I];
+            if (!(d != 0.0)) return fail(IGAMG_EINVAL, "zero diagonal in the general operator");
+            inv[I] = 1.0 / d;
+        }
+        CUDA_TRY(cudaMemcpy(base + off[2 * l], ops[l].S.data(), ops[l].S.size() * 8, cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(base + off[2 * l + 1], inv.data(), N * 8, cudaMemcpyHostToDevice));
+        StencilView& V = c->sv[l];
+        V.m[0] = ops[l].mx;
+        V.m[1] = ops[l].my;
+        V.p = p;
+        V.S = (const double*)(base + off[2 * l]);
+        V.inv = (const double*)(base + off[2 * l + 1]);
+    }
+    CUDA_TRY(cudaMemcpy(base + off[2 * L], A0inv.data(), A0inv.size() * 8, cudaMemcpyHostToDevice));
+    c->A0inv = (double*)(base + off[2 * L]);
+    c->n0 = (int)ops[0].N();
+    c->gen_ready = true;
+    drop_graphs(c);
+    return IGAMG_OK;
+}
+
+igamg_status igamg_rhs_points(igamg_ctx* c, const double* h_f, double* d_b, void* stream) {
+    if (!c || !c->general || !h_f || !d_b) return fail(IGAMG_EINVAL, "general context, f and d_b needed");
+    if (c->gdet.empty()) return fail(IGAMG_EINVAL, "call igamg_assemble_general first");
+    const size_t nq = (size_t)c->gqx.nq * c->gqy.nq;
+    std::vector<double> fq(nq);
+    for (size_t q = 0; q < nq; ++q) fq[q] = c->gdet[q] * h_f[q];
+    const std::vector<double> b = load_general(c->gqx, c->gqy, fq.data());
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemcpyAsync(d_b, b.data(), b.size() * 8, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return IGAMG_OK;
+}
+
 igamg_status igamg_rhs_sine(igamg_ctx* c, int modes, const double* h_coeffs, double* d_b, void* stream) {
+    if (c && c->general) return fail(IGAMG_EINVAL, "not available for a general-operator context");
     if (igamg_status st = check_ctx(c)) return st;
     if (modes < 1 || modes > 64 || !h_coeffs || !d_b) return fail(IGAMG_EINVAL, "bad rhs arguments");
     const HostLevel& H = c->hl.back();
@@ -1061,6 +1248,8 @@ igamg_status igamg_solve(igamg_ctx* c, const double* d_b, double* d_x, double to
     if (prec == IGAMG_FP32_IR_LEARNED && !default_cycle(c))
         return fail(IGAMG_EINVAL, "the learned post-smoother replaces Gauss-Seidel in the V-cycle (igamg_set_cycle)");
     c->fell_back = 0;
+    if (c->general && (!c->gen_ready || prec != IGAMG_FP64))
+        return fail(IGAMG_EINVAL, "general operator: call igamg_assemble_general first; FP64 cycles only");
     if (extrap != IGAMG_EXTRAP_NONE && (k < 1 || k > kMaxQ)) return fail(IGAMG_EINVAL, "k must be in [1, 12]");
     if (max_cycles < 0 || !(tol >= 0.0)) return fail(IGAMG_EINVAL, "bad max_cycles/tol");
     const int kk = (extrap == IGAMG_EXTRAP_NONE) ? 1 : k;
@@ -1079,8 +1268,9 @@ igamg_status igamg_solve(igamg_ctx* c, const double* d_b, double* d_x, double to
         CUDA_TRY(cudaMemcpyAsync(w.S, d_x, N * 8, cudaMemcpyDeviceToDevice, s));
     else
         dev::fill_zero<double>(s, w.S, N);
-    dev::xpass<double, double>(s, c->lv64[top], w.S, w.S, nullptr, 0, nullptr, nullptr, 0,
-                               w.d[top].TM, w.d[top].TK);
+    if (!c->general)
+        dev::xpass<double, double>(s, c->lv64[top], w.S, w.S, nullptr, 0, nullptr, nullptr, 0,
+                                   w.d[top].TM, w.d[top].TK);
     const double* denom = (flags & IGAMG_FLAG_ABS_TOL) ? nullptr : w.scal;
     CUDA_TRY(cudaMemcpyAsync(c->h_pin, w.scal, 8, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
@@ -1200,8 +1390,6 @@ void igamg_set_wait_limit(double seconds, int test_unset_flag) {
     set_wait_limit(seconds > 0 ? (long long)(seconds * 1e9) : 0, test_unset_flag);
 }
 
-static void drop_graphs(igamg_ctx* c);
-
 igamg_status igamg_set_sweep_form(igamg_ctx* c, int single_launch_fp32, int single_launch_fp64) {
     if (igamg_status st = check_ctx(c, false)) return st;
     if (single_launch_fp32 < -1 || single_launch_fp64 < -1)
@@ -1227,6 +1415,12 @@ igamg_status igamg_apply(igamg_ctx* c, int level, const double* d_x, double* d_y
     Workspace w = carve(c, d_ws, 1, IGAMG_FP64);
     cudaStream_t s = (cudaStream_t)stream;
     LevelBuf<double>& B = w.d[level];
+    if (c->general) {
+        if (!c->gen_ready) return fail(IGAMG_EINVAL, "call igamg_assemble_general first");
+        dev::gen_residual(s, c->sv[level], d_x, nullptr, d_y, nullptr);
+        CUDA_TRY(cudaGetLastError());
+        return IGAMG_OK;
+    }
     dev::xpass<double, double>(s, c->lv64[level], d_x, nullptr, nullptr, 0, nullptr, nullptr, 0, B.TM, B.TK);
     dev::residual<double, double>(s, c->dim, c->lv64[level], nullptr, B.TM, B.TK, d_y, nullptr);
     CUDA_TRY(cudaGetLastError());
@@ -1241,6 +1435,12 @@ igamg_status igamg_smooth(igamg_ctx* c, int level, double* d_x, const double* d_
     Workspace w = carve(c, d_ws, 1, IGAMG_FP64);
     cudaStream_t s = (cudaStream_t)stream;
     LevelBuf<double>& B = w.d[level];
+    if (c->general) {
+        if (!c->gen_ready) return fail(IGAMG_EINVAL, "call igamg_assemble_general first");
+        dev::gen_gs_sweep(s, c->sv[level], descending != 0, d_x, d_b);
+        CUDA_TRY(cudaGetLastError());
+        return IGAMG_OK;
+    }
     dev::xpass<double, double>(s, c->lv64[level], d_x, nullptr, nullptr, 0, nullptr, nullptr, 0, B.TM, B.TK);
     CUDA_TRY(clear_sync(w, s));
     sweep<double>(c, s, w, level, descending != 0, d_x, d_b, B.TM, B.TK);
@@ -1251,6 +1451,7 @@ igamg_status igamg_smooth(igamg_ctx* c, int level, double* d_x, const double* d_
 igamg_status igamg_smooth_f32(igamg_ctx* c, int level, float* d_x, const float* d_b, int descending,
                               int sums_current, void* d_ws, size_t ws_bytes, void* stream) {
     if (igamg_status st = check_ctx(c)) return st;
+    if (c && c->general) return fail(IGAMG_EINVAL, "not available for a general-operator context");
     if (level < 0 || level >= c->L || !d_x || !d_b) return fail(IGAMG_EINVAL, "bad smooth arguments");
     if (igamg_status st = check_ws(c, d_ws, ws_bytes, 1, IGAMG_FP32_IR)) return st;
     Workspace w = carve(c, d_ws, 1, IGAMG_FP32_IR);
@@ -1302,6 +1503,8 @@ igamg_status igamg_vcycle(igamg_ctx* c, double* d_x, const double* d_b, int prec
                           void* stream) {
     if (igamg_status st = check_ctx(c)) return st;
     if (!d_x || !d_b || prec < 0 || prec > 2) return fail(IGAMG_EINVAL, "bad vcycle arguments");
+    if (c->general && (!c->gen_ready || prec != IGAMG_FP64))
+        return fail(IGAMG_EINVAL, "general operator: call igamg_assemble_general first; FP64 cycles only");
     if (prec == IGAMG_FP32_IR_LEARNED && !c->cnn_w) return fail(IGAMG_EINVAL, "no learned smoother set");
     if (prec == IGAMG_FP32_IR_LEARNED && !default_cycle(c))
         return fail(IGAMG_EINVAL, "the learned post-smoother replaces Gauss-Seidel in the V-cycle (igamg_set_cycle)");
@@ -1310,8 +1513,9 @@ igamg_status igamg_vcycle(igamg_ctx* c, double* d_x, const double* d_b, int prec
     cudaStream_t s = (cudaStream_t)stream;
     const int top = c->L - 1;
     CUDA_TRY(clear_sync(w, s));
-    dev::xpass<double, double>(s, c->lv64[top], d_x, nullptr, nullptr, 0, nullptr, nullptr, 0, w.d[top].TM,
-                               w.d[top].TK);
+    if (!c->general)
+        dev::xpass<double, double>(s, c->lv64[top], d_x, nullptr, nullptr, 0, nullptr, nullptr, 0, w.d[top].TM,
+                                   w.d[top].TK);
     fixed_point_step(c, s, w, prec, d_b, d_x, d_x);
     CUDA_TRY(cudaGetLastError());
     return IGAMG_OK;
@@ -1352,6 +1556,7 @@ igamg_status igamg_extrapolate(long n, int q, int method, const double* d_S, lon
 }
 
 igamg_status igamg_set_smoother(igamg_ctx* c, const float* d_w, double stall_ratio) {
+    if (c && c->general) return fail(IGAMG_EINVAL, "not available for a general-operator context");
     if (igamg_status st = check_ctx(c)) return st;
     if (!(stall_ratio > 0.0)) return fail(IGAMG_EINVAL, "stall ratio must be positive");
     if (d_w && c->dim != 2) return fail(IGAMG_EINVAL, "the learned smoother is a 2D network");
@@ -1426,6 +1631,7 @@ void igamg_get_schedule(const igamg_ctx* c, int* gs_threads, int* tail_levels) {
 
 igamg_status igamg_autotune(igamg_ctx* c, void* d_ws, size_t ws_bytes, void* stream, int reps) {
     if (igamg_status st = check_ctx(c)) return st;
+    if (c && c->general) return fail(IGAMG_EINVAL, "not available for a general-operator context");
     if (reps < 1) return fail(IGAMG_EINVAL, "reps must be >= 1");
     if (igamg_status st = check_ws(c, d_ws, ws_bytes, 1, IGAMG_FP32_IR)) return st;
     Workspace w = carve(c, d_ws, 1, IGAMG_FP32_IR);
@@ -1524,6 +1730,7 @@ igamg_status igamg_set_coarse_tail(igamg_ctx* c, int enable) {
 igamg_status igamg_vcycle_probe(igamg_ctx* c, double* d_x, const double* d_b, double* d_x_mid, void* d_ws,
                                 size_t ws_bytes, void* stream) {
     if (c && !default_cycle(c)) return fail(IGAMG_EINVAL, "the probe follows the Gauss-Seidel V-cycle");
+    if (c && c->general) return fail(IGAMG_EINVAL, "not available for a general-operator context");
     if (igamg_status st = check_ctx(c)) return st;
     if (!d_x || !d_b || !d_x_mid) return fail(IGAMG_EINVAL, "bad probe arguments");
     if (igamg_status st = check_ws(c, d_ws, ws_bytes, 1, IGAMG_FP64)) return st;
@@ -1547,6 +1754,7 @@ igamg_status igamg_training_pairs(igamg_ctx* c, const double* d_b, const double*
                                   int max_restarts, float* d_R, float* d_E, int max_pairs, void* d_ws,
                                   size_t ws_bytes, void* stream, int* h_pairs) {
     if (c && !default_cycle(c)) return fail(IGAMG_EINVAL, "the probe follows the Gauss-Seidel V-cycle");
+    if (c && c->general) return fail(IGAMG_EINVAL, "not available for a general-operator context");
     if (igamg_status st = check_ctx(c)) return st;
     if (!d_b || !d_uh || !d_R || !d_E || !h_pairs || k < 1 || k > kMaxQ || max_restarts < 1 || max_pairs < 0 ||
         !(tol >= 0.0))
@@ -1614,6 +1822,7 @@ void igamg_destroy(igamg_ctx* c) {
     if (c->h_loop) cudaFreeHost(c->h_loop);
     if (c->h_hist) cudaFreeHost(c->h_hist);
     if (c->dmem) cudaFree(c->dmem);
+    if (c->gmem) cudaFree(c->gmem);
     delete c;
 }
 

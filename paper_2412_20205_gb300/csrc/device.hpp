@@ -94,6 +94,17 @@ struct DFView {
     float Mch[2][2 * kMaxP + 1], Mcl[2][2 * kMaxP + 1], Kch[2][2 * kMaxP + 1], Kcl[2][2 * kMaxP + 1];
 };
 
+// A 2D level of the general operator (Sec. 4.3) in stencil form:
+// S[k N + I] = A(I, I + dx + m[0] dy), k = (dy + p)(2p+1) + (dx + p), and the
+// inverse diagonal.
+struct StencilView {
+    int m[2];
+    int p;
+    const double* S;
+    const double* inv;
+    IGAMG_HD size_t n() const { return (size_t)m[0] * m[1]; }
+};
+
 // Synchronisation words of a single-launch Gauss-Seidel sweep on one level
 // (in the caller's workspace).  They are zero before a sweep and every sweep
 // leaves them zero, so they are cleared once when a workspace is taken into
@@ -299,6 +310,22 @@ cudaError_t add_loop_init_node(cudaGraph_t g, cudaGraphConditionalHandle h, cons
 void diff_sumsq(cudaStream_t s, const double* u, const double* v, size_t n, double* e, double* partial,
                 int nblocks);
 void scale_pair(cudaStream_t s, const double* r, const double* e, const double* enorm, size_t n, float* R, float* E);
+
+// ---- general operator (general.cu)
+// r = b - A x (b null: r = A x), with gen_blocks(n) per-block
+// partial sums of r^2 into partial when non-null (nparts = gen_blocks(n)).
+int gen_blocks(size_t n);
+void gen_residual(cudaStream_t s, const StencilView& V, const double* x, const double* b, double* r,
+                  double* partial);
+// One multicolour Gauss-Seidel sweep ((p+1)^2 colours in colour order, each
+// colour from the x the previous ones left), descending = reversed order.
+void gen_gs_sweep(cudaStream_t s, const StencilView& V, bool descending, double* x, const double* b);
+// x += omega D^{-1} r.
+void gen_jacobi_update(cudaStream_t s, const StencilView& V, double omega, const double* r, double* x);
+// x += P e for a 2D transfer (row form of P).
+void gen_prolong_add(cudaStream_t s, const TransferView<double>& X, const double* e, double* x);
+// e = Ainv r, dense n x n (the coarsest level).
+void gen_dense_apply(cudaStream_t s, const double* Ainv, int n, const double* r, double* e);
 
 // Partial sums of squares of v (deterministic): nblocks partials.
 void sumsq_partial(cudaStream_t s, const double* v, size_t n, double* partial, int nblocks);

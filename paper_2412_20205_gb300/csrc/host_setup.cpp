@@ -119,7 +119,7 @@ static void basis_on_span(const std::vector<double>& U, int p, int s, double x, 
 }
 
 // Values and first derivatives of N_{s-p+r}, r = 0..p, at x in span s.
-static void basis_and_derivative(const std::vector<double>& U, int p, int s, double x,
+void basis_and_derivative(const std::vector<double>& U, int p, int s, double x,
                                  double* N, double* dN) {
     basis_on_span(U, p, s, x, N);
     if (p == 0) { dN[0] = 0.0; return; }
