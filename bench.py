@@ -31,6 +31,82 @@ METRIC = "time to rel. residual 1e-10 and DOF/s: FP64 GMG+RRE vs mixed/learned f
 GS_TRAFFIC = {(2, 1024, 3): 11.77e6}
 
 
+# FP64 pipe: the nominal GB300 rate of the profiling recipe (1.25 TFLOP/s;
+# an FMA-throughput loop measured 1.20 on this machine's GB300).
+FP64_PEAK_GFLOPS = 1250.0
+
+
+def kernel_models(a, p, k):
+    """Algorithmic bytes and FP64 flops per unknown of one launch of the
+    streaming kernels of a 2D mixed-precision solve, by kernel name prefix.
+    GS row phase: the 12 B/DOF of a sweep (read x, b; write x) over the phase's
+    rows; residual + restriction and prolongation + correction: 9 B/DOF (FP32);
+    float-pair refinement kernels: four float-pair row-sum arrays (16 B) with r
+    or the iterates (20 B); CholeskyQR2 passes: the q+2 iterates (8(q+2) B),
+    (q+1)(q+3) and 2(q+1)(q+2) flops; combination x-pass: the iterates read and
+    x, T_M, T_K written, 2(q+2) + 4(2p+1) flops; FP64 residual: b, T_M, T_K
+    read, r in FP32 and FP64 written, 4(2p+1) flops."""
+    q = k
+    return {
+        "k_gs_phase2<float": (12.0, 0.0),
+        "k_residual_restrict_x<float": (9.0, 0.0),
+        "k_prolong_fused2<float": (9.0, 0.0),
+        "k_xpass_df<": (36.0, 0.0),
+        "k_residual_df<": (36.0, 0.0),
+        "k_gram_partial<": (8.0 * (q + 2), float((q + 1) * (q + 3))),
+        "k_gram2_partial<": (8.0 * (q + 2), float(2 * (q + 1) * (q + 2))),
+        "k_xpass<double, double": (8.0 * (q + 2) + 24.0, float(2 * (q + 2) + 4 * (2 * p + 1))),
+        "k_residual<double, float": (36.0, float(4 * (2 * p + 1))),
+    }
+
+
+def kernel_table(pkg, s, b, a, peak_hbm):
+    """One mixed-precision solve enqueued kernel by kernel (no graph) with
+    every launch timed by CUDA events on its own stream (igamg_profile_*).
+    Per kernel: launches, total time and share, average launch time; for the
+    streaming kernels also the finest-level launches' algorithmic bytes and
+    FP64 flops per launch and their fractions of the measured HBM copy rate
+    and of the FP64 peak.  Finest-level launches are those with the largest
+    grid of their kernel (row kernels: one CTA per row; the Gram passes run
+    on the finest level only)."""
+    import numpy as np
+    pkg.igamg_profile_start()
+    s.solve(b, tol=1e-10, method=a.method, k=a.k, prec="fp32_ir", max_cycles=200, graph=False, host_loop=True)
+    recs = pkg.igamg_profile_stop()
+    mx, my = s.levels[-1][0], s.levels[-1][1] * s.levels[-1][2]
+    models = kernel_models(a, a.p, a.k)
+    total = sum(r[1] for r in recs)
+    by = {}
+    for name, us, grid in recs:
+        by.setdefault(name, []).append((us, grid))
+    rows = []
+    for name, lst in sorted(by.items(), key=lambda kv: -sum(u for u, _ in kv[1])):
+        t = sum(u for u, _ in lst)
+        e = {"kernel": name, "launches": len(lst), "total_us": round(t, 1), "share": round(t / total, 4),
+             "avg_us": round(t / len(lst), 3)}
+        model = next((v for key, v in models.items() if name.startswith(key)), None)
+        if model is not None:
+            gmax = max(g for _, g in lst)
+            fin = [u for u, g in lst if g == gmax]
+            us = float(np.mean(fin))
+            if name.startswith(("k_gs_phase2", "k_residual_restrict_x", "k_prolong_fused2", "k_xpass_df",
+                                "k_residual_df", "k_xpass<", "k_residual<")):
+                dofs = gmax * mx                    # one CTA per row of mx unknowns
+            else:
+                dofs = s.N                          # the Gram passes: the finest vectors
+            bts, fl = model[0] * dofs, model[1] * dofs
+            e.update({"finest_launches": len(fin), "finest_avg_us": round(us, 3), "algorithmic_bytes": bts,
+                      "hbm_gbs": round(bts / (us * 1e3), 1), "hbm_frac": round(bts / (us * 1e3) / peak_hbm, 4)})
+            if fl > 0:
+                e.update({"fp64_flops": fl, "fp64_gflops": round(fl / (us * 1e3), 1),
+                          "fp64_frac": round(fl / (us * 1e3) / FP64_PEAK_GFLOPS, 4)})
+        rows.append(e)
+    return {"how": "one FP32-IR solve enqueued without the graph, every launch between CUDA events on its "
+                   "stream (launch overlap lost); fractions of measured HBM copy rate (MEASURED_PEAKS.json) "
+                   "and of the FP64 peak (1.25 TFLOP/s nominal)",
+            "total_us": round(total, 1), "kernels": rows[:16]}
+
+
 def measured_peak(key, fallback):
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -440,6 +516,8 @@ def run_ours(a, rank, world, local):
                            "cycles": jacobi["cycles"], "final_rel_residual": jacobi["final_rel_residual"],
                            "fp64_ms_per_step": jacobi["ms64"], "fp64_cycles": jacobi["cycles64"],
                            "smoother": "weighted Jacobi, omega = 2/3 (the paper's experiments), V(1,1)"}
+    if a.dim == 2 and a.prec == "fp32_ir":
+        line["kernel_table"] = kernel_table(pkg, s, b, a, peak_hbm)
     if not a.no_extra_forms and a.dim == 2 and world == 1:
         # the other two build workloads, measured in the same run (complete solves)
         sx = min(a.steps, 5)

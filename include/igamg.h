@@ -430,6 +430,18 @@ const char* igamg_last_error(void);
  * replayed), for launch accounting in benchmarks. */
 long long igamg_launch_count(void);
 
+/* Per-kernel timing for measurement.  After igamg_profile_start(), every
+ * kernel of the solver that this thread enqueues directly (not while a stream
+ * is captured into a graph: use IGAMG_FLAG_NO_GRAPH | IGAMG_FLAG_HOST_LOOP)
+ * is bracketed by CUDA events on its own stream.  igamg_profile_stop()
+ * synchronises on them, ends the profile and returns the number of launches
+ * recorded; the first cap of them are written in launch order: the kernel's
+ * name (NUL-terminated, at most name_len bytes each, in h_names, may be NULL),
+ * its duration in microseconds (h_us) and its grid size in CTAs (h_grid).
+ * The events serialise the stream, so launches lose their overlap. */
+void igamg_profile_start(void);
+long igamg_profile_stop(int cap, char* h_names, int name_len, double* h_us, int* h_grid);
+
 #ifdef __cplusplus
 }
 #endif

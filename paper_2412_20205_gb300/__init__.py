@@ -105,6 +105,8 @@ def _load():
         "igamg_status_str": (ctypes.c_char_p, [c_int]),
         "igamg_last_error": (ctypes.c_char_p, []),
         "igamg_launch_count": (ctypes.c_longlong, []),
+        "igamg_profile_start": (None, []),
+        "igamg_profile_stop": (c_long, [c_int, ctypes.c_char_p, c_int, dp, ip]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(L, name)
@@ -284,6 +286,25 @@ def igamg_destroy(ctx):
 
 def igamg_launch_count():
     return int(_load().igamg_launch_count())
+
+
+def igamg_profile_start():
+    _load().igamg_profile_start()
+
+
+def igamg_profile_stop(cap=20000, name_len=96):
+    """Per-launch records [(kernel name, microseconds, grid CTAs)] since igamg_profile_start."""
+    import numpy as np
+    names = ctypes.create_string_buffer(cap * name_len)
+    us = np.zeros(cap)
+    grid = (ctypes.c_int * cap)()
+    n = int(_load().igamg_profile_stop(cap, names, name_len, _dbl(us), grid))
+    raw = names.raw
+    out = []
+    for i in range(min(n, cap)):
+        nm = raw[i * name_len:(i + 1) * name_len].split(b"\0", 1)[0].decode(errors="replace")
+        out.append((nm, float(us[i]), int(grid[i])))
+    return out
 
 
 def igamg_set_smoother(ctx, w, stall_ratio=0.95):

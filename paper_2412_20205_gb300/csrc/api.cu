@@ -1386,6 +1386,12 @@ igamg_status igamg_device_status(const igamg_ctx* c, void* d_ws, size_t ws_bytes
     return IGAMG_OK;
 }
 
+void igamg_profile_start(void) { profile_start(); }
+
+long igamg_profile_stop(int cap, char* h_names, int name_len, double* h_us, int* h_grid) {
+    return profile_stop(cap, h_names, name_len, h_us, h_grid);
+}
+
 void igamg_set_wait_limit(double seconds, int test_unset_flag) {
     set_wait_limit(seconds > 0 ? (long long)(seconds * 1e9) : 0, test_unset_flag);
 }

@@ -189,6 +189,16 @@ struct NoOverlapScope {
     NoOverlapScope& operator=(const NoOverlapScope&) = delete;
 };
 
+// Per-launch timing for measurement (igamg_profile_start / igamg_profile_stop):
+// while a profile is active on this thread, launch_chained brackets each
+// launch with CUDA events on its stream (not during stream capture), and the
+// stop call reads the durations.  Off by default; adds nothing then.
+bool profiling();
+cudaEvent_t profile_before(cudaStream_t s);
+void profile_after(cudaStream_t s, const void* func, dim3 grid, cudaEvent_t e0);
+void profile_start();
+long profile_stop(int cap, char* names, int name_len, double* us, int* grid);
+
 #ifdef __CUDACC__
 __device__ __forceinline__ void pdl_enter() {
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -211,7 +221,9 @@ inline void launch_chained(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = launch_overlap() ? 1 : 0;
+    cudaEvent_t e0 = profiling() ? profile_before(s) : nullptr;
     cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+    if (e0) profile_after(s, (const void*)kern, grid, e0);
 }
 #endif
 

@@ -17,7 +17,11 @@
 
 #include <atomic>
 #include <cstdio>
+#include <cstdlib>
+#include <cxxabi.h>
+#include <string>
 #include <type_traits>
+#include <vector>
 
 namespace igamg {
 
@@ -29,6 +33,82 @@ std::atomic<long long> g_wait_ns{1000000000LL};      // one second
 std::atomic<int> g_wait_test{0};
 std::atomic<int> g_sync_gen{0};
 }
+namespace {
+struct ProfRecord {
+    const void* func;
+    unsigned grid;
+    cudaEvent_t e0, e1;
+};
+thread_local bool g_prof = false;
+thread_local std::vector<ProfRecord>* g_records = nullptr;
+}  // namespace
+
+bool profiling() { return g_prof; }
+
+cudaEvent_t profile_before(cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return nullptr;
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    cudaEventRecord(e, s);
+    return e;
+}
+
+void profile_after(cudaStream_t s, const void* func, dim3 grid, cudaEvent_t e0) {
+    cudaEvent_t e1 = nullptr;
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return; }
+    cudaEventRecord(e1, s);
+    if (!g_records) g_records = new std::vector<ProfRecord>();
+    g_records->push_back({func, grid.x * grid.y * grid.z, e0, e1});
+}
+
+void profile_start() {
+    g_prof = true;
+    if (!g_records) g_records = new std::vector<ProfRecord>();
+}
+
+long profile_stop(int cap, char* names, int name_len, double* us, int* grid) {
+    g_prof = false;
+    if (!g_records) return 0;
+    const long n = (long)g_records->size();
+    for (long i = 0; i < n; ++i) {
+        ProfRecord& r = (*g_records)[i];
+        cudaEventSynchronize(r.e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.e0, r.e1);
+        if (i < cap) {
+            if (us) us[i] = 1e3 * (double)ms;
+            if (grid) grid[i] = (int)r.grid;
+            if (names && name_len > 0) {
+                const char* nm = nullptr;
+                if (cudaFuncGetName(&nm, r.func) != cudaSuccess || !nm) nm = "?";
+                // "void igamg::dev::k_name<args>(params)" -> "k_name<args>"
+                int st = 0;
+                char* dm = abi::__cxa_demangle(nm, nullptr, nullptr, &st);
+                std::string full = (st == 0 && dm) ? dm : nm;
+                std::free(dm);
+                size_t depth = 0, end = full.size();
+                for (size_t c = 0; c < full.size(); ++c) {
+                    if (full[c] == '<') ++depth;
+                    else if (full[c] == '>') --depth;
+                    else if (full[c] == '(' && depth == 0) { end = c; break; }
+                }
+                std::string shortn = full.substr(0, end);
+                const size_t sp = shortn.rfind("::", shortn.find('<') == std::string::npos ? std::string::npos
+                                                                                           : shortn.find('<'));
+                if (sp != std::string::npos) shortn = shortn.substr(sp + 2);
+                if (shortn.rfind("void ", 0) == 0) shortn = shortn.substr(5);
+                std::snprintf(names + (size_t)i * name_len, name_len, "%s", shortn.c_str());
+            }
+        }
+        cudaEventDestroy(r.e0);
+        cudaEventDestroy(r.e1);
+    }
+    g_records->clear();
+    cudaGetLastError();
+    return n;
+}
+
 void set_wait_limit(long long ns, int test_unset) {
     g_wait_ns.store(ns < 0 ? 0 : ns);
     g_wait_test.store(test_unset ? 1 : 0);
