@@ -132,6 +132,11 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-count", type=int, default=256, help="problems in --workload batch256")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch schedule (profiling runs: timings under a profiler mislead the autotuner)")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="restart loop driven from the host (one graph launch per restart cycle): for profilers "
+                         "that do not follow kernels inside conditional graph nodes")
     ap.add_argument("--no-extra-forms", action="store_true",
                     help="skip the 3D 128^3 and 256-problem batch forms of the default line")
     return ap.parse_args()
@@ -369,14 +374,15 @@ def run_ours(a, rank, world, local):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     s = pkg.Solver(a.dim, a.p, a.n, k=a.k)
-    schedule = s.autotune()                 # launch schedule of the FP32 cycles, picked by timing
+    # launch schedule of the FP32 cycles, picked by timing
+    schedule = pkg.igamg_get_schedule(s.ctx) if a.no_autotune else s.autotune()
     coeffs = workloads.random_sine_coeffs(a.dim, seed=a.seed + rank, modes=16)
     b = s.rhs_sine(coeffs)
     x = torch.zeros(s.N, dtype=torch.float64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     def solve(prec):
-        return s.solve(b, x=x, tol=1e-10, method=a.method, k=a.k, prec=prec, max_cycles=200)
+        return s.solve(b, x=x, tol=1e-10, method=a.method, k=a.k, prec=prec, max_cycles=200, host_loop=a.host_loop)
 
     def timed(prec, steps):
         times = []

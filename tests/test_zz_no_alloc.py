@@ -62,3 +62,25 @@ def test_noalloc_rejects_out_of_range_restart_number(pkg):
     with pytest.raises(pkg.IgamgError) as e:
         pkg.igamg_extrapolate_noalloc(10, 13, pkg.IGAMG_RRE, S, 10, t)
     assert e.value.status == pkg.IGAMG_EINVAL
+
+
+def test_noalloc_largest_restart_number_then_smallest(pkg):
+    """The built-in scratch at its largest use -- restart number 12 on a vector
+    long enough for the most Gram partial-sum blocks (more than 304 x 256
+    entries) -- and then a restart-number-1 call, which reuses the start of
+    the scratch with stale partial sums of the large call behind it."""
+    n = 304 * 256 + 5
+    for call, (q, method) in enumerate([(12, pkg.IGAMG_RRE), (1, pkg.IGAMG_MPE)]):
+        S = _sequence(n, q, seed=30 + call)
+        St = torch.as_tensor(np.concatenate(S), dtype=torch.float64, device="cuda")
+        t_ws = torch.empty(n, dtype=torch.float64, device="cuda")
+        ws = torch.empty(pkg.igamg_extrap_workspace_bytes(n, q), dtype=torch.uint8, device="cuda")
+        g_ws, q_ws = pkg.igamg_extrapolate(n, q, method, St, n, t_ws, ws)
+        t_na = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+        g_na, q_na = pkg.igamg_extrapolate_noalloc(n, q, method, St, n, t_na)
+        torch.cuda.synchronize()
+        assert q_na == q_ws
+        assert np.allclose(g_na, g_ws, rtol=1e-12, atol=1e-15)
+        a, b = t_na.cpu().numpy(), t_ws.cpu().numpy()
+        assert np.all(np.isfinite(a))
+        assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(b)
