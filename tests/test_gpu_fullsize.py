@@ -8,8 +8,9 @@ and its shared-memory rows exceed 48 KiB.  These tests run that path:
   1024^2 (p = 3) finest level against the oracle, element by element;
 * whole FP64 solves against the oracle: 2D 1024^2 with p = 3 and p = 5,
   RRE(5), the benchmark's right-hand side (random 16-mode sine series, seed
-  0), and 3D 48^3, p = 3, RRE(10): stopping count within +-1 and, at the
-  oracle's count, solutions equal to 1e-9 (relative 2-norm and max-norm);
+  0), 1024^2 with p = 2, MPE(10), manufactured right side, and 3D 48^3,
+  p = 3, RRE(10): stopping count within +-1 and, at the oracle's count,
+  solutions equal to 1e-9 (relative 2-norm and max-norm);
 * the mixed form (FP32 V-cycles inside FP64 refinement) at 1024^2: it reaches
   the oracle's residual test and its distance from the oracle's solution is
   stated;
@@ -97,18 +98,18 @@ def test_apply_and_sweeps_1024(pkg, big2d):
     _assert_close(_np(xf), ref, 2e-5, "FP32 sweeps")
 
 
-def _fp64_vs_oracle(pkg, dim, n, p, k, coeffs, max_cycles=60):
+def _fp64_vs_oracle(pkg, dim, n, p, k, coeffs, max_cycles=60, method="rre"):
     prob = osolver.Problem(dim, n, p, coeffs)
-    ref = osolver.solve(prob, "rre", k=k, tol=1e-10, max_cycles=max_cycles, keep_iterates=True)
+    ref = osolver.solve(prob, method, k=k, tol=1e-10, max_cycles=max_cycles, keep_iterates=True)
     assert ref["converged"]
     s = pkg.Solver(dim, p, n, k=k)
     b = s.rhs_sine(coeffs)
     _assert_close(_np(b), prob.b, 1e-13, "load vector")
-    out = s.solve(b, tol=1e-10, method="rre", k=k, prec="fp64", max_cycles=max_cycles)
+    out = s.solve(b, tol=1e-10, method=method, k=k, prec="fp64", max_cycles=max_cycles)
     assert out["converged"]
     assert abs(out["cycles"] - ref["cycles"]) <= 1, (out["cycles"], ref["cycles"])
     c = min(out["cycles"], ref["cycles"])
-    out_c = s.solve(b, tol=0.0, method="rre", k=k, prec="fp64", max_cycles=c)
+    out_c = s.solve(b, tol=0.0, method=method, k=k, prec="fp64", max_cycles=c)
     assert out_c["cycles"] == c
     _assert_close(_np(out_c["x"]), ref["iterates"][c - 1], 1e-9, f"FP64 solve after {c} cycles")
     return prob, ref, s, b
@@ -129,6 +130,13 @@ def test_fp64_solve_1024_matches_oracle(pkg, p):
     d2, dm = _rel(x, ref["x"]), _relmax(x, ref["x"])
     print(f"p={p}: mixed form vs oracle solution: rel 2-norm {d2:.2e}, rel max {dm:.2e}")
     assert d2 < 1e-7 and dm < 1e-7
+    s.close()
+
+
+def test_fp64_mpe10_1024_matches_oracle(pkg):
+    """MPE with restart number 10 at 1024^2, p = 2 (the other extrapolation and
+    cycle length of the 1024^2 configuration), manufactured right-hand side."""
+    _, _, s, _ = _fp64_vs_oracle(pkg, 2, 1024, 2, 10, workloads.manufactured_coeffs(2), method="mpe")
     s.close()
 
 
