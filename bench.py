@@ -443,18 +443,20 @@ def run_ours(a, rank, world, local):
         learned = {"ms": float(np.mean(tl)), "cycles": outl["cycles"], "fell_back": outl["fell_back"],
                    "final_rel_residual": float(outl["history"][-1])}
 
-    # the paper's own smoother (Sec. 4): weighted Jacobi, omega = 2/3, same V(1,1)-cycle
-    pkg.igamg_set_cycle(s.ctx, "jacobi", 1, 2.0 / 3.0)
-    for _ in range(a.warmup):
-        torch.cuda.nvtx.range_push("jacobi_warmup_solve")   # marks the solves for profiler filters
-        solve(a.prec)
-        torch.cuda.nvtx.range_pop()
-        solve("fp64")
-    tj, outj = timed(a.prec, a.steps)
-    tj64, outj64 = timed("fp64", a.steps)
-    pkg.igamg_set_cycle(s.ctx, "gs", 1)
-    jacobi = {"ms": float(np.mean(tj)), "cycles": outj["cycles"], "ms64": float(np.mean(tj64)),
-              "cycles64": outj64["cycles"], "final_rel_residual": float(outj["history"][-1])}
+    jacobi = None
+    if a.dim == 2:     # the weighted-Jacobi cycle with omega = 2/3 stagnates in 3D (128^3, p = 3: 1.6e-3 after 200 restarts)
+        # the paper's own smoother (Sec. 4): weighted Jacobi, omega = 2/3, same V(1,1)-cycle
+        pkg.igamg_set_cycle(s.ctx, "jacobi", 1, 2.0 / 3.0)
+        for _ in range(a.warmup):
+            torch.cuda.nvtx.range_push("jacobi_warmup_solve")   # marks the solves for profiler filters
+            solve(a.prec)
+            torch.cuda.nvtx.range_pop()
+            solve("fp64")
+        tj, outj = timed(a.prec, a.steps)
+        tj64, outj64 = timed("fp64", a.steps)
+        pkg.igamg_set_cycle(s.ctx, "gs", 1)
+        jacobi = {"ms": float(np.mean(tj)), "cycles": outj["cycles"], "ms64": float(np.mean(tj64)),
+                  "cycles64": outj64["cycles"], "final_rel_residual": float(outj["history"][-1])}
 
     # Dominant kernel (ncu launch list of this workload): the FP32 row-phase
     # Gauss-Seidel kernel.  Timed here on the finest level, same launch
@@ -484,8 +486,9 @@ def run_ours(a, rank, world, local):
 
     if learned is not None:
         learned["ms"] = max_over_ranks(learned["ms"], world)
-    jacobi["ms"] = max_over_ranks(jacobi["ms"], world)
-    jacobi["ms64"] = max_over_ranks(jacobi["ms64"], world)
+    if jacobi is not None:
+        jacobi["ms"] = max_over_ranks(jacobi["ms"], world)
+        jacobi["ms64"] = max_over_ranks(jacobi["ms64"], world)
     t_max = max_over_ranks(float(np.mean(times)), world)
     t64_max = max_over_ranks(float(np.mean(times64)), world)
     e2e_max = max_over_ranks(float(np.mean(e2e_times)), world)
@@ -518,10 +521,11 @@ def run_ours(a, rank, world, local):
                                 "cycles": learned["cycles"], "fell_back": learned["fell_back"],
                                 "final_rel_residual": learned["final_rel_residual"],
                                 "network": "3x3 conv 1-16-16-1, BF16/FP32, trained on 257^2 p=3 pairs"}
-    line["jacobi_form"] = {"ms_per_step": jacobi["ms"], "value": units / (jacobi["ms"] * 1e-3), "unit": "DOF/s",
-                           "cycles": jacobi["cycles"], "final_rel_residual": jacobi["final_rel_residual"],
-                           "fp64_ms_per_step": jacobi["ms64"], "fp64_cycles": jacobi["cycles64"],
-                           "smoother": "weighted Jacobi, omega = 2/3 (the paper's experiments), V(1,1)"}
+    if jacobi is not None:
+        line["jacobi_form"] = {"ms_per_step": jacobi["ms"], "value": units / (jacobi["ms"] * 1e-3), "unit": "DOF/s",
+                               "cycles": jacobi["cycles"], "final_rel_residual": jacobi["final_rel_residual"],
+                               "fp64_ms_per_step": jacobi["ms64"], "fp64_cycles": jacobi["cycles64"],
+                               "smoother": "weighted Jacobi, omega = 2/3 (the paper's experiments), V(1,1)"}
     if a.dim == 2 and a.prec == "fp32_ir":
         line["kernel_table"] = kernel_table(pkg, s, b, a, peak_hbm)
     if not a.no_extra_forms and a.dim == 2 and world == 1:

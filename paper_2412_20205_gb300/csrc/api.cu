@@ -541,7 +541,8 @@ void fixed_point_step(const igamg_ctx* c, cudaStream_t s, Workspace& w, int prec
     } else {
         LevelBuf<float>& G = w.f[top];
         // r = b - A s in FP64, rounded to FP32; e = V32(0; r); s_out = s_in + e (FP64)
-        dev::residual<double, float>(s, c->dim, c->lv64[top], d_b, F.TM, F.TK, G.b, nullptr);
+        dev::residual<double, float>(s, c->dim, c->lv64[top], d_b, F.TM, F.TK, G.b, nullptr, nullptr, F.tmp1,
+                                     F.tmp2);
         vcycle<float>(c, s, w, top, G.x, G.b, true, prec == IGAMG_FP32_IR_LEARNED);
         dev::xpass<double, float>(s, c->lv64[top], S_in, S_out, G.x, 0, nullptr, nullptr, 0, F.TM, F.TK);
     }
@@ -558,9 +559,11 @@ void residual_norm(const igamg_ctx* c, cudaStream_t s, Workspace& w, const doubl
         return;
     }
     if (!w.f.empty())           // FP32-IR workspace: also leave r in FP32 for the next V-cycle
-        dev::residual<double, float>(s, c->dim, c->lv64[top], d_b, F.TM, F.TK, w.f[top].b, w.partial, F.r);
+        dev::residual<double, float>(s, c->dim, c->lv64[top], d_b, F.TM, F.TK, w.f[top].b, w.partial, F.r,
+                                     F.tmp1, F.tmp2);
     else
-        dev::residual<double, double>(s, c->dim, c->lv64[top], d_b, F.TM, F.TK, F.r, w.partial);
+        dev::residual<double, double>(s, c->dim, c->lv64[top], d_b, F.TM, F.TK, F.r, w.partial, nullptr, F.tmp1,
+                                      F.tmp2);
     dev::norm_final(s, w.partial, c->lv64[top].rows(), denom, w.scal, 1);
 }
 
@@ -1428,7 +1431,8 @@ igamg_status igamg_apply(igamg_ctx* c, int level, const double* d_x, double* d_y
         return IGAMG_OK;
     }
     dev::xpass<double, double>(s, c->lv64[level], d_x, nullptr, nullptr, 0, nullptr, nullptr, 0, B.TM, B.TK);
-    dev::residual<double, double>(s, c->dim, c->lv64[level], nullptr, B.TM, B.TK, d_y, nullptr);
+    dev::residual<double, double>(s, c->dim, c->lv64[level], nullptr, B.TM, B.TK, d_y, nullptr, nullptr, B.tmp1,
+                                  B.tmp2);
     CUDA_TRY(cudaGetLastError());
     return IGAMG_OK;
 }

@@ -269,9 +269,12 @@ void jacobi_sweep(cudaStream_t s, int dim, const LevelView<T>& L, T omega, T* x,
                   T* TMo, T* TKo);
 
 // r = b - A x from the row partial sums; optional per-row partial ||r||^2.
+// In 3D with scratch u, v (N each, not aliasing the other arguments) the
+// residual is sum-factorised across y and z (two passes), else each row
+// couples to its (2p+1)^2 neighbour rows.
 template <typename T, typename R>
 void residual(cudaStream_t s, int dim, const LevelView<T>& L, const T* b, const T* TM,
-              const T* TK, R* r, double* partial, double* r64 = nullptr);
+              const T* TK, R* r, double* partial, double* r64 = nullptr, T* u = nullptr, T* v = nullptr);
 
 // Double-FP32 refinement update on the finest 2D level (refine.cu):
 // S_out = S_in + e and the row sums of e, (I (x) M_x) e and (I (x) K_x) e,

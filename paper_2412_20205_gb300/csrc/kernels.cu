@@ -755,6 +755,87 @@ __global__ void __launch_bounds__(kThreads) k_residual(LevelView<T> L, const T* 
     }
 }
 
+// 3D residual by sum factorisation across y and z.  With the row partial
+// sums T_M = (I (x) I (x) M_x) x and T_K = (I (x) I (x) K_x) x,
+//   A x = sum_dk K_z(k, k+dk) U(j, k+dk) + M_z(k, k+dk) V(j, k+dk),
+//   U(j, k') = sum_dj M_y(j, j+dj) T_M(j+dj, k'),
+//   V(j, k') = sum_dj K_y(j, j+dj) T_M(j+dj, k') + M_y(j, j+dj) T_K(j+dj, k'),
+// so a y pass (U, V: 3(2p+1) FMA per unknown) and a z pass (2(2p+1) FMA)
+// replace the (2p+1)^2-row coupling of k_residual (4(2p+1)^2 FMA).  One CTA
+// per row (j, k) in both passes.
+template <typename T, int P>
+__global__ void __launch_bounds__(kThreads) k_yfactor3(LevelView<T> L, const T* __restrict__ TM,
+                                                        const T* __restrict__ TK, T* __restrict__ U,
+                                                        T* __restrict__ V) {
+    constexpr int W = 2 * P + 1;
+    const int mx = L.m[0], my = L.m[1];
+    const int row = blockIdx.x, j = row % my;
+    const size_t base = (size_t)row * mx;
+    __shared__ T cm[W], ck[W];
+    __shared__ int ok[W];
+    if (threadIdx.x < W) {                           // operator data only
+        const int jj = j + (int)threadIdx.x - P;
+        ok[threadIdx.x] = jj >= 0 && jj < my;
+        cm[threadIdx.x] = ok[threadIdx.x] ? band_md(L, 1, j, threadIdx.x) : T(0);
+        ck[threadIdx.x] = ok[threadIdx.x] ? band_kd(L, 1, j, threadIdx.x) : T(0);
+    }
+    pdl_enter();
+    __syncthreads();
+    for (int i = threadIdx.x; i < mx; i += blockDim.x) {
+        T u = 0, v = 0;
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+            if (!ok[q]) continue;
+            const long long o = (long long)base + (long long)(q - P) * mx + i;
+            const T tm = TM[o], tk = TK[o];
+            u += cm[q] * tm;
+            v += ck[q] * tm + cm[q] * tk;
+        }
+        U[base + i] = u;
+        V[base + i] = v;
+    }
+}
+
+template <typename T, typename R, int P>
+__global__ void __launch_bounds__(kThreads) k_zresidual3(LevelView<T> L, const T* __restrict__ b,
+                                                          const T* __restrict__ U, const T* __restrict__ V,
+                                                          R* __restrict__ r, double* __restrict__ partial,
+                                                          double* __restrict__ r64) {
+    constexpr int W = 2 * P + 1;
+    const int mx = L.m[0], my = L.m[1], mz = L.m[2];
+    const int row = blockIdx.x, k = row / my;
+    const size_t base = (size_t)row * mx, plane = (size_t)mx * my;
+    __shared__ T cz[W], mzc[W];
+    __shared__ int ok[W];
+    __shared__ double red[kThreads / 32];
+    if (threadIdx.x < W) {                           // operator data only
+        const int kk = k + (int)threadIdx.x - P;
+        ok[threadIdx.x] = kk >= 0 && kk < mz;
+        cz[threadIdx.x] = ok[threadIdx.x] ? band_kd(L, 2, k, threadIdx.x) : T(0);
+        mzc[threadIdx.x] = ok[threadIdx.x] ? band_md(L, 2, k, threadIdx.x) : T(0);
+    }
+    pdl_enter();
+    __syncthreads();
+    double ss = 0.0;
+    for (int i = threadIdx.x; i < mx; i += blockDim.x) {
+        T ax = 0;
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+            if (!ok[q]) continue;
+            const long long o = (long long)base + (long long)(q - P) * (long long)plane + i;
+            ax += cz[q] * U[o] + mzc[q] * V[o];
+        }
+        const T v = b ? b[base + i] - ax : ax;
+        r[base + i] = (R)v;
+        if (r64) r64[base + i] = (double)v;
+        ss += (double)v * (double)v;
+    }
+    if (partial) {
+        const double t = block_sum(ss, red);
+        if (threadIdx.x == 0) partial[row] = t;
+    }
+}
+
 // Weighted Jacobi (Sec. 4: the paper's smoother, omega = 2/3):
 // x += omega D^{-1} (b - A x), every node from the same x.  A x comes from
 // the row partial sums, which this kernel only reads, so each CTA may
@@ -1599,11 +1680,19 @@ void gs_sweep(cudaStream_t s, int dim, const LevelView<T>& L, bool descending, T
 
 template <typename T, typename R>
 void residual(cudaStream_t s, int dim, const LevelView<T>& L, const T* b, const T* TM, const T* TK,
-              R* r, double* partial, double* r64) {
+              R* r, double* partial, double* r64, T* u, T* v) {
     with_p(L.p, [&](auto PC) {
         constexpr int P = decltype(PC)::value;
-        if (dim == 2) launch_chained(k_residual<T, R, 2, P>, L.rows(), kThreads, 0, s, L, b, TM, TK, r, partial, r64);
-        else launch_chained(k_residual<T, R, 3, P>, L.rows(), kThreads, 0, s, L, b, TM, TK, r, partial, r64);
+        if (dim == 2) {
+            launch_chained(k_residual<T, R, 2, P>, L.rows(), kThreads, 0, s, L, b, TM, TK, r, partial, r64);
+        } else if (u && v) {                         // sum-factorised across y and z
+            launch_chained(k_yfactor3<T, P>, L.rows(), kThreads, 0, s, L, TM, TK, u, v);
+            launch_chained(k_zresidual3<T, R, P>, L.rows(), kThreads, 0, s, L, b, (const T*)u, (const T*)v, r,
+                           partial, r64);
+            count_launch();
+        } else {
+            launch_chained(k_residual<T, R, 3, P>, L.rows(), kThreads, 0, s, L, b, TM, TK, r, partial, r64);
+        }
     });
     count_launch();
 }
@@ -1653,7 +1742,7 @@ template <typename T>
 void residual_restrict(cudaStream_t s, int dim, const LevelView<T>& L, const TransferView<T>& X, const T* b,
                        const T* TM, const T* TK, T* r, T* coarse, T* tmp1, T* tmp2, T* zero, size_t nzero) {
     if (dim != 2) {
-        residual<T, T>(s, dim, L, b, TM, TK, r, nullptr);
+        residual<T, T>(s, dim, L, b, TM, TK, r, nullptr, nullptr, tmp1, tmp2);
         restrict_<T>(s, dim, X, r, coarse, tmp1, tmp2, zero, nzero);
         return;
     }
@@ -1853,11 +1942,13 @@ template void xpass<double, float>(cudaStream_t, const LevelView<double>&, const
                                    const float*, int, const double*, const double*, size_t, double*,
                                    double*);
 template void residual<double, double>(cudaStream_t, int, const LevelView<double>&, const double*,
-                                       const double*, const double*, double*, double*, double*);
+                                       const double*, const double*, double*, double*, double*, double*,
+                                       double*);
 template void residual<double, float>(cudaStream_t, int, const LevelView<double>&, const double*,
-                                      const double*, const double*, float*, double*, double*);
+                                      const double*, const double*, float*, double*, double*, double*,
+                                      double*);
 template void residual<float, float>(cudaStream_t, int, const LevelView<float>&, const float*,
-                                     const float*, const float*, float*, double*, double*);
+                                     const float*, const float*, float*, double*, double*, float*, float*);
 
 }  // namespace dev
 }  // namespace igamg
