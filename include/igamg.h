@@ -323,6 +323,23 @@ igamg_status igamg_set_coarse_tail(igamg_ctx* ctx, int enable);
 igamg_status igamg_set_schedule(igamg_ctx* ctx, int gs_threads, int tail_levels);
 void igamg_get_schedule(const igamg_ctx* ctx, int* gs_threads, int* tail_levels);
 
+/* Where the coarse tail runs: ctas = 1 on one CTA (the levels above), 8 or 16
+ * on one thread-block cluster of that many CTAs.  The cluster form splits
+ * every tail level's grid rows into contiguous bands, one per CTA, kept in
+ * that CTA's shared memory; the rows a step needs from a neighbouring band
+ * are read from the neighbour's shared memory (distributed shared memory),
+ * and cluster barriers order the steps.  Its levels are limited by the
+ * shared memory of one CTA per band (about 257^2 unknowns on 16 CTAs), not
+ * by 6000 unknowns.  Same colours, order and operators (FP32 rounding order
+ * aside).  Switching keeps the tail depth where the other form has it, else
+ * takes its deepest; igamg_tail_levels_available() gives the deepest tail
+ * level of each form (0: none), igamg_get_tail_ctas() the form in use.
+ * igamg_autotune times every form and depth.  Errors: EINVAL (ctas not 1, 8
+ * or 16). */
+igamg_status igamg_set_tail_ctas(igamg_ctx* ctx, int ctas);
+int igamg_get_tail_ctas(const igamg_ctx* ctx);
+int igamg_tail_levels_available(const igamg_ctx* ctx, int ctas);
+
 /* Cycle of Algorithm 2 (Sec. 2.4) used by every solve, cycle and autotune
  * call of this context.  smoother: IGAMG_SMOOTH_GS (default; multicolour
  * Gauss-Seidel, (p+1)^dim colours, ascending before and descending after the
@@ -414,6 +431,11 @@ igamg_status igamg_batch_solve(igamg_batch* batch, const double* d_b, double* d_
  * 128 streams, the host testing every residual after each round.  Same
  * arithmetic either way.  Errors: EINVAL for a null batch. */
 igamg_status igamg_batch_set_device_loop(igamg_batch* batch, int enable);
+/* Every problem's coarse tail on one CTA (ctas = 1) or on a cluster of 8 or
+ * 16 CTAs (igamg_set_tail_ctas), each at that form's deepest level.  The
+ * members' clusters run concurrently like their other kernels.  Errors:
+ * EINVAL. */
+igamg_status igamg_batch_set_tail_ctas(igamg_batch* batch, int ctas);
 /* Autotunes the batch: for every degree, igamg_autotune on the problem of
  * median size; the problems of that degree take its GS row-CTA cap and a
  * coarse tail down to the same level size.  The workspace is the batch

@@ -73,6 +73,10 @@ def _load():
         "igamg_coarse_tail_level": (c_int, [vp]),
         "igamg_set_schedule": (c_int, [vp, c_int, c_int]),
         "igamg_get_schedule": (None, [vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
+        "igamg_set_tail_ctas": (c_int, [vp, c_int]),
+        "igamg_get_tail_ctas": (c_int, [vp]),
+        "igamg_tail_levels_available": (c_int, [vp, c_int]),
+        "igamg_batch_set_tail_ctas": (c_int, [vp, c_int]),
         "igamg_set_cycle": (c_int, [vp, c_int, c_int, c_double]),
         "igamg_get_cycle": (None, [vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_double)]),
         "igamg_set_sweep_form": (c_int, [vp, c_int, c_int]),
@@ -372,7 +376,17 @@ def igamg_get_launch_overlap():
 def igamg_get_schedule(ctx):
     a, b = ctypes.c_int(), ctypes.c_int()
     _load().igamg_get_schedule(ctx, ctypes.byref(a), ctypes.byref(b))
-    return {"gs_threads": a.value, "tail_levels": b.value}
+    return {"gs_threads": a.value, "tail_levels": b.value, "tail_ctas": _load().igamg_get_tail_ctas(ctx)}
+
+
+def igamg_set_tail_ctas(ctx, ctas):
+    """Coarse tail on one CTA (1) or on a thread-block cluster of 8 or 16 CTAs."""
+    _check(_load().igamg_set_tail_ctas(ctx, int(ctas)), "igamg_set_tail_ctas")
+
+
+def igamg_tail_levels_available(ctx, ctas):
+    """Deepest tail level of the one-CTA (ctas = 1) or cluster (8, 16) form; 0: none."""
+    return _load().igamg_tail_levels_available(ctx, int(ctas))
 
 
 def igamg_autotune(ctx, ws, reps=3, stream=None):
@@ -473,6 +487,11 @@ def igamg_batch_solve(batch, count, b, x, tol, extrap, k, max_cycles, prec, ws, 
     if s not in (IGAMG_OK, IGAMG_ENOTCONV):
         _check(s, "igamg_batch_solve")
     return s, list(cyc), list(st), res
+
+
+def igamg_batch_set_tail_ctas(batch, ctas):
+    """Every problem's coarse tail on one CTA (1) or a cluster of 8 or 16 CTAs, at its deepest level."""
+    _check(_load().igamg_batch_set_tail_ctas(batch, int(ctas)), "igamg_batch_set_tail_ctas")
 
 
 def igamg_batch_set_device_loop(batch, enable):

@@ -121,6 +121,11 @@ struct igamg_ctx {
     TailView<float> tail32{};
     std::vector<TailView<float>> tails;
     bool tail_on = true;
+    // the same on a thread-block cluster (ctail32, when tail_ctas > 1);
+    // ctails[k][l] covers levels 0..l on kTailCtas[k] CTAs
+    int tail_ctas = 1;
+    ClusterTailView<float> ctail32{};
+    std::vector<ClusterTailView<float>> ctails[2];
     int gs_cap32 = 0;                       // row-CTA thread cap of FP32 GS (0: default)
     // GS sweep form per precision: levels with at least this many rows run a
     // sweep in one launch (rows wait on their earlier-phase neighbours), the
@@ -336,6 +341,41 @@ struct Views<float> {
     static std::vector<LevelBuf<float>>& buf(Workspace& w) { return w.f; }
 };
 
+// CTAs of the cluster-tail variants built at assembly.
+constexpr int kTailCtas[2] = {8, 16};
+
+// Highest level of the active coarse tail of FP32 2D cycles (0: none).
+int tail_level(const igamg_ctx* c) {
+    if (!c->tail_on) return 0;
+    return c->tail_ctas > 1 ? c->ctail32.lc : c->tail32.lc;
+}
+
+// Highest tail level available with `ctas` CTAs (1: the one-CTA tail).
+int tail_most(const igamg_ctx* c, int ctas) {
+    if (ctas == 1) return (int)c->tails.size() - 1;
+    for (int k = 0; k < 2; ++k)
+        if (kTailCtas[k] == ctas) return (int)c->ctails[k].size() - 1;
+    return 0;
+}
+
+// Selects the tail on `ctas` CTAs over levels 0..lc (lc = 0: no tail).
+void select_tail(igamg_ctx* c, int ctas, int lc) {
+    lc = std::max(0, std::min(lc, tail_most(c, ctas)));
+    c->tail_ctas = ctas;
+    c->tail_on = lc > 0;
+    if (lc == 0) return;
+    if (ctas == 1) c->tail32 = c->tails[lc];
+    else
+        for (int k = 0; k < 2; ++k)
+            if (kTailCtas[k] == ctas) c->ctail32 = c->ctails[k][lc];
+}
+
+// Levels tail_level(c)..0 of an FP32 2D V-cycle from x = 0 in the active tail.
+void run_tail(const igamg_ctx* c, cudaStream_t s, const float* b, float* x, int jacobi = 0, float omega = 0.f) {
+    if (c->tail_ctas > 1) dev::cluster_tail<float>(s, c->ctail32, b, x, jacobi, omega);
+    else dev::coarse_tail<float>(s, c->tail32, b, x, jacobi, omega);
+}
+
 // Row-CTA thread cap of the GS sweeps in cycles of type T (autotuned for FP32).
 template <typename T>
 int gs_cap(const igamg_ctx* c) { return std::is_same<T, float>::value ? c->gs_cap32 : 0; }
@@ -383,8 +423,8 @@ void mu_cycle(const igamg_ctx* c, cudaStream_t s, Workspace& w, int top, int l, 
         // FP32 2D V-cycles (Jacobi smoothing here) hand levels lc..0 to one
         // CTA, as the Gauss-Seidel V-cycle does; W-cycles revisit coarse
         // levels from nonzero iterates, which the tail does not take
-        if (c->mu == 1 && c->tail_on && c->tail32.lc > 0 && l == c->tail32.lc && l < top) {
-            dev::coarse_tail<float>(s, c->tail32, b, x, c->smoother == IGAMG_SMOOTH_JACOBI, (float)c->omega);
+        if (c->mu == 1 && tail_level(c) > 0 && l == tail_level(c) && l < top) {
+            run_tail(c, s, b, x, c->smoother == IGAMG_SMOOTH_JACOBI, (float)c->omega);
             return;
         }
     }
@@ -436,10 +476,10 @@ void vcycle(const igamg_ctx* c, cudaStream_t s, Workspace& w, int top, T* x_top,
     const auto& tv = Views<T>::tv(c);
     auto& B = Views<T>::buf(w);
     const int dim = c->dim;
-    // FP32 2D cycles hand levels lc..0 to one CTA when the hierarchy has a tail
+    // FP32 2D cycles hand levels lc..0 to one CTA or cluster when the hierarchy has a tail
     int lc = 0;
     if constexpr (std::is_same<T, float>::value)
-        if (c->tail_on && c->tail32.lc > 0 && c->tail32.lc < top) lc = c->tail32.lc;
+        if (tail_level(c) > 0 && tail_level(c) < top) lc = tail_level(c);
     const int lowest = lc > 0 ? lc + 1 : 1;
     for (int l = top; l >= lowest; --l) {
         T* x = (l == top) ? x_top : B[l].x;
@@ -461,7 +501,7 @@ void vcycle(const igamg_ctx* c, cudaStream_t s, Workspace& w, int top, T* x_top,
     }
     if (lc > 0) {
         if constexpr (std::is_same<T, float>::value)
-            dev::coarse_tail<float>(s, c->tail32, B[lc].b, B[lc].x);                   // levels lc..0
+            run_tail(c, s, B[lc].b, B[lc].x);                                            // levels lc..0
     } else {
         T* x0 = (top == 0) ? x_top : B[0].x;
         const T* b0 = (top == 0) ? b_top : B[0].b;
@@ -1051,6 +1091,59 @@ igamg_status igamg_assemble(igamg_ctx* c) {
             c->tails.push_back(v);
         }
     }
+    // Cluster tails of the FP32 2D cycle: on kTailCtas[k] CTAs, every lc
+    // whose levels fit a CTA's shared memory (ClusterTailView) and whose
+    // cluster the device can hold.
+    for (int k = 0; k < 2; ++k) c->ctails[k].assign(1, ClusterTailView<float>{});
+    if (dim == 2 && L >= 3) {
+        const int W = 2 * p + 1;
+        const int N0 = (int)c->hl[0].N(), m00 = c->hl[0].m[0], m01 = c->hl[0].m[1];
+        for (int k = 0; k < 2; ++k) {
+            const int C = kTailCtas[k];
+            for (int l = 1; l <= std::min(L - 2, kCTailLevels - 1); ++l) {
+                ClusterTailView<float> v{};
+                v.ctas = C;
+                v.lc = l;
+                int off = 0, rmax = N0, tmax = N0;
+                for (int q = 0; q <= l; ++q) v.R[q] = q == 0 ? c->hl[0].m[1] : (c->hl[q].m[1] + C - 1) / C;
+                for (int q = 1; q <= l; ++q) {                 // row pointers first: 8-byte aligned
+                    const TransferView<float>& X = c->tv32[q];
+                    v.off_rp[q] = off;
+                    off += 2 * (v.R[q] * W + v.R[q - 1] * X.rw[1] + v.R[q] * X.pw[1]);
+                }
+                for (int q = 0; q <= l; ++q) {
+                    const int mx = c->hl[q].m[0], R = v.R[q];
+                    v.off_x[q] = off; off += R * (mx + 2 * p);
+                    v.off_b[q] = off; off += R * mx;
+                    if (q == 0) continue;
+                    const LevelView<float>& Lq = c->lv32[q];
+                    const TransferView<float>& X = c->tv32[q];
+                    v.nbc[q] = Lq.tlo[0] + (mx - Lq.thi[0]);
+                    v.off_inv[q] = off; off += R * mx;
+                    v.off_tm[q] = off; off += 2 * R * mx;
+                    v.off_yb[q] = off; off += 2 * W * R;
+                    v.off_xb[q] = off; off += 2 * W * v.nbc[q];
+                    v.off_tc[q] = off; off += 2 * W;
+                    v.off_tx[q] = off; off += X.mf[0] * (1 + X.pw[0]) + X.mc[0] * (1 + X.rw[0]);
+                    v.off_ty[q] = off; off += R * X.pw[1] + v.R[q - 1] * X.rw[1];
+                    rmax = std::max(rmax, R * mx);
+                    tmax = std::max({tmax, R * X.mc[0], v.R[q - 1] * X.mf[0]});
+                }
+                v.off_cv = off; off += m00 * m00 + m01 * m01 + N0;
+                v.off_r = off; off += rmax;
+                v.off_t = off; off += tmax;
+                v.off_z = off; off += c->hl[l].m[0];
+                v.smem = (size_t)off * sizeof(float);
+                for (int q = 0; q <= l; ++q) {
+                    v.L[q] = c->lv32[q];
+                    v.X[q] = c->tv32[q];
+                }
+                v.C = c->cv32;
+                if (!dev::cluster_tail_fits(v)) break;
+                c->ctails[k].push_back(v);
+            }
+        }
+    }
     if (dim == 2) {
         DFView& D = c->dfv;
         const LevelView<double>& a = c->lv64[L - 1];
@@ -1578,7 +1671,7 @@ igamg_status igamg_set_smoother(igamg_ctx* c, const float* d_w, double stall_rat
 int igamg_smoother_fell_back(const igamg_ctx* c) { return c ? c->fell_back : 0; }
 
 int igamg_coarse_tail_level(const igamg_ctx* c) {
-    return (c && c->assembled && c->tail_on) ? c->tail32.lc : 0;
+    return (c && c->assembled) ? tail_level(c) : 0;
 }
 
 static void drop_graphs(igamg_ctx* c) {
@@ -1602,14 +1695,26 @@ igamg_status igamg_set_schedule(igamg_ctx* c, int gs_threads, int tail_levels) {
         return fail(IGAMG_EINVAL, "gs_threads must be 0, 128, 256 or 512");
     if (tail_levels < -1) return fail(IGAMG_EINVAL, "tail_levels must be >= -1");
     c->gs_cap32 = gs_threads;
-    if (tail_levels >= 0) {
-        const int most = (int)c->tails.size() - 1;
-        const int lc = std::min(tail_levels, most);
-        c->tail_on = lc > 0;
-        if (lc > 0) c->tail32 = c->tails[lc];
-    }
+    if (tail_levels >= 0) select_tail(c, c->tail_ctas, tail_levels);
     drop_graphs(c);
     return IGAMG_OK;
+}
+
+igamg_status igamg_set_tail_ctas(igamg_ctx* c, int ctas) {
+    if (igamg_status st = check_ctx(c)) return st;
+    if (ctas != 1 && ctas != kTailCtas[0] && ctas != kTailCtas[1])
+        return fail(IGAMG_EINVAL, "tail CTAs must be 1, 8 or 16");
+    // the same tail depth where the other form has it, else its deepest
+    const int want = c->tail_on ? tail_level(c) : 0;
+    select_tail(c, ctas, want > 0 ? want : tail_most(c, ctas));
+    drop_graphs(c);
+    return IGAMG_OK;
+}
+
+int igamg_get_tail_ctas(const igamg_ctx* c) { return c ? c->tail_ctas : 1; }
+
+int igamg_tail_levels_available(const igamg_ctx* c, int ctas) {
+    return (c && c->assembled) ? tail_most(c, ctas) : 0;
 }
 
 igamg_status igamg_set_cycle(igamg_ctx* c, int smoother, int mu, double omega) {
@@ -1636,7 +1741,7 @@ int igamg_get_launch_overlap(void) { return launch_overlap() ? 1 : 0; }
 
 void igamg_get_schedule(const igamg_ctx* c, int* gs_threads, int* tail_levels) {
     if (gs_threads) *gs_threads = c ? c->gs_cap32 : 0;
-    if (tail_levels) *tail_levels = (c && c->assembled && c->tail_on) ? c->tail32.lc : 0;
+    if (tail_levels) *tail_levels = (c && c->assembled) ? tail_level(c) : 0;
 }
 
 igamg_status igamg_autotune(igamg_ctx* c, void* d_ws, size_t ws_bytes, void* stream, int reps) {
@@ -1661,6 +1766,8 @@ igamg_status igamg_autotune(igamg_ctx* c, void* d_ws, size_t ws_bytes, void* str
         int cap, flow32, flow64;
         bool tail_on;
         TailView<float> tail;
+        int tail_ctas;
+        ClusterTailView<float> ctail;
         bool armed = true;
         ~Restore() {
             if (*e0) cudaEventDestroy(*e0);
@@ -1671,15 +1778,16 @@ igamg_status igamg_autotune(igamg_ctx* c, void* d_ws, size_t ws_bytes, void* str
             c->flow64 = flow64;
             c->tail_on = tail_on;
             c->tail32 = tail;
+            c->tail_ctas = tail_ctas;
+            c->ctail32 = ctail;
             drop_graphs(c);
         }
-    } restore{c, &e0, &e1, c->gs_cap32, c->flow32, c->flow64, c->tail_on, c->tail32};
+    } restore{c, &e0, &e1, c->gs_cap32, c->flow32, c->flow64, c->tail_on, c->tail32, c->tail_ctas, c->ctail32};
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
     const int caps[3] = {128, 256, 512};
     // one-launch sweep thresholds tried (rows per level; kNever = row phases only)
     const int flows[3] = {igamg_ctx::kNever, 16384, 4096};
-    const int most = (int)c->tails.size() - 1;
     auto time_cycles = [&](auto tag, float* ms) -> igamg_status {
         using T = decltype(tag);
         auto& B = Views<T>::buf(w);
@@ -1695,22 +1803,25 @@ igamg_status igamg_autotune(igamg_ctx* c, void* d_ws, size_t ws_bytes, void* str
         CUDA_TRY(cudaEventElapsedTime(ms, e0, e1));
         return IGAMG_OK;
     };
+    // coarse tails tried: none, then each depth on one CTA and on each cluster size
+    std::vector<std::pair<int, int>> tails_tried{{1, 0}};
+    for (int ctas : {1, kTailCtas[0], kTailCtas[1]})
+        for (int lc = 1; lc <= tail_most(c, ctas); ++lc) tails_tried.push_back({ctas, lc});
     float best = 1e30f;
-    int best_cap = 0, best_lc = c->tail_on ? c->tail32.lc : 0, best_flow = c->flow32;
+    int best_cap = 0, best_flow = c->flow32;
+    std::pair<int, int> best_tail{c->tail_ctas, tail_level(c)};
     for (int fi = 0; fi < 3; ++fi)
         for (int ci = 0; ci < (c->dim == 2 ? 3 : 1); ++ci)
-            for (int lc = 0; lc <= most; ++lc) {
+            for (const auto& tt : tails_tried) {
                 c->flow32 = flows[fi];
                 c->gs_cap32 = c->dim == 2 ? caps[ci] : 0;
-                c->tail_on = lc > 0;
-                if (lc > 0) c->tail32 = c->tails[lc];
+                select_tail(c, tt.first, tt.second);
                 float ms = 0.f;
                 if (igamg_status st = time_cycles(0.0f, &ms)) return st;
-                if (ms < best) { best = ms; best_cap = c->gs_cap32; best_lc = lc; best_flow = c->flow32; }
+                if (ms < best) { best = ms; best_cap = c->gs_cap32; best_tail = tt; best_flow = c->flow32; }
             }
     c->gs_cap32 = best_cap;
-    c->tail_on = best_lc > 0;
-    if (best_lc > 0) c->tail32 = c->tails[best_lc];
+    select_tail(c, best_tail.first, best_tail.second);
     c->flow32 = best_flow;
     // FP64 cycles: the sweep form only (on the same workspace; b = the FP32 b in FP64)
     float best64 = 1e30f;
@@ -1732,7 +1843,7 @@ igamg_status igamg_set_coarse_tail(igamg_ctx* c, int enable) {
     if (igamg_status st = check_ctx(c)) return st;
     const bool on = enable != 0;
     if (on == c->tail_on) return IGAMG_OK;
-    c->tail_on = on && c->tails.size() > 1;
+    c->tail_on = on && tail_most(c, c->tail_ctas) > 0;
     drop_graphs(c);                             // recapture with the other form
     return IGAMG_OK;
 }
@@ -2118,6 +2229,24 @@ igamg_status igamg_batch_set_device_loop(igamg_batch* B, int enable) {
     return IGAMG_OK;
 }
 
+igamg_status igamg_batch_set_tail_ctas(igamg_batch* B, int ctas) {
+    if (!B) return fail(IGAMG_EINVAL, "null batch");
+    if (ctas != 1 && ctas != kTailCtas[0] && ctas != kTailCtas[1])
+        return fail(IGAMG_EINVAL, "tail CTAs must be 1, 8 or 16");
+    for (auto c : B->ctx) {
+        if (igamg_status st = check_ctx(c)) return st;
+        select_tail(c, ctas, tail_most(c, ctas));
+        drop_graphs(c);
+    }
+    for (int sl = 0; sl < 2; ++sl)              // members' cycles change: recapture the loops
+        if (B->loop_exec[sl]) {
+            cudaGraphExecDestroy(B->loop_exec[sl]);
+            B->loop_exec[sl] = nullptr;
+            B->loop_key[sl] = igamg_ctx::Key{};
+        }
+    return IGAMG_OK;
+}
+
 igamg_status igamg_batch_autotune(igamg_batch* B, void* d_ws, size_t ws_bytes, void* stream, int reps) {
     const NoOverlapScope serial;                // time the schedules as batched solves run them
     if (!B || !d_ws) return fail(IGAMG_EINVAL, "bad batch autotune arguments");
@@ -2142,14 +2271,15 @@ igamg_status igamg_batch_autotune(igamg_batch* B, void* d_ws, size_t ws_bytes, v
         const int m = ids[ids.size() / 2];
         igamg_ctx* cm = B->ctx[m];
         if (igamg_status st = igamg_autotune(cm, (char*)d_ws + off[m], off[m + 1] - off[m], stream, reps)) return st;
-        const int cap = cm->gs_cap32;
-        const size_t nthr = (cm->tail_on && cm->tail32.lc > 0) ? cm->hl[cm->tail32.lc].N() : 0;
+        const int cap = cm->gs_cap32, ctas = cm->tail_ctas;
+        const size_t nthr = tail_level(cm) > 0 ? cm->hl[tail_level(cm)].N() : 0;
         for (int i : ids) {
             if (i == m) continue;
             igamg_ctx* ci = B->ctx[i];
             int lc = 0;
-            for (int l = 1; l < (int)ci->tails.size(); ++l)
+            for (int l = 1; l <= tail_most(ci, ctas); ++l)
                 if (ci->hl[l].N() <= nthr) lc = l;
+            ci->tail_ctas = ctas;
             if (igamg_status st = igamg_set_schedule(ci, cap, lc)) return st;
         }
     }

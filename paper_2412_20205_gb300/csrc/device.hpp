@@ -77,6 +77,37 @@ struct TailView {
     CoarseView<T> C;
 };
 
+// Coarse part of a 2D V-cycle run by one thread-block cluster of `ctas` CTAs
+// (levels 0..lc).  On level q >= 1, CTA r owns the grid rows
+// [r R[q], min((r + 1) R[q], m_y)); the coarsest level (R[0] = m_y) is owned
+// by CTA 0.  Every CTA keeps its rows' x (zero-padded by p columns on each
+// side), b, 1 / A_ii, T_M, T_K and y-band rows in its shared memory and reads
+// a neighbour's rows through distributed shared memory.  Offsets (elements)
+// are the same in every CTA: off_x, off_b, off_inv, off_tm (T_M then T_K,
+// R x m_x each), off_yb (M_y then K_y of the own rows, band-major, W x R
+// each), off_xb (M_x then K_x at the boundary columns i < tlo or i >= thi,
+// nbc x W each), off_tc (Toeplitz interior of M_x then K_x), off_tx (x-axis
+// transfer tables of X[q]: plo, pv, rlo, rv), off_ty (y-axis weights of X[q]:
+// pv of the own fine rows, rv of the own coarse rows of level q - 1), off_rp
+// (generic row pointers, 8-byte aligned: the y-band neighbours' T_M rows of
+// the own rows, the t rows the own coarse rows' restriction and the own fine
+// rows' prolongation combine), off_cv (coarsest V_x, V_y, laminv), off_r and
+// off_t (two scratch arrays), off_z (a zero row).  lc = 0: no cluster tail.
+constexpr int kCTailLevels = 7;
+template <typename T>
+struct ClusterTailView {
+    int lc, ctas;
+    int R[kCTailLevels], nbc[kCTailLevels];
+    int off_x[kCTailLevels], off_b[kCTailLevels], off_inv[kCTailLevels], off_tm[kCTailLevels];
+    int off_yb[kCTailLevels], off_xb[kCTailLevels], off_tc[kCTailLevels], off_tx[kCTailLevels];
+    int off_ty[kCTailLevels], off_rp[kCTailLevels];
+    int off_cv, off_r, off_t, off_z;
+    size_t smem;
+    LevelView<T> L[kCTailLevels];
+    TransferView<T> X[kCTailLevels];
+    CoarseView<T> C;
+};
+
 // Shared-memory elements (4-byte) of the staged tables of one 2D transfer:
 // plo/pv and rlo/rv of both directions.
 template <typename T>
@@ -244,6 +275,14 @@ size_t tail_smem_limit();
 // when jacobi != 0.
 template <typename T>
 void coarse_tail(cudaStream_t s, const TailView<T>& V, const T* b, T* x, int jacobi = 0, T omega = 0);
+
+// The same on one thread-block cluster (ClusterTailView).  Host side:
+// cluster_tail_fits tells whether a view's cluster can be resident on this
+// device (shared memory and cluster size).
+template <typename T>
+void cluster_tail(cudaStream_t s, const ClusterTailView<T>& V, const T* b, T* x, int jacobi = 0, T omega = 0);
+template <typename T>
+bool cluster_tail_fits(const ClusterTailView<T>& V);
 
 // T_M = (I (x) M_x) x, T_K = (I (x) K_x) x row by row.  With add != nullptr the
 // row is first replaced by x + add (written to x_out), with nS > 0 by

@@ -16,6 +16,7 @@
 #include "bands.cuh"
 
 #include <algorithm>
+#include <cooperative_groups.h>
 
 namespace igamg {
 namespace dev {
@@ -414,6 +415,484 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_coarse_tail(TailView<T> V, 
     for (int q = threadIdx.x; q < N; q += blockDim.x) x_out[q] = x[padded<P>(q % mx, q / mx, mx)];
 }
 
+// ---------------------------------------------------------------- cluster tail
+// The same coarse part of the 2D V-cycle on one thread-block cluster of C CTAs
+// (up to 16).  One SM stops paying off once a level has more than a few
+// thousand unknowns, while up to about 10^5 unknowns per level the per-level
+// kernels still spend most of their time in launch latency.  Here every CTA
+// owns a band of grid rows of each level (ClusterTailView) and keeps all of
+// its data in shared memory; the few rows a step needs from a neighbouring
+// band (the 2p rows within reach of the y-band, the rows a transfer combines)
+// are read from that CTA's shared memory through distributed shared memory,
+// and cluster barriers separate the dependent steps.  The arithmetic is that
+// of the one-CTA tail: the same colours in the same order, the same transfer
+// operators and fast diagonalisation; the off-row part of a row is summed
+// once per row phase.
+//
+// Which CTA holds a row is fixed for the launch, so every row a CTA reads is
+// resolved once, before the wait on the previous kernel, into a table of
+// generic pointers (its own shared memory or a neighbour's): the inner loops
+// do no row-owner arithmetic.  (Measured on GB300: reading the neighbours'
+// rows where they are is faster than having their owners push copies into
+// halo rows, 144 against 154 us per V-cycle tail at 1024^2, p = 3.)
+namespace cg = cooperative_groups;
+
+// Level q as CTA `rank` sees it.
+template <typename T>
+struct CLevel {
+    int mx, my, R, lo, hi, tlo, thi, nbc;
+    T* x;            // own rows, zero-padded: row lr at lr (mx + 2p), column i at + i + p
+    T* b;            // own rows, mx each
+    const T* inv;    // 1 / A_qq of the own rows
+    T* TM;           // T_M of the own rows, then T_K (at + R mx)
+    T* TK;
+    const T* yM;     // M_y(j, j + bb - p) of own row lr at yM[bb R + lr]
+    const T* yK;
+    const T* xM;     // M_x(i, i + bb - p) of boundary column slot s at xM[s W + bb]
+    const T* xK;
+    const T* tc;     // Toeplitz interior of M_x then K_x
+    const T* const* rp;   // T_M row of grid row j + bb - p for own row lr at rp[lr W + bb]
+};
+
+// Transfer X[q] (levels q - 1, q): x-axis tables in full; for the own coarse
+// rows of level q - 1 the fine rows their restriction combines (pointers to
+// the t rows, a zero row outside the grid) and weights, for the own fine rows
+// the coarse rows their prolongation combines and weights.
+template <typename T>
+struct CTransfer {
+    int pwx, rwx, pwy, rwy;
+    const int* plox;
+    const T* pvx;
+    const int* rlox;
+    const T* rvx;
+    const T* pvy;            // own fine rows x pw_y
+    const T* rvy;            // own coarse rows x rw_y
+    const T* const* rr;      // own coarse rows x rw_y
+    const T* const* pr;      // own fine rows x pw_y
+};
+
+template <typename T, int P>
+__device__ __forceinline__ CLevel<T> clevel(const ClusterTailView<T>& V, unsigned char* raw, int q, int rank) {
+    constexpr int W = 2 * P + 1;
+    T* sm = reinterpret_cast<T*>(raw);
+    CLevel<T> S;
+    S.mx = V.L[q].m[0];
+    S.my = V.L[q].m[1];
+    S.R = V.R[q];
+    S.lo = min(rank * S.R, S.my);
+    S.hi = min(S.lo + S.R, S.my);
+    S.tlo = V.L[q].tlo[0];
+    S.thi = V.L[q].thi[0];
+    S.nbc = V.nbc[q];
+    S.x = sm + V.off_x[q];
+    S.b = sm + V.off_b[q];
+    S.inv = sm + V.off_inv[q];
+    S.TM = sm + V.off_tm[q];
+    S.TK = S.TM + S.R * S.mx;
+    S.yM = sm + V.off_yb[q];
+    S.yK = S.yM + W * S.R;
+    S.xM = sm + V.off_xb[q];
+    S.xK = S.xM + S.nbc * W;
+    S.tc = sm + V.off_tc[q];
+    S.rp = reinterpret_cast<const T* const*>(raw + (size_t)V.off_rp[q] * sizeof(T));
+    return S;
+}
+
+template <typename T>
+__device__ __forceinline__ CTransfer<T> ctransfer(const ClusterTailView<T>& V, unsigned char* raw, int q) {
+    const TransferView<T>& X = V.X[q];
+    T* sm = reinterpret_cast<T*>(raw);
+    CTransfer<T> Y;
+    Y.pwx = X.pw[0];
+    Y.rwx = X.rw[0];
+    Y.pwy = X.pw[1];
+    Y.rwy = X.rw[1];
+    T* f = sm + V.off_tx[q];
+    Y.plox = reinterpret_cast<const int*>(f);
+    f += X.mf[0];
+    Y.pvx = f;
+    f += X.mf[0] * X.pw[0];
+    Y.rlox = reinterpret_cast<const int*>(f);
+    f += X.mc[0];
+    Y.rvx = f;
+    const int Rf = V.R[q], Rc = V.R[q - 1];
+    T* g = sm + V.off_ty[q];
+    Y.pvy = g;
+    Y.rvy = g + Rf * X.pw[1];
+    const T* const* rpq = reinterpret_cast<const T* const*>(raw + (size_t)V.off_rp[q] * sizeof(T));
+    Y.rr = rpq + Rf * (2 * V.L[q].p + 1);
+    Y.pr = Y.rr + Rc * X.rw[1];
+    return Y;
+}
+
+// f(k, i) for every (k, i) in [0, n) x [0, m), the CTA's threads striding
+// over k m + i without a division per element.
+template <typename F>
+__device__ __forceinline__ void grid_for(int n, int m, F&& f) {
+    const int NT = blockDim.x, dk = NT / m, di = NT - dk * m;
+    int k = (int)threadIdx.x / m, i = (int)threadIdx.x - k * m;
+    while (k < n) {
+        f(k, i);
+        i += di;
+        k += dk;
+        if (i >= m) {
+            i -= m;
+            ++k;
+        }
+    }
+}
+
+// sum_b M_x(i, b) x(i + b - p) and the K_x sum of an own row (xr: padded column i - p)
+template <typename T, int P>
+__device__ __forceinline__ void cwin(const CLevel<T>& S, const T* xr, int i, const T (&mc)[2 * P + 1],
+                                     const T (&kc)[2 * P + 1], T& sM, T& sK) {
+    constexpr int W = 2 * P + 1;
+    sM = 0;
+    sK = 0;
+    if (i >= S.tlo && i < S.thi) {
+#pragma unroll
+        for (int bb = 0; bb < W; ++bb) {
+            const T v = xr[bb];
+            sM += mc[bb] * v;
+            sK += kc[bb] * v;
+        }
+    } else {
+        const int slot = i < S.tlo ? i : S.tlo + (i - S.thi);
+#pragma unroll
+        for (int bb = 0; bb < W; ++bb) {
+            const T v = xr[bb];
+            sM += S.xM[slot * W + bb] * v;
+            sK += S.xK[slot * W + bb] * v;
+        }
+    }
+}
+
+// sum over the y-band rows bj (all, or all but the own row) of
+// K_y(j, bj) T_M(j + bj - p, i) + M_y(j, bj) T_K(j + bj - p, i) for own row
+// lr; band entries outside the matrix are zero (their pointer is the own row).
+template <typename T, int P, bool SKIP_OWN>
+__device__ __forceinline__ T ccouple(const CLevel<T>& S, int lr, int i) {
+    constexpr int W = 2 * P + 1;
+    const T* const* rp = S.rp + lr * W;
+    const int tko = S.R * S.mx;
+    T acc = 0;
+#pragma unroll
+    for (int bj = 0; bj < W; ++bj) {
+        if (SKIP_OWN && bj == P) continue;
+        const T* row = rp[bj];
+        acc += S.yK[bj * S.R + lr] * row[i] + S.yM[bj * S.R + lr] * row[tko + i];
+    }
+    return acc;
+}
+
+template <typename T, int P>
+__device__ __forceinline__ void load_tc(const CLevel<T>& S, T (&mc)[2 * P + 1], T (&kc)[2 * P + 1]) {
+#pragma unroll
+    for (int bb = 0; bb <= 2 * P; ++bb) {
+        mc[bb] = S.tc[bb];
+        kc[bb] = S.tc[2 * P + 1 + bb];
+    }
+}
+
+// T_M, T_K of the own rows from x (local only).
+template <typename T, int P>
+__device__ void cxpass(const CLevel<T>& S) {
+    T mc[2 * P + 1], kc[2 * P + 1];
+    load_tc<T, P>(S, mc, kc);
+    const int PW = S.mx + 2 * P;
+    grid_for(S.hi - S.lo, S.mx, [&](int lr, int i) {
+        T sM, sK;
+        cwin<T, P>(S, S.x + lr * PW + i, i, mc, kc, sM, sK);
+        S.TM[lr * S.mx + i] = sM;
+        S.TK[lr * S.mx + i] = sK;
+    });
+}
+
+// Barrier of row group g (G warps: warps g G .. g G + G - 1); named barrier
+// 1 + g, one warp: a warp barrier.
+__device__ __forceinline__ void group_sync(int g, int G) {
+    if (G == 1) __syncwarp();
+    else asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(32 * G) : "memory");
+}
+
+// One multicolour GS sweep.  Row phase cy: the own rows j = cy mod (p+1)
+// (no two of them couple, across the cluster too) are shared out to groups
+// of warps; a group takes its row's frozen off-row part once, runs the row's
+// p+1 x-colours and refreshes its T_M, T_K with group barriers only.  A
+// cluster barrier then publishes the phase's rows to the next phase.
+template <typename T, int P>
+__device__ void cgs(const CLevel<T>& S, T* rhs, bool descending) {
+    constexpr int P1 = P + 1;
+    T mc[2 * P + 1], kc[2 * P + 1];
+    load_tc<T, P>(S, mc, kc);
+    const int own = S.hi - S.lo, PW = S.mx + 2 * P;
+    const int NW = (int)blockDim.x >> 5, warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
+    const int want = (S.mx + 63) >> 6;                          // warps a row keeps busy
+    for (int pc = 0; pc < P1; ++pc) {
+        const int cy = descending ? P - pc : pc;
+        const int lr0 = ((cy - S.lo) % P1 + P1) % P1;          // first own row of the phase
+        const int nr = lr0 < own ? (own - 1 - lr0) / P1 + 1 : 0;
+        if (nr > 0) {
+            const int G = max(1, min(NW / nr, want)), ng = min(NW / G, 15);
+            const int g = warp / G, gl = (warp - g * G) * 32 + lane, gt = 32 * G;
+            if (g < ng)
+                for (int k = g; k < nr; k += ng) {
+                    const int lr = lr0 + k * P1;
+                    T* rr = rhs + k * S.mx;
+                    for (int i = gl; i < S.mx; i += gt) rr[i] = S.b[lr * S.mx + i] - ccouple<T, P, true>(S, lr, i);
+                    group_sync(g, G);
+                    const T ky = S.yK[P * S.R + lr], my = S.yM[P * S.R + lr];
+                    T* xrow = S.x + lr * PW;
+                    const T* inv = S.inv + lr * S.mx;
+                    for (int c = 0; c < P1; ++c) {
+                        const int cx = descending ? P - c : c;
+                        const int nx = (S.mx - cx + P) / P1;
+                        for (int sx = gl; sx < nx; sx += gt) {
+                            const int i = cx + P1 * sx;
+                            T sM, sK;
+                            cwin<T, P>(S, xrow + i, i, mc, kc, sM, sK);    // padded column i - p
+                            xrow[i + P] += (rr[i] - (ky * sM + my * sK)) * inv[i];
+                        }
+                        group_sync(g, G);
+                    }
+                    for (int i = gl; i < S.mx; i += gt) {
+                        T sM, sK;
+                        cwin<T, P>(S, xrow + i, i, mc, kc, sM, sK);
+                        S.TM[lr * S.mx + i] = sM;
+                        S.TK[lr * S.mx + i] = sK;
+                    }
+                }
+        }
+        cg::this_cluster().sync();
+    }
+}
+
+// One weighted-Jacobi sweep x += omega D^{-1} (b - A x) from the same x on
+// every node; the own T rows change only after every CTA has read them.
+template <typename T, int P>
+__device__ void cjacobi(const CLevel<T>& S, T* d, T omega) {
+    const int own = S.hi - S.lo, PW = S.mx + 2 * P;
+    grid_for(own, S.mx, [&](int lr, int i) {
+        const int q = lr * S.mx + i;
+        d[q] = omega * (S.b[q] - ccouple<T, P, false>(S, lr, i)) * S.inv[q];
+    });
+    cg::this_cluster().sync();
+    grid_for(own, S.mx, [&](int lr, int i) { S.x[lr * PW + i + P] += d[lr * S.mx + i]; });
+    __syncthreads();
+    cxpass<T, P>(S);
+    cg::this_cluster().sync();
+}
+
+// b_c = P^T (b - A x): the own rows' residual and x-axis restriction (t),
+// then the own coarse rows from the fine rows' t across the cluster.
+template <typename T, int P>
+__device__ void crestrict(const CLevel<T>& S, const CLevel<T>& Sc, const CTransfer<T>& X, T* r, T* t) {
+    const int own = S.hi - S.lo, mcx = Sc.mx;
+    grid_for(own, S.mx, [&](int lr, int i) {
+        const int q = lr * S.mx + i;
+        r[q] = S.b[q] - ccouple<T, P, false>(S, lr, i);
+    });
+    __syncthreads();
+    grid_for(own, mcx, [&](int lr, int I) {
+        const int lo = X.rlox[I];
+        T acc = 0;
+        for (int s = 0; s < X.rwx; ++s) {
+            const int f = lo + s;
+            if (f < 0 || f >= S.mx) continue;
+            acc += X.rvx[I * X.rwx + s] * r[lr * S.mx + f];
+        }
+        t[lr * mcx + I] = acc;
+    });
+    cg::this_cluster().sync();
+    grid_for(Sc.hi - Sc.lo, mcx, [&](int Jl, int I) {
+        const T* const* rows = X.rr + Jl * X.rwy;
+        T acc = 0;
+        for (int s = 0; s < X.rwy; ++s) acc += X.rvy[Jl * X.rwy + s] * rows[s][I];
+        Sc.b[Jl * mcx + I] = acc;
+    });
+    __syncthreads();
+}
+
+// x += P e: the own coarse rows' x-axis prolongation (t), then the own fine
+// rows from the coarse rows' t across the cluster, and the new T_M, T_K.
+template <typename T, int P>
+__device__ void cprolong(const CLevel<T>& S, const CLevel<T>& Sc, const CTransfer<T>& X, T* t) {
+    const int mfx = S.mx, PWc = Sc.mx + 2 * P;
+    grid_for(Sc.hi - Sc.lo, mfx, [&](int Jl, int i) {
+        const int lo = X.plox[i];
+        T acc = 0;
+        for (int s = 0; s < X.pwx; ++s) {
+            const int f = lo + s;
+            if (f < 0 || f >= Sc.mx) continue;
+            acc += X.pvx[i * X.pwx + s] * Sc.x[Jl * PWc + f + P];
+        }
+        t[Jl * mfx + i] = acc;
+    });
+    cg::this_cluster().sync();
+    const int PW = S.mx + 2 * P;
+    grid_for(S.hi - S.lo, mfx, [&](int jl, int i) {
+        const T* const* rows = X.pr + jl * X.pwy;
+        T acc = 0;
+        for (int s = 0; s < X.pwy; ++s) acc += X.pvy[jl * X.pwy + s] * rows[s][i];
+        S.x[jl * PW + i + P] += acc;
+    });
+    __syncthreads();
+    cxpass<T, P>(S);
+    cg::this_cluster().sync();
+}
+
+// Generic pointer to `local`'s counterpart in CTA o's shared memory.
+template <typename T>
+__device__ __forceinline__ const T* cptr(T* local, int o, int rank) {
+    return o == rank ? local : cg::this_cluster().map_shared_rank(local, o);
+}
+
+template <typename T, int P>
+__global__ void __launch_bounds__(kTailThreads, 1) k_cluster_tail(ClusterTailView<T> V, const T* __restrict__ b_in,
+                                                                  T* __restrict__ x_out, int jacobi, T omega) {
+    static_assert(sizeof(T) == 4, "4-byte elements (staging, integer tables)");
+    constexpr int W = 2 * P + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sm = reinterpret_cast<T*>(smem_raw);
+    const int rank = (int)cg::this_cluster().block_rank();
+    const int lc = V.lc;
+    T* r = sm + V.off_r;
+    T* t = sm + V.off_t;
+    T* zrow = sm + V.off_z;
+    // Operator data (uploaded at assembly, written by no kernel) is staged
+    // before the wait on the previous kernel; the right side b after it.
+    for (int q = 1; q <= lc; ++q) {
+        const LevelView<T>& L = V.L[q];
+        const CLevel<T> S = clevel<T, P>(V, smem_raw, q, rank);
+        const int own = S.hi - S.lo;
+        stage(const_cast<T*>(S.inv), L.invdiag + (size_t)S.lo * S.mx, own * S.mx);
+        for (int e = threadIdx.x; e < W * own; e += blockDim.x) {
+            const int bb = e / own, jl = e - bb * own;
+            cp_async4(const_cast<T*>(S.yM) + bb * S.R + jl, L.Mb[1] + bb * S.my + S.lo + jl);
+            cp_async4(const_cast<T*>(S.yK) + bb * S.R + jl, L.Kb[1] + bb * S.my + S.lo + jl);
+        }
+        for (int e = threadIdx.x; e < S.nbc * W; e += blockDim.x) {
+            const int sl = e / W, bb = e - sl * W;
+            const int i = sl < S.tlo ? sl : S.thi + (sl - S.tlo);
+            cp_async4(const_cast<T*>(S.xM) + e, L.Mb[0] + bb * S.mx + i);
+            cp_async4(const_cast<T*>(S.xK) + e, L.Kb[0] + bb * S.mx + i);
+        }
+        T* tc = sm + V.off_tc[q];
+        for (int bb = threadIdx.x; bb < W; bb += blockDim.x) {
+            tc[bb] = L.Mc[0][bb];
+            tc[W + bb] = L.Kc[0][bb];
+        }
+        const TransferView<T>& X = V.X[q];
+        const CTransfer<T> Y = ctransfer(V, smem_raw, q);
+        stage(const_cast<int*>(Y.plox), X.plo[0], X.mf[0]);
+        stage(const_cast<T*>(Y.pvx), X.pv[0], X.mf[0] * X.pw[0]);
+        stage(const_cast<int*>(Y.rlox), X.rlo[0], X.mc[0]);
+        stage(const_cast<T*>(Y.rvx), X.rv[0], X.mc[0] * X.rw[0]);
+        const int Rc = V.R[q - 1], myc = V.L[q - 1].m[1];
+        const int loc = min(rank * Rc, myc), ownc = min(loc + Rc, myc) - loc;
+        stage(const_cast<T*>(Y.pvy), X.pv[1] + (size_t)S.lo * X.pw[1], own * X.pw[1]);
+        stage(const_cast<T*>(Y.rvy), X.rv[1] + (size_t)loc * X.rw[1], ownc * X.rw[1]);
+        // row pointers: y-band neighbours, restriction and prolongation rows
+        const T** rp = const_cast<const T**>(S.rp);
+        for (int e = threadIdx.x; e < own * W; e += blockDim.x) {
+            const int lr = e / W, bb = e - lr * W, jj = S.lo + lr + bb - P;
+            if (jj < 0 || jj >= S.my) {
+                rp[e] = S.TM + lr * S.mx;                   // zero band entry
+            } else {
+                const int o = jj / S.R;
+                rp[e] = cptr(S.TM + (jj - o * S.R) * S.mx, o, rank);
+            }
+        }
+        const T** rr = const_cast<const T**>(Y.rr);
+        for (int e = threadIdx.x; e < ownc * X.rw[1]; e += blockDim.x) {
+            const int Jl = e / X.rw[1], s2 = e - Jl * X.rw[1], f = X.rlo[1][loc + Jl] + s2;
+            if (f < 0 || f >= S.my) {
+                rr[e] = zrow;
+            } else {
+                const int o = f / S.R;
+                rr[e] = cptr(t + (f - o * S.R) * X.mc[0], o, rank);
+            }
+        }
+        const T** pr = const_cast<const T**>(Y.pr);
+        for (int e = threadIdx.x; e < own * X.pw[1]; e += blockDim.x) {
+            const int jl = e / X.pw[1], s2 = e - jl * X.pw[1], F = X.plo[1][S.lo + jl] + s2;
+            if (F < 0 || F >= myc) {
+                pr[e] = zrow;
+            } else {
+                const int o = F / Rc;
+                pr[e] = cptr(t + (F - o * Rc) * X.mf[0], o, rank);
+            }
+        }
+    }
+    for (int e = threadIdx.x; e < V.L[lc].m[0]; e += blockDim.x) zrow[e] = 0;
+    CoarseView<T> Cs = V.C;                             // coarsest eigenbasis (CTA 0 only)
+    {
+        T* f = sm + V.off_cv;
+        const int m0 = V.C.m[0], m1 = V.C.m[1];
+        if (rank == 0) {
+            stage(f, V.C.V[0], m0 * m0);
+            stage(f + m0 * m0, V.C.V[1], m1 * m1);
+            stage(f + m0 * m0 + m1 * m1, V.C.laminv, m0 * m1);
+        }
+        Cs.V[0] = f;
+        Cs.V[1] = f + m0 * m0;
+        Cs.laminv = f + m0 * m0 + m1 * m1;
+    }
+    for (int q = 0; q <= lc; ++q) {                     // coarse e^0 = 0 on every level, zero pads
+        const CLevel<T> S = clevel<T, P>(V, smem_raw, q, rank);
+        for (int e = threadIdx.x; e < S.R * (S.mx + 2 * P); e += blockDim.x) S.x[e] = 0;
+        if (q > 0)
+            for (int e = threadIdx.x; e < 2 * S.R * S.mx; e += blockDim.x) S.TM[e] = 0;
+    }
+    pdl_enter();
+    {
+        const CLevel<T> S = clevel<T, P>(V, smem_raw, lc, rank);
+        stage(S.b, b_in + (size_t)S.lo * S.mx, (S.hi - S.lo) * S.mx);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    cg::this_cluster().sync();                          // every CTA's zero T rows in place
+    for (int l = lc; l >= 1; --l) {
+        const CLevel<T> S = clevel<T, P>(V, smem_raw, l, rank);
+        if (jacobi) cjacobi<T, P>(S, r, omega);                                // pre-smooth
+        else cgs<T, P>(S, r, false);
+        crestrict<T, P>(S, clevel<T, P>(V, smem_raw, l - 1, rank), ctransfer(V, smem_raw, l), r, t);
+    }
+    if (rank == 0) {                                    // direct solve, into the padded rows of x_0
+        const int m0 = Cs.m[0], m1 = Cs.m[1], N = m0 * m1;
+        const T* b0 = sm + V.off_b[0];
+        T* x0 = sm + V.off_x[0];
+        auto pass = [&](const T* in, T* out, int axis, bool transpose, bool pad) {
+            const int md = Cs.m[axis], stride = axis == 0 ? 1 : m0;
+            const T* Vm = Cs.V[axis];
+            for (int idx = threadIdx.x; idx < N; idx += blockDim.x) {
+                const int I = axis == 0 ? idx % m0 : idx / m0;
+                const int base = idx - I * stride;
+                T acc = 0;
+                for (int s = 0; s < md; ++s) acc += (transpose ? Vm[s * md + I] : Vm[I * md + s]) * in[base + s * stride];
+                out[pad ? (idx / m0) * (m0 + 2 * P) + idx % m0 + P : idx] = acc;
+            }
+            __syncthreads();
+        };
+        pass(b0, r, 0, true, false);
+        pass(r, t, 1, true, false);
+        for (int i = threadIdx.x; i < N; i += blockDim.x) t[i] *= Cs.laminv[i];
+        __syncthreads();
+        pass(t, r, 1, false, false);
+        pass(r, x0, 0, false, true);
+    }
+    cg::this_cluster().sync();
+    for (int l = 1; l <= lc; ++l) {
+        const CLevel<T> S = clevel<T, P>(V, smem_raw, l, rank);
+        cprolong<T, P>(S, clevel<T, P>(V, smem_raw, l - 1, rank), ctransfer(V, smem_raw, l), t);   // x += P e
+        if (jacobi) cjacobi<T, P>(S, r, omega);                                // post-smooth
+        else cgs<T, P>(S, r, true);
+    }
+    const CLevel<T> S = clevel<T, P>(V, smem_raw, lc, rank);
+    const int PW = S.mx + 2 * P;
+    grid_for(S.hi - S.lo, S.mx, [&](int lr, int i) { x_out[(size_t)(S.lo + lr) * S.mx + i] = S.x[lr * PW + i + P]; });
+}
+
 template <typename F>
 static void tail_with_p(int p, F&& f) {
     switch (p) {
@@ -439,6 +918,8 @@ void prepare_tail_kernels(int optin) {
         tail_with_p(p, [&](auto PC) {
             constexpr int P = decltype(PC)::value;
             cudaFuncSetAttribute(k_coarse_tail<float, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+            cudaFuncSetAttribute(k_cluster_tail<float, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+            cudaFuncSetAttribute(k_cluster_tail<float, P>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         });
     if (dev >= 0 && dev < 64) g_tail_limit[dev] = (size_t)optin;
 }
@@ -459,6 +940,55 @@ void coarse_tail(cudaStream_t s, const TailView<T>& V, const T* b, T* x, int jac
 }
 
 template void coarse_tail<float>(cudaStream_t, const TailView<float>&, const float*, float*, int, float);
+
+template <typename T>
+static cudaLaunchConfig_t cluster_config(const ClusterTailView<T>& V, cudaStream_t s, cudaLaunchAttribute* at,
+                                         bool overlap) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(V.ctas);
+    cfg.blockDim = dim3(kTailThreads);
+    cfg.dynamicSmemBytes = V.smem;
+    cfg.stream = s;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = V.ctas;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = overlap ? 2 : 1;
+    return cfg;
+}
+
+template <typename T>
+bool cluster_tail_fits(const ClusterTailView<T>& V) {
+    if (V.lc < 1 || V.ctas < 2 || V.ctas > 16 || V.smem > tail_smem_limit()) return false;
+    int n = 0;
+    tail_with_p(V.L[V.lc].p, [&](auto PC) {
+        constexpr int P = decltype(PC)::value;
+        cudaLaunchAttribute at[2];
+        const cudaLaunchConfig_t cfg = cluster_config(V, nullptr, at, false);
+        if (cudaOccupancyMaxActiveClusters(&n, k_cluster_tail<T, P>, &cfg) != cudaSuccess) n = 0;
+    });
+    cudaGetLastError();
+    return n >= 1;
+}
+
+template <typename T>
+void cluster_tail(cudaStream_t s, const ClusterTailView<T>& V, const T* b, T* x, int jacobi, T omega) {
+    tail_with_p(V.L[V.lc].p, [&](auto PC) {
+        constexpr int P = decltype(PC)::value;
+        cudaLaunchAttribute at[2];
+        const cudaLaunchConfig_t cfg = cluster_config(V, s, at, launch_overlap());
+        cudaEvent_t e0 = profiling() ? profile_before(s) : nullptr;
+        cudaLaunchKernelEx(&cfg, k_cluster_tail<T, P>, V, b, x, jacobi, omega);
+        if (e0) profile_after(s, (const void*)k_cluster_tail<T, P>, dim3(V.ctas), e0);
+    });
+    count_launch();
+}
+
+template bool cluster_tail_fits<float>(const ClusterTailView<float>&);
+template void cluster_tail<float>(cudaStream_t, const ClusterTailView<float>&, const float*, float*, int, float);
 
 }  // namespace dev
 }  // namespace igamg
