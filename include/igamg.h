@@ -340,18 +340,6 @@ igamg_status igamg_set_tail_ctas(igamg_ctx* ctx, int ctas);
 int igamg_get_tail_ctas(const igamg_ctx* ctx);
 int igamg_tail_levels_available(const igamg_ctx* ctx, int ctas);
 
-/* The cluster tail of FP64 2D V-cycles (the FP64 form and the paper's
- * precision): levels 0..tail_levels on a cluster of ctas = 8 or 16 CTAs
- * (tail_levels = 0: per-level launches down to the coarsest level, -1: the
- * deepest level that fits, which is the default with 16 CTAs; FP64 data take
- * twice the shared memory, so about 129^2 unknowns per level on 16 CTAs).
- * Same colours, order and operators as the per-level FP64 kernels, FP64
- * rounding order aside.  igamg_get_tail64 returns the form, the level in use
- * and the deepest level available with that form.  igamg_autotune times every
- * FP64 form and depth.  Errors: EINVAL. */
-igamg_status igamg_set_tail64(igamg_ctx* ctx, int ctas, int tail_levels);
-void igamg_get_tail64(const igamg_ctx* ctx, int* ctas, int* tail_levels, int* most);
-
 /* Cycle of Algorithm 2 (Sec. 2.4) used by every solve, cycle and autotune
  * call of this context.  smoother: IGAMG_SMOOTH_GS (default; multicolour
  * Gauss-Seidel, (p+1)^dim colours, ascending before and descending after the

@@ -76,8 +76,6 @@ def _load():
         "igamg_set_tail_ctas": (c_int, [vp, c_int]),
         "igamg_get_tail_ctas": (c_int, [vp]),
         "igamg_tail_levels_available": (c_int, [vp, c_int]),
-        "igamg_set_tail64": (c_int, [vp, c_int, c_int]),
-        "igamg_get_tail64": (None, [vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
         "igamg_batch_set_tail_ctas": (c_int, [vp, c_int]),
         "igamg_set_cycle": (c_int, [vp, c_int, c_int, c_double]),
         "igamg_get_cycle": (None, [vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_double)]),
@@ -384,17 +382,6 @@ def igamg_get_schedule(ctx):
 def igamg_set_tail_ctas(ctx, ctas):
     """Coarse tail on one CTA (1) or on a thread-block cluster of 8 or 16 CTAs."""
     _check(_load().igamg_set_tail_ctas(ctx, int(ctas)), "igamg_set_tail_ctas")
-
-
-def igamg_set_tail64(ctx, ctas=16, tail_levels=-1):
-    """FP64 cycles' cluster tail: ctas 8 or 16, tail_levels 0 = off, -1 = deepest."""
-    _check(_load().igamg_set_tail64(ctx, int(ctas), int(tail_levels)), "igamg_set_tail64")
-
-
-def igamg_get_tail64(ctx):
-    a, b, m = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    _load().igamg_get_tail64(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(m))
-    return {"ctas": a.value, "tail_levels": b.value, "most": m.value}
 
 
 def igamg_tail_levels_available(ctx, ctas):

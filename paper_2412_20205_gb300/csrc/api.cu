@@ -126,11 +126,6 @@ struct igamg_ctx {
     int tail_ctas = 1;
     ClusterTailView<float> ctail32{};
     std::vector<ClusterTailView<float>> ctails[2];
-    // FP64 2D cycles: levels 0..ctail64.lc on a cluster of tail64_ctas CTAs
-    // (ctail64.lc = 0: per-level launches down to the coarsest level)
-    int tail64_ctas = 16;
-    ClusterTailView<double> ctail64{};
-    std::vector<ClusterTailView<double>> ctails64[2];
     int gs_cap32 = 0;                       // row-CTA thread cap of FP32 GS (0: default)
     // GS sweep form per precision: levels with at least this many rows run a
     // sweep in one launch (rows wait on their earlier-phase neighbours), the
@@ -357,9 +352,9 @@ int tail_level(const igamg_ctx* c) {
 
 // Highest tail level available with `ctas` CTAs (1: the one-CTA tail).
 int tail_most(const igamg_ctx* c, int ctas) {
-    if (ctas == 1) return std::max(0, (int)c->tails.size() - 1);
+    if (ctas == 1) return (int)c->tails.size() - 1;
     for (int k = 0; k < 2; ++k)
-        if (kTailCtas[k] == ctas) return std::max(0, (int)c->ctails[k].size() - 1);
+        if (kTailCtas[k] == ctas) return (int)c->ctails[k].size() - 1;
     return 0;
 }
 
@@ -379,80 +374,6 @@ void select_tail(igamg_ctx* c, int ctas, int lc) {
 void run_tail(const igamg_ctx* c, cudaStream_t s, const float* b, float* x, int jacobi = 0, float omega = 0.f) {
     if (c->tail_ctas > 1) dev::cluster_tail<float>(s, c->ctail32, b, x, jacobi, omega);
     else dev::coarse_tail<float>(s, c->tail32, b, x, jacobi, omega);
-}
-
-// FP64 cycles: the tail on `ctas` (8 or 16) CTAs, levels 0..lc (0: none).
-int tail_most64(const igamg_ctx* c, int ctas) {
-    for (int k = 0; k < 2; ++k)
-        if (kTailCtas[k] == ctas) return std::max(0, (int)c->ctails64[k].size() - 1);
-    return 0;
-}
-int tail_level64(const igamg_ctx* c) { return c->ctail64.lc; }
-void select_tail64(igamg_ctx* c, int ctas, int lc) {
-    lc = std::max(0, std::min(lc, tail_most64(c, ctas)));
-    c->ctail64 = ClusterTailView<double>{};
-    c->tail64_ctas = ctas;
-    for (int k = 0; k < 2; ++k)
-        if (kTailCtas[k] == ctas && lc > 0) c->ctail64 = c->ctails64[k][lc];
-}
-
-// Cluster-tail views of a 2D hierarchy (ClusterTailView): out[k][l] covers
-// levels 0..l on kTailCtas[k] CTAs; out[k][0] is unused.  Offsets are in
-// elements of T; integer tables and row pointers are rounded up to whole
-// elements, the pointer tables come first (8-byte aligned).
-template <typename T>
-void build_cluster_tails(const igamg_ctx* c, const std::vector<LevelView<T>>& lv,
-                         const std::vector<TransferView<T>>& tv, const CoarseView<T>& cv,
-                         std::vector<ClusterTailView<T>>* out) {
-    const int p = c->p, W = 2 * p + 1, L = c->L;
-    const int ipe = (int)(sizeof(T) / sizeof(int)), ppe = (int)(sizeof(void*) / sizeof(T));
-    auto ints = [&](int n) { return (n + ipe - 1) / ipe; };
-    const int N0 = (int)c->hl[0].N(), m00 = c->hl[0].m[0], m01 = c->hl[0].m[1];
-    for (int k = 0; k < 2; ++k) {
-        out[k].assign(1, ClusterTailView<T>{});
-        const int C = kTailCtas[k];
-        for (int l = 1; l <= std::min(L - 2, kCTailLevels - 1); ++l) {
-            ClusterTailView<T> v{};
-            v.ctas = C;
-            v.lc = l;
-            int off = 0, rmax = N0, tmax = N0;
-            for (int q = 0; q <= l; ++q) v.R[q] = q == 0 ? c->hl[0].m[1] : (c->hl[q].m[1] + C - 1) / C;
-            for (int q = 1; q <= l; ++q) {
-                const TransferView<T>& X = tv[q];
-                v.off_rp[q] = off;
-                off += ppe * (v.R[q] * W + v.R[q - 1] * X.rw[1] + v.R[q] * X.pw[1]);
-            }
-            for (int q = 0; q <= l; ++q) {
-                const int mx = c->hl[q].m[0], R = v.R[q];
-                v.off_x[q] = off; off += R * (mx + 2 * p);
-                v.off_b[q] = off; off += R * mx;
-                if (q == 0) continue;
-                const TransferView<T>& X = tv[q];
-                v.nbc[q] = lv[q].tlo[0] + (mx - lv[q].thi[0]);
-                v.off_inv[q] = off; off += R * mx;
-                v.off_tm[q] = off; off += 2 * R * mx;
-                v.off_yb[q] = off; off += 2 * W * R;
-                v.off_xb[q] = off; off += 2 * W * v.nbc[q];
-                v.off_tc[q] = off; off += 2 * W;
-                v.off_tx[q] = off; off += ints(X.mf[0]) + X.mf[0] * X.pw[0] + ints(X.mc[0]) + X.mc[0] * X.rw[0];
-                v.off_ty[q] = off; off += R * X.pw[1] + v.R[q - 1] * X.rw[1];
-                rmax = std::max(rmax, R * mx);
-                tmax = std::max({tmax, R * X.mc[0], v.R[q - 1] * X.mf[0]});
-            }
-            v.off_cv = off; off += m00 * m00 + m01 * m01 + N0;
-            v.off_r = off; off += rmax;
-            v.off_t = off; off += tmax;
-            v.off_z = off; off += c->hl[l].m[0];
-            v.smem = (size_t)off * sizeof(T);
-            for (int q = 0; q <= l; ++q) {
-                v.L[q] = lv[q];
-                v.X[q] = tv[q];
-            }
-            v.C = cv;
-            if (!dev::cluster_tail_fits(v)) break;
-            out[k].push_back(v);
-        }
-    }
 }
 
 // Row-CTA thread cap of the GS sweeps in cycles of type T (autotuned for FP32).
@@ -506,11 +427,6 @@ void mu_cycle(const igamg_ctx* c, cudaStream_t s, Workspace& w, int top, int l, 
             run_tail(c, s, b, x, c->smoother == IGAMG_SMOOTH_JACOBI, (float)c->omega);
             return;
         }
-    } else {
-        if (c->mu == 1 && c->ctail64.lc > 0 && l == c->ctail64.lc && l < top) {
-            dev::cluster_tail<double>(s, c->ctail64, b, x, c->smoother == IGAMG_SMOOTH_JACOBI, c->omega);
-            return;
-        }
     }
     const size_t N = lv[l].n();
     if (zero) {
@@ -560,13 +476,10 @@ void vcycle(const igamg_ctx* c, cudaStream_t s, Workspace& w, int top, T* x_top,
     const auto& tv = Views<T>::tv(c);
     auto& B = Views<T>::buf(w);
     const int dim = c->dim;
-    // 2D cycles hand levels lc..0 to one CTA or cluster when the hierarchy has a tail
+    // FP32 2D cycles hand levels lc..0 to one CTA or cluster when the hierarchy has a tail
     int lc = 0;
-    if constexpr (std::is_same<T, float>::value) {
+    if constexpr (std::is_same<T, float>::value)
         if (tail_level(c) > 0 && tail_level(c) < top) lc = tail_level(c);
-    } else {
-        if (c->ctail64.lc > 0 && c->ctail64.lc < top) lc = c->ctail64.lc;
-    }
     const int lowest = lc > 0 ? lc + 1 : 1;
     for (int l = top; l >= lowest; --l) {
         T* x = (l == top) ? x_top : B[l].x;
@@ -589,8 +502,6 @@ void vcycle(const igamg_ctx* c, cudaStream_t s, Workspace& w, int top, T* x_top,
     if (lc > 0) {
         if constexpr (std::is_same<T, float>::value)
             run_tail(c, s, B[lc].b, B[lc].x);                                            // levels lc..0
-        else
-            dev::cluster_tail<double>(s, c->ctail64, B[lc].b, B[lc].x);
     } else {
         T* x0 = (top == 0) ? x_top : B[0].x;
         const T* b0 = (top == 0) ? b_top : B[0].b;
@@ -1180,19 +1091,59 @@ igamg_status igamg_assemble(igamg_ctx* c) {
             c->tails.push_back(v);
         }
     }
-    // Cluster tails of the 2D cycles in either precision: on kTailCtas[k]
-    // CTAs, every lc whose levels fit a CTA's shared memory and whose cluster
-    // the device can hold.
+    // Cluster tails of the FP32 2D cycle: on kTailCtas[k] CTAs, every lc
+    // whose levels fit a CTA's shared memory (ClusterTailView) and whose
+    // cluster the device can hold.
+    for (int k = 0; k < 2; ++k) c->ctails[k].assign(1, ClusterTailView<float>{});
     if (dim == 2 && L >= 3) {
-        build_cluster_tails<float>(c, c->lv32, c->tv32, c->cv32, c->ctails);
-        build_cluster_tails<double>(c, c->lv64, c->tv64, c->cv64, c->ctails64);
-    } else {
+        const int W = 2 * p + 1;
+        const int N0 = (int)c->hl[0].N(), m00 = c->hl[0].m[0], m01 = c->hl[0].m[1];
         for (int k = 0; k < 2; ++k) {
-            c->ctails[k].assign(1, ClusterTailView<float>{});
-            c->ctails64[k].assign(1, ClusterTailView<double>{});
+            const int C = kTailCtas[k];
+            for (int l = 1; l <= std::min(L - 2, kCTailLevels - 1); ++l) {
+                ClusterTailView<float> v{};
+                v.ctas = C;
+                v.lc = l;
+                int off = 0, rmax = N0, tmax = N0;
+                for (int q = 0; q <= l; ++q) v.R[q] = q == 0 ? c->hl[0].m[1] : (c->hl[q].m[1] + C - 1) / C;
+                for (int q = 1; q <= l; ++q) {                 // row pointers first: 8-byte aligned
+                    const TransferView<float>& X = c->tv32[q];
+                    v.off_rp[q] = off;
+                    off += 2 * (v.R[q] * W + v.R[q - 1] * X.rw[1] + v.R[q] * X.pw[1]);
+                }
+                for (int q = 0; q <= l; ++q) {
+                    const int mx = c->hl[q].m[0], R = v.R[q];
+                    v.off_x[q] = off; off += R * (mx + 2 * p);
+                    v.off_b[q] = off; off += R * mx;
+                    if (q == 0) continue;
+                    const LevelView<float>& Lq = c->lv32[q];
+                    const TransferView<float>& X = c->tv32[q];
+                    v.nbc[q] = Lq.tlo[0] + (mx - Lq.thi[0]);
+                    v.off_inv[q] = off; off += R * mx;
+                    v.off_tm[q] = off; off += 2 * R * mx;
+                    v.off_yb[q] = off; off += 2 * W * R;
+                    v.off_xb[q] = off; off += 2 * W * v.nbc[q];
+                    v.off_tc[q] = off; off += 2 * W;
+                    v.off_tx[q] = off; off += X.mf[0] * (1 + X.pw[0]) + X.mc[0] * (1 + X.rw[0]);
+                    v.off_ty[q] = off; off += R * X.pw[1] + v.R[q - 1] * X.rw[1];
+                    rmax = std::max(rmax, R * mx);
+                    tmax = std::max({tmax, R * X.mc[0], v.R[q - 1] * X.mf[0]});
+                }
+                v.off_cv = off; off += m00 * m00 + m01 * m01 + N0;
+                v.off_r = off; off += rmax;
+                v.off_t = off; off += tmax;
+                v.off_z = off; off += c->hl[l].m[0];
+                v.smem = (size_t)off * sizeof(float);
+                for (int q = 0; q <= l; ++q) {
+                    v.L[q] = c->lv32[q];
+                    v.X[q] = c->tv32[q];
+                }
+                v.C = c->cv32;
+                if (!dev::cluster_tail_fits(v)) break;
+                c->ctails[k].push_back(v);
+            }
         }
     }
-    select_tail64(c, kTailCtas[1], tail_most64(c, kTailCtas[1]));   // FP64 cycles: the deepest 16-CTA tail
     if (dim == 2) {
         DFView& D = c->dfv;
         const LevelView<double>& a = c->lv64[L - 1];
@@ -1762,21 +1713,6 @@ igamg_status igamg_set_tail_ctas(igamg_ctx* c, int ctas) {
 
 int igamg_get_tail_ctas(const igamg_ctx* c) { return c ? c->tail_ctas : 1; }
 
-igamg_status igamg_set_tail64(igamg_ctx* c, int ctas, int tail_levels) {
-    if (igamg_status st = check_ctx(c)) return st;
-    if ((ctas != kTailCtas[0] && ctas != kTailCtas[1]) || tail_levels < -1)
-        return fail(IGAMG_EINVAL, "FP64 tail: ctas 8 or 16, tail_levels >= -1");
-    select_tail64(c, ctas, tail_levels < 0 ? tail_most64(c, ctas) : tail_levels);
-    drop_graphs(c);
-    return IGAMG_OK;
-}
-
-void igamg_get_tail64(const igamg_ctx* c, int* ctas, int* tail_levels, int* most) {
-    if (ctas) *ctas = c ? c->tail64_ctas : 16;
-    if (tail_levels) *tail_levels = (c && c->assembled) ? tail_level64(c) : 0;
-    if (most) *most = (c && c->assembled) ? tail_most64(c, c->tail64_ctas) : 0;
-}
-
 int igamg_tail_levels_available(const igamg_ctx* c, int ctas) {
     return (c && c->assembled) ? tail_most(c, ctas) : 0;
 }
@@ -1832,8 +1768,6 @@ igamg_status igamg_autotune(igamg_ctx* c, void* d_ws, size_t ws_bytes, void* str
         TailView<float> tail;
         int tail_ctas;
         ClusterTailView<float> ctail;
-        int tail64_ctas;
-        ClusterTailView<double> ctail64;
         bool armed = true;
         ~Restore() {
             if (*e0) cudaEventDestroy(*e0);
@@ -1846,12 +1780,9 @@ igamg_status igamg_autotune(igamg_ctx* c, void* d_ws, size_t ws_bytes, void* str
             c->tail32 = tail;
             c->tail_ctas = tail_ctas;
             c->ctail32 = ctail;
-            c->tail64_ctas = tail64_ctas;
-            c->ctail64 = ctail64;
             drop_graphs(c);
         }
-    } restore{c, &e0, &e1, c->gs_cap32, c->flow32, c->flow64, c->tail_on, c->tail32, c->tail_ctas, c->ctail32,
-              c->tail64_ctas, c->ctail64};
+    } restore{c, &e0, &e1, c->gs_cap32, c->flow32, c->flow64, c->tail_on, c->tail32, c->tail_ctas, c->ctail32};
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
     const int caps[3] = {128, 256, 512};
@@ -1892,24 +1823,16 @@ igamg_status igamg_autotune(igamg_ctx* c, void* d_ws, size_t ws_bytes, void* str
     c->gs_cap32 = best_cap;
     select_tail(c, best_tail.first, best_tail.second);
     c->flow32 = best_flow;
-    // FP64 cycles: the sweep form and the cluster tail (on the same workspace;
-    // b = the FP32 b in FP64)
-    std::vector<std::pair<int, int>> tails64{{kTailCtas[1], 0}};
-    for (int ctas : kTailCtas)
-        for (int lc = 1; lc <= tail_most64(c, ctas); ++lc) tails64.push_back({ctas, lc});
+    // FP64 cycles: the sweep form only (on the same workspace; b = the FP32 b in FP64)
     float best64 = 1e30f;
     int best_flow64 = c->flow64;
-    std::pair<int, int> best_tail64{c->tail64_ctas, tail_level64(c)};
-    for (int fi = 0; fi < 3; ++fi)
-        for (const auto& tt : tails64) {
-            c->flow64 = flows[fi];
-            select_tail64(c, tt.first, tt.second);
-            float ms = 0.f;
-            if (igamg_status st = time_cycles(0.0, &ms)) return st;
-            if (ms < best64) { best64 = ms; best_flow64 = c->flow64; best_tail64 = tt; }
-        }
+    for (int fi = 0; fi < 3; ++fi) {
+        c->flow64 = flows[fi];
+        float ms = 0.f;
+        if (igamg_status st = time_cycles(0.0, &ms)) return st;
+        if (ms < best64) { best64 = ms; best_flow64 = c->flow64; }
+    }
     c->flow64 = best_flow64;
-    select_tail64(c, best_tail64.first, best_tail64.second);
     CUDA_TRY(cudaGetLastError());
     restore.armed = false;
     drop_graphs(c);

@@ -32,22 +32,10 @@ __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
-}
-
-// One element of 4 or 8 bytes (both addresses aligned to its size).
-template <typename E>
-__device__ __forceinline__ void cp_async_elem(E* dst, const E* src) {
-    static_assert(sizeof(E) == 4 || sizeof(E) == 8, "4- or 8-byte elements");
-    if constexpr (sizeof(E) == 4) cp_async4(dst, src);
-    else cp_async8(dst, src);
-}
-
 template <typename E>
 __device__ __forceinline__ void stage(E* dst, const E* src, int n) {
-    for (int q = threadIdx.x; q < n; q += blockDim.x) cp_async_elem(dst + q, src + q);
+    static_assert(sizeof(E) == 4, "4-byte elements");
+    for (int q = threadIdx.x; q < n; q += blockDim.x) cp_async4(dst + q, src + q);
 }
 
 // One level as the tail sees it, all in shared memory:
@@ -519,20 +507,19 @@ __device__ __forceinline__ CTransfer<T> ctransfer(const ClusterTailView<T>& V, u
     Y.rwx = X.rw[0];
     Y.pwy = X.pw[1];
     Y.rwy = X.rw[1];
-    constexpr int IPE = (int)(sizeof(T) / sizeof(int));      // ints per element
     T* f = sm + V.off_tx[q];
     Y.plox = reinterpret_cast<const int*>(f);
-    f += (X.mf[0] + IPE - 1) / IPE;
+    f += X.mf[0];
     Y.pvx = f;
     f += X.mf[0] * X.pw[0];
     Y.rlox = reinterpret_cast<const int*>(f);
-    f += (X.mc[0] + IPE - 1) / IPE;
+    f += X.mc[0];
     Y.rvx = f;
     const int Rf = V.R[q], Rc = V.R[q - 1];
     T* g = sm + V.off_ty[q];
     Y.pvy = g;
     Y.rvy = g + Rf * X.pw[1];
-    const T* const* rpq = reinterpret_cast<const T* const*>(raw + (size_t)V.off_rp[q] * sizeof(T));    // 8-byte aligned
+    const T* const* rpq = reinterpret_cast<const T* const*>(raw + (size_t)V.off_rp[q] * sizeof(T));
     Y.rr = rpq + Rf * (2 * V.L[q].p + 1);
     Y.pr = Y.rr + Rc * X.rw[1];
     return Y;
@@ -763,6 +750,7 @@ __device__ __forceinline__ const T* cptr(T* local, int o, int rank) {
 template <typename T, int P>
 __global__ void __launch_bounds__(kTailThreads, 1) k_cluster_tail(ClusterTailView<T> V, const T* __restrict__ b_in,
                                                                   T* __restrict__ x_out, int jacobi, T omega) {
+    static_assert(sizeof(T) == 4, "4-byte elements (staging, integer tables)");
     constexpr int W = 2 * P + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
@@ -780,14 +768,14 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_cluster_tail(ClusterTailVie
         stage(const_cast<T*>(S.inv), L.invdiag + (size_t)S.lo * S.mx, own * S.mx);
         for (int e = threadIdx.x; e < W * own; e += blockDim.x) {
             const int bb = e / own, jl = e - bb * own;
-            cp_async_elem(const_cast<T*>(S.yM) + bb * S.R + jl, L.Mb[1] + bb * S.my + S.lo + jl);
-            cp_async_elem(const_cast<T*>(S.yK) + bb * S.R + jl, L.Kb[1] + bb * S.my + S.lo + jl);
+            cp_async4(const_cast<T*>(S.yM) + bb * S.R + jl, L.Mb[1] + bb * S.my + S.lo + jl);
+            cp_async4(const_cast<T*>(S.yK) + bb * S.R + jl, L.Kb[1] + bb * S.my + S.lo + jl);
         }
         for (int e = threadIdx.x; e < S.nbc * W; e += blockDim.x) {
             const int sl = e / W, bb = e - sl * W;
             const int i = sl < S.tlo ? sl : S.thi + (sl - S.tlo);
-            cp_async_elem(const_cast<T*>(S.xM) + e, L.Mb[0] + bb * S.mx + i);
-            cp_async_elem(const_cast<T*>(S.xK) + e, L.Kb[0] + bb * S.mx + i);
+            cp_async4(const_cast<T*>(S.xM) + e, L.Mb[0] + bb * S.mx + i);
+            cp_async4(const_cast<T*>(S.xK) + e, L.Kb[0] + bb * S.mx + i);
         }
         T* tc = sm + V.off_tc[q];
         for (int bb = threadIdx.x; bb < W; bb += blockDim.x) {
@@ -932,8 +920,6 @@ void prepare_tail_kernels(int optin) {
             cudaFuncSetAttribute(k_coarse_tail<float, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
             cudaFuncSetAttribute(k_cluster_tail<float, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
             cudaFuncSetAttribute(k_cluster_tail<float, P>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-            cudaFuncSetAttribute(k_cluster_tail<double, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-            cudaFuncSetAttribute(k_cluster_tail<double, P>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         });
     if (dev >= 0 && dev < 64) g_tail_limit[dev] = (size_t)optin;
 }
@@ -1002,10 +988,7 @@ void cluster_tail(cudaStream_t s, const ClusterTailView<T>& V, const T* b, T* x,
 }
 
 template bool cluster_tail_fits<float>(const ClusterTailView<float>&);
-template bool cluster_tail_fits<double>(const ClusterTailView<double>&);
 template void cluster_tail<float>(cudaStream_t, const ClusterTailView<float>&, const float*, float*, int, float);
-template void cluster_tail<double>(cudaStream_t, const ClusterTailView<double>&, const double*, double*, int,
-                                   double);
 
 }  // namespace dev
 }  // namespace igamg

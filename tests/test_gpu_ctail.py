@@ -9,10 +9,7 @@ and with the one-CTA tail to FP32 round-off (relative 1e-5 on the
 correction, 2-norm and max-norm) and with the FP64 oracle's cycle to FP32
 accuracy (2e-5), for several depths, both cluster sizes, both smoothers,
 square and rectangular grids, p = 1..7 and bands of unequal row counts;
-whole solves converge like the per-level schedule.  The FP64 cycles' cluster
-tail (on by default) agrees with the per-level FP64 cycle and the oracle's
-cycle to 1e-12 (FP64 rounding order); the FP64 solves against the oracle in
-the other test files run through it.
+whole solves converge like the per-level schedule.
 """
 import numpy as np
 import pytest
@@ -150,53 +147,3 @@ def test_batch_members_with_cluster_tails(pkg):
     assert out["converged"], out["statuses"]
     assert np.all(np.abs(np.asarray(out["cycles"]) - np.asarray(base["cycles"])) <= 1)
     B.close()
-
-
-@pytest.mark.parametrize("n,p", SHAPES, ids=lambda c: str(c))
-@pytest.mark.parametrize("smoother", ["gs", "jacobi"])
-def test_fp64_cluster_tail_cycle_matches_oracle(pkg, n, p, smoother):
-    ns = list(n) if isinstance(n, tuple) else [n, n]
-    ctx = pkg.igamg_setup(2, p, ns, 0)
-    pkg.igamg_assemble(ctx)
-    pkg.igamg_set_cycle(ctx, smoother, 1)
-    H = omg.Hierarchy(2, ns, p)
-    ws = torch.empty(pkg.igamg_workspace_bytes(ctx, 5, pkg.IGAMG_FP64), dtype=torch.uint8, device=DEV)
-    rng = np.random.default_rng(p + 20)
-    b = load_vector(H.finest.breaks, p, rng.standard_normal((3, 3)))
-    x0 = rng.standard_normal(H.finest.N) * 1e-3
-    ref = omg.cycle(H, x0, b, smoother=smoother) - x0
-    default = pkg.igamg_get_tail64(ctx)
-    assert default["ctas"] == 16 and default["tail_levels"] == default["most"] >= 1
-
-    def cycle():
-        x = _t(x0)
-        pkg.igamg_vcycle(ctx, x, _t(b), pkg.IGAMG_FP64, ws)
-        return _np(x) - x0
-
-    pkg.igamg_set_tail64(ctx, 16, 0)
-    assert pkg.igamg_get_tail64(ctx)["tail_levels"] == 0
-    per_level = cycle()
-    assert _rel(per_level, ref) < 1e-12 and _relmax(per_level, ref) < 1e-12
-    for ctas in (8, 16):
-        pkg.igamg_set_tail64(ctx, ctas, -1)
-        most = pkg.igamg_get_tail64(ctx)["most"]
-        assert most >= 1
-        for lc in sorted({1, most}):
-            pkg.igamg_set_tail64(ctx, ctas, lc)
-            assert pkg.igamg_get_tail64(ctx)["tail_levels"] == lc
-            out = cycle()
-            assert _rel(out, per_level) < 1e-12 and _relmax(out, per_level) < 1e-12, (ctas, lc)
-            assert _rel(out, ref) < 1e-12 and _relmax(out, ref) < 1e-12, (ctas, lc)
-    with pytest.raises(pkg.IgamgError):
-        pkg.igamg_set_tail64(ctx, 1, 1)
-    pkg.igamg_destroy(ctx)
-
-
-def test_fp64_cluster_tail_depth_at_1024(pkg):
-    """FP64 rows take twice the shared memory: 16 CTAs hold levels up to
-    128^2 elements (129 rows) at 1024^2, p = 3."""
-    ctx = pkg.igamg_setup(2, 3, [1024, 1024], 0)
-    pkg.igamg_assemble(ctx)
-    t = pkg.igamg_get_tail64(ctx)
-    assert t["ctas"] == 16 and t["tail_levels"] == 4 and t["most"] == 4
-    pkg.igamg_destroy(ctx)
