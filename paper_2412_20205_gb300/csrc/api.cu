@@ -352,9 +352,9 @@ int tail_level(const igamg_ctx* c) {
 
 // Highest tail level available with `ctas` CTAs (1: the one-CTA tail).
 int tail_most(const igamg_ctx* c, int ctas) {
-    if (ctas == 1) return (int)c->tails.size() - 1;
+    if (ctas == 1) return std::max(0, (int)c->tails.size() - 1);
     for (int k = 0; k < 2; ++k)
-        if (kTailCtas[k] == ctas) return (int)c->ctails[k].size() - 1;
+        if (kTailCtas[k] == ctas) return std::max(0, (int)c->ctails[k].size() - 1);
     return 0;
 }
 
