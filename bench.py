@@ -132,6 +132,9 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-count", type=int, default=256, help="problems in --workload batch256")
+    ap.add_argument("--tail-ctas", type=int, default=0, choices=[0, 1, 8, 16],
+                    help="with --no-autotune: coarse tail on one CTA or a cluster of 8 or 16 CTAs, deepest level "
+                         "(0: the default schedule)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch schedule (profiling runs: timings under a profiler mislead the autotuner)")
     ap.add_argument("--host-loop", action="store_true",
@@ -375,6 +378,9 @@ def run_ours(a, rank, world, local):
     stream = torch.cuda.current_stream()
     s = pkg.Solver(a.dim, a.p, a.n, k=a.k)
     # launch schedule of the FP32 cycles, picked by timing
+    if a.no_autotune and a.tail_ctas:
+        pkg.igamg_set_tail_ctas(s.ctx, a.tail_ctas)
+        pkg.igamg_set_schedule(s.ctx, 0, 99)
     schedule = pkg.igamg_get_schedule(s.ctx) if a.no_autotune else s.autotune()
     coeffs = workloads.random_sine_coeffs(a.dim, seed=a.seed + rank, modes=16)
     b = s.rhs_sine(coeffs)
