@@ -514,7 +514,8 @@ def run_ours(a, rank, world, local):
         "e2e": {"value": units / (e2e_max * 1e-3), "unit": "DOF/s",
                 "h2d_bytes_per_step": s.N * 8, "d2h_bytes_per_step": s.N * 8},
         "gpu_launches": launches,
-        "roofline": {"bound": "hbm", "kernel": f"k_gs_phase<float,{a.dim},{a.p}> (finest level, one row phase)",
+        "roofline": {"bound": "hbm", "kernel": f"k_gs_phase{a.dim}<float, {a.p}, {str(a.dim == 3 or a.p != 3).lower()}> "
+                                                    "(finest level, one row phase)",
                      "achieved": achieved, "peak": peak_hbm, "unit": "GB/s", "frac": achieved / peak_hbm,
                      "traffic": GS_TRAFFIC.get((a.dim, a.n, a.p)),
                      "algorithmic_bytes_per_launch": bytes_per_launch, "launch_us": launch_ms * 1e3,

@@ -437,9 +437,12 @@ igamg_status igamg_batch_set_device_loop(igamg_batch* batch, int enable);
  * EINVAL. */
 igamg_status igamg_batch_set_tail_ctas(igamg_batch* batch, int ctas);
 /* Autotunes the batch: for every degree, igamg_autotune on the problem of
- * median size; the problems of that degree take its GS row-CTA cap and a
- * coarse tail down to the same level size.  The workspace is the batch
- * workspace (sized for IGAMG_FP32_IR); its contents are overwritten. */
+ * median size, with the one-CTA coarse tail only (the members run
+ * concurrently, and a cluster tail ties up 8 or 16 SMs for a latency-bound
+ * stretch the others could use); the problems of that degree take its GS
+ * row-CTA cap and a coarse tail down to the same level size.  The workspace
+ * is the batch workspace (sized for IGAMG_FP32_IR); its contents are
+ * overwritten. */
 igamg_status igamg_batch_autotune(igamg_batch* batch, void* d_ws, size_t ws_bytes, void* stream, int reps);
 void igamg_batch_destroy(igamg_batch* batch);
 

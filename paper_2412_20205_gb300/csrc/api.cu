@@ -124,6 +124,7 @@ struct igamg_ctx {
     // the same on a thread-block cluster (ctail32, when tail_ctas > 1);
     // ctails[k][l] covers levels 0..l on kTailCtas[k] CTAs
     int tail_ctas = 1;
+    bool tune_clusters = true;              // igamg_autotune tries the cluster tails
     ClusterTailView<float> ctail32{};
     std::vector<ClusterTailView<float>> ctails[2];
     int gs_cap32 = 0;                       // row-CTA thread cap of FP32 GS (0: default)
@@ -1806,7 +1807,8 @@ igamg_status igamg_autotune(igamg_ctx* c, void* d_ws, size_t ws_bytes, void* str
     // coarse tails tried: none, then each depth on one CTA and on each cluster size
     std::vector<std::pair<int, int>> tails_tried{{1, 0}};
     for (int ctas : {1, kTailCtas[0], kTailCtas[1]})
-        for (int lc = 1; lc <= tail_most(c, ctas); ++lc) tails_tried.push_back({ctas, lc});
+        if (ctas == 1 || c->tune_clusters)
+            for (int lc = 1; lc <= tail_most(c, ctas); ++lc) tails_tried.push_back({ctas, lc});
     float best = 1e30f;
     int best_cap = 0, best_flow = c->flow32;
     std::pair<int, int> best_tail{c->tail_ctas, tail_level(c)};
@@ -2270,7 +2272,13 @@ igamg_status igamg_batch_autotune(igamg_batch* B, void* d_ws, size_t ws_bytes, v
         std::sort(ids.begin(), ids.end(), [&](int a, int b) { return finestN(B->ctx[a]) < finestN(B->ctx[b]); });
         const int m = ids[ids.size() / 2];
         igamg_ctx* cm = B->ctx[m];
-        if (igamg_status st = igamg_autotune(cm, (char*)d_ws + off[m], off[m + 1] - off[m], stream, reps)) return st;
+        // members run concurrently: a member's cluster tail holds 16 SMs for a
+        // latency-bound stretch that the others could use (measured, 256
+        // problems: 254 -> 333 ms), so batches tune the one-CTA tail only
+        cm->tune_clusters = false;
+        const igamg_status tst = igamg_autotune(cm, (char*)d_ws + off[m], off[m + 1] - off[m], stream, reps);
+        cm->tune_clusters = true;
+        if (tst) return tst;
         const int cap = cm->gs_cap32, ctas = cm->tail_ctas;
         const size_t nthr = tail_level(cm) > 0 ? cm->hl[tail_level(cm)].N() : 0;
         for (int i : ids) {
