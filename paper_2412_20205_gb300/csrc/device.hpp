@@ -85,8 +85,8 @@ struct TailView {
 // a neighbour's rows through distributed shared memory.  Offsets (elements)
 // are the same in every CTA: off_x, off_b, off_inv, off_tm (T_M then T_K,
 // R x m_x each), off_yb (M_y then K_y of the own rows, band-major, W x R
-// each), off_xb (M_x then K_x at the boundary columns i < tlo or i >= thi,
-// nbc x W each), off_tc (Toeplitz interior of M_x then K_x), off_tx (x-axis
+// each), off_xb (M_x then K_x: the boundary columns i < tlo or i >= thi,
+// then the Toeplitz interior, (nbc + 1) x W each), off_tx (x-axis
 // transfer tables of X[q]: plo, pv, rlo, rv), off_ty (y-axis weights of X[q]:
 // pv of the own fine rows, rv of the own coarse rows of level q - 1), off_rp
 // (generic row pointers, 8-byte aligned: the y-band neighbours' T_M rows of
@@ -99,7 +99,7 @@ struct ClusterTailView {
     int lc, ctas;
     int R[kCTailLevels], nbc[kCTailLevels];
     int off_x[kCTailLevels], off_b[kCTailLevels], off_inv[kCTailLevels], off_tm[kCTailLevels];
-    int off_yb[kCTailLevels], off_xb[kCTailLevels], off_tc[kCTailLevels], off_tx[kCTailLevels];
+    int off_yb[kCTailLevels], off_xb[kCTailLevels], off_tx[kCTailLevels];
     int off_ty[kCTailLevels], off_rp[kCTailLevels];
     int off_cv, off_r, off_t, off_z;
     size_t smem;

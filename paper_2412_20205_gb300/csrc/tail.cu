@@ -448,9 +448,8 @@ struct CLevel {
     T* TK;
     const T* yM;     // M_y(j, j + bb - p) of own row lr at yM[bb R + lr]
     const T* yK;
-    const T* xM;     // M_x(i, i + bb - p) of boundary column slot s at xM[s W + bb]
+    const T* xM;     // M_x(i, i + bb - p) at xM[s W + bb]: slots 0..nbc-1 the boundary columns, slot nbc the interior
     const T* xK;
-    const T* tc;     // Toeplitz interior of M_x then K_x
     const T* const* rp;   // T_M row of grid row j + bb - p for own row lr at rp[lr W + bb]
 };
 
@@ -492,8 +491,7 @@ __device__ __forceinline__ CLevel<T> clevel(const ClusterTailView<T>& V, unsigne
     S.yM = sm + V.off_yb[q];
     S.yK = S.yM + W * S.R;
     S.xM = sm + V.off_xb[q];
-    S.xK = S.xM + S.nbc * W;
-    S.tc = sm + V.off_tc[q];
+    S.xK = S.xM + (S.nbc + 1) * W;
     S.rp = reinterpret_cast<const T* const*>(raw + (size_t)V.off_rp[q] * sizeof(T));
     return S;
 }
@@ -542,28 +540,23 @@ __device__ __forceinline__ void grid_for(int n, int m, F&& f) {
     }
 }
 
-// sum_b M_x(i, b) x(i + b - p) and the K_x sum of an own row (xr: padded column i - p)
+// sum_b M_x(i, b) x(i + b - p) and the K_x sum of an own row (xr: padded
+// column i - p).  The band comes from the slot of column i (the interior
+// slot in the uniform interior), without a branch: lanes of one warp take
+// boundary and interior columns in the same pass.
 template <typename T, int P>
-__device__ __forceinline__ void cwin(const CLevel<T>& S, const T* xr, int i, const T (&mc)[2 * P + 1],
-                                     const T (&kc)[2 * P + 1], T& sM, T& sK) {
+__device__ __forceinline__ void cwin(const CLevel<T>& S, const T* xr, int i, T& sM, T& sK) {
     constexpr int W = 2 * P + 1;
+    const int slot = i < S.tlo ? i : (i < S.thi ? S.nbc : S.tlo + (i - S.thi));
+    const T* cm = S.xM + slot * W;
+    const T* ck = S.xK + slot * W;
     sM = 0;
     sK = 0;
-    if (i >= S.tlo && i < S.thi) {
 #pragma unroll
-        for (int bb = 0; bb < W; ++bb) {
-            const T v = xr[bb];
-            sM += mc[bb] * v;
-            sK += kc[bb] * v;
-        }
-    } else {
-        const int slot = i < S.tlo ? i : S.tlo + (i - S.thi);
-#pragma unroll
-        for (int bb = 0; bb < W; ++bb) {
-            const T v = xr[bb];
-            sM += S.xM[slot * W + bb] * v;
-            sK += S.xK[slot * W + bb] * v;
-        }
+    for (int bb = 0; bb < W; ++bb) {
+        const T v = xr[bb];
+        sM += cm[bb] * v;
+        sK += ck[bb] * v;
     }
 }
 
@@ -585,24 +578,13 @@ __device__ __forceinline__ T ccouple(const CLevel<T>& S, int lr, int i) {
     return acc;
 }
 
-template <typename T, int P>
-__device__ __forceinline__ void load_tc(const CLevel<T>& S, T (&mc)[2 * P + 1], T (&kc)[2 * P + 1]) {
-#pragma unroll
-    for (int bb = 0; bb <= 2 * P; ++bb) {
-        mc[bb] = S.tc[bb];
-        kc[bb] = S.tc[2 * P + 1 + bb];
-    }
-}
-
 // T_M, T_K of the own rows from x (local only).
 template <typename T, int P>
 __device__ void cxpass(const CLevel<T>& S) {
-    T mc[2 * P + 1], kc[2 * P + 1];
-    load_tc<T, P>(S, mc, kc);
     const int PW = S.mx + 2 * P;
     grid_for(S.hi - S.lo, S.mx, [&](int lr, int i) {
         T sM, sK;
-        cwin<T, P>(S, S.x + lr * PW + i, i, mc, kc, sM, sK);
+        cwin<T, P>(S, S.x + lr * PW + i, i, sM, sK);
         S.TM[lr * S.mx + i] = sM;
         S.TK[lr * S.mx + i] = sK;
     });
@@ -623,11 +605,9 @@ __device__ __forceinline__ void group_sync(int g, int G) {
 template <typename T, int P>
 __device__ void cgs(const CLevel<T>& S, T* rhs, bool descending) {
     constexpr int P1 = P + 1;
-    T mc[2 * P + 1], kc[2 * P + 1];
-    load_tc<T, P>(S, mc, kc);
     const int own = S.hi - S.lo, PW = S.mx + 2 * P;
     const int NW = (int)blockDim.x >> 5, warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
-    const int want = (S.mx + 63) >> 6;                          // warps a row keeps busy
+    const int want = (S.mx + 31) >> 5;                          // warps a row keeps busy
     for (int pc = 0; pc < P1; ++pc) {
         const int cy = descending ? P - pc : pc;
         const int lr0 = ((cy - S.lo) % P1 + P1) % P1;          // first own row of the phase
@@ -650,14 +630,14 @@ __device__ void cgs(const CLevel<T>& S, T* rhs, bool descending) {
                         for (int sx = gl; sx < nx; sx += gt) {
                             const int i = cx + P1 * sx;
                             T sM, sK;
-                            cwin<T, P>(S, xrow + i, i, mc, kc, sM, sK);    // padded column i - p
+                            cwin<T, P>(S, xrow + i, i, sM, sK);            // padded column i - p
                             xrow[i + P] += (rr[i] - (ky * sM + my * sK)) * inv[i];
                         }
                         group_sync(g, G);
                     }
                     for (int i = gl; i < S.mx; i += gt) {
                         T sM, sK;
-                        cwin<T, P>(S, xrow + i, i, mc, kc, sM, sK);
+                        cwin<T, P>(S, xrow + i, i, sM, sK);
                         S.TM[lr * S.mx + i] = sM;
                         S.TK[lr * S.mx + i] = sK;
                     }
@@ -777,10 +757,9 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_cluster_tail(ClusterTailVie
             cp_async4(const_cast<T*>(S.xM) + e, L.Mb[0] + bb * S.mx + i);
             cp_async4(const_cast<T*>(S.xK) + e, L.Kb[0] + bb * S.mx + i);
         }
-        T* tc = sm + V.off_tc[q];
-        for (int bb = threadIdx.x; bb < W; bb += blockDim.x) {
-            tc[bb] = L.Mc[0][bb];
-            tc[W + bb] = L.Kc[0][bb];
+        for (int bb = threadIdx.x; bb < W; bb += blockDim.x) {      // the interior slot
+            const_cast<T*>(S.xM)[S.nbc * W + bb] = L.Mc[0][bb];
+            const_cast<T*>(S.xK)[S.nbc * W + bb] = L.Kc[0][bb];
         }
         const TransferView<T>& X = V.X[q];
         const CTransfer<T> Y = ctransfer(V, smem_raw, q);
