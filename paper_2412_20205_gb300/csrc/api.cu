@@ -1125,7 +1125,7 @@ igamg_status igamg_assemble(igamg_ctx* c) {
                     v.off_yb[q] = off; off += 2 * W * R;
                     v.off_xb[q] = off; off += 2 * W * (v.nbc[q] + 1);      // boundary columns and the interior
                     v.off_tx[q] = off; off += X.mf[0] * (1 + X.pw[0]) + X.mc[0] * (1 + X.rw[0]);
-                    v.off_ty[q] = off; off += R * X.pw[1] + v.R[q - 1] * X.rw[1];
+                    v.off_ty[q] = off; off += R * X.pw[1] + v.R[q - 1] * X.rw[1] + R + v.R[q - 1];
                     rmax = std::max(rmax, R * mx);
                     tmax = std::max({tmax, R * X.mc[0], v.R[q - 1] * X.mf[0]});
                 }

@@ -87,8 +87,9 @@ struct TailView {
 // R x m_x each), off_yb (M_y then K_y of the own rows, band-major, W x R
 // each), off_xb (M_x then K_x: the boundary columns i < tlo or i >= thi,
 // then the Toeplitz interior, (nbc + 1) x W each), off_tx (x-axis
-// transfer tables of X[q]: plo, pv, rlo, rv), off_ty (y-axis weights of X[q]:
-// pv of the own fine rows, rv of the own coarse rows of level q - 1), off_rp
+// transfer tables of X[q]: plo, pv, rlo, rv), off_ty (y-axis tables of X[q]:
+// pv of the own fine rows, rv of the own coarse rows of level q - 1, then plo
+// of the own fine rows and rlo of the own coarse rows), off_rp
 // (generic row pointers, 8-byte aligned: the y-band neighbours' T_M rows of
 // the own rows, the t rows the own coarse rows' restriction and the own fine
 // rows' prolongation combine), off_cv (coarsest V_x, V_y, laminv), off_r and

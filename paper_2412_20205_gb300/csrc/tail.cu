@@ -466,6 +466,8 @@ struct CTransfer {
     const T* rvx;
     const T* pvy;            // own fine rows x pw_y
     const T* rvy;            // own coarse rows x rw_y
+    const int* ploy;         // own fine rows: first coarse row of the prolongation
+    const int* rloy;         // own coarse rows: first fine row of the restriction
     const T* const* rr;      // own coarse rows x rw_y
     const T* const* pr;      // own fine rows x pw_y
 };
@@ -517,6 +519,8 @@ __device__ __forceinline__ CTransfer<T> ctransfer(const ClusterTailView<T>& V, u
     T* g = sm + V.off_ty[q];
     Y.pvy = g;
     Y.rvy = g + Rf * X.pw[1];
+    Y.ploy = reinterpret_cast<const int*>(Y.rvy + Rc * X.rw[1]);
+    Y.rloy = Y.ploy + Rf;
     const T* const* rpq = reinterpret_cast<const T* const*>(raw + (size_t)V.off_rp[q] * sizeof(T));
     Y.rr = rpq + Rf * (2 * V.L[q].p + 1);
     Y.pr = Y.rr + Rc * X.rw[1];
@@ -727,8 +731,10 @@ __device__ __forceinline__ const T* cptr(T* local, int o, int rank) {
     return o == rank ? local : cg::this_cluster().map_shared_rank(local, o);
 }
 
+constexpr int kCTailThreads = 512;
+
 template <typename T, int P>
-__global__ void __launch_bounds__(kTailThreads, 1) k_cluster_tail(ClusterTailView<T> V, const T* __restrict__ b_in,
+__global__ void __launch_bounds__(kCTailThreads, 1) k_cluster_tail(ClusterTailView<T> V, const T* __restrict__ b_in,
                                                                   T* __restrict__ x_out, int jacobi, T omega) {
     static_assert(sizeof(T) == 4, "4-byte elements (staging, integer tables)");
     constexpr int W = 2 * P + 1;
@@ -771,6 +777,8 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_cluster_tail(ClusterTailVie
         const int loc = min(rank * Rc, myc), ownc = min(loc + Rc, myc) - loc;
         stage(const_cast<T*>(Y.pvy), X.pv[1] + (size_t)S.lo * X.pw[1], own * X.pw[1]);
         stage(const_cast<T*>(Y.rvy), X.rv[1] + (size_t)loc * X.rw[1], ownc * X.rw[1]);
+        stage(const_cast<int*>(Y.ploy), X.plo[1] + S.lo, own);
+        stage(const_cast<int*>(Y.rloy), X.rlo[1] + loc, ownc);
         // row pointers: y-band neighbours, restriction and prolongation rows
         const T** rp = const_cast<const T**>(S.rp);
         for (int e = threadIdx.x; e < own * W; e += blockDim.x) {
@@ -780,26 +788,6 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_cluster_tail(ClusterTailVie
             } else {
                 const int o = jj / S.R;
                 rp[e] = cptr(S.TM + (jj - o * S.R) * S.mx, o, rank);
-            }
-        }
-        const T** rr = const_cast<const T**>(Y.rr);
-        for (int e = threadIdx.x; e < ownc * X.rw[1]; e += blockDim.x) {
-            const int Jl = e / X.rw[1], s2 = e - Jl * X.rw[1], f = X.rlo[1][loc + Jl] + s2;
-            if (f < 0 || f >= S.my) {
-                rr[e] = zrow;
-            } else {
-                const int o = f / S.R;
-                rr[e] = cptr(t + (f - o * S.R) * X.mc[0], o, rank);
-            }
-        }
-        const T** pr = const_cast<const T**>(Y.pr);
-        for (int e = threadIdx.x; e < own * X.pw[1]; e += blockDim.x) {
-            const int jl = e / X.pw[1], s2 = e - jl * X.pw[1], F = X.plo[1][S.lo + jl] + s2;
-            if (F < 0 || F >= myc) {
-                pr[e] = zrow;
-            } else {
-                const int o = F / Rc;
-                pr[e] = cptr(t + (F - o * Rc) * X.mf[0], o, rank);
             }
         }
     }
@@ -829,6 +817,34 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_cluster_tail(ClusterTailVie
         stage(S.b, b_in + (size_t)S.lo * S.mx, (S.hi - S.lo) * S.mx);
     }
     cp_async_wait_all();
+    __syncthreads();
+    for (int q = 1; q <= lc; ++q) {                     // the t rows the y-axis transfer passes combine
+        const CLevel<T> S = clevel<T, P>(V, smem_raw, q, rank);
+        const TransferView<T>& X = V.X[q];
+        const CTransfer<T> Y = ctransfer(V, smem_raw, q);
+        const int Rc = V.R[q - 1], myc = V.L[q - 1].m[1];
+        const int loc = min(rank * Rc, myc), ownc = min(loc + Rc, myc) - loc, own = S.hi - S.lo;
+        const T** rr = const_cast<const T**>(Y.rr);
+        for (int e = threadIdx.x; e < ownc * X.rw[1]; e += blockDim.x) {
+            const int Jl = e / X.rw[1], s2 = e - Jl * X.rw[1], f = Y.rloy[Jl] + s2;
+            if (f < 0 || f >= S.my) {
+                rr[e] = zrow;
+            } else {
+                const int o = f / S.R;
+                rr[e] = cptr(t + (f - o * S.R) * X.mc[0], o, rank);
+            }
+        }
+        const T** pr = const_cast<const T**>(Y.pr);
+        for (int e = threadIdx.x; e < own * X.pw[1]; e += blockDim.x) {
+            const int jl = e / X.pw[1], s2 = e - jl * X.pw[1], F = Y.ploy[jl] + s2;
+            if (F < 0 || F >= myc) {
+                pr[e] = zrow;
+            } else {
+                const int o = F / Rc;
+                pr[e] = cptr(t + (F - o * Rc) * X.mf[0], o, rank);
+            }
+        }
+    }
     __syncthreads();
     cg::this_cluster().sync();                          // every CTA's zero T rows in place
     for (int l = lc; l >= 1; --l) {
@@ -925,7 +941,7 @@ static cudaLaunchConfig_t cluster_config(const ClusterTailView<T>& V, cudaStream
                                          bool overlap) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(V.ctas);
-    cfg.blockDim = dim3(kTailThreads);
+    cfg.blockDim = dim3(kCTailThreads);
     cfg.dynamicSmemBytes = V.smem;
     cfg.stream = s;
     at[0].id = cudaLaunchAttributeClusterDimension;
