@@ -127,6 +127,9 @@ struct igamg_ctx {
     bool tune_clusters = true;              // igamg_autotune tries the cluster tails
     ClusterTailView<float> ctail32{};
     std::vector<ClusterTailView<float>> ctails[2];
+    // 3D: the cluster tail of FP32 cycles (ClusterTail3View)
+    ClusterTail3View<float> ctail3{};
+    std::vector<ClusterTail3View<float>> ctails3[2];
     int gs_cap32 = 0;                       // row-CTA thread cap of FP32 GS (0: default)
     // GS sweep form per precision: levels with at least this many rows run a
     // sweep in one launch (rows wait on their earlier-phase neighbours), the
@@ -348,14 +351,16 @@ constexpr int kTailCtas[2] = {8, 16};
 // Highest level of the active coarse tail of FP32 2D cycles (0: none).
 int tail_level(const igamg_ctx* c) {
     if (!c->tail_on) return 0;
+    if (c->dim == 3) return c->tail_ctas > 1 ? c->ctail3.lc : 0;
     return c->tail_ctas > 1 ? c->ctail32.lc : c->tail32.lc;
 }
 
 // Highest tail level available with `ctas` CTAs (1: the one-CTA tail).
 int tail_most(const igamg_ctx* c, int ctas) {
-    if (ctas == 1) return std::max(0, (int)c->tails.size() - 1);
+    if (ctas == 1) return c->dim == 3 ? 0 : std::max(0, (int)c->tails.size() - 1);
     for (int k = 0; k < 2; ++k)
-        if (kTailCtas[k] == ctas) return std::max(0, (int)c->ctails[k].size() - 1);
+        if (kTailCtas[k] == ctas)
+            return std::max(0, (int)(c->dim == 3 ? c->ctails3[k].size() : c->ctails[k].size()) - 1);
     return 0;
 }
 
@@ -368,13 +373,77 @@ void select_tail(igamg_ctx* c, int ctas, int lc) {
     if (ctas == 1) c->tail32 = c->tails[lc];
     else
         for (int k = 0; k < 2; ++k)
-            if (kTailCtas[k] == ctas) c->ctail32 = c->ctails[k][lc];
+            if (kTailCtas[k] == ctas) {
+                if (c->dim == 3) c->ctail3 = c->ctails3[k][lc];
+                else c->ctail32 = c->ctails[k][lc];
+            }
 }
 
 // Levels tail_level(c)..0 of an FP32 2D V-cycle from x = 0 in the active tail.
 void run_tail(const igamg_ctx* c, cudaStream_t s, const float* b, float* x, int jacobi = 0, float omega = 0.f) {
-    if (c->tail_ctas > 1) dev::cluster_tail<float>(s, c->ctail32, b, x, jacobi, omega);
+    if (c->dim == 3) dev::cluster_tail3<float>(s, c->ctail3, b, x, jacobi, omega);
+    else if (c->tail_ctas > 1) dev::cluster_tail<float>(s, c->ctail32, b, x, jacobi, omega);
     else dev::coarse_tail<float>(s, c->tail32, b, x, jacobi, omega);
+}
+
+// Cluster-tail views of a 3D hierarchy (ClusterTail3View): out[k][l] covers
+// levels 0..l on kTailCtas[k] CTAs (out[k][0] unused).  Offsets in floats;
+// integer tables take one element each, pointers two (the pointer tables come
+// first, 8-byte aligned).
+void build_cluster_tails3(const igamg_ctx* c, std::vector<ClusterTail3View<float>>* out) {
+    const int p = c->p, W = 2 * p + 1, W2 = W * W, L = c->L;
+    const int N0 = (int)c->hl[0].N();
+    for (int k = 0; k < 2; ++k) {
+        out[k].assign(1, ClusterTail3View<float>{});
+        const int C = kTailCtas[k];
+        for (int l = 1; l <= std::min(L - 2, kCTailLevels - 1); ++l) {
+            ClusterTail3View<float> v{};
+            v.ctas = C;
+            v.lc = l;
+            for (int q = 0; q <= l; ++q) {
+                const int rows = c->hl[q].m[1] * c->hl[q].m[2];
+                v.R[q] = q == 0 ? rows : (rows + C - 1) / C;
+            }
+            int off = 0, rmax = N0, tmax = N0;
+            for (int q = 1; q <= l; ++q) {
+                const TransferView<float>& X = c->tv32[q];
+                v.off_rp[q] = off;
+                off += 2 * (v.R[q] * W2 + v.R[q - 1] * X.rw[1] * X.rw[2] + v.R[q] * X.pw[1] * X.pw[2]);
+            }
+            for (int q = 0; q <= l; ++q) {
+                const int mx = c->hl[q].m[0], my = c->hl[q].m[1], mz = c->hl[q].m[2], R = v.R[q];
+                v.off_x[q] = off; off += R * (mx + 2 * p);
+                v.off_b[q] = off; off += R * mx;
+                if (q == 0) continue;
+                const LevelView<float>& Lq = c->lv32[q];
+                const TransferView<float>& X = c->tv32[q];
+                v.nbc[q] = Lq.tlo[0] + (mx - Lq.thi[0]);
+                v.off_inv[q] = off; off += R * mx;
+                v.off_tm[q] = off; off += 2 * R * mx;
+                v.off_cc[q] = off; off += 2 * W2 * R;
+                v.off_yb[q] = off; off += 2 * W * my;
+                v.off_zb[q] = off; off += 2 * W * mz;
+                v.off_xb[q] = off; off += 2 * W * (v.nbc[q] + 1);
+                v.off_tx[q] = off;
+                for (int d = 0; d < 3; ++d) off += X.mf[d] * (1 + X.pw[d]) + X.mc[d] * (1 + X.rw[d]);
+                rmax = std::max(rmax, R * mx);
+                tmax = std::max({tmax, R * X.mc[0], v.R[q - 1] * X.mf[0]});
+            }
+            const int m0 = c->hl[0].m[0], m1 = c->hl[0].m[1], m2 = c->hl[0].m[2];
+            v.off_cv = off; off += m0 * m0 + m1 * m1 + m2 * m2 + N0;
+            v.off_r = off; off += rmax;
+            v.off_t = off; off += tmax;
+            v.off_z = off; off += c->hl[l].m[0];
+            v.smem = (size_t)off * sizeof(float);
+            for (int q = 0; q <= l; ++q) {
+                v.L[q] = c->lv32[q];
+                v.X[q] = c->tv32[q];
+            }
+            v.C = c->cv32;
+            if (!dev::cluster_tail3_fits(v)) break;
+            out[k].push_back(v);
+        }
+    }
 }
 
 // Row-CTA thread cap of the GS sweeps in cycles of type T (autotuned for FP32).
@@ -1095,7 +1164,14 @@ igamg_status igamg_assemble(igamg_ctx* c) {
     // Cluster tails of the FP32 2D cycle: on kTailCtas[k] CTAs, every lc
     // whose levels fit a CTA's shared memory (ClusterTailView) and whose
     // cluster the device can hold.
-    for (int k = 0; k < 2; ++k) c->ctails[k].assign(1, ClusterTailView<float>{});
+    for (int k = 0; k < 2; ++k) {
+        c->ctails[k].assign(1, ClusterTailView<float>{});
+        c->ctails3[k].assign(1, ClusterTail3View<float>{});
+    }
+    if (dim == 3 && L >= 3) {
+        build_cluster_tails3(c, c->ctails3);
+        select_tail(c, kTailCtas[1], tail_most(c, kTailCtas[1]));    // 3D: the deepest 16-CTA tail
+    }
     if (dim == 2 && L >= 3) {
         const int W = 2 * p + 1;
         const int N0 = (int)c->hl[0].N(), m00 = c->hl[0].m[0], m01 = c->hl[0].m[1];

@@ -109,6 +109,36 @@ struct ClusterTailView {
     CoarseView<T> C;
 };
 
+// Coarse part of a 3D V-cycle on one thread-block cluster (levels 0..lc).
+// Grid rows (j, k) are numbered r = k m_y + j; on level q >= 1, CTA c owns
+// the rows [c R[q], min((c + 1) R[q], m_y m_z)), and CTA 0 all rows of the
+// coarsest level (R[0] = m_y m_z).  Every CTA keeps its rows' x (zero-padded
+// by p columns on each side), b, 1 / A_ii, T_M, T_K and the (2p+1)^2 row
+// couplings (weights on T_M and T_K) of each own row in shared memory, with
+// the level's whole y- and z-bands and the three axes' transfer tables.
+// Offsets (elements): off_rp (8-byte aligned generic pointers: the T_M rows of
+// the (2p+1)^2 neighbours of each own row, the t rows each own coarse row's
+// y-z restriction combines (rw_y rw_z) and each own fine row's y-z
+// prolongation combines (pw_y pw_z)), off_x, off_b, off_inv, off_tm (T_M then
+// T_K, R x m_x each), off_cc (own rows x (2p+1)^2 weight pairs), off_yb (M_y
+// then K_y, W x m_y), off_zb (M_z then K_z, W x m_z), off_xb (M_x then K_x:
+// the boundary columns, then the Toeplitz interior, (nbc + 1) x W each),
+// off_tx (for axes x, y, z: plo, pv, rlo, rv), off_cv (V_x, V_y, V_z,
+// laminv), off_r, off_t (scratch), off_z (a zero row).  lc = 0: none.
+template <typename T>
+struct ClusterTail3View {
+    int lc, ctas;
+    int R[kCTailLevels], nbc[kCTailLevels];
+    int off_rp[kCTailLevels], off_x[kCTailLevels], off_b[kCTailLevels], off_inv[kCTailLevels];
+    int off_tm[kCTailLevels], off_cc[kCTailLevels], off_yb[kCTailLevels], off_zb[kCTailLevels];
+    int off_xb[kCTailLevels], off_tx[kCTailLevels];
+    int off_cv, off_r, off_t, off_z;
+    size_t smem;
+    LevelView<T> L[kCTailLevels];
+    TransferView<T> X[kCTailLevels];
+    CoarseView<T> C;
+};
+
 // Shared-memory elements (4-byte) of the staged tables of one 2D transfer:
 // plo/pv and rlo/rv of both directions.
 template <typename T>
@@ -284,6 +314,12 @@ template <typename T>
 void cluster_tail(cudaStream_t s, const ClusterTailView<T>& V, const T* b, T* x, int jacobi = 0, T omega = 0);
 template <typename T>
 bool cluster_tail_fits(const ClusterTailView<T>& V);
+
+// The 3D form (ClusterTail3View): levels lc..0 of an FP32 3D V-cycle.
+template <typename T>
+void cluster_tail3(cudaStream_t s, const ClusterTail3View<T>& V, const T* b, T* x, int jacobi = 0, T omega = 0);
+template <typename T>
+bool cluster_tail3_fits(const ClusterTail3View<T>& V);
 
 // T_M = (I (x) M_x) x, T_K = (I (x) K_x) x row by row.  With add != nullptr the
 // row is first replaced by x + add (written to x_out), with nS > 0 by

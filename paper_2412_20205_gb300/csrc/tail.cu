@@ -548,8 +548,8 @@ __device__ __forceinline__ void grid_for(int n, int m, F&& f) {
 // column i - p).  The band comes from the slot of column i (the interior
 // slot in the uniform interior), without a branch: lanes of one warp take
 // boundary and interior columns in the same pass.
-template <typename T, int P>
-__device__ __forceinline__ void cwin(const CLevel<T>& S, const T* xr, int i, T& sM, T& sK) {
+template <typename T, int P, typename LV>
+__device__ __forceinline__ void cwin(const LV& S, const T* xr, int i, T& sM, T& sK) {
     constexpr int W = 2 * P + 1;
     const int slot = i < S.tlo ? i : (i < S.thi ? S.nbc : S.tlo + (i - S.thi));
     const T* cm = S.xM + slot * W;
@@ -888,6 +888,453 @@ __global__ void __launch_bounds__(kCTailThreads, 1) k_cluster_tail(ClusterTailVi
     grid_for(S.hi - S.lo, S.mx, [&](int lr, int i) { x_out[(size_t)(S.lo + lr) * S.mx + i] = S.x[lr * PW + i + P]; });
 }
 
+// ---------------------------------------------------------------- 3D cluster tail
+// The coarse part of the 3D V-cycle on one thread-block cluster, in the form
+// of the 2D cluster tail above: every CTA owns a range of grid rows (j, k)
+// (numbered r = k m_y + j) of each level in its shared memory, the rows a
+// step needs from other CTAs are read through distributed shared memory
+// (pointers resolved once per launch), and cluster barriers order the steps.
+// A row couples to the (2p+1)^2 rows (j + dj, k + dk) with the weights
+// K_z M_y + M_z K_y on T_M and M_z M_y on T_K (A = K_z (x) M_y (x) M_x +
+// M_z (x) K_y (x) M_x + M_z (x) M_y (x) K_x); they are formed once per launch
+// from the staged y- and z-bands.  GS runs the (p+1)^2 row phases of the
+// per-level kernels, the row's x-colours inside a phase, and the restriction
+// and prolongation apply the x axis to a CTA's own rows and the y and z axes
+// together across the cluster.
+
+template <typename T>
+struct CLevel3 {
+    int mx, my, mz, R, lo, hi, tlo, thi, nbc;
+    T* x;            // own rows, zero-padded: row lr at lr (mx + 2p), column i at + i + p
+    T* b;
+    const T* inv;
+    T* TM;           // own rows, then T_K at + R mx
+    T* TK;
+    const T* xM;     // boundary slots 0..nbc-1, interior slot nbc
+    const T* xK;
+    const T* cc;     // own row lr, neighbour q = (dk + p) W + dj + p: weights at cc[2 (lr W^2 + q)], + 1
+    const T* const* rp;   // T_M row of neighbour q of own row lr at rp[lr W^2 + q]
+};
+
+template <typename T, int P>
+__device__ __forceinline__ CLevel3<T> clevel3(const ClusterTail3View<T>& V, unsigned char* raw, int q, int rank) {
+    constexpr int W = 2 * P + 1;
+    T* sm = reinterpret_cast<T*>(raw);
+    CLevel3<T> S;
+    S.mx = V.L[q].m[0];
+    S.my = V.L[q].m[1];
+    S.mz = V.L[q].m[2];
+    S.R = V.R[q];
+    const int rows = S.my * S.mz;
+    S.lo = min(rank * S.R, rows);
+    S.hi = min(S.lo + S.R, rows);
+    S.tlo = V.L[q].tlo[0];
+    S.thi = V.L[q].thi[0];
+    S.nbc = V.nbc[q];
+    S.x = sm + V.off_x[q];
+    S.b = sm + V.off_b[q];
+    S.inv = sm + V.off_inv[q];
+    S.TM = sm + V.off_tm[q];
+    S.TK = S.TM + S.R * S.mx;
+    S.xM = sm + V.off_xb[q];
+    S.xK = S.xM + (S.nbc + 1) * W;
+    S.cc = sm + V.off_cc[q];
+    S.rp = reinterpret_cast<const T* const*>(raw + (size_t)V.off_rp[q] * sizeof(T));
+    return S;
+}
+
+// Transfer X[q] in 3D: staged tables of the three axes (plo, pv, rlo, rv),
+// and the pointer tables of the y-z passes (after the neighbour pointers of
+// level q in the off_rp region).
+template <typename T>
+struct CTransfer3 {
+    int pw[3], rw[3];
+    const int* plo[3];
+    const T* pv[3];
+    const int* rlo[3];
+    const T* rv[3];
+    const T* const* rr;      // own coarse rows x (rw_y rw_z): fine t rows, (s_z, s_y) with s_y fastest
+    const T* const* pr;      // own fine rows x (pw_y pw_z): coarse t rows
+};
+
+template <typename T>
+__device__ __forceinline__ CTransfer3<T> ctransfer3(const ClusterTail3View<T>& V, unsigned char* raw, int q) {
+    const TransferView<T>& X = V.X[q];
+    T* f = reinterpret_cast<T*>(raw) + V.off_tx[q];
+    CTransfer3<T> Y;
+    for (int d = 0; d < 3; ++d) {
+        Y.pw[d] = X.pw[d];
+        Y.rw[d] = X.rw[d];
+        Y.plo[d] = reinterpret_cast<const int*>(f);
+        f += X.mf[d];
+        Y.pv[d] = f;
+        f += X.mf[d] * X.pw[d];
+        Y.rlo[d] = reinterpret_cast<const int*>(f);
+        f += X.mc[d];
+        Y.rv[d] = f;
+        f += X.mc[d] * X.rw[d];
+    }
+    const int W = 2 * V.L[q].p + 1;
+    const T* const* rpq = reinterpret_cast<const T* const*>(raw + (size_t)V.off_rp[q] * sizeof(T));
+    Y.rr = rpq + V.R[q] * W * W;
+    Y.pr = Y.rr + V.R[q - 1] * X.rw[1] * X.rw[2];
+    return Y;
+}
+
+// Own rows [lo, hi) with j = cy and k = cz (mod p+1): with idx < 0 their
+// number, else the local index of the idx-th of them (in row order).
+template <int P>
+__device__ __forceinline__ int phase_rows3(int lo, int hi, int my, int cy, int cz, int idx) {
+    constexpr int P1 = P + 1;
+    int cnt = 0;
+    if (lo >= hi) return idx < 0 ? 0 : -1;
+    const int k0 = lo / my, k1 = (hi - 1) / my;
+    for (int k = k0; k <= k1; ++k) {
+        if (k % P1 != cz) continue;
+        const int jlo = k == k0 ? lo - k * my : 0, jhi = k == k1 ? hi - k * my : my;
+        const int j0 = jlo + ((cy - jlo) % P1 + P1) % P1;
+        const int n = j0 < jhi ? (jhi - 1 - j0) / P1 + 1 : 0;
+        if (idx >= 0 && idx < cnt + n) return k * my + j0 + (idx - cnt) * P1 - lo;
+        cnt += n;
+    }
+    return idx < 0 ? cnt : -1;
+}
+
+// sum over the (2p+1)^2 neighbour rows (all, or all but the own row) of
+// cM T_M + cK T_K at column i of own row lr (zero weights outside the grid).
+template <typename T, int P, bool SKIP_OWN>
+__device__ __forceinline__ T ccouple3(const CLevel3<T>& S, int lr, int i) {
+    constexpr int W2 = (2 * P + 1) * (2 * P + 1), OWN = P * (2 * P + 1) + P;
+    const T* const* rp = S.rp + lr * W2;
+    const T* cc = S.cc + 2 * lr * W2;
+    const int tko = S.R * S.mx;
+    T acc = 0;
+    constexpr int U = W2 > 49 ? 9 : W2;
+#pragma unroll U
+    for (int q = 0; q < W2; ++q) {
+        if (SKIP_OWN && q == OWN) continue;
+        const T* row = rp[q];
+        acc += cc[2 * q] * row[i] + cc[2 * q + 1] * row[tko + i];
+    }
+    return acc;
+}
+
+template <typename T, int P>
+__device__ void cxpass3(const CLevel3<T>& S) {
+    const int PW = S.mx + 2 * P;
+    grid_for(S.hi - S.lo, S.mx, [&](int lr, int i) {
+        T sM, sK;
+        cwin<T, P>(S, S.x + lr * PW + i, i, sM, sK);
+        S.TM[lr * S.mx + i] = sM;
+        S.TK[lr * S.mx + i] = sK;
+    });
+}
+
+// One multicolour GS sweep: (p+1)^2 row phases (cz slowest), each over the
+// own rows of the phase shared out to groups of warps, then a cluster barrier.
+template <typename T, int P>
+__device__ void cgs3(const CLevel3<T>& S, T* rhs, bool descending) {
+    constexpr int P1 = P + 1, NPH = P1 * P1, W2 = (2 * P + 1) * (2 * P + 1), OWN = P * (2 * P + 1) + P;
+    const int PW = S.mx + 2 * P;
+    const int NW = (int)blockDim.x >> 5, warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
+    const int want = (S.mx + 31) >> 5;
+    for (int ph = 0; ph < NPH; ++ph) {
+        const int c = descending ? NPH - 1 - ph : ph;
+        const int cy = c % P1, cz = c / P1;
+        const int nr = phase_rows3<P>(S.lo, S.hi, S.my, cy, cz, -1);
+        if (nr > 0) {
+            const int G = max(1, min(NW / nr, want)), ng = min(NW / G, 15);
+            const int g = warp / G, gl = (warp - g * G) * 32 + lane, gt = 32 * G;
+            if (g < ng)
+                for (int k = g; k < nr; k += ng) {
+                    const int lr = phase_rows3<P>(S.lo, S.hi, S.my, cy, cz, k);
+                    T* rr = rhs + k * S.mx;
+                    for (int i = gl; i < S.mx; i += gt) rr[i] = S.b[lr * S.mx + i] - ccouple3<T, P, true>(S, lr, i);
+                    group_sync(g, G);
+                    const T cm = S.cc[2 * (lr * W2 + OWN)], ck = S.cc[2 * (lr * W2 + OWN) + 1];
+                    T* xrow = S.x + lr * PW;
+                    const T* inv = S.inv + lr * S.mx;
+                    for (int cx_ = 0; cx_ < P1; ++cx_) {
+                        const int cx = descending ? P - cx_ : cx_;
+                        const int nx = (S.mx - cx + P) / P1;
+                        for (int sx = gl; sx < nx; sx += gt) {
+                            const int i = cx + P1 * sx;
+                            T sM, sK;
+                            cwin<T, P>(S, xrow + i, i, sM, sK);
+                            xrow[i + P] += (rr[i] - (cm * sM + ck * sK)) * inv[i];
+                        }
+                        group_sync(g, G);
+                    }
+                    for (int i = gl; i < S.mx; i += gt) {
+                        T sM, sK;
+                        cwin<T, P>(S, xrow + i, i, sM, sK);
+                        S.TM[lr * S.mx + i] = sM;
+                        S.TK[lr * S.mx + i] = sK;
+                    }
+                }
+        }
+        cg::this_cluster().sync();
+    }
+}
+
+template <typename T, int P>
+__device__ void cjacobi3(const CLevel3<T>& S, T* d, T omega) {
+    const int own = S.hi - S.lo, PW = S.mx + 2 * P;
+    grid_for(own, S.mx, [&](int lr, int i) {
+        const int q = lr * S.mx + i;
+        d[q] = omega * (S.b[q] - ccouple3<T, P, false>(S, lr, i)) * S.inv[q];
+    });
+    cg::this_cluster().sync();
+    grid_for(own, S.mx, [&](int lr, int i) { S.x[lr * PW + i + P] += d[lr * S.mx + i]; });
+    __syncthreads();
+    cxpass3<T, P>(S);
+    cg::this_cluster().sync();
+}
+
+// b_c = P^T (b - A x): residual and x-axis restriction of the own rows (t),
+// then the own coarse rows from the fine rows' t (y and z axes together).
+template <typename T, int P>
+__device__ void crestrict3(const CLevel3<T>& S, const CLevel3<T>& Sc, const CTransfer3<T>& X, T* r, T* t) {
+    const int own = S.hi - S.lo, mcx = Sc.mx;
+    grid_for(own, S.mx, [&](int lr, int i) {
+        const int q = lr * S.mx + i;
+        r[q] = S.b[q] - ccouple3<T, P, false>(S, lr, i);
+    });
+    __syncthreads();
+    grid_for(own, mcx, [&](int lr, int I) {
+        const int lo = X.rlo[0][I];
+        T acc = 0;
+        for (int s = 0; s < X.rw[0]; ++s) {
+            const int f = lo + s;
+            if (f < 0 || f >= S.mx) continue;
+            acc += X.rv[0][I * X.rw[0] + s] * r[lr * S.mx + f];
+        }
+        t[lr * mcx + I] = acc;
+    });
+    cg::this_cluster().sync();
+    const int ryz = X.rw[1] * X.rw[2];
+    grid_for(Sc.hi - Sc.lo, mcx, [&](int Jl, int I) {
+        const int rc = Sc.lo + Jl, J = rc % Sc.my, K = rc / Sc.my;
+        const T* const* rows = X.rr + Jl * ryz;
+        T acc = 0;
+        for (int sz = 0; sz < X.rw[2]; ++sz) {
+            const T wz = X.rv[2][K * X.rw[2] + sz];
+            T a2 = 0;
+            for (int sy = 0; sy < X.rw[1]; ++sy) a2 += X.rv[1][J * X.rw[1] + sy] * rows[sz * X.rw[1] + sy][I];
+            acc += wz * a2;
+        }
+        Sc.b[Jl * mcx + I] = acc;
+    });
+    __syncthreads();
+}
+
+// x += P e: x-axis prolongation of the own coarse rows (t), then the own fine
+// rows from the coarse rows' t (y and z axes together), and the new T_M, T_K.
+template <typename T, int P>
+__device__ void cprolong3(const CLevel3<T>& S, const CLevel3<T>& Sc, const CTransfer3<T>& X, T* t) {
+    const int mfx = S.mx, PWc = Sc.mx + 2 * P;
+    grid_for(Sc.hi - Sc.lo, mfx, [&](int Jl, int i) {
+        const int lo = X.plo[0][i];
+        T acc = 0;
+        for (int s = 0; s < X.pw[0]; ++s) {
+            const int f = lo + s;
+            if (f < 0 || f >= Sc.mx) continue;
+            acc += X.pv[0][i * X.pw[0] + s] * Sc.x[Jl * PWc + f + P];
+        }
+        t[Jl * mfx + i] = acc;
+    });
+    cg::this_cluster().sync();
+    const int PW = S.mx + 2 * P, pyz = X.pw[1] * X.pw[2];
+    grid_for(S.hi - S.lo, mfx, [&](int jl, int i) {
+        const int r = S.lo + jl, j = r % S.my, k = r / S.my;
+        const T* const* rows = X.pr + jl * pyz;
+        T acc = 0;
+        for (int sz = 0; sz < X.pw[2]; ++sz) {
+            const T wz = X.pv[2][k * X.pw[2] + sz];
+            T a2 = 0;
+            for (int sy = 0; sy < X.pw[1]; ++sy) a2 += X.pv[1][j * X.pw[1] + sy] * rows[sz * X.pw[1] + sy][i];
+            acc += wz * a2;
+        }
+        S.x[jl * PW + i + P] += acc;
+    });
+    __syncthreads();
+    cxpass3<T, P>(S);
+    cg::this_cluster().sync();
+}
+
+template <typename T, int P>
+__global__ void __launch_bounds__(kCTailThreads, 1) k_cluster_tail3(ClusterTail3View<T> V, const T* __restrict__ b_in,
+                                                                   T* __restrict__ x_out, int jacobi, T omega) {
+    static_assert(sizeof(T) == 4, "4-byte elements (staging, integer tables)");
+    constexpr int W = 2 * P + 1, W2 = W * W;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sm = reinterpret_cast<T*>(smem_raw);
+    const int rank = (int)cg::this_cluster().block_rank();
+    const int lc = V.lc;
+    T* r = sm + V.off_r;
+    T* t = sm + V.off_t;
+    T* zrow = sm + V.off_z;
+    // operator data and the neighbour pointers, before the wait
+    for (int q = 1; q <= lc; ++q) {
+        const LevelView<T>& L = V.L[q];
+        const CLevel3<T> S = clevel3<T, P>(V, smem_raw, q, rank);
+        const int own = S.hi - S.lo;
+        stage(const_cast<T*>(S.inv), L.invdiag + (size_t)S.lo * S.mx, own * S.mx);
+        T* yb = sm + V.off_yb[q];
+        T* zb = sm + V.off_zb[q];
+        stage(yb, L.Mb[1], W * S.my);
+        stage(yb + W * S.my, L.Kb[1], W * S.my);
+        stage(zb, L.Mb[2], W * S.mz);
+        stage(zb + W * S.mz, L.Kb[2], W * S.mz);
+        for (int e = threadIdx.x; e < S.nbc * W; e += blockDim.x) {
+            const int sl = e / W, bb = e - sl * W;
+            const int i = sl < S.tlo ? sl : S.thi + (sl - S.tlo);
+            cp_async4(const_cast<T*>(S.xM) + e, L.Mb[0] + bb * S.mx + i);
+            cp_async4(const_cast<T*>(S.xK) + e, L.Kb[0] + bb * S.mx + i);
+        }
+        for (int bb = threadIdx.x; bb < W; bb += blockDim.x) {      // the interior slot
+            const_cast<T*>(S.xM)[S.nbc * W + bb] = L.Mc[0][bb];
+            const_cast<T*>(S.xK)[S.nbc * W + bb] = L.Kc[0][bb];
+        }
+        const TransferView<T>& X = V.X[q];
+        const CTransfer3<T> Y = ctransfer3(V, smem_raw, q);
+        for (int d = 0; d < 3; ++d) {
+            stage(const_cast<int*>(Y.plo[d]), X.plo[d], X.mf[d]);
+            stage(const_cast<T*>(Y.pv[d]), X.pv[d], X.mf[d] * X.pw[d]);
+            stage(const_cast<int*>(Y.rlo[d]), X.rlo[d], X.mc[d]);
+            stage(const_cast<T*>(Y.rv[d]), X.rv[d], X.mc[d] * X.rw[d]);
+        }
+        const T** rp = const_cast<const T**>(S.rp);
+        for (int e = threadIdx.x; e < own * W2; e += blockDim.x) {
+            const int lr = e / W2, qq = e - lr * W2, row = S.lo + lr;
+            const int j = row % S.my + qq % W - P, k = row / S.my + qq / W - P;
+            if (j < 0 || j >= S.my || k < 0 || k >= S.mz) {
+                rp[e] = S.TM + lr * S.mx;                   // zero weights
+            } else {
+                const int rn = k * S.my + j, o = rn / S.R;
+                rp[e] = cptr(S.TM + (rn - o * S.R) * S.mx, o, rank);
+            }
+        }
+    }
+    for (int e = threadIdx.x; e < V.L[lc].m[0]; e += blockDim.x) zrow[e] = 0;
+    CoarseView<T> Cs = V.C;                             // coarsest eigenbasis (CTA 0 only)
+    {
+        T* f = sm + V.off_cv;
+        const int m0 = V.C.m[0], m1 = V.C.m[1], m2 = V.C.m[2];
+        if (rank == 0) {
+            stage(f, V.C.V[0], m0 * m0);
+            stage(f + m0 * m0, V.C.V[1], m1 * m1);
+            stage(f + m0 * m0 + m1 * m1, V.C.V[2], m2 * m2);
+            stage(f + m0 * m0 + m1 * m1 + m2 * m2, V.C.laminv, m0 * m1 * m2);
+        }
+        Cs.V[0] = f;
+        Cs.V[1] = f + m0 * m0;
+        Cs.V[2] = f + m0 * m0 + m1 * m1;
+        Cs.laminv = f + m0 * m0 + m1 * m1 + m2 * m2;
+    }
+    for (int q = 0; q <= lc; ++q) {                     // coarse e^0 = 0 on every level, zero pads
+        const CLevel3<T> S = clevel3<T, P>(V, smem_raw, q, rank);
+        for (int e = threadIdx.x; e < S.R * (S.mx + 2 * P); e += blockDim.x) S.x[e] = 0;
+        if (q > 0)
+            for (int e = threadIdx.x; e < 2 * S.R * S.mx; e += blockDim.x) S.TM[e] = 0;
+    }
+    pdl_enter();
+    {
+        const CLevel3<T> S = clevel3<T, P>(V, smem_raw, lc, rank);
+        stage(S.b, b_in + (size_t)S.lo * S.mx, (S.hi - S.lo) * S.mx);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    for (int q = 1; q <= lc; ++q) {                     // row weights, transfer row pointers
+        const CLevel3<T> S = clevel3<T, P>(V, smem_raw, q, rank);
+        const T* yb = sm + V.off_yb[q];
+        const T* zb = sm + V.off_zb[q];
+        const int own = S.hi - S.lo;
+        T* cc = const_cast<T*>(S.cc);
+        for (int e = threadIdx.x; e < own * W2; e += blockDim.x) {
+            const int lr = e / W2, qq = e - lr * W2, row = S.lo + lr;
+            const int j = row % S.my, k = row / S.my, bj = qq % W, bk = qq / W;
+            const T myv = yb[bj * S.my + j], kyv = yb[W * S.my + bj * S.my + j];
+            const T mzv = zb[bk * S.mz + k], kzv = zb[W * S.mz + bk * S.mz + k];
+            cc[2 * e] = kzv * myv + mzv * kyv;
+            cc[2 * e + 1] = mzv * myv;
+        }
+        const TransferView<T>& X = V.X[q];
+        const CTransfer3<T> Y = ctransfer3(V, smem_raw, q);
+        const int Rc = V.R[q - 1], myc = V.L[q - 1].m[1], mzc = V.L[q - 1].m[2];
+        const int loc = min(rank * Rc, myc * mzc), ownc = min(loc + Rc, myc * mzc) - loc;
+        const int ryz = X.rw[1] * X.rw[2], pyz = X.pw[1] * X.pw[2];
+        const T** rr = const_cast<const T**>(Y.rr);
+        for (int e = threadIdx.x; e < ownc * ryz; e += blockDim.x) {
+            const int Jl = e / ryz, s2 = e - Jl * ryz, sy = s2 % X.rw[1], sz = s2 / X.rw[1];
+            const int rc = loc + Jl, J = rc % myc, K = rc / myc;
+            const int fj = Y.rlo[1][J] + sy, fk = Y.rlo[2][K] + sz;
+            if (fj < 0 || fj >= S.my || fk < 0 || fk >= S.mz) {
+                rr[e] = zrow;
+            } else {
+                const int rn = fk * S.my + fj, o = rn / S.R;
+                rr[e] = cptr(t + (rn - o * S.R) * X.mc[0], o, rank);
+            }
+        }
+        const T** pr = const_cast<const T**>(Y.pr);
+        for (int e = threadIdx.x; e < own * pyz; e += blockDim.x) {
+            const int jl = e / pyz, s2 = e - jl * pyz, sy = s2 % X.pw[1], sz = s2 / X.pw[1];
+            const int row = S.lo + jl, j = row % S.my, k = row / S.my;
+            const int Fj = Y.plo[1][j] + sy, Fk = Y.plo[2][k] + sz;
+            if (Fj < 0 || Fj >= myc || Fk < 0 || Fk >= mzc) {
+                pr[e] = zrow;
+            } else {
+                const int rn = Fk * myc + Fj, o = rn / Rc;
+                pr[e] = cptr(t + (rn - o * Rc) * X.mf[0], o, rank);
+            }
+        }
+    }
+    __syncthreads();
+    cg::this_cluster().sync();
+    for (int l = lc; l >= 1; --l) {
+        const CLevel3<T> S = clevel3<T, P>(V, smem_raw, l, rank);
+        if (jacobi) cjacobi3<T, P>(S, r, omega);                               // pre-smooth
+        else cgs3<T, P>(S, r, false);
+        crestrict3<T, P>(S, clevel3<T, P>(V, smem_raw, l - 1, rank), ctransfer3(V, smem_raw, l), r, t);
+    }
+    if (rank == 0) {                                    // direct solve, into the padded rows of x_0
+        const int m0 = Cs.m[0], m1 = Cs.m[1], m2 = Cs.m[2], N = m0 * m1 * m2;
+        const T* b0 = sm + V.off_b[0];
+        T* x0 = sm + V.off_x[0];
+        auto pass = [&](const T* in, T* out, int axis, bool transpose, bool pad) {
+            const int md = Cs.m[axis], stride = axis == 0 ? 1 : (axis == 1 ? m0 : m0 * m1);
+            const T* Vm = Cs.V[axis];
+            for (int idx = threadIdx.x; idx < N; idx += blockDim.x) {
+                const int i0 = idx % m0, tt = idx / m0, i1 = tt % m1, i2 = tt / m1;
+                const int I = axis == 0 ? i0 : (axis == 1 ? i1 : i2);
+                const int base = idx - I * stride;
+                T acc = 0;
+                for (int s = 0; s < md; ++s) acc += (transpose ? Vm[s * md + I] : Vm[I * md + s]) * in[base + s * stride];
+                out[pad ? tt * (m0 + 2 * P) + i0 + P : idx] = acc;
+            }
+            __syncthreads();
+        };
+        pass(b0, r, 0, true, false);
+        pass(r, t, 1, true, false);
+        pass(t, r, 2, true, false);
+        for (int i = threadIdx.x; i < N; i += blockDim.x) r[i] *= Cs.laminv[i];
+        __syncthreads();
+        pass(r, t, 2, false, false);
+        pass(t, r, 1, false, false);
+        pass(r, x0, 0, false, true);
+    }
+    cg::this_cluster().sync();
+    for (int l = 1; l <= lc; ++l) {
+        const CLevel3<T> S = clevel3<T, P>(V, smem_raw, l, rank);
+        cprolong3<T, P>(S, clevel3<T, P>(V, smem_raw, l - 1, rank), ctransfer3(V, smem_raw, l), t);   // x += P e
+        if (jacobi) cjacobi3<T, P>(S, r, omega);                               // post-smooth
+        else cgs3<T, P>(S, r, true);
+    }
+    const CLevel3<T> S = clevel3<T, P>(V, smem_raw, lc, rank);
+    const int PW = S.mx + 2 * P;
+    grid_for(S.hi - S.lo, S.mx, [&](int lr, int i) { x_out[(size_t)(S.lo + lr) * S.mx + i] = S.x[lr * PW + i + P]; });
+}
+
 template <typename F>
 static void tail_with_p(int p, F&& f) {
     switch (p) {
@@ -915,6 +1362,8 @@ void prepare_tail_kernels(int optin) {
             cudaFuncSetAttribute(k_coarse_tail<float, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
             cudaFuncSetAttribute(k_cluster_tail<float, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
             cudaFuncSetAttribute(k_cluster_tail<float, P>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            cudaFuncSetAttribute(k_cluster_tail3<float, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+            cudaFuncSetAttribute(k_cluster_tail3<float, P>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         });
     if (dev >= 0 && dev < 64) g_tail_limit[dev] = (size_t)optin;
 }
@@ -982,6 +1431,54 @@ void cluster_tail(cudaStream_t s, const ClusterTailView<T>& V, const T* b, T* x,
     count_launch();
 }
 
+template <typename T>
+static cudaLaunchConfig_t cluster3_config(const ClusterTail3View<T>& V, cudaStream_t s, cudaLaunchAttribute* at,
+                                          bool overlap) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(V.ctas);
+    cfg.blockDim = dim3(kCTailThreads);
+    cfg.dynamicSmemBytes = V.smem;
+    cfg.stream = s;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = V.ctas;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = overlap ? 2 : 1;
+    return cfg;
+}
+
+template <typename T>
+bool cluster_tail3_fits(const ClusterTail3View<T>& V) {
+    if (V.lc < 1 || V.ctas < 2 || V.ctas > 16 || V.smem > tail_smem_limit()) return false;
+    int n = 0;
+    tail_with_p(V.L[V.lc].p, [&](auto PC) {
+        constexpr int P = decltype(PC)::value;
+        cudaLaunchAttribute at[2];
+        const cudaLaunchConfig_t cfg = cluster3_config(V, nullptr, at, false);
+        if (cudaOccupancyMaxActiveClusters(&n, k_cluster_tail3<T, P>, &cfg) != cudaSuccess) n = 0;
+    });
+    cudaGetLastError();
+    return n >= 1;
+}
+
+template <typename T>
+void cluster_tail3(cudaStream_t s, const ClusterTail3View<T>& V, const T* b, T* x, int jacobi, T omega) {
+    tail_with_p(V.L[V.lc].p, [&](auto PC) {
+        constexpr int P = decltype(PC)::value;
+        cudaLaunchAttribute at[2];
+        const cudaLaunchConfig_t cfg = cluster3_config(V, s, at, launch_overlap());
+        cudaEvent_t e0 = profiling() ? profile_before(s) : nullptr;
+        cudaLaunchKernelEx(&cfg, k_cluster_tail3<T, P>, V, b, x, jacobi, omega);
+        if (e0) profile_after(s, (const void*)k_cluster_tail3<T, P>, dim3(V.ctas), e0);
+    });
+    count_launch();
+}
+
+template bool cluster_tail3_fits<float>(const ClusterTail3View<float>&);
+template void cluster_tail3<float>(cudaStream_t, const ClusterTail3View<float>&, const float*, float*, int, float);
 template bool cluster_tail_fits<float>(const ClusterTailView<float>&);
 template void cluster_tail<float>(cudaStream_t, const ClusterTailView<float>&, const float*, float*, int, float);
 

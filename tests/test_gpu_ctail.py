@@ -9,7 +9,10 @@ and with the one-CTA tail to FP32 round-off (relative 1e-5 on the
 correction, 2-norm and max-norm) and with the FP64 oracle's cycle to FP32
 accuracy (2e-5), for several depths, both cluster sizes, both smoothers,
 square and rectangular grids, p = 1..7 and bands of unequal row counts;
-whole solves converge like the per-level schedule.
+whole solves converge like the per-level schedule.  The 3D form (the default
+for 3D cycles) is checked the same way: one cycle against the per-level
+cycle and the oracle's, both smoothers, several depths and shapes, and
+whole solves.
 """
 import numpy as np
 import pytest
@@ -147,3 +150,74 @@ def test_batch_members_with_cluster_tails(pkg):
     assert out["converged"], out["statuses"]
     assert np.all(np.abs(np.asarray(out["cycles"]) - np.asarray(base["cycles"])) <= 1)
     B.close()
+
+
+SHAPES3 = [(12, 3), (16, 2), ((14, 10, 9), 3), (10, 5), (17, 1), (20, 4)]
+
+
+@pytest.mark.parametrize("n,p", SHAPES3, ids=lambda c: str(c))
+@pytest.mark.parametrize("smoother", ["gs", "jacobi"])
+def test_cluster_tail3_cycle_matches_oracle_and_per_level(pkg, n, p, smoother):
+    ns = list(n) if isinstance(n, tuple) else [n, n, n]
+    ctx = pkg.igamg_setup(3, p, ns, 0)
+    pkg.igamg_assemble(ctx)
+    pkg.igamg_set_cycle(ctx, smoother, 1)
+    H = omg.Hierarchy(3, ns, p)
+    ws = torch.empty(pkg.igamg_workspace_bytes(ctx, 5, pkg.IGAMG_FP32_IR), dtype=torch.uint8, device=DEV)
+    rng = np.random.default_rng(p + 30)
+    b = load_vector(H.finest.breaks, p, rng.standard_normal((2, 2, 2)))
+    x0 = rng.standard_normal(H.finest.N) * 1e-3
+    ref = omg.cycle(H, x0, b, smoother=smoother) - x0
+
+    def cycle():
+        x = _t(x0)
+        pkg.igamg_vcycle(ctx, x, _t(b), pkg.IGAMG_FP32_IR, ws)
+        return _np(x) - x0
+
+    assert pkg.igamg_get_schedule(ctx)["tail_ctas"] == 16       # the 3D default
+    pkg.igamg_set_coarse_tail(ctx, False)
+    per_level = cycle()
+    assert _rel(per_level, ref) < 2e-5
+    pkg.igamg_set_coarse_tail(ctx, True)
+    checked = 0
+    for ctas in (8, 16):
+        most = pkg.igamg_tail_levels_available(ctx, ctas)
+        if most < 1:
+            continue
+        pkg.igamg_set_tail_ctas(ctx, ctas)
+        for lc in sorted({1, most}):
+            pkg.igamg_set_schedule(ctx, 0, lc)
+            assert pkg.igamg_coarse_tail_level(ctx) == lc
+            out = cycle()
+            assert _rel(out, per_level) < 1e-5 and _relmax(out, per_level) < 1e-5, (ctas, lc)
+            assert _rel(out, ref) < 2e-5 and _relmax(out, ref) < 2e-5, (ctas, lc)
+            checked += 1
+    assert checked >= 1
+    pkg.igamg_destroy(ctx)
+
+
+def test_cluster_tail3_depth_at_128(pkg):
+    """128^3, p = 3 (levels 9^3 .. 129^3 nodes per direction): 16 CTAs hold
+    the levels up to 33^3; the default schedule uses them."""
+    ctx = pkg.igamg_setup(3, 3, [128, 128, 128], 0)
+    pkg.igamg_assemble(ctx)
+    assert pkg.igamg_tail_levels_available(ctx, 16) == 2
+    assert pkg.igamg_coarse_tail_level(ctx) == 2
+    pkg.igamg_destroy(ctx)
+
+
+@pytest.mark.parametrize("n,p,k", [(48, 3, 10), (40, 2, 5)])
+def test_cluster_tail3_solves_like_per_level_schedule(pkg, n, p, k):
+    s = pkg.Solver(3, p, n, k=k)
+    b = s.rhs_sine(workloads.random_sine_coeffs(3, seed=p, modes=8))
+    pkg.igamg_set_coarse_tail(s.ctx, False)
+    ref32 = s.solve(b, tol=1e-10, method="rre", k=k, prec="fp32_ir", max_cycles=60)
+    assert ref32["converged"]
+    pkg.igamg_set_coarse_tail(s.ctx, True)
+    assert pkg.igamg_coarse_tail_level(s.ctx) >= 1
+    out = s.solve(b, tol=1e-10, method="rre", k=k, prec="fp32_ir", max_cycles=60)
+    assert out["converged"]
+    assert abs(out["cycles"] - ref32["cycles"]) <= 1
+    ref = s.solve(b, tol=1e-12, method="rre", k=k, prec="fp64", max_cycles=60)["x"]
+    assert float((out["x"] - ref).norm() / ref.norm()) < 1e-7
+    s.close()

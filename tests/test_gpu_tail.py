@@ -73,9 +73,12 @@ def test_tail_levels(pkg):
     pkg.igamg_assemble(ctx)
     assert pkg.igamg_coarse_tail_level(ctx) == 3
     pkg.igamg_destroy(ctx)
+    # 3D has no one-CTA tail; its coarse levels run on a 16-CTA cluster by default
     ctx = pkg.igamg_setup(3, 2, [32, 32, 32], 0)
     pkg.igamg_assemble(ctx)
-    assert pkg.igamg_coarse_tail_level(ctx) == 0
+    assert pkg.igamg_tail_levels_available(ctx, 1) == 0
+    assert pkg.igamg_get_schedule(ctx)["tail_ctas"] == 16
+    assert pkg.igamg_coarse_tail_level(ctx) == pkg.igamg_tail_levels_available(ctx, 16) >= 1
     pkg.igamg_destroy(ctx)
 
 
