@@ -152,7 +152,8 @@ def test_batch_members_with_cluster_tails(pkg):
     B.close()
 
 
-SHAPES3 = [(12, 3), (16, 2), ((14, 10, 9), 3), (10, 5), (17, 1), (20, 4)]
+# three or more levels (a tail needs a level between the finest and the coarsest)
+SHAPES3 = [(20, 3), (24, 2), ((20, 17, 24), 3), (18, 5), (20, 1), (24, 4)]
 
 
 @pytest.mark.parametrize("n,p", SHAPES3, ids=lambda c: str(c))
