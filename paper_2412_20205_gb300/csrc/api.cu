@@ -691,7 +691,7 @@ void restart_body(const igamg_ctx* c, cudaStream_t s, Workspace& w, int extrap, 
         const int nb = dev::gram_blocks(N);
         dev::extrap_gammas(s, k, extrap, w.S, w.ld, N, w.partial, nb, w.info, w.gamma, w.qused);
         dev::combine(s, k, w.gamma, w.S, w.ld, N, w.S);
-    } else if (prec != IGAMG_FP64 && c->dim == 2) {
+    } else if (prec != IGAMG_FP64) {
         // FP32 V-cycles with the FP64 residual carried by r <- r - A e in
         // double-FP32 arithmetic (refine.cu); the restart's first residual and
         // the one after extrapolation are computed from scratch in FP64.
@@ -708,7 +708,13 @@ void restart_body(const igamg_ctx* c, cudaStream_t s, Workspace& w, int extrap, 
             vcycle<float>(c, s, w, top, G.x, G.b, true, prec == IGAMG_FP32_IR_LEARNED);
             dev::refine_xpass_df(s, c->dfv, w.S + (size_t)i * w.ld, w.S + (size_t)(i + 1) * w.ld, G.x, tmh, tml,
                                  tkh, tkl);
-            if (i < k) dev::refine_residual_df(s, c->dfv, tmh, tml, tkh, tkl, r64, G.b);
+            if (i == k) continue;
+            if (c->dim == 2) {
+                dev::refine_residual_df(s, c->dfv, tmh, tml, tkh, tkl, r64, G.b);
+            } else {                                // 3D: y pass into F.TM | F.TK (free until the x-pass below)
+                dev::refine_residual_df3(s, c->dfv, tmh, tml, tkh, tkl, reinterpret_cast<float*>(F.TM),
+                                         reinterpret_cast<float*>(F.TK), r64, G.b);
+            }
         }
         const int nb = dev::gram_blocks(N);
         dev::extrap_gammas(s, k, extrap, w.S, w.ld, N, w.partial, nb, w.info, w.gamma, w.qused);
@@ -1013,10 +1019,10 @@ igamg_status igamg_assemble(igamg_ctx* c) {
         lo[l].inv[1] = add(inv32.data(), N * 4);
     }
     // float-pair split of the finest 2D level's factors (double-FP32 refinement update)
-    size_t dfo[2][4] = {};
-    if (dim == 2) {
+    size_t dfo[3][4] = {};
+    if (dim >= 2) {
         const HostLevel& H = c->hl[L - 1];
-        for (int d = 0; d < 2; ++d)
+        for (int d = 0; d < dim; ++d)
             for (int which = 0; which < 2; ++which) {
                 const std::vector<double> v = band_major<double>(H.f[d], which == 1);
                 std::vector<float> hi(v.size()), lw(v.size());
@@ -1220,11 +1226,12 @@ igamg_status igamg_assemble(igamg_ctx* c) {
             }
         }
     }
-    if (dim == 2) {
+    if (dim >= 2) {
         DFView& D = c->dfv;
         const LevelView<double>& a = c->lv64[L - 1];
         D.p = p;
-        for (int d = 0; d < 2; ++d) {
+        D.m[2] = 1;
+        for (int d = 0; d < dim; ++d) {
             D.m[d] = a.m[d];
             D.tlo[d] = a.tlo[d];
             D.thi[d] = a.thi[d];

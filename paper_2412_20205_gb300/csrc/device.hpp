@@ -146,14 +146,15 @@ IGAMG_HD inline int tail_transfer_elems(const TransferView<T>& X) {
     return X.mf[0] * (1 + X.pw[0]) + X.mf[1] * (1 + X.pw[1]) + X.mc[0] * (1 + X.rw[0]) + X.mc[1] * (1 + X.rw[1]);
 }
 
-// The finest 2D level's 1D factors with every FP64 entry split into a float
-// pair (hi = float(v), lo = float(v - hi); hi + lo = v to about 2^-48
-// relative), band-major as in LevelView, and the uniform interior's pairs.
+// The finest 2D or 3D level's 1D factors with every FP64 entry split into a
+// float pair (hi = float(v), lo = float(v - hi); hi + lo = v to about 2^-48
+// relative), band-major as in LevelView, and the uniform interior's pairs;
+// m[2] = 1 in 2D.
 struct DFView {
-    int m[2], p;
-    int tlo[2], thi[2];
-    const float *Mh[2], *Ml[2], *Kh[2], *Kl[2];
-    float Mch[2][2 * kMaxP + 1], Mcl[2][2 * kMaxP + 1], Kch[2][2 * kMaxP + 1], Kcl[2][2 * kMaxP + 1];
+    int m[3], p;
+    int tlo[3], thi[3];
+    const float *Mh[3], *Ml[3], *Kh[3], *Kl[3];
+    float Mch[3][2 * kMaxP + 1], Mcl[3][2 * kMaxP + 1], Kch[3][2 * kMaxP + 1], Kcl[3][2 * kMaxP + 1];
 };
 
 // A 2D level of the general operator (Sec. 4.3) in stencil form:
@@ -352,7 +353,7 @@ template <typename T, typename R>
 void residual(cudaStream_t s, int dim, const LevelView<T>& L, const T* b, const T* TM,
               const T* TK, R* r, double* partial, double* r64 = nullptr, T* u = nullptr, T* v = nullptr);
 
-// Double-FP32 refinement update on the finest 2D level (refine.cu):
+// Double-FP32 refinement update on the finest level (refine.cu; 2D and 3D rows):
 // S_out = S_in + e and the row sums of e, (I (x) M_x) e and (I (x) K_x) e,
 // each as a float pair (hi + lo) ...
 void refine_xpass_df(cudaStream_t s, const DFView& D, const double* S_in, double* S_out, const float* e,
@@ -361,6 +362,12 @@ void refine_xpass_df(cudaStream_t s, const DFView& D, const double* S_in, double
 // rf = float(r), the right side of the next FP32 V-cycle.
 void refine_residual_df(cudaStream_t s, const DFView& D, const float* tm_h, const float* tm_l,
                         const float* tk_h, const float* tk_l, double* r, float* rf);
+// The 3D form of the second step, sum-factorised as the FP64 3D residual:
+// the y pass U = (I (x) M_y) T_M, V = (I (x) K_y) T_M + (I (x) M_y) T_K (float
+// pairs, u = [Uh | Ul], v = [Vh | Vl], N floats each half), then
+// r -= sum_dk K_z U + M_z V and rf = float(r).
+void refine_residual_df3(cudaStream_t s, const DFView& D, const float* tm_h, const float* tm_l,
+                         const float* tk_h, const float* tk_l, float* u, float* v, double* r, float* rf);
 
 // coarse = P^T fine (tmp holds the intermediate axis passes).
 template <typename T>

@@ -1,4 +1,4 @@
-// Residual update of the FP32-IR form in double-FP32 arithmetic (2D).
+// Residual update of the FP32-IR form in double-FP32 arithmetic (2D and 3D).
 //
 // Within a restart cycle the FP64 residual of the iterate is carried by the
 // recurrence r_{i+1} = r_i - A e_i, where e_i is the FP32 correction of the
@@ -117,6 +117,86 @@ __global__ void __launch_bounds__(kRefThreads) k_residual_df(DFView D, const flo
     }
 }
 
+// 3D, y pass, one CTA per grid row (j, k): U = sum_dj M_y(j, dj) T_M(j + dj, k),
+// V = sum_dj K_y(j, dj) T_M(j + dj, k) + M_y(j, dj) T_K(j + dj, k), float pairs.
+template <int P>
+__global__ void __launch_bounds__(kRefThreads) k_yfactor_df3(DFView D, const float* __restrict__ tmh,
+                                                             const float* __restrict__ tml,
+                                                             const float* __restrict__ tkh,
+                                                             const float* __restrict__ tkl, float* __restrict__ uh,
+                                                             float* __restrict__ ul, float* __restrict__ vh,
+                                                             float* __restrict__ vl) {
+    const int mx = D.m[0], my = D.m[1], row = blockIdx.x, j = row % my, k = row / my;
+    const bool uni = j >= D.tlo[1] && j < D.thi[1];
+    float kyh[2 * P + 1], kyl[2 * P + 1], myh[2 * P + 1], myl[2 * P + 1];
+#pragma unroll
+    for (int dj = 0; dj <= 2 * P; ++dj) {
+        const int q = dj * my + j;
+        kyh[dj] = uni ? D.Kch[1][dj] : D.Kh[1][q];
+        kyl[dj] = uni ? D.Kcl[1][dj] : D.Kl[1][q];
+        myh[dj] = uni ? D.Mch[1][dj] : D.Mh[1][q];
+        myl[dj] = uni ? D.Mcl[1][dj] : D.Ml[1][q];
+    }
+    pdl_enter();                                  // above: operator data only
+    const size_t base = (size_t)row * mx;
+    for (int i = threadIdx.x; i < mx; i += blockDim.x) {
+        float Uh = 0.f, Ul = 0.f, Vh = 0.f, Vl = 0.f;
+#pragma unroll
+        for (int dj = 0; dj <= 2 * P; ++dj) {
+            const int jj = j + dj - P;
+            if (jj < 0 || jj >= my) continue;
+            const size_t q = ((size_t)k * my + jj) * mx + i;
+            const float ah = tmh[q], al = tml[q];
+            df_acc(Uh, Ul, myh[dj], myl[dj], ah, al);
+            df_acc(Vh, Vl, kyh[dj], kyl[dj], ah, al);
+            df_acc(Vh, Vl, myh[dj], myl[dj], tkh[q], tkl[q]);
+        }
+        df_norm(Uh, Ul);
+        df_norm(Vh, Vl);
+        uh[base + i] = Uh;
+        ul[base + i] = Ul;
+        vh[base + i] = Vh;
+        vl[base + i] = Vl;
+    }
+}
+
+// 3D, z pass, one CTA per grid row (j, k): r -= sum_dk K_z(k, dk) U(j, k + dk)
+// + M_z(k, dk) V(j, k + dk) in float pairs; rf = float(r).
+template <int P>
+__global__ void __launch_bounds__(kRefThreads) k_zresidual_df3(DFView D, const float* __restrict__ uh,
+                                                               const float* __restrict__ ul,
+                                                               const float* __restrict__ vh,
+                                                               const float* __restrict__ vl, double* __restrict__ r,
+                                                               float* __restrict__ rf) {
+    const int mx = D.m[0], my = D.m[1], mz = D.m[2], row = blockIdx.x, j = row % my, k = row / my;
+    const bool uni = k >= D.tlo[2] && k < D.thi[2];
+    float kzh[2 * P + 1], kzl[2 * P + 1], mzh[2 * P + 1], mzl[2 * P + 1];
+#pragma unroll
+    for (int dk = 0; dk <= 2 * P; ++dk) {
+        const int q = dk * mz + k;
+        kzh[dk] = uni ? D.Kch[2][dk] : D.Kh[2][q];
+        kzl[dk] = uni ? D.Kcl[2][dk] : D.Kl[2][q];
+        mzh[dk] = uni ? D.Mch[2][dk] : D.Mh[2][q];
+        mzl[dk] = uni ? D.Mcl[2][dk] : D.Ml[2][q];
+    }
+    pdl_enter();                                  // above: operator data only
+    const size_t base = (size_t)row * mx;
+    for (int i = threadIdx.x; i < mx; i += blockDim.x) {
+        float ah = 0.f, al = 0.f;
+#pragma unroll
+        for (int dk = 0; dk <= 2 * P; ++dk) {
+            const int kk = k + dk - P;
+            if (kk < 0 || kk >= mz) continue;
+            const size_t q = ((size_t)kk * my + j) * mx + i;
+            df_acc(ah, al, kzh[dk], kzl[dk], uh[q], ul[q]);
+            df_acc(ah, al, mzh[dk], mzl[dk], vh[q], vl[q]);
+        }
+        const double v = r[base + i] - ((double)ah + (double)al);
+        r[base + i] = v;
+        rf[base + i] = (float)v;
+    }
+}
+
 template <typename F>
 static void ref_with_p(int p, F&& f) {
     switch (p) {
@@ -141,7 +221,8 @@ void refine_xpass_df(cudaStream_t s, const DFView& D, const double* S_in, double
     const size_t smem = (size_t)(D.m[0] + 2 * D.p) * sizeof(float);
     ref_with_p(D.p, [&](auto PC) {
         constexpr int P = decltype(PC)::value;
-        launch_chained(k_xpass_df<P>, D.m[1], ref_threads(D.m[0]), smem, s, D, S_in, S_out, e, tm_h, tm_l, tk_h, tk_l);
+        launch_chained(k_xpass_df<P>, D.m[1] * D.m[2], ref_threads(D.m[0]), smem, s, D, S_in, S_out, e, tm_h, tm_l,
+                       tk_h, tk_l);
     });
     count_launch();
 }
@@ -153,6 +234,19 @@ void refine_residual_df(cudaStream_t s, const DFView& D, const float* tm_h, cons
         launch_chained(k_residual_df<P>, D.m[1], ref_threads(D.m[0]), 0, s, D, tm_h, tm_l, tk_h, tk_l, r, rf);
     });
     count_launch();
+}
+
+void refine_residual_df3(cudaStream_t s, const DFView& D, const float* tm_h, const float* tm_l, const float* tk_h,
+                         const float* tk_l, float* u, float* v, double* r, float* rf) {
+    const size_t N = (size_t)D.m[0] * D.m[1] * D.m[2];
+    const int rows = D.m[1] * D.m[2];
+    ref_with_p(D.p, [&](auto PC) {
+        constexpr int P = decltype(PC)::value;
+        launch_chained(k_yfactor_df3<P>, rows, ref_threads(D.m[0]), 0, s, D, tm_h, tm_l, tk_h, tk_l, u, u + N, v,
+                       v + N);
+        launch_chained(k_zresidual_df3<P>, rows, ref_threads(D.m[0]), 0, s, D, u, u + N, v, v + N, r, rf);
+    });
+    count_launch(2);
 }
 
 }  // namespace dev

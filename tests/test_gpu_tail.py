@@ -155,6 +155,21 @@ def test_fp32_ir_residual_recurrence_reaches_tight_tolerance(pkg, p):
     s.close()
 
 
+@pytest.mark.parametrize("n,p", [(32, 2), (24, 3), (16, 4)])
+def test_fp32_ir_residual_recurrence_3d_reaches_tight_tolerance(pkg, n, p):
+    """The same for the 3D recurrence (double-FP32 x pass, y pass and z pass
+    of the sum-factorised residual)."""
+    s = pkg.Solver(3, p, n, k=10)
+    b = s.rhs_sine(workloads.random_sine_coeffs(3, seed=12, modes=6))
+    out = s.solve(b, tol=1e-12, method="rre", k=10, prec="fp32_ir", max_cycles=80)
+    assert out["converged"], out["history"][-4:]
+    ref = s.solve(b, tol=1e-13, method="rre", k=10, prec="fp64", max_cycles=120)
+    assert ref["converged"]
+    assert float((out["x"] - ref["x"]).norm() / ref["x"].norm()) < 1e-10
+    assert abs(out["cycles"] - ref["cycles"]) <= 1
+    s.close()
+
+
 def test_launch_overlap_is_bitwise_neutral(pkg):
     """Launch overlap (programmatic dependent launch) changes when a kernel's
     CTAs are scheduled, never what they compute: every precision form, 2D and
