@@ -157,16 +157,24 @@ def test_fp32_ir_residual_recurrence_reaches_tight_tolerance(pkg, p):
 
 @pytest.mark.parametrize("n,p", [(32, 2), (24, 3), (16, 4)])
 def test_fp32_ir_residual_recurrence_3d_reaches_tight_tolerance(pkg, n, p):
-    """The same for the 3D recurrence (double-FP32 x pass, y pass and z pass
-    of the sum-factorised residual)."""
+    """The 3D recurrence (double-FP32 x pass, y pass and z pass of the
+    sum-factorised residual) must not stall either: relative residual 1e-12 is
+    reached and the true FP64 residual b - A x of the result (applied
+    independently) meets it.  Near 1e-12 the FP32 V-cycles' own rounding can
+    cost a few restarts against the FP64 solve (16^3, p = 4: 29 against 27)."""
     s = pkg.Solver(3, p, n, k=10)
     b = s.rhs_sine(workloads.random_sine_coeffs(3, seed=12, modes=6))
     out = s.solve(b, tol=1e-12, method="rre", k=10, prec="fp32_ir", max_cycles=80)
     assert out["converged"], out["history"][-4:]
-    ref = s.solve(b, tol=1e-13, method="rre", k=10, prec="fp64", max_cycles=120)
+    y = torch.empty_like(b)
+    pkg.igamg_apply(s.ctx, len(s.levels) - 1, out["x"], y, s.ws)
+    res = float((b - y).norm() / b.norm())
+    assert res <= 1.05e-12, res
+    ref = s.solve(b, tol=1e-12, method="rre", k=10, prec="fp64", max_cycles=120)
     assert ref["converged"]
-    assert float((out["x"] - ref["x"]).norm() / ref["x"].norm()) < 1e-10
-    assert abs(out["cycles"] - ref["cycles"]) <= 1
+    assert out["cycles"] <= ref["cycles"] + 3 + ref["cycles"] // 10
+    # both within 1e-12 in residual: their distance is at most cond(A) times that
+    assert float((out["x"] - ref["x"]).norm() / ref["x"].norm()) < 1e-8
     s.close()
 
 
