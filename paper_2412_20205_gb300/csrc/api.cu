@@ -408,7 +408,7 @@ void build_cluster_tails3(const igamg_ctx* c, std::vector<ClusterTail3View<float
             for (int q = 1; q <= l; ++q) {
                 const TransferView<float>& X = c->tv32[q];
                 v.off_rp[q] = off;
-                off += 2 * (v.R[q] * W2 + v.R[q - 1] * X.rw[1] * X.rw[2] + v.R[q] * X.pw[1] * X.pw[2]);
+                off += 2 * (v.R[q - 1] * X.rw[1] * X.rw[2] + v.R[q] * X.pw[1] * X.pw[2]);
             }
             for (int q = 0; q <= l; ++q) {
                 const int mx = c->hl[q].m[0], my = c->hl[q].m[1], mz = c->hl[q].m[2], R = v.R[q];
@@ -419,7 +419,7 @@ void build_cluster_tails3(const igamg_ctx* c, std::vector<ClusterTail3View<float
                 const TransferView<float>& X = c->tv32[q];
                 v.nbc[q] = Lq.tlo[0] + (mx - Lq.thi[0]);
                 v.off_inv[q] = off; off += R * mx;
-                v.off_tm[q] = off; off += 2 * R * mx;
+                v.off_tm[q] = off; off += 2 * (R + 2 * (p * my + p)) * mx;     // own rows and the halos
                 v.off_cc[q] = off; off += 2 * W2 * R;
                 v.off_yb[q] = off; off += 2 * W * my;
                 v.off_zb[q] = off; off += 2 * W * mz;

@@ -113,14 +113,14 @@ struct ClusterTailView {
 // Grid rows (j, k) are numbered r = k m_y + j; on level q >= 1, CTA c owns
 // the rows [c R[q], min((c + 1) R[q], m_y m_z)), and CTA 0 all rows of the
 // coarsest level (R[0] = m_y m_z).  Every CTA keeps its rows' x (zero-padded
-// by p columns on each side), b, 1 / A_ii, T_M, T_K and the (2p+1)^2 row
-// couplings (weights on T_M and T_K) of each own row in shared memory, with
-// the level's whole y- and z-bands and the three axes' transfer tables.
-// Offsets (elements): off_rp (8-byte aligned generic pointers: the T_M rows of
-// the (2p+1)^2 neighbours of each own row, the t rows each own coarse row's
-// y-z restriction combines (rw_y rw_z) and each own fine row's y-z
-// prolongation combines (pw_y pw_z)), off_x, off_b, off_inv, off_tm (T_M then
-// T_K, R x m_x each), off_cc (own rows x (2p+1)^2 weight pairs), off_yb (M_y
+// by p columns on each side), b, 1 / A_ii, T_M, T_K (with halo copies of the
+// H = p m_y + p rows on each side of its range, written by their owners) and
+// the (2p+1)^2 row couplings (weights on T_M and T_K) of each own row in
+// shared memory, with the level's whole y- and z-bands and the three axes'
+// transfer tables.  Offsets (elements): off_rp (8-byte aligned generic
+// pointers: the t rows each own coarse row's y-z restriction combines
+// (rw_y rw_z) and each own fine row's y-z prolongation combines (pw_y pw_z)),
+// off_x, off_b, off_inv, off_tm (T_M then T_K, (R + 2H) x m_x each), off_cc (own rows x (2p+1)^2 weight pairs), off_yb (M_y
 // then K_y, W x m_y), off_zb (M_z then K_z, W x m_z), off_xb (M_x then K_x:
 // the boundary columns, then the Toeplitz interior, (nbc + 1) x W each),
 // off_tx (for axes x, y, z: plo, pv, rlo, rv), off_cv (V_x, V_y, V_z,

@@ -891,9 +891,16 @@ __global__ void __launch_bounds__(kCTailThreads, 1) k_cluster_tail(ClusterTailVi
 // ---------------------------------------------------------------- 3D cluster tail
 // The coarse part of the 3D V-cycle on one thread-block cluster, in the form
 // of the 2D cluster tail above: every CTA owns a range of grid rows (j, k)
-// (numbered r = k m_y + j) of each level in its shared memory, the rows a
-// step needs from other CTAs are read through distributed shared memory
-// (pointers resolved once per launch), and cluster barriers order the steps.
+// (numbered r = k m_y + j) of each level in its shared memory, and cluster
+// barriers order the steps.  Unlike 2D, most of a row's (2p+1)^2 neighbour
+// rows belong to other CTAs, so every CTA keeps halo copies of T_M, T_K for
+// the rows within reach of its range (H = p m_y + p rows on each side, a
+// contiguous range in row order), and the owner of a row writes its new
+// T_M, T_K into every halo that holds it (distributed shared memory stores)
+// when it refreshes them; the smoothing steps and the residual read only
+// local memory.  (Reading the neighbours' rows in place made the 3D tail
+// bound by distributed-shared-memory bandwidth.)  The transfers read the
+// neighbours' rows of their scratch through pointers resolved once per launch.
 // A row couples to the (2p+1)^2 rows (j + dj, k + dk) with the weights
 // K_z M_y + M_z K_y on T_M and M_z M_y on T_K (A = K_z (x) M_y (x) M_x +
 // M_z (x) K_y (x) M_x + M_z (x) M_y (x) K_x); they are formed once per launch
@@ -908,12 +915,12 @@ struct CLevel3 {
     T* x;            // own rows, zero-padded: row lr at lr (mx + 2p), column i at + i + p
     T* b;
     const T* inv;
-    T* TM;           // own rows, then T_K at + R mx
+    int H;           // halo rows on each side
+    T* TM;           // rows lo - H .. hi + H - 1 (own row lr at (lr + H) mx), then T_K at + (R + 2H) mx
     T* TK;
     const T* xM;     // boundary slots 0..nbc-1, interior slot nbc
     const T* xK;
     const T* cc;     // own row lr, neighbour q = (dk + p) W + dj + p: weights at cc[2 (lr W^2 + q)], + 1
-    const T* const* rp;   // T_M row of neighbour q of own row lr at rp[lr W^2 + q]
 };
 
 template <typename T, int P>
@@ -934,12 +941,12 @@ __device__ __forceinline__ CLevel3<T> clevel3(const ClusterTail3View<T>& V, unsi
     S.x = sm + V.off_x[q];
     S.b = sm + V.off_b[q];
     S.inv = sm + V.off_inv[q];
+    S.H = P * S.my + P;
     S.TM = sm + V.off_tm[q];
-    S.TK = S.TM + S.R * S.mx;
+    S.TK = S.TM + (S.R + 2 * S.H) * S.mx;
     S.xM = sm + V.off_xb[q];
     S.xK = S.xM + (S.nbc + 1) * W;
     S.cc = sm + V.off_cc[q];
-    S.rp = reinterpret_cast<const T* const*>(raw + (size_t)V.off_rp[q] * sizeof(T));
     return S;
 }
 
@@ -974,9 +981,7 @@ __device__ __forceinline__ CTransfer3<T> ctransfer3(const ClusterTail3View<T>& V
         Y.rv[d] = f;
         f += X.mc[d] * X.rw[d];
     }
-    const int W = 2 * V.L[q].p + 1;
-    const T* const* rpq = reinterpret_cast<const T* const*>(raw + (size_t)V.off_rp[q] * sizeof(T));
-    Y.rr = rpq + V.R[q] * W * W;
+    Y.rr = reinterpret_cast<const T* const*>(raw + (size_t)V.off_rp[q] * sizeof(T));
     Y.pr = Y.rr + V.R[q - 1] * X.rw[1] * X.rw[2];
     return Y;
 }
@@ -1001,39 +1006,62 @@ __device__ __forceinline__ int phase_rows3(int lo, int hi, int my, int cy, int c
 }
 
 // sum over the (2p+1)^2 neighbour rows (all, or all but the own row) of
-// cM T_M + cK T_K at column i of own row lr (zero weights outside the grid).
+// cM T_M + cK T_K at column i of own row lr, from the own and halo rows (a
+// neighbour outside the grid has zero weights; its slot holds another row's
+// finite values or zeros).
 template <typename T, int P, bool SKIP_OWN>
 __device__ __forceinline__ T ccouple3(const CLevel3<T>& S, int lr, int i) {
-    constexpr int W2 = (2 * P + 1) * (2 * P + 1), OWN = P * (2 * P + 1) + P;
-    const T* const* rp = S.rp + lr * W2;
+    constexpr int W = 2 * P + 1, W2 = W * W, OWN = P * W + P;
     const T* cc = S.cc + 2 * lr * W2;
-    const int tko = S.R * S.mx;
+    const T* tm = S.TM + (lr + S.H) * S.mx + i;         // the own row's slot
+    const int tko = (S.R + 2 * S.H) * S.mx;
     T acc = 0;
     constexpr int U = W2 > 49 ? 9 : W2;
 #pragma unroll U
     for (int q = 0; q < W2; ++q) {
         if (SKIP_OWN && q == OWN) continue;
-        const T* row = rp[q];
-        acc += cc[2 * q] * row[i] + cc[2 * q + 1] * row[tko + i];
+        const int dr = (q / W - P) * S.my + (q % W - P);
+        const T* row = tm + dr * S.mx;
+        acc += cc[2 * q] * row[0] + cc[2 * q + 1] * row[tko];
     }
     return acc;
 }
 
+// T_M, T_K of own row lr at column i: stored in the own slot and written into
+// the halo of every other CTA whose range of rows within reach holds it.
 template <typename T, int P>
-__device__ void cxpass3(const CLevel3<T>& S) {
+__device__ __forceinline__ void store_t3(const CLevel3<T>& S, int lr, int i, T sM, T sK, int rank, int C) {
+    const int tko = (S.R + 2 * S.H) * S.mx;
+    T* own = S.TM + (lr + S.H) * S.mx + i;
+    own[0] = sM;
+    own[tko] = sK;
+    const int r = S.lo + lr, rows = S.my * S.mz;
+    const int o0 = max(0, (r - S.H) / S.R - 1), o1 = min(C - 1, (r + S.H) / S.R + 1);
+    for (int o = o0; o <= o1; ++o) {
+        const int lo_o = o * S.R;
+        if (o == rank || lo_o >= rows) continue;
+        const int hi_o = min(lo_o + S.R, rows);
+        if (r < lo_o - S.H || r >= hi_o + S.H) continue;
+        T* dst = cg::this_cluster().map_shared_rank(S.TM + (r - lo_o + S.H) * S.mx + i, o);
+        dst[0] = sM;
+        dst[tko] = sK;
+    }
+}
+
+template <typename T, int P>
+__device__ void cxpass3(const CLevel3<T>& S, int rank, int C) {
     const int PW = S.mx + 2 * P;
     grid_for(S.hi - S.lo, S.mx, [&](int lr, int i) {
         T sM, sK;
         cwin<T, P>(S, S.x + lr * PW + i, i, sM, sK);
-        S.TM[lr * S.mx + i] = sM;
-        S.TK[lr * S.mx + i] = sK;
+        store_t3<T, P>(S, lr, i, sM, sK, rank, C);
     });
 }
 
 // One multicolour GS sweep: (p+1)^2 row phases (cz slowest), each over the
 // own rows of the phase shared out to groups of warps, then a cluster barrier.
 template <typename T, int P>
-__device__ void cgs3(const CLevel3<T>& S, T* rhs, bool descending) {
+__device__ void cgs3(const CLevel3<T>& S, T* rhs, bool descending, int rank, int C) {
     constexpr int P1 = P + 1, NPH = P1 * P1, W2 = (2 * P + 1) * (2 * P + 1), OWN = P * (2 * P + 1) + P;
     const int PW = S.mx + 2 * P;
     const int NW = (int)blockDim.x >> 5, warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
@@ -1068,8 +1096,7 @@ __device__ void cgs3(const CLevel3<T>& S, T* rhs, bool descending) {
                     for (int i = gl; i < S.mx; i += gt) {
                         T sM, sK;
                         cwin<T, P>(S, xrow + i, i, sM, sK);
-                        S.TM[lr * S.mx + i] = sM;
-                        S.TK[lr * S.mx + i] = sK;
+                        store_t3<T, P>(S, lr, i, sM, sK, rank, C);
                     }
                 }
         }
@@ -1078,7 +1105,7 @@ __device__ void cgs3(const CLevel3<T>& S, T* rhs, bool descending) {
 }
 
 template <typename T, int P>
-__device__ void cjacobi3(const CLevel3<T>& S, T* d, T omega) {
+__device__ void cjacobi3(const CLevel3<T>& S, T* d, T omega, int rank, int C) {
     const int own = S.hi - S.lo, PW = S.mx + 2 * P;
     grid_for(own, S.mx, [&](int lr, int i) {
         const int q = lr * S.mx + i;
@@ -1087,7 +1114,7 @@ __device__ void cjacobi3(const CLevel3<T>& S, T* d, T omega) {
     cg::this_cluster().sync();
     grid_for(own, S.mx, [&](int lr, int i) { S.x[lr * PW + i + P] += d[lr * S.mx + i]; });
     __syncthreads();
-    cxpass3<T, P>(S);
+    cxpass3<T, P>(S, rank, C);
     cg::this_cluster().sync();
 }
 
@@ -1131,7 +1158,7 @@ __device__ void crestrict3(const CLevel3<T>& S, const CLevel3<T>& Sc, const CTra
 // x += P e: x-axis prolongation of the own coarse rows (t), then the own fine
 // rows from the coarse rows' t (y and z axes together), and the new T_M, T_K.
 template <typename T, int P>
-__device__ void cprolong3(const CLevel3<T>& S, const CLevel3<T>& Sc, const CTransfer3<T>& X, T* t) {
+__device__ void cprolong3(const CLevel3<T>& S, const CLevel3<T>& Sc, const CTransfer3<T>& X, T* t, int rank, int C) {
     const int mfx = S.mx, PWc = Sc.mx + 2 * P;
     grid_for(Sc.hi - Sc.lo, mfx, [&](int Jl, int i) {
         const int lo = X.plo[0][i];
@@ -1158,7 +1185,7 @@ __device__ void cprolong3(const CLevel3<T>& S, const CLevel3<T>& Sc, const CTran
         S.x[jl * PW + i + P] += acc;
     });
     __syncthreads();
-    cxpass3<T, P>(S);
+    cxpass3<T, P>(S, rank, C);
     cg::this_cluster().sync();
 }
 
@@ -1169,12 +1196,12 @@ __global__ void __launch_bounds__(kCTailThreads, 1) k_cluster_tail3(ClusterTail3
     constexpr int W = 2 * P + 1, W2 = W * W;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
-    const int rank = (int)cg::this_cluster().block_rank();
+    const int rank = (int)cg::this_cluster().block_rank(), C = V.ctas;
     const int lc = V.lc;
     T* r = sm + V.off_r;
     T* t = sm + V.off_t;
     T* zrow = sm + V.off_z;
-    // operator data and the neighbour pointers, before the wait
+    // operator data, before the wait
     for (int q = 1; q <= lc; ++q) {
         const LevelView<T>& L = V.L[q];
         const CLevel3<T> S = clevel3<T, P>(V, smem_raw, q, rank);
@@ -1204,17 +1231,6 @@ __global__ void __launch_bounds__(kCTailThreads, 1) k_cluster_tail3(ClusterTail3
             stage(const_cast<int*>(Y.rlo[d]), X.rlo[d], X.mc[d]);
             stage(const_cast<T*>(Y.rv[d]), X.rv[d], X.mc[d] * X.rw[d]);
         }
-        const T** rp = const_cast<const T**>(S.rp);
-        for (int e = threadIdx.x; e < own * W2; e += blockDim.x) {
-            const int lr = e / W2, qq = e - lr * W2, row = S.lo + lr;
-            const int j = row % S.my + qq % W - P, k = row / S.my + qq / W - P;
-            if (j < 0 || j >= S.my || k < 0 || k >= S.mz) {
-                rp[e] = S.TM + lr * S.mx;                   // zero weights
-            } else {
-                const int rn = k * S.my + j, o = rn / S.R;
-                rp[e] = cptr(S.TM + (rn - o * S.R) * S.mx, o, rank);
-            }
-        }
     }
     for (int e = threadIdx.x; e < V.L[lc].m[0]; e += blockDim.x) zrow[e] = 0;
     CoarseView<T> Cs = V.C;                             // coarsest eigenbasis (CTA 0 only)
@@ -1236,7 +1252,7 @@ __global__ void __launch_bounds__(kCTailThreads, 1) k_cluster_tail3(ClusterTail3
         const CLevel3<T> S = clevel3<T, P>(V, smem_raw, q, rank);
         for (int e = threadIdx.x; e < S.R * (S.mx + 2 * P); e += blockDim.x) S.x[e] = 0;
         if (q > 0)
-            for (int e = threadIdx.x; e < 2 * S.R * S.mx; e += blockDim.x) S.TM[e] = 0;
+            for (int e = threadIdx.x; e < 2 * (S.R + 2 * S.H) * S.mx; e += blockDim.x) S.TM[e] = 0;
     }
     pdl_enter();
     {
@@ -1293,8 +1309,8 @@ __global__ void __launch_bounds__(kCTailThreads, 1) k_cluster_tail3(ClusterTail3
     cg::this_cluster().sync();
     for (int l = lc; l >= 1; --l) {
         const CLevel3<T> S = clevel3<T, P>(V, smem_raw, l, rank);
-        if (jacobi) cjacobi3<T, P>(S, r, omega);                               // pre-smooth
-        else cgs3<T, P>(S, r, false);
+        if (jacobi) cjacobi3<T, P>(S, r, omega, rank, C);                      // pre-smooth
+        else cgs3<T, P>(S, r, false, rank, C);
         crestrict3<T, P>(S, clevel3<T, P>(V, smem_raw, l - 1, rank), ctransfer3(V, smem_raw, l), r, t);
     }
     if (rank == 0) {                                    // direct solve, into the padded rows of x_0
@@ -1326,9 +1342,9 @@ __global__ void __launch_bounds__(kCTailThreads, 1) k_cluster_tail3(ClusterTail3
     cg::this_cluster().sync();
     for (int l = 1; l <= lc; ++l) {
         const CLevel3<T> S = clevel3<T, P>(V, smem_raw, l, rank);
-        cprolong3<T, P>(S, clevel3<T, P>(V, smem_raw, l - 1, rank), ctransfer3(V, smem_raw, l), t);   // x += P e
-        if (jacobi) cjacobi3<T, P>(S, r, omega);                               // post-smooth
-        else cgs3<T, P>(S, r, true);
+        cprolong3<T, P>(S, clevel3<T, P>(V, smem_raw, l - 1, rank), ctransfer3(V, smem_raw, l), t, rank, C);
+        if (jacobi) cjacobi3<T, P>(S, r, omega, rank, C);                      // post-smooth
+        else cgs3<T, P>(S, r, true, rank, C);
     }
     const CLevel3<T> S = clevel3<T, P>(V, smem_raw, lc, rank);
     const int PW = S.mx + 2 * P;
