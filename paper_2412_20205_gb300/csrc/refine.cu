@@ -117,8 +117,13 @@ __global__ void __launch_bounds__(kRefThreads) k_residual_df(DFView D, const flo
     }
 }
 
-// 3D, y pass, one CTA per grid row (j, k): U = sum_dj M_y(j, dj) T_M(j + dj, k),
-// V = sum_dj K_y(j, dj) T_M(j + dj, k) + M_y(j, dj) T_K(j + dj, k), float pairs.
+// 3D passes: one CTA per block of kRowsPerCta3 consecutive rows j of one plane
+// k, its threads striding over the block's rows x columns.
+constexpr int kRowsPerCta3 = 8;
+
+// 3D, y pass: U = sum_dj M_y(j, dj) T_M(j + dj, k), V = sum_dj K_y(j, dj)
+// T_M(j + dj, k) + M_y(j, dj) T_K(j + dj, k), float pairs.  The block's rows'
+// y-band pairs are staged in shared memory.
 template <int P>
 __global__ void __launch_bounds__(kRefThreads) k_yfactor_df3(DFView D, const float* __restrict__ tmh,
                                                              const float* __restrict__ tml,
@@ -126,49 +131,57 @@ __global__ void __launch_bounds__(kRefThreads) k_yfactor_df3(DFView D, const flo
                                                              const float* __restrict__ tkl, float* __restrict__ uh,
                                                              float* __restrict__ ul, float* __restrict__ vh,
                                                              float* __restrict__ vl) {
-    const int mx = D.m[0], my = D.m[1], row = blockIdx.x, j = row % my, k = row / my;
-    const bool uni = j >= D.tlo[1] && j < D.thi[1];
-    float kyh[2 * P + 1], kyl[2 * P + 1], myh[2 * P + 1], myl[2 * P + 1];
-#pragma unroll
-    for (int dj = 0; dj <= 2 * P; ++dj) {
-        const int q = dj * my + j;
-        kyh[dj] = uni ? D.Kch[1][dj] : D.Kh[1][q];
-        kyl[dj] = uni ? D.Kcl[1][dj] : D.Kl[1][q];
-        myh[dj] = uni ? D.Mch[1][dj] : D.Mh[1][q];
-        myl[dj] = uni ? D.Mcl[1][dj] : D.Ml[1][q];
+    constexpr int W = 2 * P + 1;
+    __shared__ float cy[4][kRowsPerCta3][W];        // K_y hi, K_y lo, M_y hi, M_y lo
+    const int mx = D.m[0], my = D.m[1];
+    const int nbj = (my + kRowsPerCta3 - 1) / kRowsPerCta3;
+    const int k = blockIdx.x / nbj, j0 = (blockIdx.x - k * nbj) * kRowsPerCta3;
+    const int nr = min(kRowsPerCta3, my - j0);
+    for (int e = threadIdx.x; e < nr * W; e += blockDim.x) {
+        const int jr = e / W, dj = e - jr * W, j = j0 + jr, q = dj * my + j;
+        const bool uni = j >= D.tlo[1] && j < D.thi[1];
+        cy[0][jr][dj] = uni ? D.Kch[1][dj] : D.Kh[1][q];
+        cy[1][jr][dj] = uni ? D.Kcl[1][dj] : D.Kl[1][q];
+        cy[2][jr][dj] = uni ? D.Mch[1][dj] : D.Mh[1][q];
+        cy[3][jr][dj] = uni ? D.Mcl[1][dj] : D.Ml[1][q];
     }
+    __syncthreads();
     pdl_enter();                                  // above: operator data only
-    const size_t base = (size_t)row * mx;
-    for (int i = threadIdx.x; i < mx; i += blockDim.x) {
+    for (int e = threadIdx.x; e < nr * mx; e += blockDim.x) {
+        const int jr = e / mx, i = e - jr * mx, j = j0 + jr;
         float Uh = 0.f, Ul = 0.f, Vh = 0.f, Vl = 0.f;
 #pragma unroll
-        for (int dj = 0; dj <= 2 * P; ++dj) {
+        for (int dj = 0; dj < W; ++dj) {
             const int jj = j + dj - P;
             if (jj < 0 || jj >= my) continue;
             const size_t q = ((size_t)k * my + jj) * mx + i;
             const float ah = tmh[q], al = tml[q];
-            df_acc(Uh, Ul, myh[dj], myl[dj], ah, al);
-            df_acc(Vh, Vl, kyh[dj], kyl[dj], ah, al);
-            df_acc(Vh, Vl, myh[dj], myl[dj], tkh[q], tkl[q]);
+            df_acc(Uh, Ul, cy[2][jr][dj], cy[3][jr][dj], ah, al);
+            df_acc(Vh, Vl, cy[0][jr][dj], cy[1][jr][dj], ah, al);
+            df_acc(Vh, Vl, cy[2][jr][dj], cy[3][jr][dj], tkh[q], tkl[q]);
         }
         df_norm(Uh, Ul);
         df_norm(Vh, Vl);
-        uh[base + i] = Uh;
-        ul[base + i] = Ul;
-        vh[base + i] = Vh;
-        vl[base + i] = Vl;
+        const size_t o = ((size_t)k * my + j) * mx + i;
+        uh[o] = Uh;
+        ul[o] = Ul;
+        vh[o] = Vh;
+        vl[o] = Vl;
     }
 }
 
-// 3D, z pass, one CTA per grid row (j, k): r -= sum_dk K_z(k, dk) U(j, k + dk)
-// + M_z(k, dk) V(j, k + dk) in float pairs; rf = float(r).
+// 3D, z pass: r -= sum_dk K_z(k, dk) U(j, k + dk) + M_z(k, dk) V(j, k + dk) in
+// float pairs; rf = float(r).  The plane's z-band pairs are the CTA's.
 template <int P>
 __global__ void __launch_bounds__(kRefThreads) k_zresidual_df3(DFView D, const float* __restrict__ uh,
                                                                const float* __restrict__ ul,
                                                                const float* __restrict__ vh,
                                                                const float* __restrict__ vl, double* __restrict__ r,
                                                                float* __restrict__ rf) {
-    const int mx = D.m[0], my = D.m[1], mz = D.m[2], row = blockIdx.x, j = row % my, k = row / my;
+    const int mx = D.m[0], my = D.m[1], mz = D.m[2];
+    const int nbj = (my + kRowsPerCta3 - 1) / kRowsPerCta3;
+    const int k = blockIdx.x / nbj, j0 = (blockIdx.x - k * nbj) * kRowsPerCta3;
+    const int nr = min(kRowsPerCta3, my - j0);
     const bool uni = k >= D.tlo[2] && k < D.thi[2];
     float kzh[2 * P + 1], kzl[2 * P + 1], mzh[2 * P + 1], mzl[2 * P + 1];
 #pragma unroll
@@ -180,8 +193,8 @@ __global__ void __launch_bounds__(kRefThreads) k_zresidual_df3(DFView D, const f
         mzl[dk] = uni ? D.Mcl[2][dk] : D.Ml[2][q];
     }
     pdl_enter();                                  // above: operator data only
-    const size_t base = (size_t)row * mx;
-    for (int i = threadIdx.x; i < mx; i += blockDim.x) {
+    for (int e = threadIdx.x; e < nr * mx; e += blockDim.x) {
+        const int jr = e / mx, i = e - jr * mx, j = j0 + jr;
         float ah = 0.f, al = 0.f;
 #pragma unroll
         for (int dk = 0; dk <= 2 * P; ++dk) {
@@ -191,9 +204,10 @@ __global__ void __launch_bounds__(kRefThreads) k_zresidual_df3(DFView D, const f
             df_acc(ah, al, kzh[dk], kzl[dk], uh[q], ul[q]);
             df_acc(ah, al, mzh[dk], mzl[dk], vh[q], vl[q]);
         }
-        const double v = r[base + i] - ((double)ah + (double)al);
-        r[base + i] = v;
-        rf[base + i] = (float)v;
+        const size_t o = ((size_t)k * my + j) * mx + i;
+        const double v = r[o] - ((double)ah + (double)al);
+        r[o] = v;
+        rf[o] = (float)v;
     }
 }
 
@@ -239,12 +253,12 @@ void refine_residual_df(cudaStream_t s, const DFView& D, const float* tm_h, cons
 void refine_residual_df3(cudaStream_t s, const DFView& D, const float* tm_h, const float* tm_l, const float* tk_h,
                          const float* tk_l, float* u, float* v, double* r, float* rf) {
     const size_t N = (size_t)D.m[0] * D.m[1] * D.m[2];
-    const int rows = D.m[1] * D.m[2];
+    const int blocks = D.m[2] * ((D.m[1] + kRowsPerCta3 - 1) / kRowsPerCta3);
+    const int threads = ref_threads(D.m[0] * kRowsPerCta3);
     ref_with_p(D.p, [&](auto PC) {
         constexpr int P = decltype(PC)::value;
-        launch_chained(k_yfactor_df3<P>, rows, ref_threads(D.m[0]), 0, s, D, tm_h, tm_l, tk_h, tk_l, u, u + N, v,
-                       v + N);
-        launch_chained(k_zresidual_df3<P>, rows, ref_threads(D.m[0]), 0, s, D, u, u + N, v, v + N, r, rf);
+        launch_chained(k_yfactor_df3<P>, blocks, threads, 0, s, D, tm_h, tm_l, tk_h, tk_l, u, u + N, v, v + N);
+        launch_chained(k_zresidual_df3<P>, blocks, threads, 0, s, D, u, u + N, v, v + N, r, rf);
     });
     count_launch(2);
 }
