@@ -15,6 +15,9 @@ namespace igamg {
 namespace dev {
 
 constexpr int kRefThreads = 256;
+// 3D passes: one CTA per block of kRowsPerCta3 consecutive rows (the y and z
+// passes: rows j of one plane k), its threads striding over rows x columns.
+constexpr int kRowsPerCta3 = 8;
 
 // (sh, sl) += (ch + cl) * (vh + vl), float-pair accumulation
 __device__ __forceinline__ void df_acc(float& sh, float& sl, float ch, float cl, float vh, float vl) {
@@ -34,50 +37,56 @@ __device__ __forceinline__ void df_norm(float& sh, float& sl) {
     sh = t;
 }
 
-// One CTA per row: S_out = S_in + e; float-pair x-band sums of e.
+// One CTA per block of rb consecutive rows (2D: rb = 1): S_out = S_in + e;
+// float-pair x-band sums of e.
 template <int P>
-__global__ void __launch_bounds__(kRefThreads) k_xpass_df(DFView D, const double* __restrict__ S_in,
+__global__ void __launch_bounds__(kRefThreads) k_xpass_df(DFView D, int rb, const double* __restrict__ S_in,
                                                           double* __restrict__ S_out, const float* __restrict__ e,
                                                           float* __restrict__ tmh, float* __restrict__ tml,
                                                           float* __restrict__ tkh, float* __restrict__ tkl) {
     pdl_enter();
-    extern __shared__ float es[];                 // the row of e with a zero halo of p
-    const int mx = D.m[0];
-    const size_t base = (size_t)blockIdx.x * mx;
-    for (int ii = threadIdx.x; ii < mx + 2 * P; ii += blockDim.x) {
-        const int i = ii - P;
+    extern __shared__ float es[];                 // the rows of e, each with a zero halo of p
+    const int mx = D.m[0], rows = D.m[1] * D.m[2], PW = mx + 2 * P;
+    const int r0 = blockIdx.x * rb, nr = min(rb, rows - r0);
+    const size_t base = (size_t)r0 * mx;
+    for (int q = threadIdx.x; q < nr * PW; q += blockDim.x) {
+        const int rr = q / PW, ii = q - rr * PW, i = ii - P;
         float v = 0.f;
         if (i >= 0 && i < mx) {
-            v = e[base + i];
-            S_out[base + i] = S_in[base + i] + (double)v;
+            const size_t o = base + (size_t)rr * mx + i;
+            v = e[o];
+            S_out[o] = S_in[o] + (double)v;
         }
-        es[ii] = v;
+        es[q] = v;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < mx; i += blockDim.x) {
+    for (int q = threadIdx.x; q < nr * mx; q += blockDim.x) {
+        const int rr = q / mx, i = q - rr * mx;
+        const float* er = es + rr * PW;
         float mh = 0.f, ml = 0.f, kh = 0.f, kl = 0.f;
         if (i >= D.tlo[0] && i < D.thi[0]) {
 #pragma unroll
             for (int b = 0; b <= 2 * P; ++b) {
-                const float v = es[i + b];
+                const float v = er[i + b];
                 df_acc(mh, ml, D.Mch[0][b], D.Mcl[0][b], v, 0.f);
                 df_acc(kh, kl, D.Kch[0][b], D.Kcl[0][b], v, 0.f);
             }
         } else {
 #pragma unroll
             for (int b = 0; b <= 2 * P; ++b) {
-                const float v = es[i + b];
-                const int q = b * mx + i;
-                df_acc(mh, ml, D.Mh[0][q], D.Ml[0][q], v, 0.f);
-                df_acc(kh, kl, D.Kh[0][q], D.Kl[0][q], v, 0.f);
+                const float v = er[i + b];
+                const int qq = b * mx + i;
+                df_acc(mh, ml, D.Mh[0][qq], D.Ml[0][qq], v, 0.f);
+                df_acc(kh, kl, D.Kh[0][qq], D.Kl[0][qq], v, 0.f);
             }
         }
         df_norm(mh, ml);
         df_norm(kh, kl);
-        tmh[base + i] = mh;
-        tml[base + i] = ml;
-        tkh[base + i] = kh;
-        tkl[base + i] = kl;
+        const size_t o = base + q;
+        tmh[o] = mh;
+        tml[o] = ml;
+        tkh[o] = kh;
+        tkl[o] = kl;
     }
 }
 
@@ -116,10 +125,6 @@ __global__ void __launch_bounds__(kRefThreads) k_residual_df(DFView D, const flo
         rf[base + i] = (float)v;
     }
 }
-
-// 3D passes: one CTA per block of kRowsPerCta3 consecutive rows j of one plane
-// k, its threads striding over the block's rows x columns.
-constexpr int kRowsPerCta3 = 8;
 
 // 3D, y pass: U = sum_dj M_y(j, dj) T_M(j + dj, k), V = sum_dj K_y(j, dj)
 // T_M(j + dj, k) + M_y(j, dj) T_K(j + dj, k), float pairs.  The block's rows'
@@ -232,11 +237,13 @@ static int ref_threads(int mx) {
 
 void refine_xpass_df(cudaStream_t s, const DFView& D, const double* S_in, double* S_out, const float* e,
                      float* tm_h, float* tm_l, float* tk_h, float* tk_l) {
-    const size_t smem = (size_t)(D.m[0] + 2 * D.p) * sizeof(float);
+    // 2D rows (1025 nodes at 1024^2) fill a CTA; short 3D rows go kRowsPerCta3 to a CTA
+    const int rows = D.m[1] * D.m[2], rb = D.m[2] > 1 ? kRowsPerCta3 : 1;
+    const size_t smem = (size_t)rb * (D.m[0] + 2 * D.p) * sizeof(float);
     ref_with_p(D.p, [&](auto PC) {
         constexpr int P = decltype(PC)::value;
-        launch_chained(k_xpass_df<P>, D.m[1] * D.m[2], ref_threads(D.m[0]), smem, s, D, S_in, S_out, e, tm_h, tm_l,
-                       tk_h, tk_l);
+        launch_chained(k_xpass_df<P>, (rows + rb - 1) / rb, ref_threads(D.m[0] * rb), smem, s, D, rb, S_in, S_out, e,
+                       tm_h, tm_l, tk_h, tk_l);
     });
     count_launch();
 }
