@@ -306,13 +306,16 @@ igamg_status igamg_adam_step(int n, float* d_w, const float* d_g, float* d_m, fl
 igamg_status igamg_set_smoother(igamg_ctx* ctx, const float* d_w, double stall_ratio);
 int igamg_smoother_fell_back(const igamg_ctx* ctx);
 
-/* Coarse tail of FP32 2D V-cycles (the paper's V-cycle, Algorithm 2, with a
- * different schedule): levels 0..lc, each with at most 6000 unknowns and
- * together fitting one CTA's shared memory, run in one kernel launch instead
- * of one launch per smoothing phase and transfer pass.  Same arithmetic up to
- * FP32 rounding order.  igamg_coarse_tail_level() returns lc (0: none or
- * disabled); igamg_set_coarse_tail(ctx, 0) switches it off (on by default),
- * e.g. to compare both schedules.  FP64 cycles and 3D problems never use it. */
+/* Coarse tail of FP32 V-cycles (the paper's V-cycle, Algorithm 2, with a
+ * different schedule): levels 0..lc run in one kernel launch instead of one
+ * launch per smoothing phase and transfer pass.  2D: on one CTA (levels of at
+ * most 6000 unknowns that together fit its shared memory; the default) or on
+ * a thread-block cluster (igamg_set_tail_ctas).  3D: on a 16-CTA cluster (the
+ * default) or 8.  Same arithmetic up to FP32 rounding order.
+ * igamg_coarse_tail_level() returns lc (0: none or disabled);
+ * igamg_set_coarse_tail(ctx, 0) switches it off (on by default), e.g. to
+ * compare schedules.  FP64 cycles never use it (on GB300 the per-level FP64
+ * kernels spread over all SMs are faster). */
 int igamg_coarse_tail_level(const igamg_ctx* ctx);
 igamg_status igamg_set_coarse_tail(igamg_ctx* ctx, int enable);
 
@@ -323,14 +326,15 @@ igamg_status igamg_set_coarse_tail(igamg_ctx* ctx, int enable);
 igamg_status igamg_set_schedule(igamg_ctx* ctx, int gs_threads, int tail_levels);
 void igamg_get_schedule(const igamg_ctx* ctx, int* gs_threads, int* tail_levels);
 
-/* Where the coarse tail runs: ctas = 1 on one CTA (the levels above), 8 or 16
- * on one thread-block cluster of that many CTAs.  The cluster form splits
+/* Where the coarse tail runs: ctas = 1 on one CTA (2D only), 8 or 16 on one
+ * thread-block cluster of that many CTAs (2D and 3D).  The cluster form splits
  * every tail level's grid rows into contiguous bands, one per CTA, kept in
  * that CTA's shared memory; the rows a step needs from a neighbouring band
  * are read from the neighbour's shared memory (distributed shared memory),
- * and cluster barriers order the steps.  Its levels are limited by the
- * shared memory of one CTA per band (about 257^2 unknowns on 16 CTAs), not
- * by 6000 unknowns.  Same colours, order and operators (FP32 rounding order
+ * and cluster barriers order the steps (3D: each CTA also keeps copies of
+ * the rows within reach of its band, written by their owners).  Its levels
+ * are limited by the shared memory of one CTA per band (2D: about 257^2
+ * unknowns on 16 CTAs; 3D: about 33^3), not by 6000 unknowns.  Same colours, order and operators (FP32 rounding order
  * aside).  Switching keeps the tail depth where the other form has it, else
  * takes its deepest; igamg_tail_levels_available() gives the deepest tail
  * level of each form (0: none), igamg_get_tail_ctas() the form in use.
