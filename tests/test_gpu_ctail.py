@@ -153,7 +153,7 @@ def test_batch_members_with_cluster_tails(pkg):
 
 
 # three or more levels (a tail needs a level between the finest and the coarsest)
-SHAPES3 = [(20, 3), (24, 2), ((20, 17, 24), 3), (18, 5), (20, 1), (24, 4)]
+SHAPES3 = [(20, 3), (24, 2), ((20, 17, 24), 3), (18, 5), (20, 1), (24, 4), (18, 6)]
 
 
 @pytest.mark.parametrize("n,p", SHAPES3, ids=lambda c: str(c))
@@ -195,6 +195,23 @@ def test_cluster_tail3_cycle_matches_oracle_and_per_level(pkg, n, p, smoother):
             checked += 1
     assert checked >= 1
     pkg.igamg_destroy(ctx)
+
+
+def test_cluster_tail3_schedule_switches(pkg):
+    """3D has no one-CTA tail: asking for it switches the tail off; the cluster
+    sizes switch back; the autotuner picks one of the forms and still solves."""
+    s = pkg.Solver(3, 3, 32, k=10)
+    assert pkg.igamg_get_schedule(s.ctx)["tail_ctas"] == 16
+    pkg.igamg_set_tail_ctas(s.ctx, 1)
+    assert pkg.igamg_coarse_tail_level(s.ctx) == 0
+    pkg.igamg_set_tail_ctas(s.ctx, 8)
+    assert pkg.igamg_coarse_tail_level(s.ctx) == pkg.igamg_tail_levels_available(s.ctx, 8) >= 1
+    sch = s.autotune(reps=2)
+    assert sch["tail_ctas"] in (1, 8, 16)
+    b = s.rhs_sine(workloads.random_sine_coeffs(3, seed=9, modes=6))
+    out = s.solve(b, tol=1e-10, method="rre", k=10, prec="fp32_ir", max_cycles=60)
+    assert out["converged"]
+    s.close()
 
 
 def test_cluster_tail3_depth_at_128(pkg):
