@@ -364,6 +364,33 @@ int tail_most(const igamg_ctx* c, int ctas) {
     return 0;
 }
 
+// The static shared-memory image of a 2D cluster-tail view, built on first
+// use into device memory the context owns; false if it could not be.
+bool ensure_tail_image(ClusterTailView<float>& v) {
+    if (v.img) return true;
+    uint4* img = nullptr;
+    if (cudaMalloc(&img, (size_t)v.ctas * v.img16 * sizeof(uint4)) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (dev::cluster_tail_image(v, img) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(img);
+        return false;
+    }
+    v.img = img;
+    return true;
+}
+
+void free_tail_images(igamg_ctx* c) {
+    for (auto& vs : c->ctails)
+        for (auto& v : vs)
+            if (v.img) {
+                cudaFree(const_cast<uint4*>(v.img));
+                v.img = nullptr;
+            }
+}
+
 // Selects the tail on `ctas` CTAs over levels 0..lc (lc = 0: no tail).
 void select_tail(igamg_ctx* c, int ctas, int lc) {
     lc = std::max(0, std::min(lc, tail_most(c, ctas)));
@@ -374,8 +401,16 @@ void select_tail(igamg_ctx* c, int ctas, int lc) {
     else
         for (int k = 0; k < 2; ++k)
             if (kTailCtas[k] == ctas) {
-                if (c->dim == 3) c->ctail3 = c->ctails3[k][lc];
-                else c->ctail32 = c->ctails[k][lc];
+                if (c->dim == 3) {
+                    c->ctail3 = c->ctails3[k][lc];
+                } else if (ensure_tail_image(c->ctails[k][lc])) {
+                    c->ctail32 = c->ctails[k][lc];
+                } else {                                 // no image: the one-CTA tail instead
+                    c->tail_ctas = 1;
+                    lc = tail_most(c, 1);
+                    c->tail_on = lc > 0;
+                    if (c->tail_on) c->tail32 = c->tails[lc];
+                }
             }
 }
 
@@ -1170,6 +1205,7 @@ igamg_status igamg_assemble(igamg_ctx* c) {
     // Cluster tails of the FP32 2D cycle: on kTailCtas[k] CTAs, every lc
     // whose levels fit a CTA's shared memory (ClusterTailView) and whose
     // cluster the device can hold.
+    free_tail_images(c);
     for (int k = 0; k < 2; ++k) {
         c->ctails[k].assign(1, ClusterTailView<float>{});
         c->ctails3[k].assign(1, ClusterTail3View<float>{});
@@ -1194,16 +1230,13 @@ igamg_status igamg_assemble(igamg_ctx* c) {
                     v.off_rp[q] = off;
                     off += 2 * (v.R[q] * W + v.R[q - 1] * X.rw[1] + v.R[q] * X.pw[1]);
                 }
-                for (int q = 0; q <= l; ++q) {
+                v.npair = off / 2;
+                for (int q = 1; q <= l; ++q) {                 // static: operator data and tables
                     const int mx = c->hl[q].m[0], R = v.R[q];
-                    v.off_x[q] = off; off += R * (mx + 2 * p);
-                    v.off_b[q] = off; off += R * mx;
-                    if (q == 0) continue;
                     const LevelView<float>& Lq = c->lv32[q];
                     const TransferView<float>& X = c->tv32[q];
                     v.nbc[q] = Lq.tlo[0] + (mx - Lq.thi[0]);
                     v.off_inv[q] = off; off += R * mx;
-                    v.off_tm[q] = off; off += 2 * R * mx;
                     v.off_yb[q] = off; off += 2 * W * R;
                     v.off_xb[q] = off; off += 2 * W * (v.nbc[q] + 1);      // boundary columns and the interior
                     v.off_tx[q] = off; off += X.mf[0] * (1 + X.pw[0]) + X.mc[0] * (1 + X.rw[0]);
@@ -1212,9 +1245,17 @@ igamg_status igamg_assemble(igamg_ctx* c) {
                     tmax = std::max({tmax, R * X.mc[0], v.R[q - 1] * X.mf[0]});
                 }
                 v.off_cv = off; off += m00 * m00 + m01 * m01 + N0;
+                v.off_z = off; off += c->hl[l].m[0];
+                off = (off + 3) / 4 * 4;                       // the image: whole 16-byte units
+                v.img16 = off / 4;
+                for (int q = 0; q <= l; ++q) {                 // dynamic: iterates, right sides, row sums
+                    const int mx = c->hl[q].m[0], R = v.R[q];
+                    v.off_x[q] = off; off += R * (mx + 2 * p);
+                    v.off_b[q] = off; off += R * mx;
+                    if (q > 0) { v.off_tm[q] = off; off += 2 * R * mx; }
+                }
                 v.off_r = off; off += rmax;
                 v.off_t = off; off += tmax;
-                v.off_z = off; off += c->hl[l].m[0];
                 v.smem = (size_t)off * sizeof(float);
                 for (int q = 0; q <= l; ++q) {
                     v.L[q] = c->lv32[q];
@@ -2028,6 +2069,7 @@ void igamg_destroy(igamg_ctx* c) {
     if (c->h_hist) cudaFreeHost(c->h_hist);
     if (c->dmem) cudaFree(c->dmem);
     if (c->gmem) cudaFree(c->gmem);
+    free_tail_images(c);
     delete c;
 }
 

@@ -104,6 +104,13 @@ struct ClusterTailView {
     int off_ty[kCTailLevels], off_rp[kCTailLevels];
     int off_cv, off_r, off_t, off_z;
     size_t smem;
+    // The static part of every CTA's shared memory (the pointer tables as
+    // (owner CTA, element offset) pairs, then the operator data, transfer
+    // tables, coarsest eigenbasis and the zero row: elements [0, 4 img16)),
+    // built once per context into img[rank * img16 ..] (uint4 units); npair
+    // pointer entries start at element 0.
+    const uint4* img;
+    int img16, npair;
     LevelView<T> L[kCTailLevels];
     TransferView<T> X[kCTailLevels];
     CoarseView<T> C;
@@ -315,6 +322,10 @@ template <typename T>
 void cluster_tail(cudaStream_t s, const ClusterTailView<T>& V, const T* b, T* x, int jacobi = 0, T omega = 0);
 template <typename T>
 bool cluster_tail_fits(const ClusterTailView<T>& V);
+// Fills V's image buffer img (ctas x img16 uint4, device memory) with every
+// CTA's static shared memory; synchronous, outside stream capture.
+template <typename T>
+cudaError_t cluster_tail_image(const ClusterTailView<T>& V, uint4* img);
 
 // The 3D form (ClusterTail3View): levels lc..0 of an FP32 3D V-cycle.
 template <typename T>

@@ -31,6 +31,11 @@ __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// 16 bytes, both addresses 16-byte aligned, through L2 only
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
 
 template <typename E>
 __device__ __forceinline__ void stage(E* dst, const E* src, int n) {
@@ -733,20 +738,24 @@ __device__ __forceinline__ const T* cptr(T* local, int o, int rank) {
 
 constexpr int kCTailThreads = 512;
 
+// Every CTA's static shared memory, built once per context (cluster_tail_image):
+// the operator data, transfer tables and coarsest eigenbasis staged as the
+// tail uses them, the zero row, and each neighbour-row pointer as its
+// (owner CTA, element offset) pair, copied out to img[rank * img16 ..].
 template <typename T, int P>
-__global__ void __launch_bounds__(kCTailThreads, 1) k_cluster_tail(ClusterTailView<T> V, const T* __restrict__ b_in,
-                                                                  T* __restrict__ x_out, int jacobi, T omega) {
+__global__ void __launch_bounds__(kCTailThreads, 1) k_cluster_tail_image(ClusterTailView<T> V, uint4* img) {
     static_assert(sizeof(T) == 4, "4-byte elements (staging, integer tables)");
     constexpr int W = 2 * P + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
     const int rank = (int)cg::this_cluster().block_rank();
     const int lc = V.lc;
-    T* r = sm + V.off_r;
     T* t = sm + V.off_t;
     T* zrow = sm + V.off_z;
-    // Operator data (uploaded at assembly, written by no kernel) is staged
-    // before the wait on the previous kernel; the right side b after it.
+    uint4* s16 = reinterpret_cast<uint4*>(smem_raw);
+    for (int e = threadIdx.x; e < V.img16; e += blockDim.x) s16[e] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    auto pair_of = [&](const T* p, int o) { return make_int2(o, (int)(p - sm)); };
     for (int q = 1; q <= lc; ++q) {
         const LevelView<T>& L = V.L[q];
         const CLevel<T> S = clevel<T, P>(V, smem_raw, q, rank);
@@ -779,28 +788,80 @@ __global__ void __launch_bounds__(kCTailThreads, 1) k_cluster_tail(ClusterTailVi
         stage(const_cast<T*>(Y.rvy), X.rv[1] + (size_t)loc * X.rw[1], ownc * X.rw[1]);
         stage(const_cast<int*>(Y.ploy), X.plo[1] + S.lo, own);
         stage(const_cast<int*>(Y.rloy), X.rlo[1] + loc, ownc);
-        // row pointers: y-band neighbours, restriction and prolongation rows
-        const T** rp = const_cast<const T**>(S.rp);
+        // y-band neighbours of the own rows
+        int2* rp = reinterpret_cast<int2*>(const_cast<T**>(S.rp));
         for (int e = threadIdx.x; e < own * W; e += blockDim.x) {
             const int lr = e / W, bb = e - lr * W, jj = S.lo + lr + bb - P;
             if (jj < 0 || jj >= S.my) {
-                rp[e] = S.TM + lr * S.mx;                   // zero band entry
+                rp[e] = pair_of(S.TM + lr * S.mx, rank);    // zero band entry
             } else {
                 const int o = jj / S.R;
-                rp[e] = cptr(S.TM + (jj - o * S.R) * S.mx, o, rank);
+                rp[e] = pair_of(S.TM + (jj - o * S.R) * S.mx, o);
             }
         }
     }
-    for (int e = threadIdx.x; e < V.L[lc].m[0]; e += blockDim.x) zrow[e] = 0;
+    if (rank == 0) {                                    // coarsest eigenbasis
+        T* f = sm + V.off_cv;
+        const int m0 = V.C.m[0], m1 = V.C.m[1];
+        stage(f, V.C.V[0], m0 * m0);
+        stage(f + m0 * m0, V.C.V[1], m1 * m1);
+        stage(f + m0 * m0 + m1 * m1, V.C.laminv, m0 * m1);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    for (int q = 1; q <= lc; ++q) {                     // the t rows the y-axis transfer passes combine
+        const CLevel<T> S = clevel<T, P>(V, smem_raw, q, rank);
+        const TransferView<T>& X = V.X[q];
+        const CTransfer<T> Y = ctransfer(V, smem_raw, q);
+        const int Rc = V.R[q - 1], myc = V.L[q - 1].m[1];
+        const int loc = min(rank * Rc, myc), ownc = min(loc + Rc, myc) - loc, own = S.hi - S.lo;
+        int2* rr = reinterpret_cast<int2*>(const_cast<T**>(Y.rr));
+        for (int e = threadIdx.x; e < ownc * X.rw[1]; e += blockDim.x) {
+            const int Jl = e / X.rw[1], s2 = e - Jl * X.rw[1], f = Y.rloy[Jl] + s2;
+            if (f < 0 || f >= S.my) {
+                rr[e] = pair_of(zrow, rank);
+            } else {
+                const int o = f / S.R;
+                rr[e] = pair_of(t + (f - o * S.R) * X.mc[0], o);
+            }
+        }
+        int2* pr = reinterpret_cast<int2*>(const_cast<T**>(Y.pr));
+        for (int e = threadIdx.x; e < own * X.pw[1]; e += blockDim.x) {
+            const int jl = e / X.pw[1], s2 = e - jl * X.pw[1], F = Y.ploy[jl] + s2;
+            if (F < 0 || F >= myc) {
+                pr[e] = pair_of(zrow, rank);
+            } else {
+                const int o = F / Rc;
+                pr[e] = pair_of(t + (F - o * Rc) * X.mf[0], o);
+            }
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < V.img16; e += blockDim.x) img[(size_t)rank * V.img16 + e] = s16[e];
+}
+
+template <typename T, int P>
+__global__ void __launch_bounds__(kCTailThreads, 1) k_cluster_tail(ClusterTailView<T> V, const T* __restrict__ b_in,
+                                                                  T* __restrict__ x_out, int jacobi, T omega) {
+    static_assert(sizeof(T) == 4, "4-byte elements (staging, integer tables)");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sm = reinterpret_cast<T*>(smem_raw);
+    const int rank = (int)cg::this_cluster().block_rank();
+    const int lc = V.lc;
+    T* r = sm + V.off_r;
+    T* t = sm + V.off_t;
+    // this CTA's static shared memory from its image (operator data only,
+    // before the wait on the previous kernel), the dynamic part zeroed, the
+    // right side b after the wait; then the neighbour-row pairs become pointers
+    {
+        const uint4* src = V.img + (size_t)rank * V.img16;
+        uint4* dst = reinterpret_cast<uint4*>(smem_raw);
+        for (int e = threadIdx.x; e < V.img16; e += blockDim.x) cp_async16(dst + e, src + e);
+    }
     CoarseView<T> Cs = V.C;                             // coarsest eigenbasis (CTA 0 only)
     {
         T* f = sm + V.off_cv;
         const int m0 = V.C.m[0], m1 = V.C.m[1];
-        if (rank == 0) {
-            stage(f, V.C.V[0], m0 * m0);
-            stage(f + m0 * m0, V.C.V[1], m1 * m1);
-            stage(f + m0 * m0 + m1 * m1, V.C.laminv, m0 * m1);
-        }
         Cs.V[0] = f;
         Cs.V[1] = f + m0 * m0;
         Cs.laminv = f + m0 * m0 + m1 * m1;
@@ -818,31 +879,12 @@ __global__ void __launch_bounds__(kCTailThreads, 1) k_cluster_tail(ClusterTailVi
     }
     cp_async_wait_all();
     __syncthreads();
-    for (int q = 1; q <= lc; ++q) {                     // the t rows the y-axis transfer passes combine
-        const CLevel<T> S = clevel<T, P>(V, smem_raw, q, rank);
-        const TransferView<T>& X = V.X[q];
-        const CTransfer<T> Y = ctransfer(V, smem_raw, q);
-        const int Rc = V.R[q - 1], myc = V.L[q - 1].m[1];
-        const int loc = min(rank * Rc, myc), ownc = min(loc + Rc, myc) - loc, own = S.hi - S.lo;
-        const T** rr = const_cast<const T**>(Y.rr);
-        for (int e = threadIdx.x; e < ownc * X.rw[1]; e += blockDim.x) {
-            const int Jl = e / X.rw[1], s2 = e - Jl * X.rw[1], f = Y.rloy[Jl] + s2;
-            if (f < 0 || f >= S.my) {
-                rr[e] = zrow;
-            } else {
-                const int o = f / S.R;
-                rr[e] = cptr(t + (f - o * S.R) * X.mc[0], o, rank);
-            }
-        }
-        const T** pr = const_cast<const T**>(Y.pr);
-        for (int e = threadIdx.x; e < own * X.pw[1]; e += blockDim.x) {
-            const int jl = e / X.pw[1], s2 = e - jl * X.pw[1], F = Y.ploy[jl] + s2;
-            if (F < 0 || F >= myc) {
-                pr[e] = zrow;
-            } else {
-                const int o = F / Rc;
-                pr[e] = cptr(t + (F - o * Rc) * X.mf[0], o, rank);
-            }
+    {
+        const int2* pairs = reinterpret_cast<const int2*>(smem_raw);
+        const T** ptrs = reinterpret_cast<const T**>(smem_raw);
+        for (int e = threadIdx.x; e < V.npair; e += blockDim.x) {
+            const int2 pq = pairs[e];
+            ptrs[e] = cptr(sm + pq.y, pq.x, rank);
         }
     }
     __syncthreads();
@@ -1378,6 +1420,8 @@ void prepare_tail_kernels(int optin) {
             cudaFuncSetAttribute(k_coarse_tail<float, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
             cudaFuncSetAttribute(k_cluster_tail<float, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
             cudaFuncSetAttribute(k_cluster_tail<float, P>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            cudaFuncSetAttribute(k_cluster_tail_image<float, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+            cudaFuncSetAttribute(k_cluster_tail_image<float, P>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
             cudaFuncSetAttribute(k_cluster_tail3<float, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
             cudaFuncSetAttribute(k_cluster_tail3<float, P>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         });
@@ -1495,6 +1539,20 @@ void cluster_tail3(cudaStream_t s, const ClusterTail3View<T>& V, const T* b, T* 
 
 template bool cluster_tail3_fits<float>(const ClusterTail3View<float>&);
 template void cluster_tail3<float>(cudaStream_t, const ClusterTail3View<float>&, const float*, float*, int, float);
+template <typename T>
+cudaError_t cluster_tail_image(const ClusterTailView<T>& V, uint4* img) {
+    cudaError_t err = cudaSuccess;
+    tail_with_p(V.L[V.lc].p, [&](auto PC) {
+        constexpr int P = decltype(PC)::value;
+        cudaLaunchAttribute at[2];
+        const cudaLaunchConfig_t cfg = cluster_config(V, nullptr, at, false);
+        err = cudaLaunchKernelEx(&cfg, k_cluster_tail_image<T, P>, V, img);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(nullptr);
+    });
+    return err;
+}
+
+template cudaError_t cluster_tail_image<float>(const ClusterTailView<float>&, uint4*);
 template bool cluster_tail_fits<float>(const ClusterTailView<float>&);
 template void cluster_tail<float>(cudaStream_t, const ClusterTailView<float>&, const float*, float*, int, float);
 
