@@ -366,14 +366,18 @@ int tail_most(const igamg_ctx* c, int ctas) {
 
 // The static shared-memory image of a 2D cluster-tail view, built on first
 // use into device memory the context owns; false if it could not be.
-bool ensure_tail_image(ClusterTailView<float>& v) {
+template <typename View>
+bool ensure_tail_image(View& v) {
     if (v.img) return true;
     uint4* img = nullptr;
     if (cudaMalloc(&img, (size_t)v.ctas * v.img16 * sizeof(uint4)) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    if (dev::cluster_tail_image(v, img) != cudaSuccess) {
+    cudaError_t err;
+    if constexpr (std::is_same_v<View, ClusterTail3View<float>>) err = dev::cluster_tail3_image(v, img);
+    else err = dev::cluster_tail_image(v, img);
+    if (err != cudaSuccess) {
         cudaGetLastError();
         cudaFree(img);
         return false;
@@ -383,12 +387,14 @@ bool ensure_tail_image(ClusterTailView<float>& v) {
 }
 
 void free_tail_images(igamg_ctx* c) {
+    auto drop = [](auto& v) {
+        if (v.img) cudaFree(const_cast<uint4*>(v.img));
+        v.img = nullptr;
+    };
     for (auto& vs : c->ctails)
-        for (auto& v : vs)
-            if (v.img) {
-                cudaFree(const_cast<uint4*>(v.img));
-                v.img = nullptr;
-            }
+        for (auto& v : vs) drop(v);
+    for (auto& vs : c->ctails3)
+        for (auto& v : vs) drop(v);
 }
 
 // Selects the tail on `ctas` CTAs over levels 0..lc (lc = 0: no tail).
@@ -401,11 +407,10 @@ void select_tail(igamg_ctx* c, int ctas, int lc) {
     else
         for (int k = 0; k < 2; ++k)
             if (kTailCtas[k] == ctas) {
-                if (c->dim == 3) {
-                    c->ctail3 = c->ctails3[k][lc];
-                } else if (ensure_tail_image(c->ctails[k][lc])) {
-                    c->ctail32 = c->ctails[k][lc];
-                } else {                                 // no image: the one-CTA tail instead
+                if (c->dim == 3 ? ensure_tail_image(c->ctails3[k][lc]) : ensure_tail_image(c->ctails[k][lc])) {
+                    if (c->dim == 3) c->ctail3 = c->ctails3[k][lc];
+                    else c->ctail32 = c->ctails[k][lc];
+                } else {                                 // no image: the one-CTA tail (2D), else none
                     c->tail_ctas = 1;
                     lc = tail_most(c, 1);
                     c->tail_on = lc > 0;
@@ -445,16 +450,13 @@ void build_cluster_tails3(const igamg_ctx* c, std::vector<ClusterTail3View<float
                 v.off_rp[q] = off;
                 off += 2 * (v.R[q - 1] * X.rw[1] * X.rw[2] + v.R[q] * X.pw[1] * X.pw[2]);
             }
-            for (int q = 0; q <= l; ++q) {
+            v.npair = off / 2;
+            for (int q = 1; q <= l; ++q) {                     // static: operator data and tables
                 const int mx = c->hl[q].m[0], my = c->hl[q].m[1], mz = c->hl[q].m[2], R = v.R[q];
-                v.off_x[q] = off; off += R * (mx + 2 * p);
-                v.off_b[q] = off; off += R * mx;
-                if (q == 0) continue;
                 const LevelView<float>& Lq = c->lv32[q];
                 const TransferView<float>& X = c->tv32[q];
                 v.nbc[q] = Lq.tlo[0] + (mx - Lq.thi[0]);
                 v.off_inv[q] = off; off += R * mx;
-                v.off_tm[q] = off; off += 2 * (R + 2 * (p * my + p)) * mx;     // own rows and the halos
                 v.off_cc[q] = off; off += 2 * W2 * R;
                 v.off_yb[q] = off; off += 2 * W * my;
                 v.off_zb[q] = off; off += 2 * W * mz;
@@ -466,9 +468,17 @@ void build_cluster_tails3(const igamg_ctx* c, std::vector<ClusterTail3View<float
             }
             const int m0 = c->hl[0].m[0], m1 = c->hl[0].m[1], m2 = c->hl[0].m[2];
             v.off_cv = off; off += m0 * m0 + m1 * m1 + m2 * m2 + N0;
+            v.off_z = off; off += c->hl[l].m[0];
+            off = (off + 3) / 4 * 4;                           // the image: whole 16-byte units
+            v.img16 = off / 4;
+            for (int q = 0; q <= l; ++q) {                     // dynamic: iterates, right sides, T rows
+                const int mx = c->hl[q].m[0], my = c->hl[q].m[1], R = v.R[q];
+                v.off_x[q] = off; off += R * (mx + 2 * p);
+                v.off_b[q] = off; off += R * mx;
+                if (q > 0) { v.off_tm[q] = off; off += 2 * (R + 2 * (p * my + p)) * mx; }   // own rows, halos
+            }
             v.off_r = off; off += rmax;
             v.off_t = off; off += tmax;
-            v.off_z = off; off += c->hl[l].m[0];
             v.smem = (size_t)off * sizeof(float);
             for (int q = 0; q <= l; ++q) {
                 v.L[q] = c->lv32[q];

@@ -141,6 +141,11 @@ struct ClusterTail3View {
     int off_xb[kCTailLevels], off_tx[kCTailLevels];
     int off_cv, off_r, off_t, off_z;
     size_t smem;
+    // The static part of every CTA's shared memory, as in ClusterTailView
+    // (pointer pairs, operator data with the row weights cc, transfer tables,
+    // coarsest eigenbasis, zero row), built once per context.
+    const uint4* img;
+    int img16, npair;
     LevelView<T> L[kCTailLevels];
     TransferView<T> X[kCTailLevels];
     CoarseView<T> C;
@@ -332,6 +337,8 @@ template <typename T>
 void cluster_tail3(cudaStream_t s, const ClusterTail3View<T>& V, const T* b, T* x, int jacobi = 0, T omega = 0);
 template <typename T>
 bool cluster_tail3_fits(const ClusterTail3View<T>& V);
+template <typename T>
+cudaError_t cluster_tail3_image(const ClusterTail3View<T>& V, uint4* img);
 
 // T_M = (I (x) M_x) x, T_K = (I (x) K_x) x row by row.  With add != nullptr the
 // row is first replaced by x + add (written to x_out), with nS > 0 by

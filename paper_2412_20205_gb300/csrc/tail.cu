@@ -1231,19 +1231,23 @@ __device__ void cprolong3(const CLevel3<T>& S, const CLevel3<T>& Sc, const CTran
     cg::this_cluster().sync();
 }
 
+// Every CTA's static shared memory of the 3D tail, built once per context
+// (cluster_tail3_image), as k_cluster_tail_image does in 2D; here it also
+// holds the row weights cc.
 template <typename T, int P>
-__global__ void __launch_bounds__(kCTailThreads, 1) k_cluster_tail3(ClusterTail3View<T> V, const T* __restrict__ b_in,
-                                                                   T* __restrict__ x_out, int jacobi, T omega) {
+__global__ void __launch_bounds__(kCTailThreads, 1) k_cluster_tail3_image(ClusterTail3View<T> V, uint4* img) {
     static_assert(sizeof(T) == 4, "4-byte elements (staging, integer tables)");
     constexpr int W = 2 * P + 1, W2 = W * W;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
-    const int rank = (int)cg::this_cluster().block_rank(), C = V.ctas;
+    const int rank = (int)cg::this_cluster().block_rank();
     const int lc = V.lc;
-    T* r = sm + V.off_r;
     T* t = sm + V.off_t;
     T* zrow = sm + V.off_z;
-    // operator data, before the wait
+    uint4* s16 = reinterpret_cast<uint4*>(smem_raw);
+    for (int e = threadIdx.x; e < V.img16; e += blockDim.x) s16[e] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    auto pair_of = [&](const T* p, int o) { return make_int2(o, (int)(p - sm)); };
     for (int q = 1; q <= lc; ++q) {
         const LevelView<T>& L = V.L[q];
         const CLevel3<T> S = clevel3<T, P>(V, smem_raw, q, rank);
@@ -1274,32 +1278,13 @@ __global__ void __launch_bounds__(kCTailThreads, 1) k_cluster_tail3(ClusterTail3
             stage(const_cast<T*>(Y.rv[d]), X.rv[d], X.mc[d] * X.rw[d]);
         }
     }
-    for (int e = threadIdx.x; e < V.L[lc].m[0]; e += blockDim.x) zrow[e] = 0;
-    CoarseView<T> Cs = V.C;                             // coarsest eigenbasis (CTA 0 only)
-    {
+    if (rank == 0) {                                    // coarsest eigenbasis
         T* f = sm + V.off_cv;
         const int m0 = V.C.m[0], m1 = V.C.m[1], m2 = V.C.m[2];
-        if (rank == 0) {
-            stage(f, V.C.V[0], m0 * m0);
-            stage(f + m0 * m0, V.C.V[1], m1 * m1);
-            stage(f + m0 * m0 + m1 * m1, V.C.V[2], m2 * m2);
-            stage(f + m0 * m0 + m1 * m1 + m2 * m2, V.C.laminv, m0 * m1 * m2);
-        }
-        Cs.V[0] = f;
-        Cs.V[1] = f + m0 * m0;
-        Cs.V[2] = f + m0 * m0 + m1 * m1;
-        Cs.laminv = f + m0 * m0 + m1 * m1 + m2 * m2;
-    }
-    for (int q = 0; q <= lc; ++q) {                     // coarse e^0 = 0 on every level, zero pads
-        const CLevel3<T> S = clevel3<T, P>(V, smem_raw, q, rank);
-        for (int e = threadIdx.x; e < S.R * (S.mx + 2 * P); e += blockDim.x) S.x[e] = 0;
-        if (q > 0)
-            for (int e = threadIdx.x; e < 2 * (S.R + 2 * S.H) * S.mx; e += blockDim.x) S.TM[e] = 0;
-    }
-    pdl_enter();
-    {
-        const CLevel3<T> S = clevel3<T, P>(V, smem_raw, lc, rank);
-        stage(S.b, b_in + (size_t)S.lo * S.mx, (S.hi - S.lo) * S.mx);
+        stage(f, V.C.V[0], m0 * m0);
+        stage(f + m0 * m0, V.C.V[1], m1 * m1);
+        stage(f + m0 * m0 + m1 * m1, V.C.V[2], m2 * m2);
+        stage(f + m0 * m0 + m1 * m1 + m2 * m2, V.C.laminv, m0 * m1 * m2);
     }
     cp_async_wait_all();
     __syncthreads();
@@ -1322,29 +1307,80 @@ __global__ void __launch_bounds__(kCTailThreads, 1) k_cluster_tail3(ClusterTail3
         const int Rc = V.R[q - 1], myc = V.L[q - 1].m[1], mzc = V.L[q - 1].m[2];
         const int loc = min(rank * Rc, myc * mzc), ownc = min(loc + Rc, myc * mzc) - loc;
         const int ryz = X.rw[1] * X.rw[2], pyz = X.pw[1] * X.pw[2];
-        const T** rr = const_cast<const T**>(Y.rr);
+        int2* rr = reinterpret_cast<int2*>(const_cast<T**>(Y.rr));
         for (int e = threadIdx.x; e < ownc * ryz; e += blockDim.x) {
             const int Jl = e / ryz, s2 = e - Jl * ryz, sy = s2 % X.rw[1], sz = s2 / X.rw[1];
             const int rc = loc + Jl, J = rc % myc, K = rc / myc;
             const int fj = Y.rlo[1][J] + sy, fk = Y.rlo[2][K] + sz;
             if (fj < 0 || fj >= S.my || fk < 0 || fk >= S.mz) {
-                rr[e] = zrow;
+                rr[e] = pair_of(zrow, rank);
             } else {
                 const int rn = fk * S.my + fj, o = rn / S.R;
-                rr[e] = cptr(t + (rn - o * S.R) * X.mc[0], o, rank);
+                rr[e] = pair_of(t + (rn - o * S.R) * X.mc[0], o);
             }
         }
-        const T** pr = const_cast<const T**>(Y.pr);
+        int2* pr = reinterpret_cast<int2*>(const_cast<T**>(Y.pr));
         for (int e = threadIdx.x; e < own * pyz; e += blockDim.x) {
             const int jl = e / pyz, s2 = e - jl * pyz, sy = s2 % X.pw[1], sz = s2 / X.pw[1];
             const int row = S.lo + jl, j = row % S.my, k = row / S.my;
             const int Fj = Y.plo[1][j] + sy, Fk = Y.plo[2][k] + sz;
             if (Fj < 0 || Fj >= myc || Fk < 0 || Fk >= mzc) {
-                pr[e] = zrow;
+                pr[e] = pair_of(zrow, rank);
             } else {
                 const int rn = Fk * myc + Fj, o = rn / Rc;
-                pr[e] = cptr(t + (rn - o * Rc) * X.mf[0], o, rank);
+                pr[e] = pair_of(t + (rn - o * Rc) * X.mf[0], o);
             }
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < V.img16; e += blockDim.x) img[(size_t)rank * V.img16 + e] = s16[e];
+}
+
+template <typename T, int P>
+__global__ void __launch_bounds__(kCTailThreads, 1) k_cluster_tail3(ClusterTail3View<T> V, const T* __restrict__ b_in,
+                                                                   T* __restrict__ x_out, int jacobi, T omega) {
+    static_assert(sizeof(T) == 4, "4-byte elements (staging, integer tables)");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sm = reinterpret_cast<T*>(smem_raw);
+    const int rank = (int)cg::this_cluster().block_rank(), C = V.ctas;
+    const int lc = V.lc;
+    T* r = sm + V.off_r;
+    T* t = sm + V.off_t;
+    // this CTA's static shared memory from its image before the wait, the
+    // dynamic part zeroed, b after it; then the pairs become pointers
+    {
+        const uint4* src = V.img + (size_t)rank * V.img16;
+        uint4* dst = reinterpret_cast<uint4*>(smem_raw);
+        for (int e = threadIdx.x; e < V.img16; e += blockDim.x) cp_async16(dst + e, src + e);
+    }
+    CoarseView<T> Cs = V.C;                             // coarsest eigenbasis (CTA 0 only)
+    {
+        T* f = sm + V.off_cv;
+        const int m0 = V.C.m[0], m1 = V.C.m[1], m2 = V.C.m[2];
+        Cs.V[0] = f;
+        Cs.V[1] = f + m0 * m0;
+        Cs.V[2] = f + m0 * m0 + m1 * m1;
+        Cs.laminv = f + m0 * m0 + m1 * m1 + m2 * m2;
+    }
+    for (int q = 0; q <= lc; ++q) {                     // coarse e^0 = 0 on every level, zero pads
+        const CLevel3<T> S = clevel3<T, P>(V, smem_raw, q, rank);
+        for (int e = threadIdx.x; e < S.R * (S.mx + 2 * P); e += blockDim.x) S.x[e] = 0;
+        if (q > 0)
+            for (int e = threadIdx.x; e < 2 * (S.R + 2 * S.H) * S.mx; e += blockDim.x) S.TM[e] = 0;
+    }
+    pdl_enter();
+    {
+        const CLevel3<T> S = clevel3<T, P>(V, smem_raw, lc, rank);
+        stage(S.b, b_in + (size_t)S.lo * S.mx, (S.hi - S.lo) * S.mx);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    {
+        const int2* pairs = reinterpret_cast<const int2*>(smem_raw);
+        const T** ptrs = reinterpret_cast<const T**>(smem_raw);
+        for (int e = threadIdx.x; e < V.npair; e += blockDim.x) {
+            const int2 pq = pairs[e];
+            ptrs[e] = cptr(sm + pq.y, pq.x, rank);
         }
     }
     __syncthreads();
@@ -1424,6 +1460,8 @@ void prepare_tail_kernels(int optin) {
             cudaFuncSetAttribute(k_cluster_tail_image<float, P>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
             cudaFuncSetAttribute(k_cluster_tail3<float, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
             cudaFuncSetAttribute(k_cluster_tail3<float, P>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            cudaFuncSetAttribute(k_cluster_tail3_image<float, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+            cudaFuncSetAttribute(k_cluster_tail3_image<float, P>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         });
     if (dev >= 0 && dev < 64) g_tail_limit[dev] = (size_t)optin;
 }
@@ -1537,6 +1575,20 @@ void cluster_tail3(cudaStream_t s, const ClusterTail3View<T>& V, const T* b, T* 
     count_launch();
 }
 
+template <typename T>
+cudaError_t cluster_tail3_image(const ClusterTail3View<T>& V, uint4* img) {
+    cudaError_t err = cudaSuccess;
+    tail_with_p(V.L[V.lc].p, [&](auto PC) {
+        constexpr int P = decltype(PC)::value;
+        cudaLaunchAttribute at[2];
+        const cudaLaunchConfig_t cfg = cluster3_config(V, nullptr, at, false);
+        err = cudaLaunchKernelEx(&cfg, k_cluster_tail3_image<T, P>, V, img);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(nullptr);
+    });
+    return err;
+}
+
+template cudaError_t cluster_tail3_image<float>(const ClusterTail3View<float>&, uint4*);
 template bool cluster_tail3_fits<float>(const ClusterTail3View<float>&);
 template void cluster_tail3<float>(cudaStream_t, const ClusterTail3View<float>&, const float*, float*, int, float);
 template <typename T>
