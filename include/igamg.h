@@ -338,12 +338,13 @@ void igamg_get_schedule(const igamg_ctx* ctx, int* gs_threads, int* tail_levels)
  * aside).  Switching keeps the tail depth where the other form has it, else
  * takes its deepest; igamg_tail_levels_available() gives the deepest tail
  * level of each form (0: none), igamg_get_tail_ctas() the form in use.
- * igamg_autotune times every form and depth.  The first use of a 2D cluster
- * tail depth builds, once, each CTA's unchanging shared memory (operator
- * data, transfer tables, neighbour-row addresses) into device memory the
- * context owns and frees in igamg_destroy; every cycle then copies it in.  Where
- * that memory cannot be had, the one-CTA tail is used.  Errors: EINVAL (ctas
- * not 1, 8 or 16). */
+ * igamg_autotune times every form and depth.  The first use of a cluster-tail
+ * depth (3D: the default one at set-up) builds, once, each CTA's unchanging
+ * shared memory (operator data, transfer tables, neighbour-row addresses)
+ * into device memory the context owns and frees in igamg_destroy; every cycle
+ * then copies it in.  Where that memory cannot be had, 2D falls back to the
+ * one-CTA tail and 3D to per-level launches.  Errors: EINVAL (ctas not 1, 8
+ * or 16). */
 igamg_status igamg_set_tail_ctas(igamg_ctx* ctx, int ctas);
 int igamg_get_tail_ctas(const igamg_ctx* ctx);
 int igamg_tail_levels_available(const igamg_ctx* ctx, int ctas);
